@@ -1,0 +1,319 @@
+"""Benchmark: fwd+adjoint pattern*slices per second of the layer-wise multislice step.
+
+One step is one gradient step of Algorithm 1 (Sec. 3.3) on slice 0 of the
+W = 128, L = 4, S = 1024 workload: transmission, window gather, the multislice
+forward through all four slices, far-field loss and residual, the adjoint back
+through every slice, the atomic-free overlap-add of the slice gradient and of
+the illumination map, the FP64 step-size reduction and the update of V_0.
+value = S * L / (time per step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded sample
+of the same workload); it is a reported baseline, not the target.
+Under torchrun (N > 1) every rank runs an independent replica (the method's
+positions could be sharded, but this build is single-GPU): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import synth  # noqa: E402
+
+METRIC = "fwd+adjoint patterns·slices/s"
+UNIT = "pattern·slices/s"
+CFG = synth.C2
+LAYER = 0
+
+
+def fft_flops(S, L, W):
+    """Algorithmic FLOPs of one fwd+adjoint pass: (4L-2) 2-D FFTs of W x W per position,
+    5 N log2 N each (the standard complex-FFT count)."""
+    n = W * W
+    return S * (4 * L - 2) * 5.0 * n * math.log2(n)
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(msp, torch, dev, cfg):
+    """Seeded synthetic specimen, probe guess, raster and Poisson-noisy intensities."""
+    pos = synth.scan_positions(cfg)
+    gd = synth.geometry(cfg, n_pos=len(pos))
+    g = msp.geometry(**gd)
+    V_true = synth.potential_slices(cfg).astype(np.float32)
+    p_true = synth.probe(cfg).astype(np.complex64)
+    p_guess = synth.probe(cfg, defocus_A=cfg.defocus_guess_A or cfg.defocus_A).astype(np.complex64)
+    d_pos = torch.from_numpy(pos).to(dev)
+    ws = msp.make_workspace(g, dev)
+    I_clean = msp.forward(g, torch.from_numpy(p_true).to(dev), torch.from_numpy(V_true).to(dev), d_pos, ws=ws)
+    I_meas = synth.poisson_counts(I_clean.cpu().numpy().astype(np.float64), cfg.dose, cfg.seed).astype(np.float32)
+    return g, gd, pos, d_pos, ws, V_true, p_guess, I_meas
+
+
+def cpu_baseline(cfg, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload's positions."""
+    from oracle import msp_oracle as O
+    pos = synth.scan_positions(cfg)
+    gd = synth.geometry(cfg)
+    V = np.zeros((cfg.n_slices, cfg.obj, cfg.obj))
+    probe = synth.probe(cfg, defocus_A=cfg.defocus_guess_A or cfg.defocus_A)
+    I_fake = np.abs(np.fft.fft2(probe)) ** 2
+    n = 4
+    t_used = 0.0
+    done = 0
+    while True:
+        sub = pos[done:done + n]
+        I = np.broadcast_to(I_fake, (len(sub),) + I_fake.shape)
+        t0 = time.perf_counter()
+        O.layer_step(dict(gd, n_pos=len(sub)), probe, sub, I, LAYER, V=V)
+        t_used += time.perf_counter() - t0
+        done += len(sub)
+        if t_used > budget_s or done >= len(pos):
+            break
+        n = min(len(pos) - done, max(4, int(n * 2)))
+    return {"value": done * cfg.n_slices / t_used, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {len(pos)} scan positions of {cfg.name}, FP64 numpy oracle layer step "
+                      f"(slice {LAYER}), single thread, {t_used:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    per_step = []
+    base = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(CFG, budget_s=max(2.0, 20.0 / max(1, args.steps + args.warmup)))
+        if i >= args.warmup:
+            per_step.append(r["value"])
+            base = r
+    value = float(np.median(per_step))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": CFG.n_pos * CFG.n_slices / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CFG.name, "call": "oracle.layer_step(slice 0)", "parallelism": "cpu, 1 thread"},
+            "cpu_baseline": dict(base, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_msp(args, rank, world, local_rank):
+    import torch
+    from paper_2205_03902_gb300 import msp
+    import __graft_entry__
+    __graft_entry__.build()
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg = CFG
+    g, gd, pos, d_pos, ws, V_true, p_guess, I_meas_h = make_inputs(msp, torch, dev, cfg)
+    S, L, W = cfg.n_pos, cfg.n_slices, cfg.win
+    probe = torch.from_numpy(p_guess).to(dev)
+    V = torch.zeros((L, cfg.obj, cfg.obj), dtype=torch.float32, device=dev)   # Alg. 1 starts from V = 0
+    I_meas = torch.from_numpy(I_meas_h).to(dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    mu = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        msp.layer_step(g, probe, V, d_pos, I_meas, LAYER, ws=ws, loss_before=loss, mu=mu)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    loss_first = float(loss.item())
+
+    msp.profile_read(reset=True)
+    msp.profile_enable(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))          # L2 flushed between timed steps (outside the events)
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = msp.profile_read(reset=True)
+    msp.profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * S * L / (ms_per_step * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned), copies timed ----
+    h_I = torch.from_numpy(I_meas_h).pin_memory()
+    h_V = torch.zeros((L, cfg.obj, cfg.obj), dtype=torch.float32).pin_memory()
+    h_p = torch.from_numpy(p_guess).pin_memory()
+    h_pos = torch.from_numpy(pos).pin_memory()
+    h_out = torch.empty((cfg.obj, cfg.obj), dtype=torch.float32).pin_memory()
+    h_scal = torch.empty(2, dtype=torch.float64).pin_memory()
+    scal = torch.empty(2, dtype=torch.float64, device=dev)
+    e_steps = max(3, min(args.steps, 10))
+    h2d = h_I.numel() * 4 + h_V.numel() * 4 + h_p.numel() * 8 + h_pos.numel() * 4
+    d2h = h_out.numel() * 4 + h_scal.numel() * 8
+    for k in range(e_steps + 1):
+        if k == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        I_meas.copy_(h_I, non_blocking=True)
+        V.copy_(h_V, non_blocking=True)
+        probe.copy_(h_p, non_blocking=True)
+        d_pos.copy_(h_pos, non_blocking=True)
+        msp.layer_step(g, probe, V, d_pos, I_meas, LAYER, ws=ws, loss_before=scal[0:1], mu=scal[1:2])
+        h_out.copy_(V[LAYER], non_blocking=True)
+        h_scal.copy_(scal, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    e2e_value = world * S * L / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peaks = read_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    fused_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
+    achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("position_kernel_layer_c2_bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "call": f"msp_layer_step(layer={LAYER}, auto step)",
+                   "positions": S, "slices": L, "window": W, "object": [cfg.obj, cfg.obj],
+                   "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "kernel": "position_kernel<128, LAYER> (fused fwd+adjoint)",
+                     "kernel_ms": fused_ms,
+                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["all_launches"]),
+        "clocks": clocks,
+        "loss_first_timed_step": loss_first,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_msp(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

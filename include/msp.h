@@ -1,0 +1,160 @@
+/*
+ * msp.h -- C ABI of libmsp, the GB300 (sm_103a) hot path of inverse multislice
+ * ptychography by layer-wise optimisation (arXiv 2205.03902).
+ *
+ * The library computes, for S scan positions at once, the multislice forward
+ * model of Sec. 2.1 (E_1 = P o X_1, E_m = V_z(E_{m-1}) o X_m, I = |F(E_M)|^2),
+ * the amplitude-flow loss and its Wirtinger gradient of Sec. 3.2, and the
+ * gradient steps of Algorithm 1 (Sec. 3.3) and of the probe problem (Sec. 3.5).
+ *
+ * Conventions shared by every entry point
+ *   - Slices are given as real projected potentials V (V*angstrom); the slice
+ *     transmission is X_m = exp(i sigma V_m) (the phase grating of Sec. 2.1).
+ *   - Window model: scan position s uses the W x W window of every slice whose
+ *     top-left object pixel is pos[s] = (y, x); the probe is one W x W array.
+ *     Every window must lie inside the object: 0 <= y <= Ny - W, 0 <= x <= Nx - W.
+ *   - F is the unnormalised 2-D DFT (kernel exp(-2 pi i k.n / W)), F^-1 = F^H / W^2.
+ *     Intensities are in unshifted FFT order (zero frequency at [0][0]).
+ *   - Fresnel propagator h = exp(-i pi dz lambda (qy^2 + qx^2)), Eq. (fresnel_element)
+ *     with zero tilt, q_k = k / (W pixel) for k < W/2 and (k - W) / (W pixel) otherwise.
+ *     The slices are separated by dz; no propagation follows the last slice.
+ *   - Loss: L = sum_s sum_k (sqrt(I_meas) - |Psi|)^2 (Sec. 3.2, no factor 1/2), with
+ *     Psi/|Psi| taken as 0 where Psi == 0.
+ *   - Complex arrays are interleaved float pairs (re, im), row-major.
+ *
+ * Memory and ownership
+ *   - Every array argument is a DEVICE pointer owned by the caller, 16-byte aligned.
+ *     Scalars written by the library (loss, step size) are device doubles.
+ *   - The library allocates nothing.  Scratch space is the caller's workspace `ws`
+ *     of at least msp_workspace_bytes(geometry) bytes (256-byte aligned), valid
+ *     for the current device; one workspace serves one call at a time.
+ *   - All compute calls are asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream).  Results are valid once the stream has reached them.
+ *
+ * Errors
+ *   - Every entry point returns an msp_status.  Argument errors are found on the
+ *     host before anything is launched (MSP_EINVAL / MSP_EUNSUPPORTED); a failed
+ *     launch returns MSP_ECUDA.  Nothing throws or exits across the ABI.
+ *   - A scan window outside the object cannot be seen on the host (positions live
+ *     on the device): the kernels skip such a position (its outputs are zero) and
+ *     raise a flag in the workspace, which msp_check_workspace reports as MSP_EINVAL.
+ *   - msp_last_error_message() describes the most recent failure of this thread.
+ *
+ * Results are deterministic: no atomics are used on data, every sum runs in a
+ * fixed order, so repeated calls on the same device give bit-identical results.
+ */
+#ifndef MSP_H
+#define MSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSP_OK = 0,
+  MSP_EINVAL = 1,        /* bad argument, null pointer, workspace too small, window outside object */
+  MSP_ENOMEM = 2,        /* reserved: the library never allocates */
+  MSP_ECUDA = 3,         /* a CUDA launch or runtime call failed */
+  MSP_EUNSUPPORTED = 4,  /* valid but not implemented here (window size, parametrisation) */
+  MSP_ETIMEOUT = 5       /* reserved for bounded device-side waits */
+} msp_status;
+
+/* Slice parametrisation.  Only MSP_PARAM_POTENTIAL (X_m = exp(i sigma V_m)) is
+ * implemented on the GPU; MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED. */
+enum { MSP_PARAM_POTENTIAL = 0, MSP_PARAM_TRANSMISSION = 1 };
+
+/* Statement of the problem (Sec. 2.1).  Supported windows: W = 64 or 128. */
+typedef struct {
+  int32_t n_slices;     /* L (the paper's M), >= 1                                 */
+  int32_t obj_ny;       /* object rows Ny >= W                                     */
+  int32_t obj_nx;       /* object columns Nx >= W                                  */
+  int32_t win;          /* W: probe window side = detector side                   */
+  int32_t n_pos;        /* S: scan positions, >= 0                                 */
+  int32_t param;        /* MSP_PARAM_POTENTIAL                                     */
+  double wavelength_A;  /* electron wavelength lambda in angstrom (Sec. 5.3.2)    */
+  double sigma;         /* interaction constant, rad / (V angstrom)               */
+  double dz_A;          /* slice separation = Fresnel distance Delta (Eq. fresnel_element) */
+  double pixel_A;       /* real-space pixel size in angstrom                       */
+} msp_geometry;
+
+/* Checks a geometry on the host.  MSP_OK, MSP_EINVAL or MSP_EUNSUPPORTED. */
+msp_status msp_validate_geometry(const msp_geometry* g);
+
+/* Workspace bytes every compute call on `g` needs on the current device
+ * (0 if the geometry is invalid). */
+size_t msp_workspace_bytes(const msp_geometry* g);
+
+/* Forward model (Sec. 2.1, Eq. intensity measurements):
+ *   probe  [W][W] complex   incident probe P
+ *   V      [L][Ny][Nx] float projected potentials
+ *   pos    [S][2] int32     window top-left (y, x) per scan position
+ *   I_out  [S][W][W] float  far-field intensities |F(E_M^s)|^2 (written) */
+msp_status msp_forward(const msp_geometry* g, const float* probe, const float* V,
+                       const int32_t* pos, float* I_out,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Loss and gradients (Sec. 3.2 applied to Eq. Opt_Prob_Layerwise):
+ *   I_meas  [S][W][W] float     measured intensities
+ *   loss    device double [1]   L (written; may be NULL)
+ *   dV      [L][Ny][Nx] float   dL/dV = 2 sigma Im(conj(X) o dL/dconj(X)), overlap-added
+ *                               over all positions (written; may be NULL)
+ *   dprobe  [W][W] complex      dL/dconj(P) = sum_s conj(X_1[win_s]) o chi_1^s (may be NULL) */
+msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float* V,
+                         const int32_t* pos, const float* I_meas,
+                         double* loss, float* dV, float* dprobe,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* One gradient step of Algorithm 1 on slice `layer` (0-based), Eq.
+ * (Opt_Prob_Amplitude_Flow_Step) with the other slices fixed:
+ *   V[layer] <- V[layer] - mu dL/dV[layer]
+ * step > 0 sets mu; step <= 0 takes mu = 1 / (2 sigma^2 W^2 max_pixel sum_s |psi_in,l^s|^2),
+ * the spectral step ||Q_l||^-2 of Sec. 3.2 carried to the potential.
+ *   V          [L][Ny][Nx] float, updated in place (only slice `layer` changes)
+ *   loss_before device double [1], loss at the incoming V (may be NULL)
+ *   mu_out      device double [1], step size used (may be NULL) */
+msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V,
+                          const int32_t* pos, const float* I_meas, int32_t layer,
+                          double step, double* loss_before, double* mu_out,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* One amplitude-flow step on the probe (Sec. 3.5, Eq. Opt_Est_Probe, all positions):
+ *   probe <- probe - mu sum_s conj(X_1[win_s]) o chi_1^s
+ * step > 0 sets mu; step <= 0 takes mu = 1 / (S W^2) (= ||Q_p||^-2 for pure-phase slices).
+ * normalize != 0 then rescales the probe so that W^2 ||p||^2 = mean_s sum_k I_meas^s.
+ *   probe  [W][W] complex, updated in place; loss_before / mu_out as above. */
+msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V,
+                          const int32_t* pos, const float* I_meas, double step,
+                          int32_t normalize, double* loss_before, double* mu_out,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronises `stream`, then reports (and clears) the workspace flag raised when
+ * a scan window of the most recent compute call on `ws` lay outside the object
+ * (every compute call clears the flag when it starts): MSP_OK or MSP_EINVAL. */
+msp_status msp_check_workspace(void* ws, void* stream);
+
+/* Profiling hooks, off by default.  While enabled, every launch of the fused
+ * per-position kernel (the forward / adjoint of all positions) is bracketed by
+ * CUDA events recorded on its stream. */
+msp_status msp_profile_enable(int32_t on);
+
+/* Waits for the recorded events and returns, since the last reset: the summed
+ * duration in ms and the number of fused-kernel launches timed, and the number of
+ * kernels libmsp launched in total (counted whether or not timing is enabled).
+ * Any output pointer may be NULL (host pointers); reset != 0 starts a new interval. */
+msp_status msp_profile_read(double* fused_ms, int64_t* fused_launches, int64_t* all_launches,
+                            int32_t reset);
+
+/* Human-readable status name; never NULL. */
+const char* msp_status_string(msp_status s);
+
+/* Detail of this thread's most recent failure ("" if none); never NULL. */
+const char* msp_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSP_H */

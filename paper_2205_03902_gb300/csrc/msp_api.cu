@@ -1,0 +1,691 @@
+// msp_api.cu -- C ABI of libmsp: argument checks, workspace carve-up, and the
+// element-wise / reduction kernels around the fused per-position kernel.
+//
+//   transmission      X_m = exp(i sigma V_m) over the whole object (Sec. 2.1)
+//   propagator        H / W^2, Eq. (fresnel_element) with zero tilt
+//   gather            atomic-free overlap-add of per-position window gradients
+//                     into object-frame maps, every pixel summing its covering
+//                     positions in ascending scan order (the sum over s of
+//                     Eq. Opt_Prob_Layerwise)
+//   reductions        FP64, fixed order: loss, illumination maximum, pattern sums
+//   updates           the gradient steps of Algorithm 1 and of Sec. 3.5
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <vector>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "msp.h"
+#include "msp_kernels.cuh"
+
+namespace msp {
+
+cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int grid, cudaStream_t st);
+int position_ctas_per_sm(int win);
+
+// ---------------------------------------------------------------------------
+// element-wise kernels
+// ---------------------------------------------------------------------------
+
+__global__ void transmission_kernel(const float* __restrict__ V, float2* __restrict__ T, size_t n, float sigma) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float sn, cs;
+    sincosf(sigma * V[i], &sn, &cs);
+    T[i] = make_float2(cs, sn);
+  }
+}
+
+// H[ky][kx] = exp(-i pi dz lambda (qy^2 + qx^2)) / W^2; the phase / pi is formed and
+// reduced modulo 2 in double precision, the sine and cosine taken in single.
+__global__ void propagator_kernel(float2* __restrict__ H, int W, double dzlam, double dq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= W * W) return;
+  const int ky = i / W, kx = i % W;
+  const double qy = (double)(ky < W / 2 ? ky : ky - W) * dq;
+  const double qx = (double)(kx < W / 2 ? kx : kx - W) * dq;
+  double t = dzlam * (qy * qy + qx * qx);   // phase / pi
+  t = t - 2.0 * floor(t * 0.5);
+  float sn, cs;
+  sincospif((float)t, &sn, &cs);
+  const float inv = 1.0f / ((float)W * (float)W);
+  H[i] = make_float2(cs * inv, -sn * inv);
+}
+
+// Overlap-add of per-position window arrays into object-frame maps.  One CTA owns a
+// 32 x 32 object tile of one slice; positions are visited in ascending order, so the
+// sum at every pixel has a fixed order (bit-reproducible, no atomics).
+template <int NCH>
+__global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ src0, const float* __restrict__ src1,
+                                                     int nl_src, const int2* __restrict__ pos, int S, int W,
+                                                     int Ny, int Nx, float* __restrict__ out0,
+                                                     float* __restrict__ out1, double* __restrict__ blockmax) {
+  __shared__ int2 spos[256];
+  __shared__ float wmax[8];
+  const int tid = threadIdx.x;
+  const int tx = tid & 31, ty = tid >> 5;
+  const int l = blockIdx.z;
+  const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * 32;
+  const int px = tx0 + tx;
+  const size_t WW = (size_t)W * W;
+  float acc0[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc1[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int base = 0; base < S; base += 256) {
+    const int n = min(256, S - base);
+    __syncthreads();
+    if (tid < n) spos[tid] = pos[base + tid];
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += 8) {
+      float v0[8][4], v1[8][4];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u;
+        const int2 ps = (k < n) ? spos[k] : make_int2(-(1 << 29), -(1 << 29));
+        const int dx = px - ps.y;
+        const bool inx = (unsigned)dx < (unsigned)W;
+        const float* s0 = src0 + ((size_t)(base + k) * nl_src + l) * WW;
+        const float* s1 = (NCH == 2) ? src1 + (size_t)(base + k) * WW : nullptr;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int dy = ty0 + ty + 8 * i - ps.x;
+          const bool in = inx && ((unsigned)dy < (unsigned)W);
+          v0[u][i] = in ? s0[(size_t)dy * W + dx] : 0.f;
+          if (NCH == 2) v1[u][i] = in ? s1[(size_t)dy * W + dx] : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc0[i] += v0[u][i];
+          if (NCH == 2) acc1[i] += v1[u][i];
+        }
+      }
+    }
+  }
+  float m = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int py = ty0 + ty + 8 * i;
+    if (py < Ny && px < Nx) {
+      out0[((size_t)l * Ny + py) * Nx + px] = acc0[i];
+      if (NCH == 2) {
+        out1[(size_t)py * Nx + px] = acc1[i];
+        m = fmaxf(m, acc1[i]);
+      }
+    }
+  }
+  if (NCH == 2) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+      float b = 0.f;
+      for (int w = 0; w < 8; ++w) b = fmaxf(b, wmax[w]);
+      blockmax[blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
+    }
+  }
+}
+
+// Single-block FP64 reduction in a fixed order.  op 0: sum, 1: max.
+__global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__ in, int n, int op,
+                                                      double* __restrict__ out, double* __restrict__ out2) {
+  __shared__ double sh[1024];
+  const int tid = threadIdx.x;
+  double a = 0.0;
+  for (int i = tid; i < n; i += 1024) a = (op == 0) ? a + in[i] : fmax(a, in[i]);
+  sh[tid] = a;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] = (op == 0) ? sh[tid] + sh[tid + s] : fmax(sh[tid], sh[tid + s]);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[0] = sh[0];
+    if (out2) out2[0] = sh[0];
+  }
+}
+
+// Block partial sums (FP64) of a float array; grid size fixed by the caller.
+__global__ void __launch_bounds__(256) sum_blocks_kernel(const float* __restrict__ x, size_t n,
+                                                         double* __restrict__ part) {
+  __shared__ double sh[256];
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t b0 = blockIdx.x * chunk;
+  const size_t b1 = min(n, b0 + chunk);
+  double a = 0.0;
+  for (size_t i = b0 + threadIdx.x; i < b1; i += 256) a += (double)x[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// dprobe[i] = sum_b part[b][i] in CTA order (FP64 accumulation).
+__global__ void dprobe_reduce_kernel(const float2* __restrict__ part, int G, int WW, float2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= WW) return;
+  double re = 0.0, im = 0.0;
+  for (int b = 0; b < G; ++b) {
+    const float2 v = part[(size_t)b * WW + i];
+    re += v.x;
+    im += v.y;
+  }
+  out[i] = make_float2((float)re, (float)im);
+}
+
+// Step size of a layer step: mu = step, or 1 / (2 sigma^2 W^2 max illumination).
+__global__ void layer_mu_kernel(double* scal, double step, double two_sig2_w2, double* mu_out) {
+  double mu = step;
+  if (!(step > 0.0)) {
+    const double m = scal[2];
+    mu = (m > 0.0) ? 1.0 / (two_sig2_w2 * m) : 0.0;
+  }
+  scal[1] = mu;
+  if (mu_out) mu_out[0] = mu;
+}
+
+__global__ void layer_update_kernel(float* __restrict__ V, const float* __restrict__ dV, size_t n,
+                                    const double* __restrict__ scal) {
+  const double mu = scal[1];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    V[i] = (float)((double)V[i] - mu * (double)dV[i]);
+}
+
+// Probe step p <- p - mu dprobe, optionally rescaled so that W^2 ||p||^2 = mean pattern sum.
+__global__ void __launch_bounds__(1024) probe_update_kernel(float2* __restrict__ probe, const float2* __restrict__ d,
+                                                            int WW, double mu, int normalize, double target,
+                                                            const double* __restrict__ sumI, int S,
+                                                            double* __restrict__ mu_out) {
+  __shared__ double sh[1024];
+  const int tid = threadIdx.x;
+  double a = 0.0;
+  for (int i = tid; i < WW; i += 1024) {
+    const float2 p = probe[i], g = d[i];
+    const double re = (double)p.x - mu * (double)g.x;
+    const double im = (double)p.y - mu * (double)g.y;
+    probe[i] = make_float2((float)re, (float)im);
+    a += re * re + im * im;
+  }
+  if (tid == 0 && mu_out) mu_out[0] = mu;
+  if (!normalize) return;
+  sh[tid] = a;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] += sh[tid + s];
+    __syncthreads();
+  }
+  const double cur = (double)WW * sh[0];
+  const double tgt = (S > 0) ? sumI[0] / (double)S : target;
+  const double scale = (cur > 0.0 && tgt > 0.0) ? sqrt(tgt / cur) : 1.0;
+  for (int i = tid; i < WW; i += 1024) {
+    const float2 p = probe[i];
+    probe[i] = make_float2((float)(p.x * scale), (float)(p.y * scale));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+// ---- profiling: launch counter and optional events around the fused kernel ----
+static std::atomic<long long> g_launches{0};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<cudaEvent_t> g_ev_pool;   // pairs (start, stop)
+static size_t g_ev_used = 0;                 // pairs recorded since the last read
+static double g_prof_ms = 0.0;
+static long long g_prof_n = 0;
+
+static inline void counted(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Drains recorded event pairs into the running sum (caller holds g_prof_mu).
+static cudaError_t prof_drain() {
+  for (size_t i = 0; i < g_ev_used; ++i) {
+    cudaError_t e = cudaEventSynchronize(g_ev_pool[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, g_ev_pool[2 * i], g_ev_pool[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    g_prof_ms += ms;
+    ++g_prof_n;
+  }
+  g_ev_used = 0;
+  return cudaSuccess;
+}
+
+static msp_status fail(msp_status s, const std::string& m) {
+  g_err = m;
+  return s;
+}
+
+#define MSP_CK(call)                                                                      \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(MSP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DevInfo {
+  bool init = false;
+  int sms = 0;
+  int cta64 = 1, cta128 = 1;
+};
+static DevInfo g_dev[64];
+static std::mutex g_dev_mu;
+
+static bool device_info(DevInfo* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DevInfo& d = g_dev[dev];
+  if (!d.init) {
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    d.cta64 = position_ctas_per_sm(64);
+    d.cta128 = position_ctas_per_sm(128);
+    d.init = true;
+  }
+  *out = d;
+  return true;
+}
+
+static msp_status check_geometry(const msp_geometry* g) {
+  if (!g) return fail(MSP_EINVAL, "geometry is NULL");
+  if (g->win != 64 && g->win != 128)
+    return fail(MSP_EUNSUPPORTED, "window size " + std::to_string(g->win) + " (supported: 64, 128)");
+  if (g->param != MSP_PARAM_POTENTIAL)
+    return fail(MSP_EUNSUPPORTED, "only the potential parametrisation exp(i sigma V) is implemented");
+  if (g->n_slices < 1) return fail(MSP_EINVAL, "n_slices < 1");
+  if (g->obj_ny < g->win || g->obj_nx < g->win) return fail(MSP_EINVAL, "object smaller than the window");
+  if (g->n_pos < 0) return fail(MSP_EINVAL, "n_pos < 0");
+  if (!(std::isfinite(g->wavelength_A) && g->wavelength_A > 0)) return fail(MSP_EINVAL, "wavelength must be > 0");
+  if (!(std::isfinite(g->pixel_A) && g->pixel_A > 0)) return fail(MSP_EINVAL, "pixel size must be > 0");
+  if (!(std::isfinite(g->dz_A) && g->dz_A >= 0)) return fail(MSP_EINVAL, "slice thickness must be >= 0");
+  if (!std::isfinite(g->sigma)) return fail(MSP_EINVAL, "sigma must be finite");
+  const double cells = (double)g->n_slices * g->obj_ny * g->obj_nx;
+  if (cells > 4.0e9) return fail(MSP_EUNSUPPORTED, "object too large");
+  if ((size_t)((g->obj_nx + 31) / 32) * ((g->obj_ny + 31) / 32) > (size_t)kRedSlots)
+    return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
+  return MSP_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int grid_cap(const DevInfo& d, int win) { return d.sms * (win == 64 ? d.cta64 : d.cta128); }
+
+// Carve the workspace; with base == nullptr only the size is computed.
+static Workspace layout(const msp_geometry* g, int gcap, char* base) {
+  Workspace w{};
+  const size_t W = g->win, WW = W * W, S = (size_t)g->n_pos, L = g->n_slices;
+  const size_t plane = (size_t)g->obj_ny * g->obj_nx;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+  w.err = (int*)take(sizeof(int));
+  w.scal = (double*)take(16 * sizeof(double));
+  w.red = (double*)take(kRedSlots * sizeof(double));
+  w.H = (float2*)take(WW * sizeof(float2));
+  w.T = (float2*)take(L * plane * sizeof(float2));
+  w.stash = (float2*)take((size_t)gcap * L * WW * sizeof(float2));
+  w.wgrad = (float*)take(S * (L > 2 ? L : 2) * WW * sizeof(float));
+  w.willum = base ? w.wgrad + S * WW : nullptr;
+  w.dprobe_part = (float2*)take((size_t)gcap * WW * sizeof(float2));
+  w.dprobe_sum = (float2*)take(WW * sizeof(float2));
+  w.loss_part = (double*)take((S > 0 ? S : 1) * sizeof(double));
+  w.map0 = (float*)take(plane * sizeof(float));
+  w.map1 = (float*)take(plane * sizeof(float));
+  w.bytes = off;
+  return w;
+}
+
+static bool misaligned(const void* p, size_t a) { return ((uintptr_t)p) % a != 0; }
+
+struct Call {
+  DevInfo dev;
+  Workspace ws;
+  int gcap = 0;
+  int grid = 0;
+  cudaStream_t st = nullptr;
+};
+
+static msp_status begin(const msp_geometry* g, void* ws, size_t ws_bytes, void* stream, Call* c) {
+  msp_status s = check_geometry(g);
+  if (s != MSP_OK) return s;
+  if (!device_info(&c->dev)) return fail(MSP_ECUDA, "no current CUDA device");
+  c->gcap = grid_cap(c->dev, g->win);
+  const size_t need = layout(g, c->gcap, nullptr).bytes;
+  if (!ws) return fail(MSP_EINVAL, "workspace is NULL");
+  if (misaligned(ws, 256)) return fail(MSP_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < need)
+    return fail(MSP_EINVAL, "workspace too small: " + std::to_string(ws_bytes) + " < " + std::to_string(need));
+  c->ws = layout(g, c->gcap, (char*)ws);
+  c->grid = g->n_pos < c->gcap ? g->n_pos : c->gcap;
+  c->st = (cudaStream_t)stream;
+  return MSP_OK;
+}
+
+static msp_status need_ptr(const void* p, const char* name) {
+  if (!p) return fail(MSP_EINVAL, std::string(name) + " is NULL");
+  if (misaligned(p, 16)) return fail(MSP_EINVAL, std::string(name) + " must be 16-byte aligned");
+  return MSP_OK;
+}
+
+#define MSP_TRY(expr)            \
+  do {                           \
+    msp_status s_ = (expr);      \
+    if (s_ != MSP_OK) return s_; \
+  } while (0)
+
+static msp_status prepare(const msp_geometry* g, const float* V, Call& c) {
+  const int W = g->win;
+  MSP_CK(cudaMemsetAsync(c.ws.err, 0, sizeof(int), c.st));
+  propagator_kernel<<<(W * W + 255) / 256, 256, 0, c.st>>>(c.ws.H, W, g->dz_A * g->wavelength_A,
+                                                          1.0 / ((double)W * g->pixel_A));
+  MSP_CK(cudaGetLastError());
+  counted();
+  const size_t n = (size_t)g->n_slices * g->obj_ny * g->obj_nx;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)c.dev.sms * 16);
+  transmission_kernel<<<blocks, 256, 0, c.st>>>(V, c.ws.T, n, (float)g->sigma);
+  MSP_CK(cudaGetLastError());
+  counted();
+  return MSP_OK;
+}
+
+static PosParams base_params(const msp_geometry* g, const float* probe, const int32_t* pos, Call& c) {
+  PosParams p{};
+  p.probe = (const float2*)probe;
+  p.T = c.ws.T;
+  p.H = c.ws.H;
+  p.pos = (const int2*)pos;
+  p.stash = c.ws.stash;
+  p.wgrad = c.ws.wgrad;
+  p.willum = c.ws.willum;
+  p.dprobe_part = c.ws.dprobe_part;
+  p.loss_part = c.ws.loss_part;
+  p.err = c.ws.err;
+  p.L = g->n_slices;
+  p.Ny = g->obj_ny;
+  p.Nx = g->obj_nx;
+  p.S = g->n_pos;
+  p.two_sigma = (float)(2.0 * g->sigma);
+  return p;
+}
+
+static msp_status run_position(const msp_geometry* g, int mode, const PosParams& p, Call& c) {
+  if (g->n_pos == 0) return MSP_OK;
+  std::unique_lock<std::mutex> lk(g_prof_mu);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (g_prof_on) {
+    if (g_ev_used * 2 + 2 > g_ev_pool.size()) {
+      if (g_ev_pool.size() >= 8192) {
+        MSP_CK(prof_drain());
+      } else {
+        for (int k = 0; k < 2; ++k) {
+          cudaEvent_t ev;
+          MSP_CK(cudaEventCreate(&ev));
+          g_ev_pool.push_back(ev);
+        }
+      }
+    }
+    e0 = g_ev_pool[2 * g_ev_used];
+    e1 = g_ev_pool[2 * g_ev_used + 1];
+    MSP_CK(cudaEventRecord(e0, c.st));
+  }
+  MSP_CK(launch_position_kernel(g->win, mode, p, c.grid, c.st));
+  counted();
+  if (g_prof_on) {
+    MSP_CK(cudaEventRecord(e1, c.st));
+    ++g_ev_used;
+  }
+  return MSP_OK;
+}
+
+static msp_status reduce_loss(const msp_geometry* g, Call& c, double* extra) {
+  if (g->n_pos == 0) {
+    MSP_CK(cudaMemsetAsync(c.ws.scal, 0, sizeof(double), c.st));
+    if (extra) MSP_CK(cudaMemsetAsync(extra, 0, sizeof(double), c.st));
+    return MSP_OK;
+  }
+  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.loss_part, g->n_pos, 0, c.ws.scal, extra);
+  MSP_CK(cudaGetLastError());
+  counted();
+  return MSP_OK;
+}
+
+}  // namespace msp
+
+using namespace msp;
+
+extern "C" {
+
+msp_status msp_validate_geometry(const msp_geometry* g) {
+  g_err.clear();
+  return check_geometry(g);
+}
+
+size_t msp_workspace_bytes(const msp_geometry* g) {
+  if (check_geometry(g) != MSP_OK) return 0;
+  DevInfo d;
+  if (!device_info(&d)) return 0;
+  return layout(g, grid_cap(d, g->win), nullptr).bytes;
+}
+
+msp_status msp_forward(const msp_geometry* g, const float* probe, const float* V, const int32_t* pos, float* I_out,
+                       void* ws, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  Call c;
+  MSP_TRY(begin(g, ws, ws_bytes, stream, &c));
+  MSP_TRY(need_ptr(probe, "probe"));
+  MSP_TRY(need_ptr(V, "V"));
+  if (g->n_pos > 0) {
+    MSP_TRY(need_ptr(pos, "pos"));
+    MSP_TRY(need_ptr(I_out, "I_out"));
+  }
+  MSP_TRY(prepare(g, V, c));
+  PosParams p = base_params(g, probe, pos, c);
+  p.I_out = I_out;
+  return run_position(g, MODE_FORWARD, p, c);
+}
+
+msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float* V, const int32_t* pos,
+                         const float* I_meas, double* loss, float* dV, float* dprobe, void* ws, size_t ws_bytes,
+                         void* stream) {
+  g_err.clear();
+  Call c;
+  MSP_TRY(begin(g, ws, ws_bytes, stream, &c));
+  MSP_TRY(need_ptr(probe, "probe"));
+  MSP_TRY(need_ptr(V, "V"));
+  if (g->n_pos > 0) {
+    MSP_TRY(need_ptr(pos, "pos"));
+    MSP_TRY(need_ptr(I_meas, "I_meas"));
+  }
+  if (loss && misaligned(loss, 8)) return fail(MSP_EINVAL, "loss must be 8-byte aligned");
+  if (dV) MSP_TRY(need_ptr(dV, "dV"));
+  if (dprobe) MSP_TRY(need_ptr(dprobe, "dprobe"));
+  MSP_TRY(prepare(g, V, c));
+  const int W = g->win;
+  const size_t WW = (size_t)W * W;
+  const size_t plane = (size_t)g->obj_ny * g->obj_nx;
+  PosParams p = base_params(g, probe, pos, c);
+  p.I_meas = I_meas;
+  p.want_dprobe = dprobe != nullptr;
+  if (g->n_pos == 0) {
+    if (dV) MSP_CK(cudaMemsetAsync(dV, 0, (size_t)g->n_slices * plane * sizeof(float), c.st));
+    if (dprobe) MSP_CK(cudaMemsetAsync(dprobe, 0, WW * sizeof(float2), c.st));
+    return reduce_loss(g, c, loss);
+  }
+  MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
+  if (dV) {
+    dim3 grid((g->obj_nx + 31) / 32, (g->obj_ny + 31) / 32, g->n_slices);
+    gather_kernel<1><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos, W,
+                                             g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
+    MSP_CK(cudaGetLastError());
+  counted();
+  }
+  if (dprobe) {
+    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.grid, (int)WW,
+                                                                   (float2*)dprobe);
+    MSP_CK(cudaGetLastError());
+  counted();
+  }
+  return reduce_loss(g, c, loss);
+}
+
+msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, const int32_t* pos,
+                          const float* I_meas, int32_t layer, double step, double* loss_before, double* mu_out,
+                          void* ws, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  Call c;
+  MSP_TRY(begin(g, ws, ws_bytes, stream, &c));
+  MSP_TRY(need_ptr(probe, "probe"));
+  MSP_TRY(need_ptr(V, "V"));
+  if (layer < 0 || layer >= g->n_slices) return fail(MSP_EINVAL, "layer out of range");
+  if (!std::isfinite(step)) return fail(MSP_EINVAL, "step must be finite");
+  if (g->n_pos > 0) {
+    MSP_TRY(need_ptr(pos, "pos"));
+    MSP_TRY(need_ptr(I_meas, "I_meas"));
+  }
+  if (loss_before && misaligned(loss_before, 8)) return fail(MSP_EINVAL, "loss_before must be 8-byte aligned");
+  if (mu_out && misaligned(mu_out, 8)) return fail(MSP_EINVAL, "mu_out must be 8-byte aligned");
+  MSP_TRY(prepare(g, V, c));
+  const int W = g->win;
+  const size_t plane = (size_t)g->obj_ny * g->obj_nx;
+  if (g->n_pos == 0) {
+    MSP_CK(cudaMemsetAsync(c.ws.scal, 0, 16 * sizeof(double), c.st));
+    layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, 0.0, mu_out);
+    MSP_CK(cudaGetLastError());
+  counted();
+    return reduce_loss(g, c, loss_before);
+  }
+  PosParams p = base_params(g, probe, pos, c);
+  p.I_meas = I_meas;
+  p.layer = layer;
+  MSP_TRY(run_position(g, MODE_LAYER, p, c));
+  dim3 grid((g->obj_nx + 31) / 32, (g->obj_ny + 31) / 32, 1);
+  const int nblk = (int)(grid.x * grid.y);
+  if (nblk > kRedSlots) return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
+  gather_kernel<2><<<grid, 256, 0, c.st>>>(c.ws.wgrad, c.ws.willum, 1, (const int2*)pos, g->n_pos, W, g->obj_ny,
+                                           g->obj_nx, c.ws.map0, c.ws.map1, c.ws.red);
+  MSP_CK(cudaGetLastError());
+  counted();
+  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nblk, 1, c.ws.scal + 2, nullptr);
+  MSP_CK(cudaGetLastError());
+  counted();
+  const double two_sig2_w2 = 2.0 * g->sigma * g->sigma * (double)W * (double)W;
+  layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, two_sig2_w2, mu_out);
+  MSP_CK(cudaGetLastError());
+  counted();
+  MSP_TRY(reduce_loss(g, c, loss_before));
+  const int blocks = (int)std::min<size_t>((plane + 255) / 256, (size_t)c.dev.sms * 8);
+  layer_update_kernel<<<blocks, 256, 0, c.st>>>(V + (size_t)layer * plane, c.ws.map0, plane, c.ws.scal);
+  MSP_CK(cudaGetLastError());
+  counted();
+  return MSP_OK;
+}
+
+msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, const int32_t* pos,
+                          const float* I_meas, double step, int32_t normalize, double* loss_before, double* mu_out,
+                          void* ws, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  Call c;
+  MSP_TRY(begin(g, ws, ws_bytes, stream, &c));
+  MSP_TRY(need_ptr(probe, "probe"));
+  MSP_TRY(need_ptr(V, "V"));
+  if (!std::isfinite(step)) return fail(MSP_EINVAL, "step must be finite");
+  if (g->n_pos > 0) {
+    MSP_TRY(need_ptr(pos, "pos"));
+    MSP_TRY(need_ptr(I_meas, "I_meas"));
+  }
+  if (loss_before && misaligned(loss_before, 8)) return fail(MSP_EINVAL, "loss_before must be 8-byte aligned");
+  if (mu_out && misaligned(mu_out, 8)) return fail(MSP_EINVAL, "mu_out must be 8-byte aligned");
+  MSP_TRY(prepare(g, V, c));
+  const int W = g->win;
+  const size_t WW = (size_t)W * W;
+  const int S = g->n_pos;
+  const double mu = (step > 0.0) ? step : (S > 0 ? 1.0 / ((double)S * (double)WW) : 0.0);
+  if (S == 0) {
+    MSP_CK(cudaMemsetAsync(c.ws.dprobe_sum, 0, WW * sizeof(float2), c.st));
+  } else {
+    PosParams p = base_params(g, probe, pos, c);
+    p.I_meas = I_meas;
+    p.want_dprobe = 1;
+    MSP_TRY(run_position(g, MODE_PROBE, p, c));
+    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.grid, (int)WW,
+                                                                   c.ws.dprobe_sum);
+    MSP_CK(cudaGetLastError());
+  counted();
+  }
+  MSP_TRY(reduce_loss(g, c, loss_before));
+  if (normalize && S > 0) {
+    const int nb = 1024;
+    sum_blocks_kernel<<<nb, 256, 0, c.st>>>(I_meas, (size_t)S * WW, c.ws.red);
+    MSP_CK(cudaGetLastError());
+  counted();
+    reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nb, 0, c.ws.scal + 3, nullptr);
+    MSP_CK(cudaGetLastError());
+  counted();
+  }
+  probe_update_kernel<<<1, 1024, 0, c.st>>>((float2*)probe, c.ws.dprobe_sum, (int)WW, mu,
+                                            (normalize && S > 0) ? 1 : 0, 0.0, c.ws.scal + 3, S, mu_out);
+  MSP_CK(cudaGetLastError());
+  counted();
+  return MSP_OK;
+}
+
+msp_status msp_profile_enable(int32_t on) {
+  g_err.clear();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = on != 0;
+  return MSP_OK;
+}
+
+msp_status msp_profile_read(double* fused_ms, int64_t* fused_launches, int64_t* all_launches, int32_t reset) {
+  g_err.clear();
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  MSP_CK(prof_drain());
+  if (fused_ms) *fused_ms = g_prof_ms;
+  if (fused_launches) *fused_launches = g_prof_n;
+  if (all_launches) *all_launches = g_launches.load();
+  if (reset) {
+    g_prof_ms = 0.0;
+    g_prof_n = 0;
+    g_launches.store(0);
+  }
+  return MSP_OK;
+}
+
+msp_status msp_check_workspace(void* ws, void* stream) {
+  g_err.clear();
+  if (!ws) return fail(MSP_EINVAL, "workspace is NULL");
+  MSP_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int flag = 0;
+  MSP_CK(cudaMemcpy(&flag, ws, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    MSP_CK(cudaMemset(ws, 0, sizeof(int)));
+    return fail(MSP_EINVAL, "a scan window lies outside the object (position skipped)");
+  }
+  return MSP_OK;
+}
+
+const char* msp_status_string(msp_status s) {
+  switch (s) {
+    case MSP_OK: return "MSP_OK";
+    case MSP_EINVAL: return "MSP_EINVAL";
+    case MSP_ENOMEM: return "MSP_ENOMEM";
+    case MSP_ECUDA: return "MSP_ECUDA";
+    case MSP_EUNSUPPORTED: return "MSP_EUNSUPPORTED";
+    case MSP_ETIMEOUT: return "MSP_ETIMEOUT";
+  }
+  return "MSP_UNKNOWN";
+}
+
+const char* msp_last_error_message(void) { return g_err.c_str(); }
+
+}  // extern "C"

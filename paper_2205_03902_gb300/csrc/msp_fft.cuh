@@ -1,0 +1,137 @@
+// msp_fft.cuh -- shared-memory-resident 2-D FFT building blocks for sm_103a.
+//
+// The Fourier operator F of the multislice model (Sec. 2.1 / 2.2) is the
+// unnormalised 2-D DFT of a W x W wave.  A W-point line transform is split
+// W = N1 * 8 (four-step Cooley-Tukey): eight threads share one line, thread j
+// holds the line elements j, j+8, j+16, ...  (N1 complex values in registers),
+//   step A: an N1-point DFT in registers over those elements,
+//   step B: twiddle by w_W^(j k1),
+//   exchange through the line's own shared-memory storage (warp-synchronous),
+//   step C: N1/8 eight-point DFTs in registers.
+// The output indices k1 + N1 k2 held by thread j are again exactly the set
+// {j + 8m}, so every line transform starts and ends with the same thread/index
+// ownership and consecutive passes need no re-distribution beyond the row <->
+// column transpose through shared memory.
+//
+// The inverse transform is conj(F(conj(x))) (unnormalised); negations fold into
+// the arithmetic, so one forward kernel of small DFTs serves both directions.
+//
+// Shared-memory layout of the wave: element (r, c) lives at r*W + (c ^ swz(r)),
+// swz(r) = ((r & 1) << 3) | (r & 6).  With eight threads per line and four lines
+// per warp this makes every access of the row and column passes, including the
+// exchange pattern below, free of bank conflicts for 8-byte elements.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace msp {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// cos(2 pi k / 16) and sin(2 pi k / 16) for k = 0..3 (exact values of the regular 16-gon).
+constexpr float kC1 = 0.92387953251128675613f;   // cos(pi/8)
+constexpr float kS1 = 0.38268343236508977173f;   // sin(pi/8)
+constexpr float kR2 = 0.70710678118654752440f;   // cos(pi/4)
+
+// v * w_16^K with w_16 = exp(-2 pi i / 16); K in [0, 16).  Trivial factors are
+// special-cased so that no multiplication by 0 or 1 is issued.
+template <int K>
+__device__ __forceinline__ float2 tw16(float2 v) {
+  constexpr int k = K & 15;
+  if constexpr (k == 0) return v;
+  else if constexpr (k == 4) return make_float2(v.y, -v.x);           // * (-i)
+  else if constexpr (k == 8) return make_float2(-v.x, -v.y);          // * (-1)
+  else if constexpr (k == 12) return make_float2(-v.y, v.x);          // * (+i)
+  else if constexpr (k == 2) return make_float2(kR2 * (v.x + v.y), kR2 * (v.y - v.x));
+  else if constexpr (k == 6) return make_float2(kR2 * (v.y - v.x), -kR2 * (v.x + v.y));
+  else if constexpr (k == 10) return make_float2(-kR2 * (v.x + v.y), kR2 * (v.x - v.y));
+  else if constexpr (k == 14) return make_float2(kR2 * (v.x - v.y), kR2 * (v.x + v.y));
+  else {
+    // general: (a + ib)(c - is) with c = cos(2 pi k/16), s = sin(2 pi k/16)
+    constexpr float c = (k == 1 || k == 15) ? kC1 : (k == 3 || k == 13) ? kS1 : (k == 5 || k == 11) ? -kS1 : -kC1;
+    constexpr float s = (k == 1 || k == 7) ? kS1 : (k == 3 || k == 5) ? kC1 : (k == 9 || k == 15) ? -kS1 : -kC1;
+    return make_float2(fmaf(v.x, c, v.y * s), fmaf(v.y, c, -v.x * s));
+  }
+}
+
+// Radix-2 decimation-in-time butterflies of an N-point DFT, N <= 16.
+template <int N, int K>
+__device__ __forceinline__ void dit_bfly(const float2* E, const float2* O, float2* X) {
+  if constexpr (K < N / 2) {
+    const float2 t = tw16<(K * 16) / N>(O[K]);
+    X[K] = cadd(E[K], t);
+    X[K + N / 2] = csub(E[K], t);
+    dit_bfly<N, K + 1>(E, O, X);
+  }
+}
+
+// X[k] = sum_n x[n*S] w_N^(n k), forward DFT in registers (all indices compile-time).
+template <int N, int S>
+__device__ __forceinline__ void dft(const float2* x, float2* X) {
+  if constexpr (N == 1) {
+    X[0] = x[0];
+  } else if constexpr (N == 2) {
+    X[0] = cadd(x[0], x[S]);
+    X[1] = csub(x[0], x[S]);
+  } else {
+    float2 E[N / 2], O[N / 2];
+    dft<N / 2, 2 * S>(x, E);
+    dft<N / 2, 2 * S>(x + S, O);
+    dit_bfly<N, 0>(E, O, X);
+  }
+}
+
+__device__ __forceinline__ int swz(int r) { return ((r & 1) << 3) | (r & 6); }
+
+// Line transform of a W-point line held by 8 threads (lane group), in place in `v`:
+// on entry v[m] is line element j + 8m, on exit v[m] is spectrum element j + 8m.
+// `addr(i)` maps a line index to the float2 offset in shared memory.
+// `tw[k1]` = w_W^(j k1) (forward sign).  INV selects the unnormalised inverse.
+template <int W, bool INV, typename Addr>
+__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2 (&tw)[W / 8], float2* sm,
+                                         int j, Addr addr) {
+  constexpr int N1 = W / 8;
+  constexpr int NC = N1 / 8;
+  float2 y[N1];
+  if constexpr (INV) {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = cconj(v[m]);
+  }
+  // step A: DFT over n1 of x[8 n1 + j]
+  dft<N1, 1>(v, y);
+  // step B: twiddles, then exchange: Y[n2 = j][k1] -> line position 8 k1 + (j ^ (k1 & 7)).
+  // The line storage may still hold this group's inputs: wait for every lane's loads.
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    const float2 t = (k1 == 0) ? y[k1] : cmul(y[k1], tw[k1]);
+    sm[addr(8 * k1 + (j ^ (k1 & 7)))] = t;
+  }
+  __syncwarp();
+  float2 b[NC][8];
+#pragma unroll
+  for (int mc = 0; mc < NC; ++mc) {
+    const int k1 = j + 8 * mc;
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) b[mc][n2] = sm[addr(8 * k1 + (n2 ^ j))];
+  }
+  __syncwarp();
+  // step C: eight-point DFTs over n2; X[k1 + N1 k2] with k1 = j + 8 mc is v[mc + NC k2]
+#pragma unroll
+  for (int mc = 0; mc < NC; ++mc) {
+    float2 X[8];
+    dft<8, 1>(b[mc], X);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[mc + NC * k2] = INV ? cconj(X[k2]) : X[k2];
+  }
+}
+
+}  // namespace msp

@@ -1,0 +1,52 @@
+// msp_kernels.cuh -- kernel parameter blocks and launch helpers shared by the
+// translation units of libmsp.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace msp {
+
+enum Mode { MODE_FORWARD = 0, MODE_LOSS_GRAD = 1, MODE_LAYER = 2, MODE_PROBE = 3 };
+
+// Everything the fused per-position kernel reads or writes.
+struct PosParams {
+  const float2* probe;     // [W][W]
+  const float2* T;         // [L][Ny][Nx] slice transmissions exp(i sigma V)
+  const float2* H;         // [W][W] Fresnel propagator / W^2
+  const int2* pos;         // [S] window top-left (y, x)
+  const float* I_meas;     // [S][W][W]
+  float* I_out;            // [S][W][W]                (forward)
+  float2* stash;           // [G][Ls][W][W] exit waves kept for the adjoint
+  float* wgrad;            // [S][Lg][W][W] per-position window gradients
+  float* willum;           // [S][W][W] per-position |psi_in,l|^2 (layer step)
+  float2* dprobe_part;     // [G][W][W] per-CTA probe-gradient partial sums
+  double* loss_part;       // [S] per-position loss
+  int* err;                // error flags
+  int L, Ny, Nx, S;
+  int layer;               // slice of a layer step
+  int want_dprobe;
+  float two_sigma;
+};
+
+// Workspace carve-up (all offsets 256-byte aligned).
+struct Workspace {
+  int* err;
+  double* scal;            // [16] scalars: 0 loss, 1 mu, 2 max illum, 3 sum I, 4 probe norm
+  double* red;             // [kRedSlots] block partials of FP64 reductions
+  float2* H;
+  float2* T;
+  float2* stash;
+  float* wgrad;
+  float* willum;
+  float2* dprobe_part;
+  float2* dprobe_sum;      // [W][W]
+  double* loss_part;       // [S]
+  float* map0;             // [Ny][Nx] layer gradient map
+  float* map1;             // [Ny][Nx] illumination map
+  size_t bytes;
+};
+
+constexpr int kRedSlots = 8192;
+
+}  // namespace msp

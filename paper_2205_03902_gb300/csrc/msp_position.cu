@@ -1,0 +1,310 @@
+// msp_position.cu -- the fused per-position multislice forward / adjoint kernel.
+//
+// One CTA owns one scan position at a time (persistent grid, positions
+// s = blockIdx.x, blockIdx.x + gridDim.x, ...).  The W x W complex wave stays
+// in shared memory for the whole position: every slice's transmit (Sec. 2.1,
+// E_m = V_z(E_{m-1}) o X_m), Fresnel propagation F^-1(H o F .) and the far-field
+// transform F(E_M) run on it in place, then the amplitude-flow residual
+// (Sec. 3.2) and the adjoint recursion chi_{m-1} = G^H (conj(X_m) o chi_m)
+// (Sec. 3.3, the prefix / suffix products R_l and S_l applied matrix-free).
+//
+// The only per-slice global traffic is the transmission window (read), the exit
+// wave of each slice (written to this CTA's stash slot on the way forward, read
+// back on the way down; the slots are reused position after position so they
+// stay L2-resident) and the per-position window gradient.
+#include "msp_fft.cuh"
+#include "msp_kernels.cuh"
+
+namespace msp {
+
+template <int W>
+struct Geo {
+  static constexpr int NT = 4 * W;        // threads per CTA
+  static constexpr int N1 = W / 8;        // values per thread per line
+  static constexpr int GROUPS = NT / 8;   // eight-thread line groups
+  static constexpr int LPG = W / GROUPS;  // lines per group per pass
+};
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
+  using G = Geo<W>;
+  constexpr int N1 = G::N1;
+  extern __shared__ float2 sm[];
+  __shared__ float red[G::NT / 32];
+
+  const int tid = threadIdx.x;
+  const int j = tid & 7;
+  const int grp = tid >> 3;
+  const size_t WW = (size_t)W * W;
+  const size_t plane = (size_t)p.Ny * p.Nx;
+
+  // twiddles w_W^(j k1) = exp(-2 pi i j k1 / W)
+  float2 tw[N1];
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    float sn, cs;
+    sincospif(2.0f * (float)((j * k1) % W) / (float)W, &sn, &cs);
+    tw[k1] = make_float2(cs, -sn);
+  }
+
+  auto rowaddr = [](int r) { return [r](int i) { return r * W + (i ^ swz(r)); }; };
+  auto coladdr = [](int c) { return [c](int i) { return i * W + (c ^ swz(i)); }; };
+
+  const int L = p.L;
+  const bool need_stash = (MODE == MODE_LOSS_GRAD) || (MODE == MODE_LAYER);
+  const int lowest = (MODE == MODE_LAYER) ? p.layer : 0;
+  bool first_dprobe = true;
+
+  for (int s = blockIdx.x; s < p.S; s += gridDim.x) {
+    const int2 ps = p.pos[s];
+    const int y0 = ps.x, x0 = ps.y;
+    const bool ok = (y0 >= 0) && (x0 >= 0) && (y0 <= p.Ny - W) && (x0 <= p.Nx - W);
+    if (!ok) {
+      if (tid == 0) atomicOr(p.err, 1);
+      // outputs of a skipped position are zero
+      if (MODE == MODE_FORWARD) {
+        for (size_t i = tid; i < WW; i += G::NT) p.I_out[s * WW + i] = 0.f;
+      } else {
+        if (tid == 0) p.loss_part[s] = 0.0;
+        if (MODE == MODE_LOSS_GRAD)
+          for (size_t i = tid; i < WW * L; i += G::NT) p.wgrad[s * WW * L + i] = 0.f;
+        if (MODE == MODE_LAYER)
+          for (size_t i = tid; i < WW; i += G::NT) { p.wgrad[s * WW + i] = 0.f; p.willum[s * WW + i] = 0.f; }
+      }
+      continue;  // uniform across the CTA
+    }
+    const size_t win0 = (size_t)y0 * p.Nx + x0;
+    float2* stash = p.stash + (size_t)blockIdx.x * (MODE == MODE_LOSS_GRAD ? L : 1) * WW;
+
+    // ---------------- forward: slice 0, rows ----------------
+#pragma unroll 1
+    for (int it = 0; it < G::LPG; ++it) {
+      const int r = grp + G::GROUPS * it;
+      float2 v[N1];
+      const float2* T0 = p.T + win0 + (size_t)r * p.Nx;
+#pragma unroll
+      for (int m = 0; m < N1; ++m) v[m] = cmul(p.probe[r * W + j + 8 * m], T0[j + 8 * m]);
+      if (need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];
+      }
+      line_fft<W, false>(v, tw, sm, j, rowaddr(r));
+#pragma unroll
+      for (int m = 0; m < N1; ++m) sm[rowaddr(r)(j + 8 * m)] = v[m];
+    }
+    __syncthreads();
+
+    float lsum = 0.f;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+      if (l < L - 1) {
+        // columns: F, x H / W^2, F^-1 (unnormalised)
+#pragma unroll 1
+        for (int it = 0; it < G::LPG; ++it) {
+          const int c = grp + G::GROUPS * it;
+          float2 v[N1];
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = sm[coladdr(c)(j + 8 * m)];
+          line_fft<W, false>(v, tw, sm, j, coladdr(c));
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], p.H[(j + 8 * m) * W + c]);
+          line_fft<W, true>(v, tw, sm, j, coladdr(c));
+#pragma unroll
+          for (int m = 0; m < N1; ++m) sm[coladdr(c)(j + 8 * m)] = v[m];
+        }
+        __syncthreads();
+        // rows: F^-1, transmit slice l+1, keep the exit wave, F
+        const float2* Tl = p.T + (size_t)(l + 1) * plane + win0;
+        const bool keep = need_stash && (MODE == MODE_LOSS_GRAD || p.layer == l + 1);
+        float2* st = stash + (MODE == MODE_LOSS_GRAD ? (size_t)(l + 1) * WW : 0);
+#pragma unroll 1
+        for (int it = 0; it < G::LPG; ++it) {
+          const int r = grp + G::GROUPS * it;
+          float2 v[N1];
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = sm[rowaddr(r)(j + 8 * m)];
+          line_fft<W, true>(v, tw, sm, j, rowaddr(r));
+          const float2* Tr = Tl + (size_t)r * p.Nx;
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], Tr[j + 8 * m]);
+          if (keep) {
+#pragma unroll
+            for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];
+          }
+          line_fft<W, false>(v, tw, sm, j, rowaddr(r));
+#pragma unroll
+          for (int m = 0; m < N1; ++m) sm[rowaddr(r)(j + 8 * m)] = v[m];
+        }
+        __syncthreads();
+      } else {
+        // far field Psi = F(E_L): finish with the column transforms
+#pragma unroll 1
+        for (int it = 0; it < G::LPG; ++it) {
+          const int c = grp + G::GROUPS * it;
+          float2 v[N1];
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = sm[coladdr(c)(j + 8 * m)];
+          line_fft<W, false>(v, tw, sm, j, coladdr(c));
+          if (MODE == MODE_FORWARD) {
+            float* out = p.I_out + s * WW + c;
+#pragma unroll
+            for (int m = 0; m < N1; ++m) out[(j + 8 * m) * W] = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+          } else {
+            // amplitude-flow residual R = Psi - sqrt(I) Psi / |Psi| (0 where Psi == 0)
+            const float* im = p.I_meas + s * WW + c;
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+              const float a = sqrtf(fmaf(v[m].x, v[m].x, v[m].y * v[m].y));
+              const float rt = sqrtf(im[(j + 8 * m) * W]);
+              const float d = rt - a;
+              lsum = fmaf(d, d, lsum);
+              const float f = (a > 0.f) ? (1.f - rt / a) : 0.f;
+              v[m] = make_float2(v[m].x * f, v[m].y * f);
+            }
+            // chi = F^H R: inverse column transforms now, rows below
+            line_fft<W, true>(v, tw, sm, j, coladdr(c));
+#pragma unroll
+            for (int m = 0; m < N1; ++m) sm[coladdr(c)(j + 8 * m)] = v[m];
+          }
+        }
+        if (MODE != MODE_FORWARD) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+          if ((tid & 31) == 0) red[tid >> 5] = lsum;
+        }
+        __syncthreads();
+        if (MODE != MODE_FORWARD && tid == 0) {
+          double acc = 0.0;
+#pragma unroll 1
+          for (int w = 0; w < G::NT / 32; ++w) acc += (double)red[w];
+          p.loss_part[s] = acc;
+        }
+      }
+    }
+    if (MODE == MODE_FORWARD) {
+      __syncthreads();
+      continue;
+    }
+
+    // ---------------- adjoint: slices L-1 .. lowest ----------------
+#pragma unroll 1
+    for (int l = L - 1; l >= lowest; --l) {
+      const bool grad_here = (MODE == MODE_LOSS_GRAD) || (MODE == MODE_LAYER && l == p.layer);
+      const bool go_on = (l > lowest) || (l == 0 && MODE != MODE_LAYER && p.want_dprobe);
+      const float2* Tl = p.T + (size_t)l * plane + win0;
+      const float2* st = stash + (MODE == MODE_LOSS_GRAD ? (size_t)l * WW : 0);
+      float* wg = p.wgrad + (MODE == MODE_LOSS_GRAD ? ((size_t)s * L + l) * WW : (size_t)s * WW);
+#pragma unroll 1
+      for (int it = 0; it < G::LPG; ++it) {
+        const int r = grp + G::GROUPS * it;
+        float2 v[N1];
+#pragma unroll
+        for (int m = 0; m < N1; ++m) v[m] = sm[rowaddr(r)(j + 8 * m)];
+        line_fft<W, true>(v, tw, sm, j, rowaddr(r));   // v = chi_l (row r)
+        if (grad_here) {
+          // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
+#pragma unroll
+          for (int m = 0; m < N1; ++m) {
+            const float2 e = st[r * W + j + 8 * m];
+            wg[r * W + j + 8 * m] = p.two_sigma * fmaf(e.x, v[m].y, -e.y * v[m].x);
+            if (MODE == MODE_LAYER) p.willum[s * WW + r * W + j + 8 * m] = fmaf(e.x, e.x, e.y * e.y);
+          }
+        }
+        if (go_on) {
+          const float2* Tr = Tl + (size_t)r * p.Nx;
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], Tr[j + 8 * m]);   // conj(X_l) o chi_l
+          if (l == 0) {
+            float2* dp = p.dprobe_part + (size_t)blockIdx.x * WW + r * W;
+            if (first_dprobe) {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) dp[j + 8 * m] = v[m];
+            } else {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) dp[j + 8 * m] = cadd(dp[j + 8 * m], v[m]);
+            }
+          } else {
+            line_fft<W, false>(v, tw, sm, j, rowaddr(r));
+#pragma unroll
+            for (int m = 0; m < N1; ++m) sm[rowaddr(r)(j + 8 * m)] = v[m];
+          }
+        }
+      }
+      if (l == 0 && go_on) first_dprobe = false;
+      if (!go_on || l == 0) break;
+      __syncthreads();
+      // columns of G^H: F, x conj(H) / W^2, F^-1
+#pragma unroll 1
+      for (int it = 0; it < G::LPG; ++it) {
+        const int c = grp + G::GROUPS * it;
+        float2 v[N1];
+#pragma unroll
+        for (int m = 0; m < N1; ++m) v[m] = sm[coladdr(c)(j + 8 * m)];
+        line_fft<W, false>(v, tw, sm, j, coladdr(c));
+#pragma unroll
+        for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], p.H[(j + 8 * m) * W + c]);
+        line_fft<W, true>(v, tw, sm, j, coladdr(c));
+#pragma unroll
+        for (int m = 0; m < N1; ++m) sm[coladdr(c)(j + 8 * m)] = v[m];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+
+  // a CTA whose every position was skipped still owns a (zero) probe partial
+  if ((MODE == MODE_LOSS_GRAD || MODE == MODE_PROBE) && p.want_dprobe && first_dprobe) {
+    float2* dp = p.dprobe_part + (size_t)blockIdx.x * WW;
+    for (size_t i = tid; i < WW; i += G::NT) dp[i] = make_float2(0.f, 0.f);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// launch helpers
+// ----------------------------------------------------------------------------
+
+template <int W, int MODE>
+static cudaError_t launch_one(const PosParams& p, int grid, cudaStream_t st) {
+  const size_t smem = (size_t)W * W * sizeof(float2);
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(position_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done[dev] = true;
+  }
+  position_kernel<W, MODE><<<grid, 4 * W, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t launch_w(int mode, const PosParams& p, int grid, cudaStream_t st) {
+  switch (mode) {
+    case MODE_FORWARD: return launch_one<W, MODE_FORWARD>(p, grid, st);
+    case MODE_LOSS_GRAD: return launch_one<W, MODE_LOSS_GRAD>(p, grid, st);
+    case MODE_LAYER: return launch_one<W, MODE_LAYER>(p, grid, st);
+    default: return launch_one<W, MODE_PROBE>(p, grid, st);
+  }
+}
+
+cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int grid, cudaStream_t st) {
+  if (win == 64) return launch_w<64>(mode, p, grid, st);
+  return launch_w<128>(mode, p, grid, st);
+}
+
+// CTAs of the fused kernel that fit on one SM (same for every mode of a window size).
+int position_ctas_per_sm(int win) {
+  int n = 0;
+  const size_t smem = (size_t)win * win * sizeof(float2);
+  if (win == 64) {
+    cudaFuncSetAttribute(position_kernel<64, MODE_LOSS_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, position_kernel<64, MODE_LOSS_GRAD>, 4 * 64, smem);
+  } else {
+    cudaFuncSetAttribute(position_kernel<128, MODE_LOSS_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, position_kernel<128, MODE_LOSS_GRAD>, 4 * 128, smem);
+  }
+  return n < 1 ? 1 : n;
+}
+
+}  // namespace msp

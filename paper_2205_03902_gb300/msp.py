@@ -1,0 +1,253 @@
+"""Python binding of libmsp (ctypes).  Argument marshalling only.
+
+Every entry point takes CUDA tensors, checks their dtype / shape / device,
+hands raw device pointers and the current stream to the C ABI declared in
+`include/msp.h`, and raises `MspError` on a non-zero status.  All arithmetic
+runs in the library's kernels; there is no fallback of any kind: without the
+built `lib/libmsp.so` every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmsp.so")
+
+MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EUNSUPPORTED, MSP_ETIMEOUT = range(6)
+MSP_PARAM_POTENTIAL, MSP_PARAM_TRANSMISSION = 0, 1
+
+
+class MspError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    """msp_geometry (include/msp.h): the statement of the problem, Sec. 2.1."""
+    _fields_ = [
+        ("n_slices", ctypes.c_int32),
+        ("obj_ny", ctypes.c_int32),
+        ("obj_nx", ctypes.c_int32),
+        ("win", ctypes.c_int32),
+        ("n_pos", ctypes.c_int32),
+        ("param", ctypes.c_int32),
+        ("wavelength_A", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("dz_A", ctypes.c_double),
+        ("pixel_A", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def geometry(n_slices, obj_ny, obj_nx, win, n_pos, wavelength_A, sigma, dz_A, pixel_A,
+             param=MSP_PARAM_POTENTIAL, **_ignored) -> Geometry:
+    return Geometry(int(n_slices), int(obj_ny), int(obj_nx), int(win), int(n_pos), int(param),
+                    float(wavelength_A), float(sigma), float(dz_A), float(pixel_A))
+
+
+_lib = None
+_P = ctypes.c_void_p
+_G = ctypes.POINTER(Geometry)
+_SIGS = {
+    "msp_validate_geometry": ([_G], ctypes.c_int),
+    "msp_workspace_bytes": ([_G], ctypes.c_size_t),
+    "msp_forward": ([_G, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_loss_grad": ([_G, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_layer_step": ([_G, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P],
+                       ctypes.c_int),
+    "msp_probe_step": ([_G, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P],
+                       ctypes.c_int),
+    "msp_check_workspace": ([_P, _P], ctypes.c_int),
+    "msp_profile_enable": ([ctypes.c_int32], ctypes.c_int),
+    "msp_profile_read": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32], ctypes.c_int),
+    "msp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "msp_last_error_message": ([], ctypes.c_char_p),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libmsp; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmsp is not built ({LIB_PATH} missing): run paper_2205_03902_gb300/build.py")
+        dll = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(dll, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = dll
+    return _lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != MSP_OK:
+        l = lib()
+        detail = l.msp_last_error_message().decode() or l.msp_status_string(status).decode()
+        raise MspError(status, where, detail)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, name, dtype, shape, device):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if t.device != device:
+        raise ValueError(f"{name} must live on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def workspace_bytes(g: Geometry) -> int:
+    n = lib().msp_workspace_bytes(ctypes.byref(g))
+    if n == 0:
+        _check(lib().msp_validate_geometry(ctypes.byref(g)), "msp_workspace_bytes")
+        raise MspError(MSP_ECUDA, "msp_workspace_bytes", "no CUDA device")
+    return int(n)
+
+
+@dataclass
+class Workspace:
+    """Caller-owned scratch for one call at a time (allocated through torch)."""
+    buf: torch.Tensor
+
+    @property
+    def nbytes(self) -> int:
+        return self.buf.numel()
+
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+
+def make_workspace(g: Geometry, device=None) -> Workspace:
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n = workspace_bytes(g)
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return Workspace(buf[off:off + n])
+
+
+def _ws(g, ws, device):
+    if ws is None:
+        return make_workspace(g, device)
+    if ws.nbytes < workspace_bytes(g):
+        raise ValueError("workspace too small for this geometry")
+    return ws
+
+
+def _arrays(g: Geometry, probe, V, pos, I=None, I_name="I_meas"):
+    device = V.device
+    W, L, Ny, Nx, S = g.win, g.n_slices, g.obj_ny, g.obj_nx, g.n_pos
+    _need(probe, "probe", torch.complex64, (W, W), device)
+    _need(V, "V", torch.float32, (L, Ny, Nx), device)
+    _need(pos, "pos", torch.int32, (S, 2), device)
+    if I is not None:
+        _need(I, I_name, torch.float32, (S, W, W), device)
+    return device
+
+
+def forward(g: Geometry, probe, V, pos, out=None, ws=None, stream=None):
+    """Far-field intensities [S][W][W] (msp_forward)."""
+    device = _arrays(g, probe, V, pos)
+    if out is None:
+        out = torch.empty((g.n_pos, g.win, g.win), dtype=torch.float32, device=device)
+    _arrays(g, probe, V, pos, out, "out")
+    ws = _ws(g, ws, device)
+    _check(lib().msp_forward(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(pos), _ptr(out), ws.ptr(), ws.nbytes,
+                             _stream(stream)), "msp_forward")
+    return out
+
+
+def loss_grad(g: Geometry, probe, V, pos, I_meas, want_dV=True, want_dprobe=True, ws=None, stream=None,
+              loss=None, dV=None, dprobe=None):
+    """(loss [1] float64, dV [L][Ny][Nx] or None, dprobe [W][W] complex64 or None) (msp_loss_grad)."""
+    device = _arrays(g, probe, V, pos, I_meas)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=device)
+    if want_dV and dV is None:
+        dV = torch.empty_like(V)
+    if want_dprobe and dprobe is None:
+        dprobe = torch.empty_like(probe)
+    ws = _ws(g, ws, device)
+    _check(lib().msp_loss_grad(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(pos), _ptr(I_meas), _ptr(loss),
+                               _ptr(dV if want_dV else None), _ptr(dprobe if want_dprobe else None), ws.ptr(),
+                               ws.nbytes, _stream(stream)), "msp_loss_grad")
+    return loss, (dV if want_dV else None), (dprobe if want_dprobe else None)
+
+
+def layer_step(g: Geometry, probe, V, pos, I_meas, layer: int, step: float = 0.0, ws=None, stream=None,
+               loss_before=None, mu=None):
+    """One Algorithm-1 gradient step on slice `layer`, V updated in place; returns (loss_before, mu)."""
+    device = _arrays(g, probe, V, pos, I_meas)
+    if loss_before is None:
+        loss_before = torch.empty(1, dtype=torch.float64, device=device)
+    if mu is None:
+        mu = torch.empty(1, dtype=torch.float64, device=device)
+    ws = _ws(g, ws, device)
+    _check(lib().msp_layer_step(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(pos), _ptr(I_meas), int(layer),
+                                float(step), _ptr(loss_before), _ptr(mu), ws.ptr(), ws.nbytes, _stream(stream)),
+           "msp_layer_step")
+    return loss_before, mu
+
+
+def probe_step(g: Geometry, probe, V, pos, I_meas, step: float = 0.0, normalize: bool = False, ws=None,
+               stream=None, loss_before=None, mu=None):
+    """One amplitude-flow step on the probe, updated in place; returns (loss_before, mu)."""
+    device = _arrays(g, probe, V, pos, I_meas)
+    if loss_before is None:
+        loss_before = torch.empty(1, dtype=torch.float64, device=device)
+    if mu is None:
+        mu = torch.empty(1, dtype=torch.float64, device=device)
+    ws = _ws(g, ws, device)
+    _check(lib().msp_probe_step(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(pos), _ptr(I_meas), float(step),
+                                1 if normalize else 0, _ptr(loss_before), _ptr(mu), ws.ptr(), ws.nbytes,
+                                _stream(stream)), "msp_probe_step")
+    return loss_before, mu
+
+
+def check_workspace(ws: Workspace, stream=None) -> None:
+    """Raises MspError(MSP_EINVAL) if the last call on `ws` skipped a window outside the object."""
+    _check(lib().msp_check_workspace(ws.ptr(), _stream(stream)), "msp_check_workspace")
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket every fused-kernel launch with CUDA events on its stream."""
+    _check(lib().msp_profile_enable(1 if on else 0), "msp_profile_enable")
+
+
+def profile_read(reset: bool = True) -> dict:
+    """{'fused_ms', 'fused_launches', 'all_launches'} since the last reset (waits for the events)."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    total = ctypes.c_int64(0)
+    _check(lib().msp_profile_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(total), 1 if reset else 0),
+           "msp_profile_read")
+    return {"fused_ms": ms.value, "fused_launches": n.value, "all_launches": total.value}
+
+
+def validate_geometry(g: Geometry) -> int:
+    return int(lib().msp_validate_geometry(ctypes.byref(g)))
+
+
+def status_string(status: int) -> str:
+    return lib().msp_status_string(int(status)).decode()

@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol `include/msp.h` declares, and rejects bad arguments on the host
+before anything is launched."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2205_03902_gb300 import msp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return msp.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "msp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(msp_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["msp_forward", "msp_loss_grad", "msp_layer_step", "msp_probe_step", "msp_workspace_bytes"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def geom(**kw):
+    base = dict(n_slices=4, obj_ny=384, obj_nx=384, win=128, n_pos=16, wavelength_A=0.06979,
+                sigma=1.5433e-3, dz_A=2.0, pixel_A=0.15)
+    base.update(kw)
+    return msp.geometry(**base)
+
+
+@pytest.mark.parametrize("kw,status", [
+    ({}, msp.MSP_OK),
+    (dict(win=64, obj_ny=96, obj_nx=96), msp.MSP_OK),
+    (dict(win=96), msp.MSP_EUNSUPPORTED),
+    (dict(win=256, obj_ny=640, obj_nx=640), msp.MSP_EUNSUPPORTED),
+    (dict(param=msp.MSP_PARAM_TRANSMISSION), msp.MSP_EUNSUPPORTED),
+    (dict(n_slices=0), msp.MSP_EINVAL),
+    (dict(obj_ny=100), msp.MSP_EINVAL),
+    (dict(n_pos=-1), msp.MSP_EINVAL),
+    (dict(wavelength_A=0.0), msp.MSP_EINVAL),
+    (dict(pixel_A=-1.0), msp.MSP_EINVAL),
+    (dict(dz_A=float("nan")), msp.MSP_EINVAL),
+    (dict(sigma=float("inf")), msp.MSP_EINVAL),
+])
+def test_geometry_validation(lib, kw, status):
+    assert msp.validate_geometry(geom(**kw)) == status
+
+
+def test_null_geometry_and_status_strings(lib):
+    assert lib.msp_validate_geometry(None) == msp.MSP_EINVAL
+    assert b"NULL" in lib.msp_last_error_message()
+    for s, name in enumerate(["MSP_OK", "MSP_EINVAL", "MSP_ENOMEM", "MSP_ECUDA", "MSP_EUNSUPPORTED", "MSP_ETIMEOUT"]):
+        assert msp.status_string(s) == name
+    assert msp.status_string(99) == "MSP_UNKNOWN"
+
+
+def test_compute_calls_reject_bad_geometry_before_touching_the_device(lib):
+    g = geom(win=32)
+    st = lib.msp_forward(ctypes.byref(g), None, None, None, None, None, 0, None)
+    assert st == msp.MSP_EUNSUPPORTED
+    g = geom(n_slices=0)
+    st = lib.msp_loss_grad(ctypes.byref(g), None, None, None, None, None, None, None, None, 0, None)
+    assert st == msp.MSP_EINVAL
+    assert lib.msp_workspace_bytes(ctypes.byref(g)) == 0
