@@ -21,6 +21,13 @@ Conventions (readings of the paper where it is silent):
   * The loss is the amplitude-flow objective without a factor 1/2 (Sec. 3.2).
   * Potential mode: X_m = exp(i sigma V_m) with a real projected potential V_m.
     Transmission mode: X_m is a free complex array (the paper's o_m).
+  * Zero rule (Sec. 3.2 sets Qz/|Qz| to 0 where Qz = 0): a far-field value counts as
+    zero when |Psi_k| <= ZERO_RULE_TAU * ||p||_2.  By Parseval ||p||_2 is the RMS
+    far-field amplitude of every pattern of pure-phase slices, so this resolves
+    "Psi_k = 0" at 1e-5 of the RMS amplitude, far above round-off.  At the paper's
+    identity initialisation the exit wave is band-limited by the probe aperture and
+    Psi vanishes outside it in exact arithmetic; the rule gives that exact-arithmetic
+    residual instead of one whose phase is set by round-off.
 
 Parity status: every function here is pinned by `tests/test_oracle_pins.py`
 (closed forms, the paper's dense-matrix formulation, Parseval, finite
@@ -29,6 +36,8 @@ differences, brute-force spectral norms); no function is unpinned.
 from __future__ import annotations
 
 import numpy as np
+
+ZERO_RULE_TAU = 1e-5
 
 
 # ----------------------------------------------------------------------------
@@ -157,12 +166,18 @@ def forward_circulant(geom: dict, probe, shifts, V=None, T=None) -> np.ndarray:
 # grad = Q^H (Qz - Qz/|Qz| o sqrt(y)) with the fraction set to 0 where Qz = 0.
 # ----------------------------------------------------------------------------
 
-def far_field_residual(psi_far, i_meas):
-    """Loss term and the residual R = Psi - sqrt(I) Psi/|Psi| (0 where Psi == 0)."""
+def zero_threshold(probe) -> float:
+    """Amplitude at or below which a far-field value counts as zero (see the zero rule)."""
+    return ZERO_RULE_TAU * float(np.linalg.norm(np.asarray(probe).ravel()))
+
+
+def far_field_residual(psi_far, i_meas, thr=0.0):
+    """Loss term and the residual R = Psi - sqrt(I) Psi/|Psi|, the fraction taken as 0
+    where |Psi| <= thr (Sec. 3.2; thr = 0 is the literal rule)."""
     amp = np.abs(psi_far)
     root = np.sqrt(np.asarray(i_meas, dtype=np.float64))
     loss = float(np.sum((root - amp) ** 2))
-    nz = amp != 0.0
+    nz = amp > thr
     phase = np.zeros_like(psi_far)
     phase[nz] = psi_far[nz] / amp[nz]
     return loss, psi_far - root * phase
@@ -201,10 +216,11 @@ def loss_grad(geom: dict, probe, pos, i_meas, V=None, T=None, wrap=False, want_p
     dX = np.zeros_like(X)
     dprobe = np.zeros((w, w), dtype=np.complex128)
     loss = 0.0
+    thr = zero_threshold(probe)
     for s, (y, x) in enumerate(np.asarray(pos)):
         y, x = int(y), int(x)
         incident, _, psi_far = position_forward(probe, X, y, x, h, wrap)
-        ls, r = far_field_residual(psi_far, i_meas[s])
+        ls, r = far_field_residual(psi_far, i_meas[s], thr)
         loss += ls
         chi = dft2_adjoint(r)
         grads, dp = position_backward(X, y, x, h, incident, chi, 0, wrap)
@@ -227,10 +243,11 @@ def layer_quantities(geom: dict, probe, pos, i_meas, layer: int, V=None, T=None,
     dXl = np.zeros(X.shape[1:], dtype=np.complex128)
     illum = np.zeros(X.shape[1:])
     loss = 0.0
+    thr = zero_threshold(probe)
     for s, (y, x) in enumerate(np.asarray(pos)):
         y, x = int(y), int(x)
         incident, _, psi_far = position_forward(probe, X, y, x, h, wrap)
-        ls, r = far_field_residual(psi_far, i_meas[s])
+        ls, r = far_field_residual(psi_far, i_meas[s], thr)
         loss += ls
         grads, _ = position_backward(X, y, x, h, incident, dft2_adjoint(r), layer, wrap)
         window_add(dXl, y, x, grads[layer], wrap)
@@ -299,6 +316,47 @@ def layerwise_estimation(geom: dict, probe, pos, i_meas, V0, sweeps: int, steps_
                 V, loss, _ = layer_step(geom, probe, pos, i_meas, layer, V=V)
                 history.append(loss)
     return V, history
+
+
+def residual_conditioning(geom: dict, probe, pos, i_meas, V=None, T=None, band=0.0):
+    """How strongly a state amplifies rounding in the forward model into its gradients.
+
+    A forward whose far field carries an absolute error e ||p|| per value (||p|| being the
+    RMS far-field amplitude) changes R = Psi - sqrt(I) Psi/|Psi| by about e ||p|| m_k at
+    value k, with m_k = max(1, sqrt(I_k) / |Psi_k|) above the zero-rule threshold (the phase
+    of a small Psi_k is scaled by sqrt(I_k)) and m_k = 1 below it.  Returns
+    (kappa, cancellation, flip):
+      kappa = ||p|| sqrt(sum_k m_k^2) / ||R||, so the relative gradient error is ~ e kappa
+        (it reduces to ||Psi|| / ||R|| where every |Psi_k| >= sqrt(I_k));
+      cancellation = sum_s ||g_s|| / ||sum_s g_s|| of the per-position probe gradients g_s;
+      flip = sqrt(sum I_k over far-field values within `band` (absolute amplitude) of the
+        threshold) / ||R||: the largest relative change of R if a computation uncertain by
+        `band` decided those values the other way.
+    """
+    X = slices_of(geom, V, T)
+    w = geom["win"]
+    h = fresnel_propagator(w, geom["pixel_A"], geom["wavelength_A"], geom["dz_A"])
+    thr = zero_threshold(probe)
+    pnorm = float(np.linalg.norm(np.asarray(probe).ravel()))
+    nR = m2 = terms = flip2 = 0.0
+    acc = np.zeros((w, w), dtype=np.complex128)
+    for s, (y, x) in enumerate(np.asarray(pos)):
+        incident, _, psi_far = position_forward(probe, X, int(y), int(x), h)
+        _, r = far_field_residual(psi_far, i_meas[s], thr)
+        amp = np.abs(psi_far)
+        root = np.sqrt(np.asarray(i_meas[s], dtype=np.float64))
+        above = amp > thr
+        m = np.ones_like(amp)
+        m[above] = np.maximum(1.0, root[above] / amp[above])
+        m2 += float(np.sum(m * m))
+        nR += float(np.sum(np.abs(r) ** 2))
+        flip2 += float(np.sum((root ** 2)[np.abs(amp - thr) <= band]))
+        _, g = position_backward(X, int(y), int(x), h, incident, dft2_adjoint(r), 0)
+        terms += float(np.linalg.norm(g))
+        acc += g
+    kappa = pnorm * float(np.sqrt(m2 / nR)) if nR > 0 else float("inf")
+    flip = float(np.sqrt(flip2 / nR)) if nR > 0 else 0.0
+    return kappa, terms / max(float(np.linalg.norm(acc)), 1e-300), flip
 
 
 # ----------------------------------------------------------------------------

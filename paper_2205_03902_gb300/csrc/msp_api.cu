@@ -2,7 +2,7 @@
 // element-wise / reduction kernels around the fused per-position kernel.
 //
 //   transmission      X_m = exp(i sigma V_m) over the whole object (Sec. 2.1)
-//   propagator        H / W^2, Eq. (fresnel_element) with zero tilt
+//   propagator        separable factor of H / W^2, Eq. (fresnel_element), zero tilt
 //   gather            atomic-free overlap-add of per-position window gradients
 //                     into object-frame maps, every pixel summing its covering
 //                     positions in ascending scan order (the sum over s of
@@ -39,20 +39,20 @@ __global__ void transmission_kernel(const float* __restrict__ V, float2* __restr
   }
 }
 
-// H[ky][kx] = exp(-i pi dz lambda (qy^2 + qx^2)) / W^2; the phase / pi is formed and
-// reduced modulo 2 in double precision, the sine and cosine taken in single.
-__global__ void propagator_kernel(float2* __restrict__ H, int W, double dzlam, double dq) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= W * W) return;
-  const int ky = i / W, kx = i % W;
-  const double qy = (double)(ky < W / 2 ? ky : ky - W) * dq;
-  const double qx = (double)(kx < W / 2 ? kx : kx - W) * dq;
-  double t = dzlam * (qy * qy + qx * qx);   // phase / pi
+// Separable Fresnel propagator, Eq. (fresnel_element) with zero tilt:
+// h(ky, kx) = exp(-i pi dz lambda (qy^2 + qx^2)) / W^2 = h1(ky) h1(kx) with
+// h1(k) = exp(-i pi dz lambda q_k^2) / W, evaluated in double precision and rounded
+// once to single (the table's rounding is shared by every position, so it is kept at
+// half a unit in the last place).
+__global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, double dq) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= W) return;
+  const double q = (double)(k < W / 2 ? k : k - W) * dq;
+  double t = dzlam * q * q;   // phase / pi
   t = t - 2.0 * floor(t * 0.5);
-  float sn, cs;
-  sincospif((float)t, &sn, &cs);
-  const float inv = 1.0f / ((float)W * (float)W);
-  H[i] = make_float2(cs * inv, -sn * inv);
+  double sn, cs;
+  sincospi(t, &sn, &cs);
+  h1[k] = make_float2((float)(cs / W), (float)(-sn / W));
 }
 
 // Overlap-add of per-position window arrays into object-frame maps.  One CTA owns a
@@ -129,6 +129,25 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
       blockmax[blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
     }
   }
+}
+
+// out = tau^2 * sum |p|^2 (FP64, fixed order): the squared zero-rule threshold.
+__global__ void __launch_bounds__(1024) zero_threshold_kernel(const float2* __restrict__ probe, int WW, double tau2,
+                                                              double* __restrict__ out) {
+  __shared__ double sh[1024];
+  const int tid = threadIdx.x;
+  double a = 0.0;
+  for (int i = tid; i < WW; i += 1024) {
+    const float2 v = probe[i];
+    a += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  sh[tid] = a;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] += sh[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) out[0] = tau2 * sh[0];
 }
 
 // Single-block FP64 reduction in a fixed order.  op 0: sum, 1: max.
@@ -331,7 +350,7 @@ static Workspace layout(const msp_geometry* g, int gcap, char* base) {
   w.err = (int*)take(sizeof(int));
   w.scal = (double*)take(16 * sizeof(double));
   w.red = (double*)take(kRedSlots * sizeof(double));
-  w.H = (float2*)take(WW * sizeof(float2));
+  w.h1 = (float2*)take(W * sizeof(float2));
   w.T = (float2*)take(L * plane * sizeof(float2));
   w.stash = (float2*)take((size_t)gcap * L * WW * sizeof(float2));
   w.wgrad = (float*)take(S * (L > 2 ? L : 2) * WW * sizeof(float));
@@ -383,11 +402,15 @@ static msp_status need_ptr(const void* p, const char* name) {
     if (s_ != MSP_OK) return s_; \
   } while (0)
 
-static msp_status prepare(const msp_geometry* g, const float* V, Call& c) {
+static msp_status prepare(const msp_geometry* g, const float* probe, const float* V, Call& c) {
   const int W = g->win;
   MSP_CK(cudaMemsetAsync(c.ws.err, 0, sizeof(int), c.st));
-  propagator_kernel<<<(W * W + 255) / 256, 256, 0, c.st>>>(c.ws.H, W, g->dz_A * g->wavelength_A,
-                                                          1.0 / ((double)W * g->pixel_A));
+  zero_threshold_kernel<<<1, 1024, 0, c.st>>>((const float2*)probe, W * W, kZeroRuleTau * kZeroRuleTau,
+                                              c.ws.scal + 5);
+  MSP_CK(cudaGetLastError());
+  counted();
+  propagator_kernel<<<(W + 255) / 256, 256, 0, c.st>>>(c.ws.h1, W, g->dz_A * g->wavelength_A,
+                                                      1.0 / ((double)W * g->pixel_A));
   MSP_CK(cudaGetLastError());
   counted();
   const size_t n = (size_t)g->n_slices * g->obj_ny * g->obj_nx;
@@ -402,7 +425,7 @@ static PosParams base_params(const msp_geometry* g, const float* probe, const in
   PosParams p{};
   p.probe = (const float2*)probe;
   p.T = c.ws.T;
-  p.H = c.ws.H;
+  p.h1 = c.ws.h1;
   p.pos = (const int2*)pos;
   p.stash = c.ws.stash;
   p.wgrad = c.ws.wgrad;
@@ -410,6 +433,7 @@ static PosParams base_params(const msp_geometry* g, const float* probe, const in
   p.dprobe_part = c.ws.dprobe_part;
   p.loss_part = c.ws.loss_part;
   p.err = c.ws.err;
+  p.zthr2 = c.ws.scal + 5;
   p.L = g->n_slices;
   p.Ny = g->obj_ny;
   p.Nx = g->obj_nx;
@@ -488,7 +512,7 @@ msp_status msp_forward(const msp_geometry* g, const float* probe, const float* V
     MSP_TRY(need_ptr(pos, "pos"));
     MSP_TRY(need_ptr(I_out, "I_out"));
   }
-  MSP_TRY(prepare(g, V, c));
+  MSP_TRY(prepare(g, probe, V, c));
   PosParams p = base_params(g, probe, pos, c);
   p.I_out = I_out;
   return run_position(g, MODE_FORWARD, p, c);
@@ -509,7 +533,7 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   if (loss && misaligned(loss, 8)) return fail(MSP_EINVAL, "loss must be 8-byte aligned");
   if (dV) MSP_TRY(need_ptr(dV, "dV"));
   if (dprobe) MSP_TRY(need_ptr(dprobe, "dprobe"));
-  MSP_TRY(prepare(g, V, c));
+  MSP_TRY(prepare(g, probe, V, c));
   const int W = g->win;
   const size_t WW = (size_t)W * W;
   const size_t plane = (size_t)g->obj_ny * g->obj_nx;
@@ -554,7 +578,7 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   }
   if (loss_before && misaligned(loss_before, 8)) return fail(MSP_EINVAL, "loss_before must be 8-byte aligned");
   if (mu_out && misaligned(mu_out, 8)) return fail(MSP_EINVAL, "mu_out must be 8-byte aligned");
-  MSP_TRY(prepare(g, V, c));
+  MSP_TRY(prepare(g, probe, V, c));
   const int W = g->win;
   const size_t plane = (size_t)g->obj_ny * g->obj_nx;
   if (g->n_pos == 0) {
@@ -605,7 +629,7 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, c
   }
   if (loss_before && misaligned(loss_before, 8)) return fail(MSP_EINVAL, "loss_before must be 8-byte aligned");
   if (mu_out && misaligned(mu_out, 8)) return fail(MSP_EINVAL, "mu_out must be 8-byte aligned");
-  MSP_TRY(prepare(g, V, c));
+  MSP_TRY(prepare(g, probe, V, c));
   const int W = g->win;
   const size_t WW = (size_t)W * W;
   const int S = g->n_pos;

@@ -94,9 +94,11 @@ __device__ __forceinline__ int swz(int r) { return ((r & 1) << 3) | (r & 6); }
 // Line transform of a W-point line held by 8 threads (lane group), in place in `v`:
 // on entry v[m] is line element j + 8m, on exit v[m] is spectrum element j + 8m.
 // `addr(i)` maps a line index to the float2 offset in shared memory.
-// `tw[k1]` = w_W^(j k1) (forward sign).  INV selects the unnormalised inverse.
+// `tws[k1 * 8 + j]` = w_W^(j k1) (forward sign), a shared table read without bank
+// conflicts (eight distinct words per instruction, broadcast across the warp's lines).
+// INV selects the unnormalised inverse.
 template <int W, bool INV, typename Addr>
-__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2 (&tw)[W / 8], float2* sm,
+__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2* __restrict__ tws, float2* sm,
                                          int j, Addr addr) {
   constexpr int N1 = W / 8;
   constexpr int NC = N1 / 8;
@@ -112,7 +114,7 @@ __device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2 (&tw)[
   __syncwarp();
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) {
-    const float2 t = (k1 == 0) ? y[k1] : cmul(y[k1], tw[k1]);
+    const float2 t = (k1 == 0) ? y[k1] : cmul(y[k1], tws[k1 * 8 + j]);
     sm[addr(8 * k1 + (j ^ (k1 & 7)))] = t;
   }
   __syncwarp();

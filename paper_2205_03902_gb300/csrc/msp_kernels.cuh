@@ -13,7 +13,7 @@ enum Mode { MODE_FORWARD = 0, MODE_LOSS_GRAD = 1, MODE_LAYER = 2, MODE_PROBE = 3
 struct PosParams {
   const float2* probe;     // [W][W]
   const float2* T;         // [L][Ny][Nx] slice transmissions exp(i sigma V)
-  const float2* H;         // [W][W] Fresnel propagator / W^2
+  const float2* h1;        // [W] separable propagator factor exp(-i pi dz lambda q_k^2) / W
   const int2* pos;         // [S] window top-left (y, x)
   const float* I_meas;     // [S][W][W]
   float* I_out;            // [S][W][W]                (forward)
@@ -22,6 +22,7 @@ struct PosParams {
   float* willum;           // [S][W][W] per-position |psi_in,l|^2 (layer step)
   float2* dprobe_part;     // [G][W][W] per-CTA probe-gradient partial sums
   double* loss_part;       // [S] per-position loss
+  const double* zthr2;     // [1] squared far-field amplitude that counts as zero
   int* err;                // error flags
   int L, Ny, Nx, S;
   int layer;               // slice of a layer step
@@ -32,9 +33,9 @@ struct PosParams {
 // Workspace carve-up (all offsets 256-byte aligned).
 struct Workspace {
   int* err;
-  double* scal;            // [16] scalars: 0 loss, 1 mu, 2 max illum, 3 sum I, 4 probe norm
+  double* scal;            // [16] scalars: 0 loss, 1 mu, 2 max illum, 3 sum I, 5 zero-rule threshold^2
   double* red;             // [kRedSlots] block partials of FP64 reductions
-  float2* H;
+  float2* h1;              // [W]
   float2* T;
   float2* stash;
   float* wgrad;
@@ -48,5 +49,11 @@ struct Workspace {
 };
 
 constexpr int kRedSlots = 8192;
+
+// Zero rule of the amplitude-flow gradient (Sec. 3.2: Qz/|Qz| := 0 where Qz = 0),
+// resolved at the arithmetic's resolution: a far-field value counts as zero when
+// |Psi_k| <= kZeroRuleTau * ||p||_2, the probe norm being the RMS far-field amplitude
+// of every pattern of pure-phase slices (Parseval).
+constexpr double kZeroRuleTau = 1e-5;
 
 }  // namespace msp

@@ -8,6 +8,18 @@
 // (Sec. 3.2) and the adjoint recursion chi_{m-1} = G^H (conj(X_m) o chi_m)
 // (Sec. 3.3, the prefix / suffix products R_l and S_l applied matrix-free).
 //
+// A propagation is  rows F -> [columns F, x H, columns F^-1] -> rows F^-1: the
+// column transforms and the propagator run back to back in registers, and the
+// inverse row transform of one slice, the transmit of the next slice and its
+// forward row transform also run back to back in registers.  Each phase is one
+// read and one write of the wave in shared memory plus the in-line exchange.
+//
+// The propagator is separable, h(ky, kx) = h1(ky) h1(kx) with
+// h1(k) = exp(-i pi dz lambda q_k^2) / W (the 1/W^2 of F^-1 folded in), so it is
+// a W-entry shared table.  Global operands of a phase (transmission window,
+// measured intensities, stashed exit waves) are loaded before the line transform
+// that precedes their use, so their latency hides behind the arithmetic.
+//
 // The only per-slice global traffic is the transmission window (read), the exit
 // wave of each slice (written to this CTA's stash slot on the way forward, read
 // back on the way down; the slots are reused position after position so they
@@ -25,11 +37,24 @@ struct Geo {
   static constexpr int LPG = W / GROUPS;  // lines per group per pass
 };
 
+template <int W>
+struct RowAddr {
+  int r;
+  __device__ __forceinline__ int operator()(int i) const { return r * W + (i ^ swz(r)); }
+};
+template <int W>
+struct ColAddr {
+  int c;
+  __device__ __forceinline__ int operator()(int i) const { return i * W + (c ^ swz(i)); }
+};
+
 template <int W, int MODE>
 __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   using G = Geo<W>;
   constexpr int N1 = G::N1;
   extern __shared__ float2 sm[];
+  __shared__ float2 s_tw[N1 * 8];   // w_W^(j k1) at [k1 * 8 + j]
+  __shared__ float2 s_h1[W];        // h1(k) = exp(-i pi dz lambda q_k^2) / W
   __shared__ float red[G::NT / 32];
 
   const int tid = threadIdx.x;
@@ -38,19 +63,17 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   const size_t WW = (size_t)W * W;
   const size_t plane = (size_t)p.Ny * p.Nx;
 
-  // twiddles w_W^(j k1) = exp(-2 pi i j k1 / W)
-  float2 tw[N1];
-#pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) {
-    float sn, cs;
-    sincospif(2.0f * (float)((j * k1) % W) / (float)W, &sn, &cs);
-    tw[k1] = make_float2(cs, -sn);
+  if (tid < N1 * 8) {   // evaluated in double, rounded once
+    const int k1 = tid >> 3, jj = tid & 7;
+    double sn, cs;
+    sincospi(2.0 * (double)((jj * k1) % W) / (double)W, &sn, &cs);
+    s_tw[tid] = make_float2((float)cs, (float)-sn);
   }
-
-  auto rowaddr = [](int r) { return [r](int i) { return r * W + (i ^ swz(r)); }; };
-  auto coladdr = [](int c) { return [c](int i) { return i * W + (c ^ swz(i)); }; };
+  if (tid < W) s_h1[tid] = p.h1[tid];
+  __syncthreads();
 
   const int L = p.L;
+  const float zthr2 = (MODE == MODE_FORWARD) ? 0.f : (float)p.zthr2[0];
   const bool need_stash = (MODE == MODE_LOSS_GRAD) || (MODE == MODE_LAYER);
   const int lowest = (MODE == MODE_LAYER) ? p.layer : 0;
   bool first_dprobe = true;
@@ -88,9 +111,9 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];
       }
-      line_fft<W, false>(v, tw, sm, j, rowaddr(r));
+      line_fft<W, false>(v, s_tw, sm, j, RowAddr<W>{r});
 #pragma unroll
-      for (int m = 0; m < N1; ++m) sm[rowaddr(r)(j + 8 * m)] = v[m];
+      for (int m = 0; m < N1; ++m) sm[RowAddr<W>{r}(j + 8 * m)] = v[m];
     }
     __syncthreads();
 
@@ -102,15 +125,17 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
         for (int it = 0; it < G::LPG; ++it) {
           const int c = grp + G::GROUPS * it;
+          const ColAddr<W> ca{c};
           float2 v[N1];
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = sm[coladdr(c)(j + 8 * m)];
-          line_fft<W, false>(v, tw, sm, j, coladdr(c));
+          for (int m = 0; m < N1; ++m) v[m] = sm[ca(j + 8 * m)];
+          line_fft<W, false>(v, s_tw, sm, j, ca);
+          const float2 hx = s_h1[c];
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], p.H[(j + 8 * m) * W + c]);
-          line_fft<W, true>(v, tw, sm, j, coladdr(c));
+          for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], cmul(s_h1[j + 8 * m], hx));
+          line_fft<W, true>(v, s_tw, sm, j, ca);
 #pragma unroll
-          for (int m = 0; m < N1; ++m) sm[coladdr(c)(j + 8 * m)] = v[m];
+          for (int m = 0; m < N1; ++m) sm[ca(j + 8 * m)] = v[m];
         }
         __syncthreads();
         // rows: F^-1, transmit slice l+1, keep the exit wave, F
@@ -120,20 +145,23 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
         for (int it = 0; it < G::LPG; ++it) {
           const int r = grp + G::GROUPS * it;
-          float2 v[N1];
-#pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = sm[rowaddr(r)(j + 8 * m)];
-          line_fft<W, true>(v, tw, sm, j, rowaddr(r));
+          const RowAddr<W> ra{r};
+          float2 t[N1], v[N1];
           const float2* Tr = Tl + (size_t)r * p.Nx;
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], Tr[j + 8 * m]);
+          for (int m = 0; m < N1; ++m) t[m] = Tr[j + 8 * m];     // in flight during the transform
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = sm[ra(j + 8 * m)];
+          line_fft<W, true>(v, s_tw, sm, j, ra);
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], t[m]);
           if (keep) {
 #pragma unroll
             for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];
           }
-          line_fft<W, false>(v, tw, sm, j, rowaddr(r));
+          line_fft<W, false>(v, s_tw, sm, j, ra);
 #pragma unroll
-          for (int m = 0; m < N1; ++m) sm[rowaddr(r)(j + 8 * m)] = v[m];
+          for (int m = 0; m < N1; ++m) sm[ra(j + 8 * m)] = v[m];
         }
         __syncthreads();
       } else {
@@ -141,30 +169,38 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
         for (int it = 0; it < G::LPG; ++it) {
           const int c = grp + G::GROUPS * it;
+          const ColAddr<W> ca{c};
           float2 v[N1];
+          float im[N1];
+          if (MODE != MODE_FORWARD) {
+            const float* ip = p.I_meas + s * WW + c;
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = sm[coladdr(c)(j + 8 * m)];
-          line_fft<W, false>(v, tw, sm, j, coladdr(c));
+            for (int m = 0; m < N1; ++m) im[m] = ip[(j + 8 * m) * W];   // in flight during the transform
+          }
+#pragma unroll
+          for (int m = 0; m < N1; ++m) v[m] = sm[ca(j + 8 * m)];
+          line_fft<W, false>(v, s_tw, sm, j, ca);
           if (MODE == MODE_FORWARD) {
             float* out = p.I_out + s * WW + c;
 #pragma unroll
             for (int m = 0; m < N1; ++m) out[(j + 8 * m) * W] = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
           } else {
-            // amplitude-flow residual R = Psi - sqrt(I) Psi / |Psi| (0 where Psi == 0)
-            const float* im = p.I_meas + s * WW + c;
+            // amplitude-flow residual R = Psi - sqrt(I) Psi / |Psi| (fraction 0 where Psi counts as 0)
 #pragma unroll
             for (int m = 0; m < N1; ++m) {
-              const float a = sqrtf(fmaf(v[m].x, v[m].x, v[m].y * v[m].y));
-              const float rt = sqrtf(im[(j + 8 * m) * W]);
+              const float a2 = fmaf(v[m].x, v[m].x, v[m].y * v[m].y);
+              const float a = sqrtf(a2);
+              const float rt = sqrtf(im[m]);
               const float d = rt - a;
               lsum = fmaf(d, d, lsum);
-              const float f = (a > 0.f) ? (1.f - rt / a) : 0.f;
+              // below the threshold the fraction is 0, so R = Psi (f = 1); a2 > zthr2 >= 0 implies a > 0
+              const float f = (a2 > zthr2) ? (1.f - rt / a) : 1.f;
               v[m] = make_float2(v[m].x * f, v[m].y * f);
             }
             // chi = F^H R: inverse column transforms now, rows below
-            line_fft<W, true>(v, tw, sm, j, coladdr(c));
+            line_fft<W, true>(v, s_tw, sm, j, ca);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) sm[coladdr(c)(j + 8 * m)] = v[m];
+            for (int m = 0; m < N1; ++m) sm[ca(j + 8 * m)] = v[m];
           }
         }
         if (MODE != MODE_FORWARD) {
@@ -197,17 +233,21 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
       for (int it = 0; it < G::LPG; ++it) {
         const int r = grp + G::GROUPS * it;
-        float2 v[N1];
+        const RowAddr<W> ra{r};
+        float2 e[N1], v[N1];
+        if (grad_here) {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) v[m] = sm[rowaddr(r)(j + 8 * m)];
-        line_fft<W, true>(v, tw, sm, j, rowaddr(r));   // v = chi_l (row r)
+          for (int m = 0; m < N1; ++m) e[m] = st[r * W + j + 8 * m];   // in flight during the transform
+        }
+#pragma unroll
+        for (int m = 0; m < N1; ++m) v[m] = sm[ra(j + 8 * m)];
+        line_fft<W, true>(v, s_tw, sm, j, ra);   // v = chi_l (row r)
         if (grad_here) {
           // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
 #pragma unroll
           for (int m = 0; m < N1; ++m) {
-            const float2 e = st[r * W + j + 8 * m];
-            wg[r * W + j + 8 * m] = p.two_sigma * fmaf(e.x, v[m].y, -e.y * v[m].x);
-            if (MODE == MODE_LAYER) p.willum[s * WW + r * W + j + 8 * m] = fmaf(e.x, e.x, e.y * e.y);
+            wg[r * W + j + 8 * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
+            if (MODE == MODE_LAYER) p.willum[s * WW + r * W + j + 8 * m] = fmaf(e[m].x, e[m].x, e[m].y * e[m].y);
           }
         }
         if (go_on) {
@@ -224,9 +264,9 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               for (int m = 0; m < N1; ++m) dp[j + 8 * m] = cadd(dp[j + 8 * m], v[m]);
             }
           } else {
-            line_fft<W, false>(v, tw, sm, j, rowaddr(r));
+            line_fft<W, false>(v, s_tw, sm, j, ra);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) sm[rowaddr(r)(j + 8 * m)] = v[m];
+            for (int m = 0; m < N1; ++m) sm[ra(j + 8 * m)] = v[m];
           }
         }
       }
@@ -237,15 +277,17 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
       for (int it = 0; it < G::LPG; ++it) {
         const int c = grp + G::GROUPS * it;
+        const ColAddr<W> ca{c};
         float2 v[N1];
 #pragma unroll
-        for (int m = 0; m < N1; ++m) v[m] = sm[coladdr(c)(j + 8 * m)];
-        line_fft<W, false>(v, tw, sm, j, coladdr(c));
+        for (int m = 0; m < N1; ++m) v[m] = sm[ca(j + 8 * m)];
+        line_fft<W, false>(v, s_tw, sm, j, ca);
+        const float2 hx = s_h1[c];
 #pragma unroll
-        for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], p.H[(j + 8 * m) * W + c]);
-        line_fft<W, true>(v, tw, sm, j, coladdr(c));
+        for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], cmul(s_h1[j + 8 * m], hx));
+        line_fft<W, true>(v, s_tw, sm, j, ca);
 #pragma unroll
-        for (int m = 0; m < N1; ++m) sm[coladdr(c)(j + 8 * m)] = v[m];
+        for (int m = 0; m < N1; ++m) sm[ca(j + 8 * m)] = v[m];
       }
       __syncthreads();
     }

@@ -428,3 +428,39 @@ def test_potential_step_is_the_tangent_projection_of_the_transmission_step(layer
     np.testing.assert_allclose(Vn[layer] - V[layer], tangent, rtol=1e-9, atol=1e-14)
     others = [m for m in range(V.shape[0]) if m != layer]
     assert np.array_equal(Vn[others], V[others])
+
+
+def test_zero_rule_gives_the_exact_arithmetic_residual_at_identity_initialisation():
+    """With identity slices (V = 0, the paper's initialisation) and an aperture-limited probe,
+    Psi = h^(L-1) F(p) vanishes outside the aperture in exact arithmetic, and so does the
+    exact residual.  The rule's residual there is Psi itself (round-off, ~1e-15) and
+    Psi (1 - sqrt(I)/|Psi|) inside; the literal '== 0' test applied to round-off values gives
+    residuals of size sqrt(I) outside, with phases set by round-off."""
+    cfg = synth.C1
+    gd = synth.geometry(cfg, n_pos=1)
+    p = synth.probe(cfg)
+    X = np.ones((cfg.n_slices, cfg.obj, cfg.obj), dtype=complex)
+    h = O.fresnel_propagator(cfg.win, gd["pixel_A"], gd["wavelength_A"], gd["dz_A"])
+    _, _, far = O.position_forward(p, X, 10, 12, h)
+    q = np.fft.fftfreq(cfg.win, d=cfg.pixel_A)
+    inside = (q[:, None] ** 2 + q[None, :] ** 2) <= (cfg.aperture_mrad * 1e-3 / gd["wavelength_A"]) ** 2
+    I = np.abs(far) ** 2 * 1.1 + 0.5          # dark-field counts everywhere
+    _, r = O.far_field_residual(far, I, O.zero_threshold(p))
+    assert np.abs(r[~inside]).max() <= 1e-12
+    np.testing.assert_allclose(r[inside], far[inside] * (1 - np.sqrt(I[inside]) / np.abs(far[inside])), rtol=1e-12)
+    _, r_literal = O.far_field_residual(far, I, 0.0)
+    assert np.abs(r_literal[~inside]).max() > 0.5
+    # the threshold sits far below every in-aperture amplitude
+    assert O.zero_threshold(p) < 1e-3 * np.abs(far[inside]).min()
+
+
+def test_residual_conditioning_closed_forms():
+    """With I = 0 the residual is Psi itself and every m_k = 1, so kappa = ||p|| sqrt(S W^2) / ||Psi||
+    = 1 for pure-phase slices (Parseval); scaling all intensities does not change the
+    cancellation of a single position (1 exactly)."""
+    g, probe, pos, I, V = make_problem(7)
+    kappa, canc, flip = O.residual_conditioning(g, probe, pos, np.zeros_like(I), V=V)
+    assert kappa == pytest.approx(1.0, rel=1e-12)
+    assert flip == 0.0
+    _, canc1, _ = O.residual_conditioning(g, probe, pos[:1], I[:1], V=V)
+    assert canc1 == pytest.approx(1.0, rel=1e-12)
