@@ -130,6 +130,27 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V,
                           int32_t normalize, double* loss_before, double* mu_out,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* msp_forward for callers that cannot allocate device memory.  The paper has no
+ * counterpart; it exists because some callers cannot call cudaMalloc (a host
+ * application that owns all device memory through its own pool, or a loop that
+ * must not allocate once running, since an allocation can synchronise the device)
+ * and so cannot provide the workspace msp_forward takes.  Same arguments and
+ * results as msp_forward except:
+ *   - no workspace: the scratch (slice transmissions, propagator factor, an error
+ *     word) is one 16 MiB file-scope device array that every GPU loading the library
+ *     holds until the process exits; L * Ny * Nx may not exceed 2,096,640 (returns
+ *     MSP_EUNSUPPORTED, with the reason in msp_last_error_message(), otherwise);
+ *   - window_error (device int32, may be NULL) is set to 0, or to 1 if a window lay
+ *     outside the object (that position's pattern is then zero);
+ *   - the first call on a device looks up the array's device address (with that
+ *     device current) and caches it; make that first call before any stream capture;
+ *   - every call uses the same array: calls that may overlap on the GPU (other
+ *     streams, other host threads) race and must be serialised by the caller.
+ * Nothing is allocated or freed, by this library or on its behalf. */
+msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const float* V,
+                               const int32_t* pos, float* I_out, int32_t* window_error,
+                               void* stream);
+
 /* Synchronises `stream`, then reports (and clears) the workspace flag raised when
  * a scan window of the most recent compute call on `ws` lay outside the object
  * (every compute call clears the flag when it starts): MSP_OK or MSP_EINVAL. */

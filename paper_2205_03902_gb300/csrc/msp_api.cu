@@ -287,6 +287,9 @@ static msp_status fail(msp_status s, const std::string& m) {
   return s;
 }
 
+// For entry points defined in other translation units.
+msp_status set_last_error(msp_status s, const std::string& m) { return fail(s, m); }
+
 #define MSP_CK(call)                                                                      \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \

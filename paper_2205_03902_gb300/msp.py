@@ -65,6 +65,7 @@ _SIGS = {
     "msp_probe_step": ([_G, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P],
                        ctypes.c_int),
     "msp_check_workspace": ([_P, _P], ctypes.c_int),
+    "msp_forward_noalloc": ([_G, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "msp_profile_enable": ([ctypes.c_int32], ctypes.c_int),
     "msp_profile_read": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int32], ctypes.c_int),
@@ -175,6 +176,16 @@ def forward(g: Geometry, probe, V, pos, out=None, ws=None, stream=None):
     ws = _ws(g, ws, device)
     _check(lib().msp_forward(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(pos), _ptr(out), ws.ptr(), ws.nbytes,
                              _stream(stream)), "msp_forward")
+    return out
+
+
+def forward_noalloc(g: Geometry, probe, V, pos, out, window_error=None, stream=None):
+    """msp_forward without a workspace: for callers that cannot allocate device memory.
+    `out` (and the optional int32 `window_error`) must be supplied by the caller."""
+    _arrays(g, probe, V, pos)
+    _arrays(g, probe, V, pos, out, "out")
+    _check(lib().msp_forward_noalloc(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(pos), _ptr(out),
+                                     _ptr(window_error), _stream(stream)), "msp_forward_noalloc")
     return out
 
 
