@@ -45,6 +45,24 @@ def fft_flops(S, L, W):
     return S * (4 * L - 2) * 5.0 * n * math.log2(n)
 
 
+KERNEL_SOURCES = ["paper_2205_03902_gb300/csrc/msp_position.cu", "paper_2205_03902_gb300/csrc/msp_fft.cuh",
+                  "paper_2205_03902_gb300/csrc/msp_kernels.cuh"]
+
+
+def measured_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu capture, or None if
+    the kernel's sources changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        h = hashlib.sha1()
+        for f in KERNEL_SOURCES:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        return rec["dram_bytes_per_launch"] if rec.get("source_sha1") == h.hexdigest() else None
+    except Exception:
+        return None
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -68,7 +86,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -266,13 +284,7 @@ def run_msp(args, rank, world, local_rank):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x clock
     fused_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
     achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("position_kernel_layer_c2_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = measured_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -301,7 +313,7 @@ def run_msp(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -56,17 +56,23 @@ __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, 
 }
 
 // Overlap-add of per-position window arrays into object-frame maps.  One CTA owns a
-// 32 x 32 object tile of one slice; positions are visited in ascending order, so the
-// sum at every pixel has a fixed order (bit-reproducible, no atomics).
+// 32 x 32 object tile of one slice.  Positions are taken in chunks of 256: the chunk's
+// positions whose window overlaps the tile are compacted (ballot, order kept) into a
+// shared list, and the CTA adds their window values in ascending scan order.  Every
+// pixel therefore sums its covering positions in a fixed order (bit-reproducible, no
+// atomics), and no thread spends time on positions that miss its tile.
 template <int NCH>
 __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ src0, const float* __restrict__ src1,
                                                      int nl_src, const int2* __restrict__ pos, int S, int W,
                                                      int Ny, int Nx, float* __restrict__ out0,
                                                      float* __restrict__ out1, double* __restrict__ blockmax) {
   __shared__ int2 spos[256];
+  __shared__ int sidx[256];
+  __shared__ int wcount[8];
   __shared__ float wmax[8];
   const int tid = threadIdx.x;
-  const int tx = tid & 31, ty = tid >> 5;
+  const int lane = tid & 31, w = tid >> 5;
+  const int tx = lane, ty = w;
   const int l = blockIdx.z;
   const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * 32;
   const int px = tx0 + tx;
@@ -75,29 +81,50 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   float acc1[4] = {0.f, 0.f, 0.f, 0.f};
   for (int base = 0; base < S; base += 256) {
     const int n = min(256, S - base);
+    int2 ps = make_int2(0, 0);
+    bool ov = false;
+    if (tid < n) {
+      ps = pos[base + tid];
+      ov = ps.x < ty0 + 32 && ps.x + W > ty0 && ps.y < tx0 + 32 && ps.y + W > tx0;
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, ov);
+    __syncthreads();                      // the previous chunk's list is no longer read
+    if (lane == 0) wcount[w] = __popc(mask);
     __syncthreads();
-    if (tid < n) spos[tid] = pos[base + tid];
-    __syncthreads();
-    for (int k0 = 0; k0 < n; k0 += 8) {
-      float v0[8][4], v1[8][4];
+    int off = 0, total = 0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int k = k0 + u;
-        const int2 ps = (k < n) ? spos[k] : make_int2(-(1 << 29), -(1 << 29));
-        const int dx = px - ps.y;
+    for (int i = 0; i < 8; ++i) {
+      off += (i < w) ? wcount[i] : 0;
+      total += wcount[i];
+    }
+    if (ov) {
+      const int q = off + __popc(mask & ((1u << lane) - 1u));
+      spos[q] = ps;
+      sidx[q] = base + tid;
+    }
+    __syncthreads();
+    for (int q0 = 0; q0 < total; q0 += 4) {
+      float v0[4][4], v1[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u;
+        const bool live = q < total;
+        const int2 pq = live ? spos[q] : make_int2(-(1 << 29), -(1 << 29));
+        const int sq = live ? sidx[q] : 0;
+        const int dx = px - pq.y;
         const bool inx = (unsigned)dx < (unsigned)W;
-        const float* s0 = src0 + ((size_t)(base + k) * nl_src + l) * WW;
-        const float* s1 = (NCH == 2) ? src1 + (size_t)(base + k) * WW : nullptr;
+        const float* s0 = src0 + ((size_t)sq * nl_src + l) * WW;
+        const float* s1 = (NCH == 2) ? src1 + (size_t)sq * WW : nullptr;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int dy = ty0 + ty + 8 * i - ps.x;
+          const int dy = ty0 + ty + 8 * i - pq.x;
           const bool in = inx && ((unsigned)dy < (unsigned)W);
           v0[u][i] = in ? s0[(size_t)dy * W + dx] : 0.f;
           if (NCH == 2) v1[u][i] = in ? s1[(size_t)dy * W + dx] : 0.f;
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 4; ++u) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           acc0[i] += v0[u][i];
@@ -121,33 +148,36 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   if (NCH == 2) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((tid & 31) == 0) wmax[tid >> 5] = m;
+    if (lane == 0) wmax[w] = m;
     __syncthreads();
     if (tid == 0) {
       float b = 0.f;
-      for (int w = 0; w < 8; ++w) b = fmaxf(b, wmax[w]);
+      for (int i = 0; i < 8; ++i) b = fmaxf(b, wmax[i]);
       blockmax[blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
     }
   }
 }
 
-// out = tau^2 * sum |p|^2 (FP64, fixed order): the squared zero-rule threshold.
+// out = tau^2 * sum |p|^2, the squared zero-rule threshold (a threshold needs no more
+// than single-precision partial sums; the total is formed in double, in a fixed order).
 __global__ void __launch_bounds__(1024) zero_threshold_kernel(const float2* __restrict__ probe, int WW, double tau2,
                                                               double* __restrict__ out) {
-  __shared__ double sh[1024];
+  __shared__ float wsum[32];
   const int tid = threadIdx.x;
-  double a = 0.0;
+  float a = 0.f;
   for (int i = tid; i < WW; i += 1024) {
     const float2 v = probe[i];
-    a += (double)v.x * v.x + (double)v.y * v.y;
+    a = fmaf(v.x, v.x, fmaf(v.y, v.y, a));
   }
-  sh[tid] = a;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((tid & 31) == 0) wsum[tid >> 5] = a;
   __syncthreads();
-  for (int s = 512; s > 0; s >>= 1) {
-    if (tid < s) sh[tid] += sh[tid + s];
-    __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 32; ++i) t += (double)wsum[i];
+    out[0] = tau2 * t;
   }
-  if (tid == 0) out[0] = tau2 * sh[0];
 }
 
 // Single-block FP64 reduction in a fixed order.  op 0: sum, 1: max.

@@ -6,7 +6,7 @@
 // holds the line elements j, j+8, j+16, ...  (N1 complex values in registers),
 //   step A: an N1-point DFT in registers over those elements,
 //   step B: twiddle by w_W^(j k1),
-//   exchange through the line's own shared-memory storage (warp-synchronous),
+//   exchange through a small shared buffer private to the group (warp-synchronous),
 //   step C: N1/8 eight-point DFTs in registers.
 // The output indices k1 + N1 k2 held by thread j are again exactly the set
 // {j + 8m}, so every line transform starts and ends with the same thread/index
@@ -18,8 +18,8 @@
 //
 // Shared-memory layout of the wave: element (r, c) lives at r*W + (c ^ swz(r)),
 // swz(r) = ((r & 1) << 3) | (r & 6).  With eight threads per line and four lines
-// per warp this makes every access of the row and column passes, including the
-// exchange pattern below, free of bank conflicts for 8-byte elements.
+// per warp this makes every row and column access of the wave free of bank
+// conflicts for 8-byte elements.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -93,15 +93,19 @@ __device__ __forceinline__ int swz(int r) { return ((r & 1) << 3) | (r & 6); }
 
 // Line transform of a W-point line held by 8 threads (lane group), in place in `v`:
 // on entry v[m] is line element j + 8m, on exit v[m] is spectrum element j + 8m.
-// `addr(i)` maps a line index to the float2 offset in shared memory.
+// `xb` is the group's private exchange buffer of 8 * (N1 + 1) float2: thread j writes
+// its step-A results Y[j][k1] at xb[j (N1 + 1) + k1] and reads Y[n2][k1] at
+// xb[n2 (N1 + 1) + k1]; the odd stride N1 + 1 spreads both patterns over distinct banks
+// (and consecutive groups' buffers start half a bank row apart), so the exchange is
+// conflict-free and its addresses are a per-thread base plus immediate offsets.
 // `tws[k1 * 8 + j]` = w_W^(j k1) (forward sign), a shared table read without bank
 // conflicts (eight distinct words per instruction, broadcast across the warp's lines).
 // INV selects the unnormalised inverse.
-template <int W, bool INV, typename Addr>
-__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2* __restrict__ tws, float2* sm,
-                                         int j, Addr addr) {
+template <int W, bool INV>
+__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2* __restrict__ tws, float2* xb, int j) {
   constexpr int N1 = W / 8;
   constexpr int NC = N1 / 8;
+  constexpr int XS = N1 + 1;
   float2 y[N1];
   if constexpr (INV) {
 #pragma unroll
@@ -109,23 +113,19 @@ __device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2* __res
   }
   // step A: DFT over n1 of x[8 n1 + j]
   dft<N1, 1>(v, y);
-  // step B: twiddles, then exchange: Y[n2 = j][k1] -> line position 8 k1 + (j ^ (k1 & 7)).
-  // The line storage may still hold this group's inputs: wait for every lane's loads.
-  __syncwarp();
+  // step B: twiddles, then exchange Y[n2 = j][k1]
+  float2* xw = xb + j * XS;
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) {
-    const float2 t = (k1 == 0) ? y[k1] : cmul(y[k1], tws[k1 * 8 + j]);
-    sm[addr(8 * k1 + (j ^ (k1 & 7)))] = t;
-  }
+  for (int k1 = 0; k1 < N1; ++k1) xw[k1] = (k1 == 0) ? y[k1] : cmul(y[k1], tws[k1 * 8 + j]);
   __syncwarp();
   float2 b[NC][8];
+  const float2* xr = xb + j;
 #pragma unroll
   for (int mc = 0; mc < NC; ++mc) {
-    const int k1 = j + 8 * mc;
 #pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) b[mc][n2] = sm[addr(8 * k1 + (n2 ^ j))];
+    for (int n2 = 0; n2 < 8; ++n2) b[mc][n2] = xr[n2 * XS + 8 * mc];
   }
-  __syncwarp();
+  __syncwarp();   // the buffer is reused by this group's next transform
   // step C: eight-point DFTs over n2; X[k1 + N1 k2] with k1 = j + 8 mc is v[mc + NC k2]
 #pragma unroll
   for (int mc = 0; mc < NC; ++mc) {

@@ -8,6 +8,9 @@
 // (Sec. 3.2) and the adjoint recursion chi_{m-1} = G^H (conj(X_m) o chi_m)
 // (Sec. 3.3, the prefix / suffix products R_l and S_l applied matrix-free).
 //
+// Each eight-thread line group owns a small padded exchange buffer next to the
+// wave, so the in-line exchange never touches the wave itself.
+//
 // A propagation is  rows F -> [columns F, x H, columns F^-1] -> rows F^-1: the
 // column transforms and the propagator run back to back in registers, and the
 // inverse row transform of one slice, the transmit of the next slice and its
@@ -37,16 +40,32 @@ struct Geo {
   static constexpr int LPG = W / GROUPS;  // lines per group per pass
 };
 
+// Shared-memory offset of element j + 8m of wave row r: (j + 8m) ^ swz(r) flips bits 0-2
+// by swz(r) & 7 and bit 3 by swz(r) & 8, i.e. adds +-8 for even / odd m.
 template <int W>
-struct RowAddr {
-  int r;
-  __device__ __forceinline__ int operator()(int i) const { return r * W + (i ^ swz(r)); }
+struct RowIdx {
+  int be, bo;
+  __device__ __forceinline__ RowIdx(int r, int j) {
+    const int sw = swz(r);
+    const int base = r * W + (j ^ (sw & 7));
+    be = base + (sw & 8);
+    bo = base - (sw & 8);
+  }
+  __device__ __forceinline__ int operator()(int m) const { return ((m & 1) ? bo : be) + 8 * m; }
 };
+// Element j + 8m of wave column c: swz depends on the row's low three bits only (= j).
 template <int W>
-struct ColAddr {
-  int c;
-  __device__ __forceinline__ int operator()(int i) const { return i * W + (c ^ swz(i)); }
+struct ColIdx {
+  int b;
+  __device__ __forceinline__ ColIdx(int c, int j) : b(j * W + (c ^ swz(j))) {}
+  __device__ __forceinline__ int operator()(int m) const { return b + 8 * m * W; }
 };
+
+// Dynamic shared memory: the wave, then one exchange buffer per eight-thread line group.
+template <int W>
+constexpr size_t position_smem_bytes() {
+  return ((size_t)W * W + (size_t)(W / 2) * 8 * (W / 8 + 1)) * sizeof(float2);
+}
 
 template <int W, int MODE>
 __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
@@ -62,6 +81,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   const int grp = tid >> 3;
   const size_t WW = (size_t)W * W;
   const size_t plane = (size_t)p.Ny * p.Nx;
+  float2* xb = sm + W * W + grp * 8 * (N1 + 1);   // this group's exchange buffer
 
   if (tid < N1 * 8) {   // evaluated in double, rounded once
     const int k1 = tid >> 3, jj = tid & 7;
@@ -111,9 +131,9 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];
       }
-      line_fft<W, false>(v, s_tw, sm, j, RowAddr<W>{r});
+      line_fft<W, false>(v, s_tw, xb, j);
 #pragma unroll
-      for (int m = 0; m < N1; ++m) sm[RowAddr<W>{r}(j + 8 * m)] = v[m];
+      for (int m = 0; m < N1; ++m) sm[RowIdx<W>(r, j)(m)] = v[m];
     }
     __syncthreads();
 
@@ -125,17 +145,17 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
         for (int it = 0; it < G::LPG; ++it) {
           const int c = grp + G::GROUPS * it;
-          const ColAddr<W> ca{c};
+          const ColIdx<W> ca(c, j);
           float2 v[N1];
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = sm[ca(j + 8 * m)];
-          line_fft<W, false>(v, s_tw, sm, j, ca);
+          for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
+          line_fft<W, false>(v, s_tw, xb, j);
           const float2 hx = s_h1[c];
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], cmul(s_h1[j + 8 * m], hx));
-          line_fft<W, true>(v, s_tw, sm, j, ca);
+          line_fft<W, true>(v, s_tw, xb, j);
 #pragma unroll
-          for (int m = 0; m < N1; ++m) sm[ca(j + 8 * m)] = v[m];
+          for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
         }
         __syncthreads();
         // rows: F^-1, transmit slice l+1, keep the exit wave, F
@@ -145,23 +165,23 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
         for (int it = 0; it < G::LPG; ++it) {
           const int r = grp + G::GROUPS * it;
-          const RowAddr<W> ra{r};
+          const RowIdx<W> ra(r, j);
           float2 t[N1], v[N1];
           const float2* Tr = Tl + (size_t)r * p.Nx;
 #pragma unroll
           for (int m = 0; m < N1; ++m) t[m] = Tr[j + 8 * m];     // in flight during the transform
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = sm[ra(j + 8 * m)];
-          line_fft<W, true>(v, s_tw, sm, j, ra);
+          for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
+          line_fft<W, true>(v, s_tw, xb, j);
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], t[m]);
           if (keep) {
 #pragma unroll
             for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];
           }
-          line_fft<W, false>(v, s_tw, sm, j, ra);
+          line_fft<W, false>(v, s_tw, xb, j);
 #pragma unroll
-          for (int m = 0; m < N1; ++m) sm[ra(j + 8 * m)] = v[m];
+          for (int m = 0; m < N1; ++m) sm[ra(m)] = v[m];
         }
         __syncthreads();
       } else {
@@ -169,7 +189,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
         for (int it = 0; it < G::LPG; ++it) {
           const int c = grp + G::GROUPS * it;
-          const ColAddr<W> ca{c};
+          const ColIdx<W> ca(c, j);
           float2 v[N1];
           float im[N1];
           if (MODE != MODE_FORWARD) {
@@ -178,8 +198,8 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
             for (int m = 0; m < N1; ++m) im[m] = ip[(j + 8 * m) * W];   // in flight during the transform
           }
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = sm[ca(j + 8 * m)];
-          line_fft<W, false>(v, s_tw, sm, j, ca);
+          for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
+          line_fft<W, false>(v, s_tw, xb, j);
           if (MODE == MODE_FORWARD) {
             float* out = p.I_out + s * WW + c;
 #pragma unroll
@@ -198,9 +218,9 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               v[m] = make_float2(v[m].x * f, v[m].y * f);
             }
             // chi = F^H R: inverse column transforms now, rows below
-            line_fft<W, true>(v, s_tw, sm, j, ca);
+            line_fft<W, true>(v, s_tw, xb, j);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) sm[ca(j + 8 * m)] = v[m];
+            for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
           }
         }
         if (MODE != MODE_FORWARD) {
@@ -233,15 +253,15 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
       for (int it = 0; it < G::LPG; ++it) {
         const int r = grp + G::GROUPS * it;
-        const RowAddr<W> ra{r};
+        const RowIdx<W> ra(r, j);
         float2 e[N1], v[N1];
         if (grad_here) {
 #pragma unroll
           for (int m = 0; m < N1; ++m) e[m] = st[r * W + j + 8 * m];   // in flight during the transform
         }
 #pragma unroll
-        for (int m = 0; m < N1; ++m) v[m] = sm[ra(j + 8 * m)];
-        line_fft<W, true>(v, s_tw, sm, j, ra);   // v = chi_l (row r)
+        for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
+        line_fft<W, true>(v, s_tw, xb, j);   // v = chi_l (row r)
         if (grad_here) {
           // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
 #pragma unroll
@@ -264,9 +284,9 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               for (int m = 0; m < N1; ++m) dp[j + 8 * m] = cadd(dp[j + 8 * m], v[m]);
             }
           } else {
-            line_fft<W, false>(v, s_tw, sm, j, ra);
+            line_fft<W, false>(v, s_tw, xb, j);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) sm[ra(j + 8 * m)] = v[m];
+            for (int m = 0; m < N1; ++m) sm[ra(m)] = v[m];
           }
         }
       }
@@ -277,17 +297,17 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll 1
       for (int it = 0; it < G::LPG; ++it) {
         const int c = grp + G::GROUPS * it;
-        const ColAddr<W> ca{c};
+        const ColIdx<W> ca(c, j);
         float2 v[N1];
 #pragma unroll
-        for (int m = 0; m < N1; ++m) v[m] = sm[ca(j + 8 * m)];
-        line_fft<W, false>(v, s_tw, sm, j, ca);
+        for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
+        line_fft<W, false>(v, s_tw, xb, j);
         const float2 hx = s_h1[c];
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], cmul(s_h1[j + 8 * m], hx));
-        line_fft<W, true>(v, s_tw, sm, j, ca);
+        line_fft<W, true>(v, s_tw, xb, j);
 #pragma unroll
-        for (int m = 0; m < N1; ++m) sm[ca(j + 8 * m)] = v[m];
+        for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
       }
       __syncthreads();
     }
@@ -307,7 +327,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 
 template <int W, int MODE>
 static cudaError_t launch_one(const PosParams& p, int grid, cudaStream_t st) {
-  const size_t smem = (size_t)W * W * sizeof(float2);
+  const size_t smem = position_smem_bytes<W>();
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -338,7 +358,7 @@ cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int gr
 // CTAs of the fused kernel that fit on one SM (same for every mode of a window size).
 int position_ctas_per_sm(int win) {
   int n = 0;
-  const size_t smem = (size_t)win * win * sizeof(float2);
+  const size_t smem = win == 64 ? position_smem_bytes<64>() : position_smem_bytes<128>();
   if (win == 64) {
     cudaFuncSetAttribute(position_kernel<64, MODE_LOSS_GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, position_kernel<64, MODE_LOSS_GRAD>, 4 * 64, smem);
