@@ -55,37 +55,40 @@ __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, 
   h1[k] = make_float2((float)(cs / W), (float)(-sn / W));
 }
 
-// Overlap-add of per-position window arrays into object-frame maps.  One CTA owns a
-// 32 x 32 object tile of one slice.  Positions are taken in chunks of 256: the chunk's
-// positions whose window overlaps the tile are compacted (ballot, order kept) into a
-// shared list, and the CTA adds their window values in ascending scan order.  Every
-// pixel therefore sums its covering positions in a fixed order (bit-reproducible, no
-// atomics), and no thread spends time on positions that miss its tile.
+// Overlap-add of per-position window arrays into object-frame maps.  One CTA of 256
+// threads owns a 16 x 16 object tile of one slice (one pixel per thread).  Positions
+// are taken in chunks of 256: the chunk's positions whose window overlaps the tile are
+// compacted (ballot, order kept) into a shared list, and the CTA adds their window
+// values in ascending scan order, eight positions in flight per thread.  Every pixel
+// therefore sums its covering positions in a fixed order (bit-reproducible, no atomics)
+// and no thread spends time on positions that miss its tile.
+constexpr int kGatherTile = 16;
+
 template <int NCH>
 __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ src0, const float* __restrict__ src1,
                                                      int nl_src, const int2* __restrict__ pos, int S, int W,
                                                      int Ny, int Nx, float* __restrict__ out0,
                                                      float* __restrict__ out1, double* __restrict__ blockmax) {
+  constexpr int T = kGatherTile;
+  constexpr int U = 8;
   __shared__ int2 spos[256];
   __shared__ int sidx[256];
   __shared__ int wcount[8];
   __shared__ float wmax[8];
   const int tid = threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
-  const int tx = lane, ty = w;
   const int l = blockIdx.z;
-  const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * 32;
-  const int px = tx0 + tx;
+  const int tx0 = blockIdx.x * T, ty0 = blockIdx.y * T;
+  const int px = tx0 + (tid % T), py = ty0 + (tid / T);
   const size_t WW = (size_t)W * W;
-  float acc0[4] = {0.f, 0.f, 0.f, 0.f};
-  float acc1[4] = {0.f, 0.f, 0.f, 0.f};
+  float acc0 = 0.f, acc1 = 0.f;
   for (int base = 0; base < S; base += 256) {
     const int n = min(256, S - base);
     int2 ps = make_int2(0, 0);
     bool ov = false;
     if (tid < n) {
       ps = pos[base + tid];
-      ov = ps.x < ty0 + 32 && ps.x + W > ty0 && ps.y < tx0 + 32 && ps.y + W > tx0;
+      ov = ps.x < ty0 + T && ps.x + W > ty0 && ps.y < tx0 + T && ps.y + W > tx0;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, ov);
     __syncthreads();                      // the previous chunk's list is no longer read
@@ -103,46 +106,33 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
       sidx[q] = base + tid;
     }
     __syncthreads();
-    for (int q0 = 0; q0 < total; q0 += 4) {
-      float v0[4][4], v1[4][4];
+    for (int q0 = 0; q0 < total; q0 += U) {
+      float v0[U], v1[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int q = q0 + u;
         const bool live = q < total;
         const int2 pq = live ? spos[q] : make_int2(-(1 << 29), -(1 << 29));
         const int sq = live ? sidx[q] : 0;
-        const int dx = px - pq.y;
-        const bool inx = (unsigned)dx < (unsigned)W;
-        const float* s0 = src0 + ((size_t)sq * nl_src + l) * WW;
-        const float* s1 = (NCH == 2) ? src1 + (size_t)sq * WW : nullptr;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int dy = ty0 + ty + 8 * i - pq.x;
-          const bool in = inx && ((unsigned)dy < (unsigned)W);
-          v0[u][i] = in ? s0[(size_t)dy * W + dx] : 0.f;
-          if (NCH == 2) v1[u][i] = in ? s1[(size_t)dy * W + dx] : 0.f;
-        }
+        const int dx = px - pq.y, dy = py - pq.x;
+        const bool in = ((unsigned)dx < (unsigned)W) && ((unsigned)dy < (unsigned)W);
+        const size_t o = (size_t)dy * W + dx;
+        v0[u] = in ? src0[((size_t)sq * nl_src + l) * WW + o] : 0.f;
+        if (NCH == 2) v1[u] = in ? src1[(size_t)sq * WW + o] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          acc0[i] += v0[u][i];
-          if (NCH == 2) acc1[i] += v1[u][i];
-        }
+      for (int u = 0; u < U; ++u) {
+        acc0 += v0[u];
+        if (NCH == 2) acc1 += v1[u];
       }
     }
   }
   float m = 0.f;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int py = ty0 + ty + 8 * i;
-    if (py < Ny && px < Nx) {
-      out0[((size_t)l * Ny + py) * Nx + px] = acc0[i];
-      if (NCH == 2) {
-        out1[(size_t)py * Nx + px] = acc1[i];
-        m = fmaxf(m, acc1[i]);
-      }
+  if (py < Ny && px < Nx) {
+    out0[((size_t)l * Ny + py) * Nx + px] = acc0;
+    if (NCH == 2) {
+      out1[(size_t)py * Nx + px] = acc1;
+      m = acc1;
     }
   }
   if (NCH == 2) {
@@ -364,7 +354,7 @@ static msp_status check_geometry(const msp_geometry* g) {
   if (!std::isfinite(g->sigma)) return fail(MSP_EINVAL, "sigma must be finite");
   const double cells = (double)g->n_slices * g->obj_ny * g->obj_nx;
   if (cells > 4.0e9) return fail(MSP_EUNSUPPORTED, "object too large");
-  if ((size_t)((g->obj_nx + 31) / 32) * ((g->obj_ny + 31) / 32) > (size_t)kRedSlots)
+  if ((size_t)((g->obj_nx + 15) / 16) * ((g->obj_ny + 15) / 16) > (size_t)kRedSlots)
     return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
   return MSP_OK;
 }
@@ -580,7 +570,7 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   }
   MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
   if (dV) {
-    dim3 grid((g->obj_nx + 31) / 32, (g->obj_ny + 31) / 32, g->n_slices);
+    dim3 grid((g->obj_nx + kGatherTile - 1) / kGatherTile, (g->obj_ny + kGatherTile - 1) / kGatherTile, g->n_slices);
     gather_kernel<1><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos, W,
                                              g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
     MSP_CK(cudaGetLastError());
@@ -625,7 +615,7 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   p.I_meas = I_meas;
   p.layer = layer;
   MSP_TRY(run_position(g, MODE_LAYER, p, c));
-  dim3 grid((g->obj_nx + 31) / 32, (g->obj_ny + 31) / 32, 1);
+  dim3 grid((g->obj_nx + kGatherTile - 1) / kGatherTile, (g->obj_ny + kGatherTile - 1) / kGatherTile, 1);
   const int nblk = (int)(grid.x * grid.y);
   if (nblk > kRedSlots) return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
   gather_kernel<2><<<grid, 256, 0, c.st>>>(c.ws.wgrad, c.ws.willum, 1, (const int2*)pos, g->n_pos, W, g->obj_ny,

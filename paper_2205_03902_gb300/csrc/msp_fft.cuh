@@ -98,11 +98,46 @@ __device__ __forceinline__ int swz(int r) { return ((r & 1) << 3) | (r & 6); }
 // xb[n2 (N1 + 1) + k1]; the odd stride N1 + 1 spreads both patterns over distinct banks
 // (and consecutive groups' buffers start half a bank row apart), so the exchange is
 // conflict-free and its addresses are a per-thread base plus immediate offsets.
-// `tws[k1 * 8 + j]` = w_W^(j k1) (forward sign), a shared table read without bank
-// conflicts (eight distinct words per instruction, broadcast across the warp's lines).
-// INV selects the unnormalised inverse.
-template <int W, bool INV>
-__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2* __restrict__ tws, float2* xb, int j) {
+// `tw.get<k1>()` = w_W^(j k1) (forward sign), from the shared table (read without bank
+// conflicts: eight distinct words per instruction, broadcast across the warp's lines) or
+// from registers.  INV selects the unnormalised inverse.
+// Twiddles w_W^(j k1) of thread j, read from the shared table [k1 * 8 + j].
+struct SharedTwiddles {
+  const float2* __restrict__ t;
+  int j;
+  template <int K1>
+  __device__ __forceinline__ float2 get() const { return t[K1 * 8 + j]; }
+};
+
+// Twiddles of thread j held in registers: w^(j k) for k < 8, and w^(j k) = w^(8j) w^(j (k - 8))
+// for k >= 8 (one extra rounded product).
+template <int W>
+struct RegisterTwiddles {
+  float2 r[8];   // r[0] unused (k1 = 0 is never multiplied); r[k] = w^(j k), k = 1..7
+  float2 w8;     // w^(8 j)
+  __device__ __forceinline__ RegisterTwiddles(const float2* __restrict__ t, int j) {
+#pragma unroll
+    for (int k = 1; k < 8; ++k) r[k] = t[k * 8 + j];
+    w8 = (W / 8 > 8) ? t[8 * 8 + j] : make_float2(1.f, 0.f);
+  }
+  template <int K1>
+  __device__ __forceinline__ float2 get() const {
+    if constexpr (K1 < 8) return r[K1];
+    else if constexpr (K1 == 8) return w8;
+    else return cmul(w8, r[K1 - 8]);
+  }
+};
+
+template <int K1, int N1, typename Tw>
+__device__ __forceinline__ void twiddle_store(const float2* y, float2* xw, const Tw& tw) {
+  if constexpr (K1 < N1) {
+    xw[K1] = (K1 == 0) ? y[K1] : cmul(y[K1], tw.template get<K1>());
+    twiddle_store<K1 + 1, N1>(y, xw, tw);
+  }
+}
+
+template <int W, bool INV, typename Tw>
+__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const Tw& tw, float2* xb, int j) {
   constexpr int N1 = W / 8;
   constexpr int NC = N1 / 8;
   constexpr int XS = N1 + 1;
@@ -115,8 +150,7 @@ __device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const float2* __res
   dft<N1, 1>(v, y);
   // step B: twiddles, then exchange Y[n2 = j][k1]
   float2* xw = xb + j * XS;
-#pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) xw[k1] = (k1 == 0) ? y[k1] : cmul(y[k1], tws[k1 * 8 + j]);
+  twiddle_store<0, N1>(y, xw, tw);
   __syncwarp();
   float2 b[NC][8];
   const float2* xr = xb + j;

@@ -30,6 +30,11 @@
 #include "msp_fft.cuh"
 #include "msp_kernels.cuh"
 
+// Twiddles of the line transforms from shared memory (0) or registers (1).
+#ifndef MSP_TWIDDLE_REGISTERS
+#define MSP_TWIDDLE_REGISTERS 1
+#endif
+
 namespace msp {
 
 template <int W>
@@ -91,6 +96,11 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   }
   if (tid < W) s_h1[tid] = p.h1[tid];
   __syncthreads();
+#if MSP_TWIDDLE_REGISTERS
+  const RegisterTwiddles<W> tw(s_tw, j);
+#else
+  const SharedTwiddles tw{s_tw, j};
+#endif
 
   const int L = p.L;
   const float zthr2 = (MODE == MODE_FORWARD) ? 0.f : (float)p.zthr2[0];
@@ -131,7 +141,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];
       }
-      line_fft<W, false>(v, s_tw, xb, j);
+      line_fft<W, false>(v, tw, xb, j);
 #pragma unroll
       for (int m = 0; m < N1; ++m) sm[RowIdx<W>(r, j)(m)] = v[m];
     }
@@ -149,11 +159,11 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           float2 v[N1];
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
-          line_fft<W, false>(v, s_tw, xb, j);
+          line_fft<W, false>(v, tw, xb, j);
           const float2 hx = s_h1[c];
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], cmul(s_h1[j + 8 * m], hx));
-          line_fft<W, true>(v, s_tw, xb, j);
+          line_fft<W, true>(v, tw, xb, j);
 #pragma unroll
           for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
         }
@@ -172,14 +182,14 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           for (int m = 0; m < N1; ++m) t[m] = Tr[j + 8 * m];     // in flight during the transform
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
-          line_fft<W, true>(v, s_tw, xb, j);
+          line_fft<W, true>(v, tw, xb, j);
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], t[m]);
           if (keep) {
 #pragma unroll
             for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];
           }
-          line_fft<W, false>(v, s_tw, xb, j);
+          line_fft<W, false>(v, tw, xb, j);
 #pragma unroll
           for (int m = 0; m < N1; ++m) sm[ra(m)] = v[m];
         }
@@ -199,7 +209,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
-          line_fft<W, false>(v, s_tw, xb, j);
+          line_fft<W, false>(v, tw, xb, j);
           if (MODE == MODE_FORWARD) {
             float* out = p.I_out + s * WW + c;
 #pragma unroll
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               v[m] = make_float2(v[m].x * f, v[m].y * f);
             }
             // chi = F^H R: inverse column transforms now, rows below
-            line_fft<W, true>(v, s_tw, xb, j);
+            line_fft<W, true>(v, tw, xb, j);
 #pragma unroll
             for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
           }
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         }
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
-        line_fft<W, true>(v, s_tw, xb, j);   // v = chi_l (row r)
+        line_fft<W, true>(v, tw, xb, j);   // v = chi_l (row r)
         if (grad_here) {
           // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
 #pragma unroll
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               for (int m = 0; m < N1; ++m) dp[j + 8 * m] = cadd(dp[j + 8 * m], v[m]);
             }
           } else {
-            line_fft<W, false>(v, s_tw, xb, j);
+            line_fft<W, false>(v, tw, xb, j);
 #pragma unroll
             for (int m = 0; m < N1; ++m) sm[ra(m)] = v[m];
           }
@@ -301,11 +311,11 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         float2 v[N1];
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
-        line_fft<W, false>(v, s_tw, xb, j);
+        line_fft<W, false>(v, tw, xb, j);
         const float2 hx = s_h1[c];
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], cmul(s_h1[j + 8 * m], hx));
-        line_fft<W, true>(v, s_tw, xb, j);
+        line_fft<W, true>(v, tw, xb, j);
 #pragma unroll
         for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
       }
