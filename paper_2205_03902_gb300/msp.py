@@ -262,3 +262,36 @@ def validate_geometry(g: Geometry) -> int:
 
 def status_string(status: int) -> str:
     return lib().msp_status_string(int(status)).decode()
+
+
+class MultisliceLoss(torch.autograd.Function):
+    """The amplitude-flow loss of the multislice model as a differentiable function of the
+    slice potentials V (real) and the probe (complex), computed by msp_loss_grad in one fused
+    forward + adjoint pass: the gradients are produced together with the loss and returned
+    by `backward` (scaled by the incoming gradient of the loss).
+
+    PyTorch's gradient of a real function of a complex tensor is the conjugate Wirtinger
+    derivative times two; the library returns dL/dconj(P), so the probe gradient is 2 dprobe.
+    """
+
+    @staticmethod
+    def forward(ctx, V, probe, geom, pos, I_meas, ws):
+        loss, dV, dprobe = loss_grad(geom, probe.detach(), V.detach(), pos, I_meas,
+                                     want_dV=V.requires_grad, want_dprobe=probe.requires_grad, ws=ws)
+        ctx.save_for_backward(*(t for t in (dV, dprobe) if t is not None))
+        ctx.has = (dV is not None, dprobe is not None)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        saved = list(ctx.saved_tensors)
+        dV = saved.pop(0) if ctx.has[0] else None
+        dprobe = saved.pop(0) if ctx.has[1] else None
+        gV = None if dV is None else dV * grad_loss.to(dV.dtype)
+        gp = None if dprobe is None else dprobe * (2.0 * grad_loss.to(torch.float32))
+        return gV, gp, None, None, None, None
+
+
+def multislice_loss(geom: Geometry, V, probe, pos, I_meas, ws=None):
+    """Differentiable loss L(V, probe) (float64 scalar tensor); see MultisliceLoss."""
+    return MultisliceLoss.apply(V, probe, geom, pos, I_meas, _ws(geom, ws, V.device))

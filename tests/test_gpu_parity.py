@@ -123,11 +123,22 @@ def c2_strong():
     return strong_case(synth.C2, sub=(13, 13))
 
 
-ALL = ["c1", "c2_ragged", "c1_strong", "c2_strong"]
+@pytest.fixture(scope="module")
+def c3_sub():
+    # the eight-slice workload (rotated lattices, 1e5 e/pattern) on an 8 x 8 sub-scan
+    return Case(synth.C3, sub=(8, 8))
 
 
-def test_strong_states_are_well_conditioned(c1_strong, c2_strong):
-    for c in (c1_strong, c2_strong):
+@pytest.fixture(scope="module")
+def c3_strong():
+    return strong_case(synth.C3, sub=(8, 8))
+
+
+ALL = ["c1", "c2_ragged", "c1_strong", "c2_strong", "c3_sub", "c3_strong"]
+
+
+def test_strong_states_are_well_conditioned(c1_strong, c2_strong, c3_strong):
+    for c in (c1_strong, c2_strong, c3_strong):
         assert derived_tol(c.gd, c.probe, c.pos, c.I, c.V, probe_grad=True) <= TOL
 
 
@@ -184,7 +195,8 @@ def test_optional_outputs(msp, c1):
 # --------------------------------------------------------------------------- steps
 
 @pytest.mark.parametrize("which,layer", [("c1", 0), ("c1", 1), ("c2_ragged", 0), ("c2_ragged", 2),
-                                         ("c1_strong", 1), ("c2_strong", 0), ("c2_strong", 3)])
+                                         ("c1_strong", 1), ("c2_strong", 0), ("c2_strong", 3),
+                                         ("c3_sub", 5), ("c3_strong", 7)])
 def test_layer_step(msp, which, layer, request):
     c = request.getfixturevalue(which)
     g, p, V, pos, I = c.dev(msp)
