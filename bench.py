@@ -312,7 +312,7 @@ def run_msp(args, rank, world, local_rank):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x clock
     fused_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
     achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
-    traffic = measured_traffic()
+    traffic = measured_traffic() if cfg is synth.C2 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -323,7 +323,8 @@ def run_msp(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
-                     "kernel": "position_kernel<128, LAYER> (fused fwd+adjoint)",
+                     "kernel": ("position_cluster_kernel<LAYER> (fused fwd+adjoint, 4-CTA cluster)" if W == 256
+                   else f"position_kernel<{W}, LAYER> (fused fwd+adjoint)"),
                      "kernel_ms": fused_ms,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -345,7 +346,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="c2", choices=sorted(synth.CONFIGS),
+                    help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration)")
     args = ap.parse_args()
+    global CFG
+    CFG = synth.CONFIGS[args.config]
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))

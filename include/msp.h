@@ -66,12 +66,13 @@ typedef enum {
  * implemented on the GPU; MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED. */
 enum { MSP_PARAM_POTENTIAL = 0, MSP_PARAM_TRANSMISSION = 1 };
 
-/* Statement of the problem (Sec. 2.1).  Supported windows: W = 64 or 128. */
+/* Statement of the problem (Sec. 2.1).  Supported windows: W = 64, 128 or 256 (W = 256 runs
+ * each position on a four-CTA thread-block cluster). */
 typedef struct {
   int32_t n_slices;     /* L (the paper's M), >= 1                                 */
   int32_t obj_ny;       /* object rows Ny >= W                                     */
   int32_t obj_nx;       /* object columns Nx >= W                                  */
-  int32_t win;          /* W: probe window side = detector side                   */
+  int32_t win;          /* W: probe window side = detector side (64, 128, 256)    */
   int32_t n_pos;        /* S: scan positions, >= 0                                 */
   int32_t param;        /* MSP_PARAM_POTENTIAL                                     */
   double wavelength_A;  /* electron wavelength lambda in angstrom (Sec. 5.3.2)    */

@@ -25,7 +25,7 @@
 namespace msp {
 
 cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int grid, cudaStream_t st);
-int position_ctas_per_sm(int win);
+int position_slots(int win);
 
 // ---------------------------------------------------------------------------
 // element-wise kernels
@@ -319,7 +319,7 @@ msp_status set_last_error(msp_status s, const std::string& m) { return fail(s, m
 struct DevInfo {
   bool init = false;
   int sms = 0;
-  int cta64 = 1, cta128 = 1;
+  int slots64 = 1, slots128 = 1, slots256 = 1;   // persistent-grid slots per window size
 };
 static DevInfo g_dev[64];
 static std::mutex g_dev_mu;
@@ -331,8 +331,9 @@ static bool device_info(DevInfo* out) {
   DevInfo& d = g_dev[dev];
   if (!d.init) {
     if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
-    d.cta64 = position_ctas_per_sm(64);
-    d.cta128 = position_ctas_per_sm(128);
+    d.slots64 = position_slots(64);
+    d.slots128 = position_slots(128);
+    d.slots256 = position_slots(256);
     d.init = true;
   }
   *out = d;
@@ -341,8 +342,8 @@ static bool device_info(DevInfo* out) {
 
 static msp_status check_geometry(const msp_geometry* g) {
   if (!g) return fail(MSP_EINVAL, "geometry is NULL");
-  if (g->win != 64 && g->win != 128)
-    return fail(MSP_EUNSUPPORTED, "window size " + std::to_string(g->win) + " (supported: 64, 128)");
+  if (g->win != 64 && g->win != 128 && g->win != 256)
+    return fail(MSP_EUNSUPPORTED, "window size " + std::to_string(g->win) + " (supported: 64, 128, 256)");
   if (g->param != MSP_PARAM_POTENTIAL)
     return fail(MSP_EUNSUPPORTED, "only the potential parametrisation exp(i sigma V) is implemented");
   if (g->n_slices < 1) return fail(MSP_EINVAL, "n_slices < 1");
@@ -361,7 +362,12 @@ static msp_status check_geometry(const msp_geometry* g) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static int grid_cap(const DevInfo& d, int win) { return d.sms * (win == 64 ? d.cta64 : d.cta128); }
+static int grid_cap(const DevInfo& d, int win) {
+  return win == 64 ? d.slots64 : (win == 128 ? d.slots128 : d.slots256);
+}
+
+// Loss partials per position: one per CTA that holds part of the wave.
+static int loss_slots(int win) { return win == 256 ? 4 : 1; }
 
 // Carve the workspace; with base == nullptr only the size is computed.
 static Workspace layout(const msp_geometry* g, int gcap, char* base) {
@@ -380,7 +386,7 @@ static Workspace layout(const msp_geometry* g, int gcap, char* base) {
   w.willum = base ? w.wgrad + S * WW : nullptr;
   w.dprobe_part = (float2*)take((size_t)gcap * WW * sizeof(float2));
   w.dprobe_sum = (float2*)take(WW * sizeof(float2));
-  w.loss_part = (double*)take((S > 0 ? S : 1) * sizeof(double));
+  w.loss_part = (double*)take((S > 0 ? S : 1) * loss_slots((int)W) * sizeof(double));
   w.map0 = (float*)take(plane * sizeof(float));
   w.map1 = (float*)take(plane * sizeof(float));
   w.bytes = off;
@@ -500,7 +506,7 @@ static msp_status reduce_loss(const msp_geometry* g, Call& c, double* extra) {
     if (extra) MSP_CK(cudaMemsetAsync(extra, 0, sizeof(double), c.st));
     return MSP_OK;
   }
-  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.loss_part, g->n_pos, 0, c.ws.scal, extra);
+  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.loss_part, g->n_pos * loss_slots(g->win), 0, c.ws.scal, extra);
   MSP_CK(cudaGetLastError());
   counted();
   return MSP_OK;

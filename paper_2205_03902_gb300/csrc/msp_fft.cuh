@@ -8,6 +8,7 @@
 //   step B: twiddle by w_W^(j k1),
 //   exchange through a small shared buffer private to the group (warp-synchronous),
 //   step C: N1/8 eight-point DFTs in registers.
+// (W = 256 uses sixteen threads per line and sixteen-point DFTs in both steps.)
 // The output indices k1 + N1 k2 held by thread j are again exactly the set
 // {j + 8m}, so every line transform starts and ends with the same thread/index
 // ownership and consecutive passes need no re-distribution beyond the row <->
@@ -91,34 +92,25 @@ __device__ __forceinline__ void dft(const float2* x, float2* X) {
 
 __device__ __forceinline__ int swz(int r) { return ((r & 1) << 3) | (r & 6); }
 
-// Line transform of a W-point line held by 8 threads (lane group), in place in `v`:
-// on entry v[m] is line element j + 8m, on exit v[m] is spectrum element j + 8m.
-// `xb` is the group's private exchange buffer of 8 * (N1 + 1) float2: thread j writes
-// its step-A results Y[j][k1] at xb[j (N1 + 1) + k1] and reads Y[n2][k1] at
-// xb[n2 (N1 + 1) + k1]; the odd stride N1 + 1 spreads both patterns over distinct banks
-// (and consecutive groups' buffers start half a bank row apart), so the exchange is
-// conflict-free and its addresses are a per-thread base plus immediate offsets.
-// `tw.get<k1>()` = w_W^(j k1) (forward sign), from the shared table (read without bank
-// conflicts: eight distinct words per instruction, broadcast across the warp's lines) or
-// from registers.  INV selects the unnormalised inverse.
-// Twiddles w_W^(j k1) of thread j, read from the shared table [k1 * 8 + j].
+// Twiddles w_W^(j k1) of thread j (of T per line), read from the shared table [k1 * T + j].
+template <int T = 8>
 struct SharedTwiddles {
   const float2* __restrict__ t;
   int j;
   template <int K1>
-  __device__ __forceinline__ float2 get() const { return t[K1 * 8 + j]; }
+  __device__ __forceinline__ float2 get() const { return t[K1 * T + j]; }
 };
 
 // Twiddles of thread j held in registers: w^(j k) for k < 8, and w^(j k) = w^(8j) w^(j (k - 8))
-// for k >= 8 (one extra rounded product).
-template <int W>
+// for k >= 8 (one extra rounded product).  `t` is the shared table [k1 * T + j].
+template <int W, int T = 8>
 struct RegisterTwiddles {
   float2 r[8];   // r[0] unused (k1 = 0 is never multiplied); r[k] = w^(j k), k = 1..7
   float2 w8;     // w^(8 j)
   __device__ __forceinline__ RegisterTwiddles(const float2* __restrict__ t, int j) {
 #pragma unroll
-    for (int k = 1; k < 8; ++k) r[k] = t[k * 8 + j];
-    w8 = (W / 8 > 8) ? t[8 * 8 + j] : make_float2(1.f, 0.f);
+    for (int k = 1; k < 8; ++k) r[k] = t[k * T + j];
+    w8 = (W / T > 8) ? t[8 * T + j] : make_float2(1.f, 0.f);
   }
   template <int K1>
   __device__ __forceinline__ float2 get() const {
@@ -136,37 +128,48 @@ __device__ __forceinline__ void twiddle_store(const float2* y, float2* xw, const
   }
 }
 
-template <int W, bool INV, typename Tw>
-__device__ __forceinline__ void line_fft(float2 (&v)[W / 8], const Tw& tw, float2* xb, int j) {
-  constexpr int N1 = W / 8;
-  constexpr int NC = N1 / 8;
+// Line transform of a W-point line held by T threads (lane group, T = 8 or 16), in place
+// in `v`: on entry v[m] is line element j + T m, on exit v[m] is spectrum element j + T m.
+// W = N1 T (four-step): step A is an N1-point DFT in registers over x[T n1 + j], step B
+// the twiddles w_W^(j k1), then an exchange, then step C, N1/T T-point DFTs.
+// `xb` is the group's private exchange buffer of T * (N1 + 1) float2: thread j writes
+// its step-A results Y[j][k1] at xb[j (N1 + 1) + k1] and reads Y[n2][k1] at
+// xb[n2 (N1 + 1) + k1]; the odd stride N1 + 1 spreads both patterns over distinct banks
+// (and, for T = 8, consecutive groups' buffers start half a bank row apart), so the
+// exchange is conflict-free and its addresses are a per-thread base plus immediate offsets.
+// `tw.get<k1>()` = w_W^(j k1) (forward sign).  INV selects the unnormalised inverse.
+template <int W, bool INV, typename Tw, int T = 8>
+__device__ __forceinline__ void line_fft(float2 (&v)[W / T], const Tw& tw, float2* xb, int j) {
+  constexpr int N1 = W / T;
+  constexpr int NC = N1 / T;
   constexpr int XS = N1 + 1;
+  static_assert(N1 % T == 0, "W / T must be a multiple of T");
   float2 y[N1];
   if constexpr (INV) {
 #pragma unroll
     for (int m = 0; m < N1; ++m) v[m] = cconj(v[m]);
   }
-  // step A: DFT over n1 of x[8 n1 + j]
+  // step A: DFT over n1 of x[T n1 + j]
   dft<N1, 1>(v, y);
   // step B: twiddles, then exchange Y[n2 = j][k1]
   float2* xw = xb + j * XS;
   twiddle_store<0, N1>(y, xw, tw);
   __syncwarp();
-  float2 b[NC][8];
+  float2 b[NC][T];
   const float2* xr = xb + j;
 #pragma unroll
   for (int mc = 0; mc < NC; ++mc) {
 #pragma unroll
-    for (int n2 = 0; n2 < 8; ++n2) b[mc][n2] = xr[n2 * XS + 8 * mc];
+    for (int n2 = 0; n2 < T; ++n2) b[mc][n2] = xr[n2 * XS + T * mc];
   }
   __syncwarp();   // the buffer is reused by this group's next transform
-  // step C: eight-point DFTs over n2; X[k1 + N1 k2] with k1 = j + 8 mc is v[mc + NC k2]
+  // step C: T-point DFTs over n2; X[k1 + N1 k2] with k1 = j + T mc is v[mc + NC k2]
 #pragma unroll
   for (int mc = 0; mc < NC; ++mc) {
-    float2 X[8];
-    dft<8, 1>(b[mc], X);
+    float2 X[T];
+    dft<T, 1>(b[mc], X);
 #pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) v[mc + NC * k2] = INV ? cconj(X[k2]) : X[k2];
+    for (int k2 = 0; k2 < T; ++k2) v[mc + NC * k2] = INV ? cconj(X[k2]) : X[k2];
   }
 }
 

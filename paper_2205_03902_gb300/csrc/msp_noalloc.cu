@@ -26,7 +26,7 @@
 namespace msp {
 
 cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int grid, cudaStream_t st);
-int position_ctas_per_sm(int win);
+int position_slots(int win);
 __global__ void transmission_kernel(const float* __restrict__ V, float2* __restrict__ T, size_t n, float sigma);
 __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, double dq);
 
@@ -116,7 +116,7 @@ extern "C" msp_status msp_forward_noalloc(const msp_geometry* g, const float* pr
   p.Ny = g->obj_ny;
   p.Nx = g->obj_nx;
   p.S = g->n_pos;
-  const int cap = sms * position_ctas_per_sm(W);
+  const int cap = position_slots(W);
   e = launch_position_kernel(W, MODE_FORWARD, p, g->n_pos < cap ? g->n_pos : cap, st);
   if (e != cudaSuccess) return noalloc_fail(MSP_ECUDA, std::string("forward kernel: ") + cudaGetErrorString(e));
   return MSP_OK;

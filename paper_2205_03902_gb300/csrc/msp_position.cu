@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   if (tid < W) s_h1[tid] = p.h1[tid];
   __syncthreads();
 #if MSP_TWIDDLE_REGISTERS
-  const RegisterTwiddles<W> tw(s_tw, j);
+  const RegisterTwiddles<W, 8> tw(s_tw, j);
 #else
-  const SharedTwiddles tw{s_tw, j};
+  const SharedTwiddles<8> tw{s_tw, j};
 #endif
 
   const int L = p.L;
@@ -360,13 +360,18 @@ static cudaError_t launch_w(int mode, const PosParams& p, int grid, cudaStream_t
   }
 }
 
+cudaError_t launch_position_cluster_kernel(int mode, const PosParams& p, int clusters, cudaStream_t st);
+int position_clusters_resident();
+
+// `grid` counts position slots: CTAs for W = 64 / 128, four-CTA clusters for W = 256.
 cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int grid, cudaStream_t st) {
   if (win == 64) return launch_w<64>(mode, p, grid, st);
-  return launch_w<128>(mode, p, grid, st);
+  if (win == 128) return launch_w<128>(mode, p, grid, st);
+  return launch_position_cluster_kernel(mode, p, grid, st);
 }
 
 // CTAs of the fused kernel that fit on one SM (same for every mode of a window size).
-int position_ctas_per_sm(int win) {
+static int position_ctas_per_sm(int win) {
   int n = 0;
   const size_t smem = win == 64 ? position_smem_bytes<64>() : position_smem_bytes<128>();
   if (win == 64) {
@@ -377,6 +382,16 @@ int position_ctas_per_sm(int win) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, position_kernel<128, MODE_LOSS_GRAD>, 4 * 128, smem);
   }
   return n < 1 ? 1 : n;
+}
+
+// Positions the fused kernel processes at once on the current device (its persistent
+// grid): resident CTAs for W = 64 / 128, resident four-CTA clusters for W = 256.
+int position_slots(int win) {
+  if (win == 256) return position_clusters_resident();
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms * position_ctas_per_sm(win);
 }
 
 }  // namespace msp

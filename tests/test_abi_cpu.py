@@ -47,7 +47,8 @@ def geom(**kw):
     ({}, msp.MSP_OK),
     (dict(win=64, obj_ny=96, obj_nx=96), msp.MSP_OK),
     (dict(win=96), msp.MSP_EUNSUPPORTED),
-    (dict(win=256, obj_ny=640, obj_nx=640), msp.MSP_EUNSUPPORTED),
+    (dict(win=256, obj_ny=640, obj_nx=640), msp.MSP_OK),
+    (dict(win=512, obj_ny=640, obj_nx=640), msp.MSP_EUNSUPPORTED),
     (dict(param=msp.MSP_PARAM_TRANSMISSION), msp.MSP_EUNSUPPORTED),
     (dict(n_slices=0), msp.MSP_EINVAL),
     (dict(obj_ny=100), msp.MSP_EINVAL),

@@ -1,7 +1,8 @@
 """GPU parity: libmsp (FP32, sm_103a) against the FP64 oracle on identical seeded inputs.
 
-Tolerances.  Intensities and the loss must match to a relative L2 error of 1e-5 on
-every state.  Gradients are linear in the far-field residual R = Psi - sqrt(I) Psi/|Psi|,
+Tolerances.  Intensities must match to a relative L2 error of 1e-5 on every state.
+The loss differences FP32 amplitudes (bar max(1e-5, 2 e ||Psi|| / ||sqrt(I) - |Psi|||)).
+Gradients are linear in the far-field residual R = Psi - sqrt(I) Psi/|Psi|,
 which inherits the forward's absolute rounding error amplified by the state's
 conditioning kappa (see `oracle.msp_oracle.residual_conditioning`: ~||Psi|| / ||R||, larger
 where a small model amplitude meets a large measured one and the residual is set by
@@ -63,6 +64,15 @@ def derived_tol(gd, probe, pos, I, V, probe_grad=False):
     return max(TOL, (e * kappa + flip) * (canc if probe_grad else 1.0))
 
 
+def loss_tol(gd, probe, n_pos, loss_ref):
+    """The loss sum_k (sqrt(I) - |Psi|)^2 differences FP32 amplitudes: its relative error is about
+    2 e ||Psi|| / ||sqrt(I) - |Psi||| with ||Psi||^2 = S W^2 ||p||^2 (Parseval, pure-phase slices)."""
+    if loss_ref <= 0:
+        return TOL
+    kappa = np.sqrt(n_pos * gd["win"] ** 2 * float(np.sum(np.abs(probe) ** 2)) / loss_ref)
+    return max(TOL, 2 * fwd_err(gd["n_slices"]) * kappa)
+
+
 class Case:
     """A seeded problem: geometry, probe, positions, measured intensities, current V.
     Every input is rounded to FP32 once, so both sides see identical values."""
@@ -88,6 +98,9 @@ class Case:
         if not hasattr(self, key):
             setattr(self, key, derived_tol(self.gd, self.probe, self.pos, self.I, self.V, probe_grad))
         return getattr(self, key)
+
+    def ltol(self, loss_ref):
+        return TOL if self.strong else loss_tol(self.gd, self.probe, len(self.pos), loss_ref)
 
     def dev(self, msp):
         g = msp.geometry(**self.gd)
@@ -134,11 +147,27 @@ def c3_strong():
     return strong_case(synth.C3, sub=(8, 8))
 
 
-ALL = ["c1", "c2_ragged", "c1_strong", "c2_strong", "c3_sub", "c3_strong"]
+@pytest.fixture(scope="module")
+def c4_sub():
+    # the sixteen-slice W = 256 workload (four-CTA clusters) on a 3 x 3 sub-scan
+    return Case(synth.C4, sub=(3, 3), noisy=False)
 
 
-def test_strong_states_are_well_conditioned(c1_strong, c2_strong, c3_strong):
-    for c in (c1_strong, c2_strong, c3_strong):
+W256_L3 = synth.Workload("w256_L3_obj640", 3, 640, 0.1, 1.0, 30, 256, (48, 48), 8, 30.0, 100.0, None, seed=3)
+
+
+@pytest.fixture(scope="module")
+def c4_strong():
+    # W = 256 with three slices on 7 x 7 = 49 positions: more positions than resident
+    # four-CTA clusters, with a ragged tail
+    return strong_case(W256_L3, sub=(7, 7))
+
+
+ALL = ["c1", "c2_ragged", "c1_strong", "c2_strong", "c3_sub", "c3_strong", "c4_sub", "c4_strong"]
+
+
+def test_strong_states_are_well_conditioned(c1_strong, c2_strong, c3_strong, c4_strong):
+    for c in (c1_strong, c2_strong, c3_strong, c4_strong):
         assert derived_tol(c.gd, c.probe, c.pos, c.I, c.V, probe_grad=True) <= TOL
 
 
@@ -165,8 +194,8 @@ def test_loss_and_gradients(msp, which, request):
     ref = O.loss_grad(c.gd, c.probe, c.pos, c.I, V=c.V)
     errs = dict(loss=abs(loss.item() - ref["loss"]) / ref["loss"], dV=rel(dV.cpu().numpy(), ref["dV"]),
                 dprobe=rel(dprobe.cpu().numpy(), ref["dprobe"]))
-    print(which, errs, "bars", c.tol(), c.tol(True))
-    assert errs["loss"] <= TOL
+    print(which, errs, "bars", c.ltol(ref["loss"]), c.tol(), c.tol(True))
+    assert errs["loss"] <= c.ltol(ref["loss"])
     assert errs["dV"] <= c.tol()
     assert errs["dprobe"] <= c.tol(probe_grad=True)
     for l in range(c.gd["n_slices"]):
@@ -196,13 +225,13 @@ def test_optional_outputs(msp, c1):
 
 @pytest.mark.parametrize("which,layer", [("c1", 0), ("c1", 1), ("c2_ragged", 0), ("c2_ragged", 2),
                                          ("c1_strong", 1), ("c2_strong", 0), ("c2_strong", 3),
-                                         ("c3_sub", 5), ("c3_strong", 7)])
+                                         ("c3_sub", 5), ("c3_strong", 7), ("c4_strong", 0), ("c4_strong", 2), ("c4_sub", 11)])
 def test_layer_step(msp, which, layer, request):
     c = request.getfixturevalue(which)
     g, p, V, pos, I = c.dev(msp)
     loss, mu = msp.layer_step(g, p, V, pos, I, layer)
     Vn, loss_ref, mu_ref = O.layer_step(c.gd, c.probe, c.pos, c.I, layer, V=c.V)
-    assert abs(loss.item() - loss_ref) / loss_ref <= TOL
+    assert abs(loss.item() - loss_ref) / loss_ref <= c.ltol(loss_ref)
     assert abs(mu.item() - mu_ref) / mu_ref <= TOL
     Vg = V.cpu().numpy()
     assert rel(Vg[layer] - c.V[layer], Vn[layer] - c.V[layer]) <= c.tol()   # the update itself
@@ -220,14 +249,14 @@ def test_layer_step_fixed_step(msp, c1_strong):
     assert rel(V.cpu().numpy()[1] - c.V[1], Vn[1] - c.V[1]) <= TOL
 
 
-@pytest.mark.parametrize("which", ["c2_ragged", "c2_strong"])
+@pytest.mark.parametrize("which", ["c2_ragged", "c2_strong", "c4_strong"])
 @pytest.mark.parametrize("normalize", [False, True])
 def test_probe_step(msp, which, normalize, request):
     c = request.getfixturevalue(which)
     g, p, V, pos, I = c.dev(msp)
     loss, mu = msp.probe_step(g, p, V, pos, I, normalize=normalize)
     pn, loss_ref, mu_ref = O.probe_step(c.gd, c.probe, c.pos, c.I, V=c.V, normalize=normalize)
-    assert abs(loss.item() - loss_ref) / loss_ref <= TOL
+    assert abs(loss.item() - loss_ref) / loss_ref <= c.ltol(loss_ref)
     assert mu.item() == pytest.approx(mu_ref, rel=1e-15)
     assert rel(p.cpu().numpy(), pn) <= TOL
     if not normalize:
@@ -281,7 +310,7 @@ def test_single_position_at_the_far_corner(msp):
     g, p, V, pos, I = c.dev(msp)
     loss, dV, dprobe = msp.loss_grad(g, p, V, pos, I)
     ref = O.loss_grad(c.gd, c.probe, c.pos, c.I, V=c.V)
-    assert abs(loss.item() - ref["loss"]) / ref["loss"] <= TOL
+    assert abs(loss.item() - ref["loss"]) / ref["loss"] <= c.ltol(ref["loss"])
     assert rel(dV.cpu().numpy(), ref["dV"]) <= TOL
     assert rel(dprobe.cpu().numpy(), ref["dprobe"]) <= TOL
 
@@ -384,4 +413,4 @@ def test_full_c2_workload_sampled(msp):
     for s, (y, x) in enumerate(pos):
         _, _, far = O.position_forward(probe, X, int(y), int(x), h)
         loss_ref += O.far_field_residual(far, I_meas[s], thr)[0]
-    assert abs(loss.item() - loss_ref) / loss_ref <= TOL
+    assert abs(loss.item() - loss_ref) / loss_ref <= loss_tol(gd, probe, len(pos), loss_ref)
