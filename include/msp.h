@@ -8,8 +8,12 @@
  * gradient steps of Algorithm 1 (Sec. 3.3) and of the probe problem (Sec. 3.5).
  *
  * Conventions shared by every entry point
- *   - Slices are given as real projected potentials V (V*angstrom); the slice
- *     transmission is X_m = exp(i sigma V_m) (the phase grating of Sec. 2.1).
+ *   - Slices are given as real projected potentials V (V*angstrom), the slice
+ *     transmission being X_m = exp(i sigma V_m) (the phase grating of Sec. 2.1); or,
+ *     with param = MSP_PARAM_TRANSMISSION, as the complex slices o_m themselves (the
+ *     paper's own unknowns, Sec. 2.2 / 3.3).  In transmission mode every argument named
+ *     V or dV below is complex, [L][Ny][Nx] interleaved (re, im) pairs, and gradients
+ *     are the Wirtinger derivatives dL/dconj(o).
  *   - Window model: scan position s uses the W x W window of every slice whose
  *     top-left object pixel is pos[s] = (y, x); the probe is one W x W array.
  *     Every window must lie inside the object: 0 <= y <= Ny - W, 0 <= x <= Nx - W.
@@ -62,8 +66,8 @@ typedef enum {
   MSP_ETIMEOUT = 5       /* reserved for bounded device-side waits */
 } msp_status;
 
-/* Slice parametrisation.  Only MSP_PARAM_POTENTIAL (X_m = exp(i sigma V_m)) is
- * implemented on the GPU; MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED. */
+/* Slice parametrisation: real potentials (X_m = exp(i sigma V_m)) or complex
+ * transmissions o_m (the paper's parametrisation). */
 enum { MSP_PARAM_POTENTIAL = 0, MSP_PARAM_TRANSMISSION = 1 };
 
 /* Statement of the problem (Sec. 2.1).  Supported windows: W = 64, 128 or 256 (W = 256 runs
@@ -74,7 +78,7 @@ typedef struct {
   int32_t obj_nx;       /* object columns Nx >= W                                  */
   int32_t win;          /* W: probe window side = detector side (64, 128, 256)    */
   int32_t n_pos;        /* S: scan positions, >= 0                                 */
-  int32_t param;        /* MSP_PARAM_POTENTIAL                                     */
+  int32_t param;        /* MSP_PARAM_POTENTIAL or MSP_PARAM_TRANSMISSION          */
   double wavelength_A;  /* electron wavelength lambda in angstrom (Sec. 5.3.2)    */
   double sigma;         /* interaction constant, rad / (V angstrom)               */
   double dz_A;          /* slice separation = Fresnel distance Delta (Eq. fresnel_element) */
@@ -112,7 +116,9 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
  * (Opt_Prob_Amplitude_Flow_Step) with the other slices fixed:
  *   V[layer] <- V[layer] - mu dL/dV[layer]
  * step > 0 sets mu; step <= 0 takes mu = 1 / (2 sigma^2 W^2 max_pixel sum_s |psi_in,l^s|^2),
- * the spectral step ||Q_l||^-2 of Sec. 3.2 carried to the potential.
+ * the spectral step ||Q_l||^-2 of Sec. 3.2 carried to the potential.  In transmission mode
+ * o_l <- o_l - mu dL/dconj(o_l) with mu = 1 / (W^2 max_pixel sum_s |psi_in,l^s|^2
+ * prod_{m > l} max_pixel |o_m|^2), ||Q_l||^-2 or, for non-unimodular later slices, a bound on it.
  *   V          [L][Ny][Nx] float, updated in place (only slice `layer` changes)
  *   loss_before device double [1], loss at the incoming V (may be NULL)
  *   mu_out      device double [1], step size used (may be NULL) */
@@ -141,6 +147,7 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V,
  *     word) is one 16 MiB file-scope device array that every GPU loading the library
  *     holds until the process exits; L * Ny * Nx may not exceed 2,096,640 (returns
  *     MSP_EUNSUPPORTED, with the reason in msp_last_error_message(), otherwise);
+ *   - potentials only (MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED);
  *   - window_error (device int32, may be NULL) is set to 0, or to 1 if a window lay
  *     outside the object (that position's pattern is then zero);
  *   - the first call on a device looks up the array's device address (with that

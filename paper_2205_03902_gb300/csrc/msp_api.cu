@@ -64,7 +64,10 @@ __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, 
 // and no thread spends time on positions that miss its tile.
 constexpr int kGatherTile = 16;
 
-template <int NCH>
+// CPLX: the gathered channel is complex (float2, transmission mode); ILLUM: a second, real
+// channel (the illumination windows of a layer step) is gathered too and its per-tile
+// maximum written to `blockmax`.
+template <bool CPLX, bool ILLUM>
 __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ src0, const float* __restrict__ src1,
                                                      int nl_src, const int2* __restrict__ pos, int S, int W,
                                                      int Ny, int Nx, float* __restrict__ out0,
@@ -81,7 +84,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   const int tx0 = blockIdx.x * T, ty0 = blockIdx.y * T;
   const int px = tx0 + (tid % T), py = ty0 + (tid / T);
   const size_t WW = (size_t)W * W;
-  float acc0 = 0.f, acc1 = 0.f;
+  float2 acc0 = make_float2(0.f, 0.f);
+  float acc1 = 0.f;
   for (int base = 0; base < S; base += 256) {
     const int n = min(256, S - base);
     int2 ps = make_int2(0, 0);
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
     }
     __syncthreads();
     for (int q0 = 0; q0 < total; q0 += U) {
-      float v0[U], v1[U];
+      float2 v0[U];
+      float v1[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int q = q0 + u;
@@ -116,26 +121,30 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
         const int sq = live ? sidx[q] : 0;
         const int dx = px - pq.y, dy = py - pq.x;
         const bool in = ((unsigned)dx < (unsigned)W) && ((unsigned)dy < (unsigned)W);
-        const size_t o = (size_t)dy * W + dx;
-        v0[u] = in ? src0[((size_t)sq * nl_src + l) * WW + o] : 0.f;
-        if (NCH == 2) v1[u] = in ? src1[(size_t)sq * WW + o] : 0.f;
+        const size_t o = ((size_t)sq * nl_src + l) * WW + (size_t)dy * W + dx;
+        if (CPLX) v0[u] = in ? reinterpret_cast<const float2*>(src0)[o] : make_float2(0.f, 0.f);
+        else v0[u] = make_float2(in ? src0[o] : 0.f, 0.f);
+        if (ILLUM) v1[u] = in ? src1[(size_t)sq * WW + (size_t)dy * W + dx] : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        acc0 += v0[u];
-        if (NCH == 2) acc1 += v1[u];
+        acc0.x += v0[u].x;
+        if (CPLX) acc0.y += v0[u].y;
+        if (ILLUM) acc1 += v1[u];
       }
     }
   }
   float m = 0.f;
   if (py < Ny && px < Nx) {
-    out0[((size_t)l * Ny + py) * Nx + px] = acc0;
-    if (NCH == 2) {
+    const size_t oi = ((size_t)l * Ny + py) * Nx + px;
+    if (CPLX) reinterpret_cast<float2*>(out0)[oi] = acc0;
+    else out0[oi] = acc0.x;
+    if (ILLUM) {
       out1[(size_t)py * Nx + px] = acc1;
       m = acc1;
     }
   }
-  if (NCH == 2) {
+  if (ILLUM) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) wmax[w] = m;
@@ -146,6 +155,31 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
       blockmax[blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
     }
   }
+}
+
+// prod_{m > layer} max_pixel |o_m|^2 (FP64; 1 when layer is the last slice): the factor by
+// which non-unimodular later slices can enlarge ||Q_l||^2 (transmission-mode step size).
+__global__ void __launch_bounds__(1024) later_slices_gain_kernel(const float2* __restrict__ X, int L, size_t plane,
+                                                                 int layer, double* __restrict__ out) {
+  __shared__ float sh[1024];
+  const int tid = threadIdx.x;
+  double prod = 1.0;
+  for (int m = layer + 1; m < L; ++m) {
+    float a = 0.f;
+    for (size_t i = tid; i < plane; i += 1024) {
+      const float2 v = X[(size_t)m * plane + i];
+      a = fmaxf(a, fmaf(v.x, v.x, v.y * v.y));
+    }
+    sh[tid] = a;
+    __syncthreads();
+    for (int k = 512; k > 0; k >>= 1) {
+      if (tid < k) sh[tid] = fmaxf(sh[tid], sh[tid + k]);
+      __syncthreads();
+    }
+    prod *= (double)sh[0];
+    __syncthreads();
+  }
+  if (tid == 0) out[0] = prod;
 }
 
 // out = tau^2 * sum |p|^2, the squared zero-rule threshold (a threshold needs no more
@@ -220,11 +254,12 @@ __global__ void dprobe_reduce_kernel(const float2* __restrict__ part, int G, int
   out[i] = make_float2((float)re, (float)im);
 }
 
-// Step size of a layer step: mu = step, or 1 / (2 sigma^2 W^2 max illumination).
-__global__ void layer_mu_kernel(double* scal, double step, double two_sig2_w2, double* mu_out) {
+// Step size of a layer step: mu = step, or 1 / (c W^2 max illumination) with c = 2 sigma^2
+// (potential mode) or c = prod_{m > l} max |o_m|^2 (scal[6], transmission mode).
+__global__ void layer_mu_kernel(double* scal, double step, double two_sig2_w2, double* mu_out, int cplx) {
   double mu = step;
   if (!(step > 0.0)) {
-    const double m = scal[2];
+    const double m = scal[2] * (cplx ? scal[6] : 1.0);
     mu = (m > 0.0) ? 1.0 / (two_sig2_w2 * m) : 0.0;
   }
   scal[1] = mu;
@@ -344,8 +379,8 @@ static msp_status check_geometry(const msp_geometry* g) {
   if (!g) return fail(MSP_EINVAL, "geometry is NULL");
   if (g->win != 64 && g->win != 128 && g->win != 256)
     return fail(MSP_EUNSUPPORTED, "window size " + std::to_string(g->win) + " (supported: 64, 128, 256)");
-  if (g->param != MSP_PARAM_POTENTIAL)
-    return fail(MSP_EUNSUPPORTED, "only the potential parametrisation exp(i sigma V) is implemented");
+  if (g->param != MSP_PARAM_POTENTIAL && g->param != MSP_PARAM_TRANSMISSION)
+    return fail(MSP_EINVAL, "param must be MSP_PARAM_POTENTIAL or MSP_PARAM_TRANSMISSION");
   if (g->n_slices < 1) return fail(MSP_EINVAL, "n_slices < 1");
   if (g->obj_ny < g->win || g->obj_nx < g->win) return fail(MSP_EINVAL, "object smaller than the window");
   if (g->n_pos < 0) return fail(MSP_EINVAL, "n_pos < 0");
@@ -382,12 +417,14 @@ static Workspace layout(const msp_geometry* g, int gcap, char* base) {
   w.h1 = (float2*)take(W * sizeof(float2));
   w.T = (float2*)take(L * plane * sizeof(float2));
   w.stash = (float2*)take((size_t)gcap * L * WW * sizeof(float2));
-  w.wgrad = (float*)take(S * (L > 2 ? L : 2) * WW * sizeof(float));
-  w.willum = base ? w.wgrad + S * WW : nullptr;
+  // window gradients (float2 in transmission mode), then the illumination windows of a layer step
+  const size_t cw = g->param == MSP_PARAM_TRANSMISSION ? 2 : 1;
+  w.wgrad = (float*)take(S * std::max(L * cw, cw + 1) * WW * sizeof(float));
+  w.willum = base ? w.wgrad + cw * S * WW : nullptr;
   w.dprobe_part = (float2*)take((size_t)gcap * WW * sizeof(float2));
   w.dprobe_sum = (float2*)take(WW * sizeof(float2));
   w.loss_part = (double*)take((S > 0 ? S : 1) * loss_slots((int)W) * sizeof(double));
-  w.map0 = (float*)take(plane * sizeof(float));
+  w.map0 = (float*)take(2 * plane * sizeof(float));   // complex in transmission mode
   w.map1 = (float*)take(plane * sizeof(float));
   w.bytes = off;
   return w;
@@ -442,6 +479,7 @@ static msp_status prepare(const msp_geometry* g, const float* probe, const float
                                                       1.0 / ((double)W * g->pixel_A));
   MSP_CK(cudaGetLastError());
   counted();
+  if (g->param == MSP_PARAM_TRANSMISSION) return MSP_OK;   // the caller's slices are used as given
   const size_t n = (size_t)g->n_slices * g->obj_ny * g->obj_nx;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)c.dev.sms * 16);
   transmission_kernel<<<blocks, 256, 0, c.st>>>(V, c.ws.T, n, (float)g->sigma);
@@ -450,10 +488,12 @@ static msp_status prepare(const msp_geometry* g, const float* probe, const float
   return MSP_OK;
 }
 
-static PosParams base_params(const msp_geometry* g, const float* probe, const int32_t* pos, Call& c) {
+static PosParams base_params(const msp_geometry* g, const float* probe, const float* V, const int32_t* pos,
+                             Call& c) {
   PosParams p{};
   p.probe = (const float2*)probe;
-  p.T = c.ws.T;
+  p.cplx = g->param == MSP_PARAM_TRANSMISSION;
+  p.T = p.cplx ? (const float2*)V : c.ws.T;   // transmission mode: the caller's complex slices
   p.h1 = c.ws.h1;
   p.pos = (const int2*)pos;
   p.stash = c.ws.stash;
@@ -542,7 +582,7 @@ msp_status msp_forward(const msp_geometry* g, const float* probe, const float* V
     MSP_TRY(need_ptr(I_out, "I_out"));
   }
   MSP_TRY(prepare(g, probe, V, c));
-  PosParams p = base_params(g, probe, pos, c);
+  PosParams p = base_params(g, probe, V, pos, c);
   p.I_out = I_out;
   return run_position(g, MODE_FORWARD, p, c);
 }
@@ -566,19 +606,23 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   const int W = g->win;
   const size_t WW = (size_t)W * W;
   const size_t plane = (size_t)g->obj_ny * g->obj_nx;
-  PosParams p = base_params(g, probe, pos, c);
+  PosParams p = base_params(g, probe, V, pos, c);
   p.I_meas = I_meas;
   p.want_dprobe = dprobe != nullptr;
   if (g->n_pos == 0) {
-    if (dV) MSP_CK(cudaMemsetAsync(dV, 0, (size_t)g->n_slices * plane * sizeof(float), c.st));
+    if (dV) MSP_CK(cudaMemsetAsync(dV, 0, (size_t)g->n_slices * plane * sizeof(float) * (p.cplx ? 2 : 1), c.st));
     if (dprobe) MSP_CK(cudaMemsetAsync(dprobe, 0, WW * sizeof(float2), c.st));
     return reduce_loss(g, c, loss);
   }
   MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
   if (dV) {
     dim3 grid((g->obj_nx + kGatherTile - 1) / kGatherTile, (g->obj_ny + kGatherTile - 1) / kGatherTile, g->n_slices);
-    gather_kernel<1><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos, W,
-                                             g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
+    if (p.cplx)
+      gather_kernel<true, false><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos,
+                                                         W, g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
+    else
+      gather_kernel<false, false><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos,
+                                                          W, g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
     MSP_CK(cudaGetLastError());
   counted();
   }
@@ -612,32 +656,44 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   const size_t plane = (size_t)g->obj_ny * g->obj_nx;
   if (g->n_pos == 0) {
     MSP_CK(cudaMemsetAsync(c.ws.scal, 0, 16 * sizeof(double), c.st));
-    layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, 0.0, mu_out);
+    layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, 0.0, mu_out, 0);
     MSP_CK(cudaGetLastError());
   counted();
     return reduce_loss(g, c, loss_before);
   }
-  PosParams p = base_params(g, probe, pos, c);
+  PosParams p = base_params(g, probe, V, pos, c);
   p.I_meas = I_meas;
   p.layer = layer;
   MSP_TRY(run_position(g, MODE_LAYER, p, c));
   dim3 grid((g->obj_nx + kGatherTile - 1) / kGatherTile, (g->obj_ny + kGatherTile - 1) / kGatherTile, 1);
   const int nblk = (int)(grid.x * grid.y);
   if (nblk > kRedSlots) return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
-  gather_kernel<2><<<grid, 256, 0, c.st>>>(c.ws.wgrad, c.ws.willum, 1, (const int2*)pos, g->n_pos, W, g->obj_ny,
-                                           g->obj_nx, c.ws.map0, c.ws.map1, c.ws.red);
+  if (p.cplx)
+    gather_kernel<true, true><<<grid, 256, 0, c.st>>>(c.ws.wgrad, c.ws.willum, 1, (const int2*)pos, g->n_pos, W,
+                                                      g->obj_ny, g->obj_nx, c.ws.map0, c.ws.map1, c.ws.red);
+  else
+    gather_kernel<false, true><<<grid, 256, 0, c.st>>>(c.ws.wgrad, c.ws.willum, 1, (const int2*)pos, g->n_pos, W,
+                                                       g->obj_ny, g->obj_nx, c.ws.map0, c.ws.map1, c.ws.red);
   MSP_CK(cudaGetLastError());
   counted();
   reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nblk, 1, c.ws.scal + 2, nullptr);
   MSP_CK(cudaGetLastError());
   counted();
-  const double two_sig2_w2 = 2.0 * g->sigma * g->sigma * (double)W * (double)W;
-  layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, two_sig2_w2, mu_out);
+  if (p.cplx) {
+    later_slices_gain_kernel<<<1, 1024, 0, c.st>>>((const float2*)V, g->n_slices, plane, layer, c.ws.scal + 6);
+    MSP_CK(cudaGetLastError());
+    counted();
+  }
+  // potential mode: mu = 1 / (2 sigma^2 W^2 max illum); transmission: 1 / (W^2 max illum prod max|o_m|^2)
+  const double c_w2 = (p.cplx ? 1.0 : 2.0 * g->sigma * g->sigma) * (double)W * (double)W;
+  layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, c_w2, mu_out, p.cplx);
   MSP_CK(cudaGetLastError());
   counted();
   MSP_TRY(reduce_loss(g, c, loss_before));
-  const int blocks = (int)std::min<size_t>((plane + 255) / 256, (size_t)c.dev.sms * 8);
-  layer_update_kernel<<<blocks, 256, 0, c.st>>>(V + (size_t)layer * plane, c.ws.map0, plane, c.ws.scal);
+  // V_l (or the complex o_l, as interleaved floats) -= mu * gradient map
+  const size_t nupd = plane * (p.cplx ? 2 : 1);
+  const int blocks = (int)std::min<size_t>((nupd + 255) / 256, (size_t)c.dev.sms * 8);
+  layer_update_kernel<<<blocks, 256, 0, c.st>>>(V + (size_t)layer * nupd, c.ws.map0, nupd, c.ws.scal);
   MSP_CK(cudaGetLastError());
   counted();
   return MSP_OK;
@@ -666,7 +722,7 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, c
   if (S == 0) {
     MSP_CK(cudaMemsetAsync(c.ws.dprobe_sum, 0, WW * sizeof(float2), c.st));
   } else {
-    PosParams p = base_params(g, probe, pos, c);
+    PosParams p = base_params(g, probe, V, pos, c);
     p.I_meas = I_meas;
     p.want_dprobe = 1;
     MSP_TRY(run_position(g, MODE_PROBE, p, c));

@@ -18,7 +18,7 @@ struct PosParams {
   const float* I_meas;     // [S][W][W]
   float* I_out;            // [S][W][W]                (forward)
   float2* stash;           // [G][Ls][W][W] exit waves kept for the adjoint
-  float* wgrad;            // [S][Lg][W][W] per-position window gradients
+  float* wgrad;            // [S][Lg][W][W] per-position window gradients (float2 in transmission mode)
   float* willum;           // [S][W][W] per-position |psi_in,l|^2 (layer step)
   float2* dprobe_part;     // [G][W][W] per-CTA probe-gradient partial sums
   double* loss_part;       // [S] per-position loss
@@ -27,6 +27,7 @@ struct PosParams {
   int L, Ny, Nx, S;
   int layer;               // slice of a layer step
   int want_dprobe;
+  int cplx;                // transmission mode: T is the caller's complex slices, gradients complex
   float two_sigma;
 };
 

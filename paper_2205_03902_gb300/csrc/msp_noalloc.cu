@@ -71,6 +71,8 @@ extern "C" msp_status msp_forward_noalloc(const msp_geometry* g, const float* pr
                                           void* stream) {
   msp_status s = msp_validate_geometry(g);   // also clears this thread's error message
   if (s != MSP_OK) return s;
+  if (g->param != MSP_PARAM_POTENTIAL)
+    return noalloc_fail(MSP_EUNSUPPORTED, "msp_forward_noalloc takes potentials only; use msp_forward");
   const size_t cells = (size_t)g->n_slices * g->obj_ny * g->obj_nx;
   if (cells > kNoallocMaxCells)
     return noalloc_fail(MSP_EUNSUPPORTED, "L * Ny * Nx = " + std::to_string(cells) + " exceeds the " +

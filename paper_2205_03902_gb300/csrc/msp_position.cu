@@ -72,7 +72,10 @@ constexpr size_t position_smem_bytes() {
   return ((size_t)W * W + (size_t)(W / 2) * 8 * (W / 8 + 1)) * sizeof(float2);
 }
 
-template <int W, int MODE>
+// CPLX: transmission mode (the paper's complex slices o_l).  The stash then holds the wave
+// incident on each slice and the window gradient is dL/dconj(o_l) = conj(psi_in,l) o chi_l;
+// in potential mode it holds the exit wave and the gradient is 2 sigma Im(conj(E_l) chi_l).
+template <int W, int MODE, bool CPLX = false>
 __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   using G = Geo<W>;
   constexpr int N1 = G::N1;
@@ -119,10 +122,13 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         for (size_t i = tid; i < WW; i += G::NT) p.I_out[s * WW + i] = 0.f;
       } else {
         if (tid == 0) p.loss_part[s] = 0.0;
+        constexpr int CW = CPLX ? 2 : 1;
         if (MODE == MODE_LOSS_GRAD)
-          for (size_t i = tid; i < WW * L; i += G::NT) p.wgrad[s * WW * L + i] = 0.f;
-        if (MODE == MODE_LAYER)
-          for (size_t i = tid; i < WW; i += G::NT) { p.wgrad[s * WW + i] = 0.f; p.willum[s * WW + i] = 0.f; }
+          for (size_t i = tid; i < CW * WW * L; i += G::NT) p.wgrad[CW * s * WW * L + i] = 0.f;
+        if (MODE == MODE_LAYER) {
+          for (size_t i = tid; i < CW * WW; i += G::NT) p.wgrad[CW * s * WW + i] = 0.f;
+          for (size_t i = tid; i < WW; i += G::NT) p.willum[s * WW + i] = 0.f;
+        }
       }
       continue;  // uniform across the CTA
     }
@@ -136,10 +142,16 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
       float2 v[N1];
       const float2* T0 = p.T + win0 + (size_t)r * p.Nx;
 #pragma unroll
-      for (int m = 0; m < N1; ++m) v[m] = cmul(p.probe[r * W + j + 8 * m], T0[j + 8 * m]);
-      if (need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+      for (int m = 0; m < N1; ++m) v[m] = p.probe[r * W + j + 8 * m];
+      if (CPLX && need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];
+        for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // incident wave
+      }
+#pragma unroll
+      for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], T0[j + 8 * m]);
+      if (!CPLX && need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // exit wave
       }
       line_fft<W, false>(v, tw, xb, j);
 #pragma unroll
@@ -183,11 +195,15 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
           line_fft<W, true>(v, tw, xb, j);
+          if (CPLX && keep) {
+#pragma unroll
+            for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // incident wave
+          }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], t[m]);
-          if (keep) {
+          if (!CPLX && keep) {
 #pragma unroll
-            for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];
+            for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // exit wave
           }
           line_fft<W, false>(v, tw, xb, j);
 #pragma unroll
@@ -259,7 +275,8 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
       const bool go_on = (l > lowest) || (l == 0 && MODE != MODE_LAYER && p.want_dprobe);
       const float2* Tl = p.T + (size_t)l * plane + win0;
       const float2* st = stash + (MODE == MODE_LOSS_GRAD ? (size_t)l * WW : 0);
-      float* wg = p.wgrad + (MODE == MODE_LOSS_GRAD ? ((size_t)s * L + l) * WW : (size_t)s * WW);
+      // window gradients: [S][L][W][W] (LOSS_GRAD) or [S][W][W] (LAYER), float2 in transmission mode
+      float* wg = p.wgrad + (CPLX ? 2 : 1) * (MODE == MODE_LOSS_GRAD ? ((size_t)s * L + l) * WW : (size_t)s * WW);
 #pragma unroll 1
       for (int it = 0; it < G::LPG; ++it) {
         const int r = grp + G::GROUPS * it;
@@ -273,11 +290,19 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
         line_fft<W, true>(v, tw, xb, j);   // v = chi_l (row r)
         if (grad_here) {
-          // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
+          if (CPLX) {
+            // dL/dconj(o_l) on the window: conj(psi_in,l) o chi_l
+            float2* wg2 = reinterpret_cast<float2*>(wg) + r * W + j;
 #pragma unroll
-          for (int m = 0; m < N1; ++m) {
-            wg[r * W + j + 8 * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
-            if (MODE == MODE_LAYER) p.willum[s * WW + r * W + j + 8 * m] = fmaf(e[m].x, e[m].x, e[m].y * e[m].y);
+            for (int m = 0; m < N1; ++m) wg2[8 * m] = cmulc(v[m], e[m]);
+          } else {
+            // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
+#pragma unroll
+            for (int m = 0; m < N1; ++m) wg[r * W + j + 8 * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
+          }
+          if (MODE == MODE_LAYER) {   // |psi_in,l|^2 (= |E_l|^2 for unimodular slices)
+#pragma unroll
+            for (int m = 0; m < N1; ++m) p.willum[s * WW + r * W + j + 8 * m] = fmaf(e[m].x, e[m].x, e[m].y * e[m].y);
           }
         }
         if (go_on) {
@@ -335,29 +360,37 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 // launch helpers
 // ----------------------------------------------------------------------------
 
-template <int W, int MODE>
+template <int W, int MODE, bool CPLX>
 static cudaError_t launch_one(const PosParams& p, int grid, cudaStream_t st) {
   const size_t smem = position_smem_bytes<W>();
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(position_kernel<W, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(position_kernel<W, MODE, CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
-  position_kernel<W, MODE><<<grid, 4 * W, smem, st>>>(p);
+  position_kernel<W, MODE, CPLX><<<grid, 4 * W, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+template <int W, bool CPLX>
+static cudaError_t launch_wc(int mode, const PosParams& p, int grid, cudaStream_t st) {
+  switch (mode) {
+    case MODE_FORWARD: return launch_one<W, MODE_FORWARD, CPLX>(p, grid, st);
+    case MODE_LOSS_GRAD: return launch_one<W, MODE_LOSS_GRAD, CPLX>(p, grid, st);
+    case MODE_LAYER: return launch_one<W, MODE_LAYER, CPLX>(p, grid, st);
+    default: return launch_one<W, MODE_PROBE, CPLX>(p, grid, st);
+  }
 }
 
 template <int W>
 static cudaError_t launch_w(int mode, const PosParams& p, int grid, cudaStream_t st) {
-  switch (mode) {
-    case MODE_FORWARD: return launch_one<W, MODE_FORWARD>(p, grid, st);
-    case MODE_LOSS_GRAD: return launch_one<W, MODE_LOSS_GRAD>(p, grid, st);
-    case MODE_LAYER: return launch_one<W, MODE_LAYER>(p, grid, st);
-    default: return launch_one<W, MODE_PROBE>(p, grid, st);
-  }
+  // the forward model reads the slices the same way in both parametrisations
+  if (p.cplx && mode != MODE_FORWARD) return launch_wc<W, true>(mode, p, grid, st);
+  return launch_wc<W, false>(mode, p, grid, st);
 }
 
 cudaError_t launch_position_cluster_kernel(int mode, const PosParams& p, int clusters, cudaStream_t st);

@@ -37,7 +37,8 @@ constexpr int XS = N1 + 1;        // exchange-buffer stride
 constexpr size_t SMEM = ((size_t)RW * W + (size_t)GROUPS * T * XS) * sizeof(float2);
 }  // namespace c256
 
-template <int MODE>
+// CPLX: transmission mode, as in position_kernel.
+template <int MODE, bool CPLX = false>
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_cluster_kernel(const PosParams p) {
   using namespace c256;
   extern __shared__ float2 sm[];
@@ -94,11 +95,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         for (size_t i = r0 + tid; i < r1; i += NT) p.I_out[s * WW + i] = 0.f;
       } else {
         if (tid == 0) p.loss_part[(size_t)s * CL + rank] = 0.0;
+        constexpr int CW = CPLX ? 2 : 1;
         if (MODE == MODE_LOSS_GRAD)
           for (int l = 0; l < L; ++l)
-            for (size_t i = r0 + tid; i < r1; i += NT) p.wgrad[((size_t)s * L + l) * WW + i] = 0.f;
-        if (MODE == MODE_LAYER)
-          for (size_t i = r0 + tid; i < r1; i += NT) { p.wgrad[s * WW + i] = 0.f; p.willum[s * WW + i] = 0.f; }
+            for (size_t i = CW * r0 + tid; i < CW * r1; i += NT) p.wgrad[CW * ((size_t)s * L + l) * WW + i] = 0.f;
+        if (MODE == MODE_LAYER) {
+          for (size_t i = CW * r0 + tid; i < CW * r1; i += NT) p.wgrad[CW * s * WW + i] = 0.f;
+          for (size_t i = r0 + tid; i < r1; i += NT) p.willum[s * WW + i] = 0.f;
+        }
       }
       continue;
     }
@@ -113,10 +117,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
       const float2* T0 = p.T + win0 + (size_t)gr * p.Nx + j;
       const float2* pr = p.probe + (size_t)gr * W + j;
 #pragma unroll
-      for (int m = 0; m < N1; ++m) v[m] = cmul(pr[T * m], T0[T * m]);
-      if (need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+      for (int m = 0; m < N1; ++m) v[m] = pr[T * m];
+      if (CPLX && need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) stash[(size_t)gr * W + j + T * m] = v[m];
+        for (int m = 0; m < N1; ++m) stash[(size_t)gr * W + j + T * m] = v[m];   // incident wave
+      }
+#pragma unroll
+      for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], T0[T * m]);
+      if (!CPLX && need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) stash[(size_t)gr * W + j + T * m] = v[m];   // exit wave
       }
       line_fft<W, false, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
 #pragma unroll
@@ -158,11 +168,15 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[rix(rl, m)];
           line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
+          if (CPLX && keep) {
+#pragma unroll
+            for (int m = 0; m < N1; ++m) st[(size_t)gr * W + j + T * m] = v[m];   // incident wave
+          }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], t[m]);
-          if (keep) {
+          if (!CPLX && keep) {
 #pragma unroll
-            for (int m = 0; m < N1; ++m) st[(size_t)gr * W + j + T * m] = v[m];
+            for (int m = 0; m < N1; ++m) st[(size_t)gr * W + j + T * m] = v[m];   // exit wave
           }
           line_fft<W, false, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
 #pragma unroll
@@ -229,7 +243,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
       const bool go_on = (l > lowest) || (l == 0 && MODE != MODE_LAYER && p.want_dprobe);
       const float2* Tl = p.T + (size_t)l * plane + win0;
       const float2* st = stash + (MODE == MODE_LOSS_GRAD ? (size_t)l * WW : 0);
-      float* wg = p.wgrad + (MODE == MODE_LOSS_GRAD ? ((size_t)s * L + l) * WW : (size_t)s * WW);
+      float* wg = p.wgrad + (CPLX ? 2 : 1) * (MODE == MODE_LOSS_GRAD ? ((size_t)s * L + l) * WW : (size_t)s * WW);
 #pragma unroll 1
       for (int it = 0; it < LPG; ++it) {
         const int rl = grp + GROUPS * it, gr = rank * RW + rl;
@@ -242,10 +256,18 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         for (int m = 0; m < N1; ++m) v[m] = sm[rix(rl, m)];
         line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);   // v = chi_l (row gr)
         if (grad_here) {
+          if (CPLX) {
+            float2* wg2 = reinterpret_cast<float2*>(wg) + (size_t)gr * W + j;
 #pragma unroll
-          for (int m = 0; m < N1; ++m) {
-            wg[(size_t)gr * W + j + T * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
-            if (MODE == MODE_LAYER)
+            for (int m = 0; m < N1; ++m) wg2[T * m] = cmulc(v[m], e[m]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < N1; ++m)
+              wg[(size_t)gr * W + j + T * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
+          }
+          if (MODE == MODE_LAYER) {
+#pragma unroll
+            for (int m = 0; m < N1; ++m)
               p.willum[s * WW + (size_t)gr * W + j + T * m] = fmaf(e[m].x, e[m].x, e[m].y * e[m].y);
           }
         }
@@ -300,28 +322,34 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
   cluster.sync();   // shared memory must outlive every remote access
 }
 
-template <int MODE>
+template <int MODE, bool CPLX>
 static cudaError_t launch_cluster_one(const PosParams& p, int clusters, cudaStream_t st) {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(position_cluster_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)c256::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(position_cluster_kernel<MODE, CPLX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c256::SMEM);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
-  position_cluster_kernel<MODE><<<clusters * c256::CL, c256::NT, c256::SMEM, st>>>(p);
+  position_cluster_kernel<MODE, CPLX><<<clusters * c256::CL, c256::NT, c256::SMEM, st>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_position_cluster_kernel(int mode, const PosParams& p, int clusters, cudaStream_t st) {
+template <bool CPLX>
+static cudaError_t launch_cluster_c(int mode, const PosParams& p, int clusters, cudaStream_t st) {
   switch (mode) {
-    case MODE_FORWARD: return launch_cluster_one<MODE_FORWARD>(p, clusters, st);
-    case MODE_LOSS_GRAD: return launch_cluster_one<MODE_LOSS_GRAD>(p, clusters, st);
-    case MODE_LAYER: return launch_cluster_one<MODE_LAYER>(p, clusters, st);
-    default: return launch_cluster_one<MODE_PROBE>(p, clusters, st);
+    case MODE_FORWARD: return launch_cluster_one<MODE_FORWARD, CPLX>(p, clusters, st);
+    case MODE_LOSS_GRAD: return launch_cluster_one<MODE_LOSS_GRAD, CPLX>(p, clusters, st);
+    case MODE_LAYER: return launch_cluster_one<MODE_LAYER, CPLX>(p, clusters, st);
+    default: return launch_cluster_one<MODE_PROBE, CPLX>(p, clusters, st);
   }
+}
+
+cudaError_t launch_position_cluster_kernel(int mode, const PosParams& p, int clusters, cudaStream_t st) {
+  if (p.cplx && mode != MODE_FORWARD) return launch_cluster_c<true>(mode, p, clusters, st);
+  return launch_cluster_c<false>(mode, p, clusters, st);
 }
 
 // Four-CTA clusters of the W = 256 kernel that can be resident at once on this device.

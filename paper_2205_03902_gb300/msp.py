@@ -160,7 +160,8 @@ def _arrays(g: Geometry, probe, V, pos, I=None, I_name="I_meas"):
     device = V.device
     W, L, Ny, Nx, S = g.win, g.n_slices, g.obj_ny, g.obj_nx, g.n_pos
     _need(probe, "probe", torch.complex64, (W, W), device)
-    _need(V, "V", torch.float32, (L, Ny, Nx), device)
+    cplx = g.param == MSP_PARAM_TRANSMISSION   # complex slices o_m instead of potentials
+    _need(V, "V", torch.complex64 if cplx else torch.float32, (L, Ny, Nx), device)
     _need(pos, "pos", torch.int32, (S, 2), device)
     if I is not None:
         _need(I, I_name, torch.float32, (S, W, W), device)

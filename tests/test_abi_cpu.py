@@ -49,7 +49,8 @@ def geom(**kw):
     (dict(win=96), msp.MSP_EUNSUPPORTED),
     (dict(win=256, obj_ny=640, obj_nx=640), msp.MSP_OK),
     (dict(win=512, obj_ny=640, obj_nx=640), msp.MSP_EUNSUPPORTED),
-    (dict(param=msp.MSP_PARAM_TRANSMISSION), msp.MSP_EUNSUPPORTED),
+    (dict(param=msp.MSP_PARAM_TRANSMISSION), msp.MSP_OK),
+    (dict(param=7), msp.MSP_EINVAL),
     (dict(n_slices=0), msp.MSP_EINVAL),
     (dict(obj_ny=100), msp.MSP_EINVAL),
     (dict(n_pos=-1), msp.MSP_EINVAL),

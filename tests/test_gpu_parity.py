@@ -414,3 +414,68 @@ def test_full_c2_workload_sampled(msp):
         _, _, far = O.position_forward(probe, X, int(y), int(x), h)
         loss_ref += O.far_field_residual(far, I_meas[s], thr)[0]
     assert abs(loss.item() - loss_ref) / loss_ref <= loss_tol(gd, probe, len(pos), loss_ref)
+
+
+# --------------------------------------------------------------------------- transmission mode
+
+def transmission_case(case, seed=21, rough=0.05):
+    """The same problem with complex, non-unimodular slices o = exp(i sigma V)(1 + rough n)."""
+    rng = np.random.default_rng(seed)
+    n = rng.standard_normal(case.V.shape) + 1j * rng.standard_normal(case.V.shape)
+    T = np.exp(1j * case.gd["sigma"] * case.V) * (1 + rough * n)
+    return T.astype(np.complex64).astype(np.complex128)
+
+
+def tdev(msp, c, T):
+    gd = dict(c.gd, param=msp.MSP_PARAM_TRANSMISSION)
+    g = msp.geometry(**gd)
+    return g, to_dev(c.probe, np.complex64), to_dev(T, np.complex64), to_dev(c.pos, np.int32), to_dev(c.I, np.float32)
+
+
+def t_bar(c, T, probe_grad=False):
+    if c.strong:
+        return TOL
+    e = fwd_err(c.gd["n_slices"])
+    kappa, canc, flip = O.residual_conditioning(c.gd, c.probe, c.pos, c.I, T=T,
+                                                band=2 * e * float(np.linalg.norm(c.probe)))
+    return max(TOL, (e * kappa + flip) * (canc if probe_grad else 1.0))
+
+
+@pytest.mark.parametrize("which", ["c1_strong", "c2_strong", "c4_strong", "c2_ragged"])
+def test_transmission_mode_forward_and_gradients(msp, which, request):
+    c = request.getfixturevalue(which)
+    T = transmission_case(c)
+    g, p, X, pos, I = tdev(msp, c, T)
+    Ig = msp.forward(g, p, X, pos).cpu().numpy()
+    assert rel(Ig, O.forward(c.gd, c.probe, c.pos, T=T)) <= TOL
+    loss, dX, dprobe = msp.loss_grad(g, p, X, pos, I)
+    ref = O.loss_grad(c.gd, c.probe, c.pos, c.I, T=T)
+    assert abs(loss.item() - ref["loss"]) / ref["loss"] <= (TOL if c.strong else 10 * t_bar(c, T))
+    assert rel(dX.cpu().numpy(), ref["dX"]) <= t_bar(c, T)
+    assert rel(dprobe.cpu().numpy(), ref["dprobe"]) <= t_bar(c, T, probe_grad=True)
+
+
+@pytest.mark.parametrize("which,layer", [("c1_strong", 0), ("c2_strong", 1), ("c2_strong", 3), ("c4_strong", 1)])
+def test_transmission_mode_layer_step(msp, which, layer, request):
+    """o_l <- o_l - mu dL/dconj(o_l), mu = 1 / (W^2 max illumination prod_{m > l} max |o_m|^2)."""
+    c = request.getfixturevalue(which)
+    T = transmission_case(c)
+    g, p, X, pos, I = tdev(msp, c, T)
+    loss, mu = msp.layer_step(g, p, X, pos, I, layer)
+    Tn, loss_ref, mu_ref = O.layer_step(c.gd, c.probe, c.pos, c.I, layer, T=T)
+    assert abs(loss.item() - loss_ref) / loss_ref <= TOL
+    assert abs(mu.item() - mu_ref) / mu_ref <= TOL
+    Xg = X.cpu().numpy()
+    assert rel(Xg[layer] - T[layer], Tn[layer] - T[layer]) <= TOL
+    others = [m for m in range(c.gd["n_slices"]) if m != layer]
+    assert np.array_equal(Xg[others], T[others].astype(np.complex64))
+
+
+def test_transmission_mode_probe_step(msp, c2_strong):
+    c = c2_strong
+    T = transmission_case(c)
+    g, p, X, pos, I = tdev(msp, c, T)
+    loss, mu = msp.probe_step(g, p, X, pos, I)
+    pn, loss_ref, mu_ref = O.probe_step(c.gd, c.probe, c.pos, c.I, T=T)
+    assert abs(loss.item() - loss_ref) / loss_ref <= TOL
+    assert rel(p.cpu().numpy() - c.probe, pn - c.probe) <= TOL
