@@ -63,6 +63,22 @@ def measured_traffic():
         return None
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The slowest rank's time: every rank contributes x, all receive the maximum."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, ms_per_step: float) -> float:
+    """Whole-job pattern*slices per second: every rank processes its own replica of the
+    workload each step, and the job's step takes as long as its slowest rank's."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -239,13 +255,9 @@ def run_msp(args, rank, world, local_rank):
     prof = msp.profile_read(reset=True)
     msp.profile_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * S * L / (ms_per_step * 1e-3)
+    value = job_throughput(world, S * L, ms_per_step)
 
     # ---- end to end through the public API with host buffers (pinned), copies timed ----
     # Every step copies its inputs from pinned host memory and reads its result (the
@@ -299,7 +311,7 @@ def run_msp(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e_steps
     assert np.isfinite(h_scal[e_steps % 2].numpy()).all()
-    e2e_value = world * S * L / e2e_s
+    e2e_value = job_throughput(world, S * L, 1e3 * max_over_ranks(e2e_s, dist, dev))
 
     if rank != 0:
         if dist:
