@@ -120,11 +120,11 @@ struct RegisterTwiddles {
   }
 };
 
-template <int K1, int N1, typename Tw>
+template <int K1, int N1, typename Tw, int STRIDE = 1>
 __device__ __forceinline__ void twiddle_store(const float2* y, float2* xw, const Tw& tw) {
   if constexpr (K1 < N1) {
-    xw[K1] = (K1 == 0) ? y[K1] : cmul(y[K1], tw.template get<K1>());
-    twiddle_store<K1 + 1, N1>(y, xw, tw);
+    xw[K1 * STRIDE] = (K1 == 0) ? y[K1] : cmul(y[K1], tw.template get<K1>());
+    twiddle_store<K1 + 1, N1, Tw, STRIDE>(y, xw, tw);
   }
 }
 
@@ -138,6 +138,47 @@ __device__ __forceinline__ void twiddle_store(const float2* y, float2* xw, const
 // (and, for T = 8, consecutive groups' buffers start half a bank row apart), so the
 // exchange is conflict-free and its addresses are a per-thread base plus immediate offsets.
 // `tw.get<k1>()` = w_W^(j k1) (forward sign).  INV selects the unnormalised inverse.
+// Exchange layout with the step-A results transposed (eight threads per line): row k1 of
+// the group's buffer holds Y[0..7][k1] at stride kXRow, so thread j writes Y[j][k1] at
+// xb[k1 kXRow + j] (64-bit stores) and reads its step-C operands Y[0..7][k1] for
+// k1 = j + 8 mc as four 128-bit loads per row.  With kXRow = 10 and group buffers
+// kXGroup(N1) apart (an odd multiple of eight float2) both patterns are conflict-free.
+constexpr int kXRow = 10;
+__host__ __device__ constexpr int kXGroup(int n1) { return n1 * kXRow + 8; }
+
+template <int W, bool INV, typename Tw>
+__device__ __forceinline__ void line_fft_t(float2 (&v)[W / 8], const Tw& tw, float2* xb, int j) {
+  constexpr int N1 = W / 8;
+  constexpr int NC = N1 / 8;
+  float2 y[N1];
+  if constexpr (INV) {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = cconj(v[m]);
+  }
+  dft<N1, 1>(v, y);
+  twiddle_store<0, N1, Tw, kXRow>(y, xb + j, tw);
+  __syncwarp();
+  float2 b[NC][8];
+#pragma unroll
+  for (int mc = 0; mc < NC; ++mc) {
+    const float4* row = reinterpret_cast<const float4*>(xb + (j + 8 * mc) * kXRow);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 f = row[q];
+      b[mc][2 * q] = make_float2(f.x, f.y);
+      b[mc][2 * q + 1] = make_float2(f.z, f.w);
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int mc = 0; mc < NC; ++mc) {
+    float2 X[8];
+    dft<8, 1>(b[mc], X);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[mc + NC * k2] = INV ? cconj(X[k2]) : X[k2];
+  }
+}
+
 template <int W, bool INV, typename Tw, int T = 8>
 __device__ __forceinline__ void line_fft(float2 (&v)[W / T], const Tw& tw, float2* xb, int j) {
   constexpr int N1 = W / T;

@@ -34,8 +34,18 @@
 #ifndef MSP_TWIDDLE_REGISTERS
 #define MSP_TWIDDLE_REGISTERS 1
 #endif
+// In-line exchange with row-major (0) or transposed (1) step-A results.
+#ifndef MSP_TRANSPOSED_EXCHANGE
+#define MSP_TRANSPOSED_EXCHANGE 1
+#endif
 
 namespace msp {
+
+#if MSP_TRANSPOSED_EXCHANGE
+#define LINE_FFT line_fft_t
+#else
+#define LINE_FFT line_fft
+#endif
 
 template <int W>
 struct Geo {
@@ -68,8 +78,12 @@ struct ColIdx {
 
 // Dynamic shared memory: the wave, then one exchange buffer per eight-thread line group.
 template <int W>
+__host__ __device__ constexpr int exchange_floats2() {
+  return MSP_TRANSPOSED_EXCHANGE ? kXGroup(W / 8) : 8 * (W / 8 + 1);
+}
+template <int W>
 constexpr size_t position_smem_bytes() {
-  return ((size_t)W * W + (size_t)(W / 2) * 8 * (W / 8 + 1)) * sizeof(float2);
+  return ((size_t)W * W + (size_t)(W / 2) * exchange_floats2<W>()) * sizeof(float2);
 }
 
 // CPLX: transmission mode (the paper's complex slices o_l).  The stash then holds the wave
@@ -89,7 +103,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   const int grp = tid >> 3;
   const size_t WW = (size_t)W * W;
   const size_t plane = (size_t)p.Ny * p.Nx;
-  float2* xb = sm + W * W + grp * 8 * (N1 + 1);   // this group's exchange buffer
+  float2* xb = sm + W * W + grp * exchange_floats2<W>();   // this group's exchange buffer
 
   if (tid < N1 * 8) {   // evaluated in double, rounded once
     const int k1 = tid >> 3, jj = tid & 7;
@@ -153,7 +167,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // exit wave
       }
-      line_fft<W, false>(v, tw, xb, j);
+      LINE_FFT<W, false>(v, tw, xb, j);
 #pragma unroll
       for (int m = 0; m < N1; ++m) sm[RowIdx<W>(r, j)(m)] = v[m];
     }
@@ -171,11 +185,11 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           float2 v[N1];
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
-          line_fft<W, false>(v, tw, xb, j);
+          LINE_FFT<W, false>(v, tw, xb, j);
           const float2 hx = s_h1[c];
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], cmul(s_h1[j + 8 * m], hx));
-          line_fft<W, true>(v, tw, xb, j);
+          LINE_FFT<W, true>(v, tw, xb, j);
 #pragma unroll
           for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
         }
@@ -194,7 +208,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           for (int m = 0; m < N1; ++m) t[m] = Tr[j + 8 * m];     // in flight during the transform
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
-          line_fft<W, true>(v, tw, xb, j);
+          LINE_FFT<W, true>(v, tw, xb, j);
           if (CPLX && keep) {
 #pragma unroll
             for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // incident wave
@@ -205,7 +219,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 #pragma unroll
             for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // exit wave
           }
-          line_fft<W, false>(v, tw, xb, j);
+          LINE_FFT<W, false>(v, tw, xb, j);
 #pragma unroll
           for (int m = 0; m < N1; ++m) sm[ra(m)] = v[m];
         }
@@ -225,7 +239,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
-          line_fft<W, false>(v, tw, xb, j);
+          LINE_FFT<W, false>(v, tw, xb, j);
           if (MODE == MODE_FORWARD) {
             float* out = p.I_out + s * WW + c;
 #pragma unroll
@@ -244,7 +258,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               v[m] = make_float2(v[m].x * f, v[m].y * f);
             }
             // chi = F^H R: inverse column transforms now, rows below
-            line_fft<W, true>(v, tw, xb, j);
+            LINE_FFT<W, true>(v, tw, xb, j);
 #pragma unroll
             for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
           }
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         }
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
-        line_fft<W, true>(v, tw, xb, j);   // v = chi_l (row r)
+        LINE_FFT<W, true>(v, tw, xb, j);   // v = chi_l (row r)
         if (grad_here) {
           if (CPLX) {
             // dL/dconj(o_l) on the window: conj(psi_in,l) o chi_l
@@ -319,7 +333,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               for (int m = 0; m < N1; ++m) dp[j + 8 * m] = cadd(dp[j + 8 * m], v[m]);
             }
           } else {
-            line_fft<W, false>(v, tw, xb, j);
+            LINE_FFT<W, false>(v, tw, xb, j);
 #pragma unroll
             for (int m = 0; m < N1; ++m) sm[ra(m)] = v[m];
           }
@@ -336,11 +350,11 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         float2 v[N1];
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
-        line_fft<W, false>(v, tw, xb, j);
+        LINE_FFT<W, false>(v, tw, xb, j);
         const float2 hx = s_h1[c];
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], cmul(s_h1[j + 8 * m], hx));
-        line_fft<W, true>(v, tw, xb, j);
+        LINE_FFT<W, true>(v, tw, xb, j);
 #pragma unroll
         for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
       }
