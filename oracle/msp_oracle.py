@@ -360,6 +360,170 @@ def residual_conditioning(geom: dict, probe, pos, i_meas, V=None, T=None, band=0
 
 
 # ----------------------------------------------------------------------------
+# Algorithm 2 (Sparse Matrix Decomposition, Sec. 3.4) on the paper's circulant model:
+# an N x N object, the probe shifted cyclically, dense N^2 x N^2 matrices, row-major vec.
+# ----------------------------------------------------------------------------
+
+def dft_matrix_2d(n: int) -> np.ndarray:
+    """F_2D = F_1 (x) F_1, the unnormalised 2-D DFT of a row-major vectorised n x n array (Sec. 2.2)."""
+    f1 = np.exp(-2j * np.pi * np.outer(np.arange(n), np.arange(n)) / n)
+    return np.kron(f1, f1)
+
+
+def propagator_matrix(geom: dict, n: int) -> np.ndarray:
+    """G = F^-1 diag(vec H) F (Sec. 2.2)."""
+    F = dft_matrix_2d(n)
+    h = fresnel_propagator(n, geom["pixel_A"], geom["wavelength_A"], geom["dz_A"]).ravel()
+    return (np.conj(F).T / n ** 2) @ (h[:, None] * F)
+
+
+def probe_matrix(probe, shifts) -> np.ndarray:
+    """P = (p^1, ..., p^S), p^s = vec of the probe shifted cyclically by shift s (Sec. 2.1)."""
+    return np.stack([np.roll(np.asarray(probe, dtype=np.complex128), (int(a), int(b)), axis=(0, 1)).ravel()
+                     for a, b in np.asarray(shifts)], axis=1)
+
+
+def measurement_matrix(i_meas) -> np.ndarray:
+    """I = (i^1, ..., i^S) with i^s = vec I^s."""
+    i_meas = np.asarray(i_meas, dtype=np.float64)
+    return i_meas.reshape(i_meas.shape[0], -1).T
+
+
+def transfer_matrix(G, o) -> np.ndarray:
+    """A_M = O_M prod_m G O_m (Eq. exit_wave_mslices) from the slice diagonals o [M][N^2]."""
+    A = np.diag(o[0])
+    for m in range(1, len(o)):
+        A = o[m][:, None] * (G @ A)
+    return A
+
+
+def shift_operator_norm(probe) -> float:
+    """||P||_2 taken as max_k |(F p)_k|.  P x is the cyclic convolution of p with the shifts'
+    impulses weighted by x, so ||P||_2 <= ||C(p)||_2 = max |F p|, with equality when the shifts
+    are all N^2 cyclic shifts (the paper's full raster scan, Table 1)."""
+    return float(np.max(np.abs(np.fft.fft2(np.asarray(probe, dtype=np.complex128)))))
+
+
+def matrix_objective_residual(A, F, P, I):
+    """U = F A P, the objective 1/2 sum (sqrt(I) - |U|)^2 of Eq. (Opt_Prob_Matrix) and
+    R = (|U| - sqrt(I)) o U/|U| = U - sqrt(I) U/|U|, the fraction taken as 0 where
+    |U| <= 1e-5 times the RMS measured amplitude sqrt(mean I)."""
+    U = F @ A @ P
+    amp = np.abs(U)
+    root = np.sqrt(I)
+    objective = 0.5 * float(np.sum((root - amp) ** 2))
+    thr = ZERO_RULE_TAU * float(np.sqrt(np.mean(I)))
+    ph = np.zeros_like(U)
+    nz = amp > thr
+    ph[nz] = U[nz] / amp[nz]
+    return objective, U - root * ph
+
+
+def matrix_step(A, F, P, I, mu):
+    """One gradient step of Eq. (Opt_Prob_Matrix):
+    A <- A - mu F^H ((|FAP| - sqrt(I)) o FAP/|FAP|) P^H.  Returns (new A, objective before)."""
+    objective, R = matrix_objective_residual(A, F, P, I)
+    return A - mu * (np.conj(F).T @ R @ np.conj(P).T), objective
+
+
+def matrix_step_size(probe) -> float:
+    """mu = 1 / (||F_2D||^2 ||P||^2) = 1 / (N^2 ||P||^2) (Sec. 3.4)."""
+    n2 = np.asarray(probe).size
+    return 1.0 / (n2 * shift_operator_norm(probe) ** 2)
+
+
+def prefix_suffix(G, o, layer):
+    """R_l = prod_{m > l} O_m G and S_l = prod_{m < l} G O_m (Eq. Layerwise_Prefix_Suffix), dense."""
+    n = G.shape[0]
+    R = np.eye(n, dtype=complex)
+    for m in range(layer + 1, len(o)):
+        R = o[m][:, None] * (G @ R)
+    S = np.eye(n, dtype=complex)
+    for m in range(0, layer):
+        S = G @ (o[m][:, None] * S)
+    return R, S
+
+
+def decomposition_gradient(Ahat, G, o, lam, layer):
+    """diag of lam R_l^H (lam R_l O_l S_l - Ahat) S_l^H, the gradient of
+    1/2 ||Ahat - lam R_l O_l S_l||_F^2 with respect to conj(diag O_l) (Eq. Prox_Min)."""
+    R, S = prefix_suffix(G, o, layer)
+    M = lam * ((R * o[layer][None, :]) @ S) - Ahat
+    return lam * np.sum((np.conj(R).T @ M) * np.conj(S), axis=1)
+
+
+def decomposition_step_size(o, lam, layer) -> float:
+    """mu = 1/c with c = (lam prod_{m != l} max|o_m|)^2 >= (lam ||R_l|| ||S_l||)^2, since every
+    G_m is unitary and ||O_m||_2 = max |o_m|."""
+    bound = abs(lam) * float(np.prod([np.max(np.abs(o[m])) for m in range(len(o)) if m != layer]))
+    return 1.0 / bound ** 2 if bound > 0 else 0.0
+
+
+def project_diagonal_unit(x) -> np.ndarray:
+    """The projection P of Eq. (Prox_Min): keep the diagonal, scale it to unit Frobenius norm."""
+    nrm = float(np.linalg.norm(x))
+    return x / nrm if nrm > 0 else x
+
+
+def decomposition_sweep(Ahat, G, o, lam):
+    """One pass of the layer loop of Algorithm 2: every slice takes the proximal step of
+    Eq. (Prox_Min) with the prefix, suffix and lambda of iteration t (all slices at O^t).
+    Returns (new slices, objective 1/2 ||Ahat - lam A(O^t)||_F^2)."""
+    objective = 0.5 * float(np.sum(np.abs(Ahat - lam * transfer_matrix(G, o)) ** 2))
+    new = []
+    for layer in range(len(o)):
+        g = decomposition_gradient(Ahat, G, o, lam, layer)
+        new.append(project_diagonal_unit(o[layer] - decomposition_step_size(o, lam, layer) * g))
+    return new, objective
+
+
+def update_lambda(Ahat, Atilde) -> float:
+    """lambda = Re Tr(Ahat^H Atilde) / Tr(Atilde^H Atilde) (Eq. Update Lambda), the real
+    least-squares scale of Atilde."""
+    den = float(np.real(np.vdot(Atilde.ravel(), Atilde.ravel())))
+    return float(np.real(np.vdot(Ahat.ravel(), Atilde.ravel()))) / den if den > 0 else 0.0
+
+
+def decomposition_update(Ahat, G, o, lam):
+    """Layer sweep, lambda update and A^{t+1} = lambda^{t+1} A(O^{t+1}) (Algorithm 2, one iteration
+    after the matrix estimate).  Returns (new slices, new lambda, new A, objective before)."""
+    new, objective = decomposition_sweep(Ahat, G, o, lam)
+    At = transfer_matrix(G, new)
+    lam_new = update_lambda(Ahat, At)
+    return new, lam_new, lam_new * At, objective
+
+
+def final_slices(o, lam):
+    """The returned slices lambda^(1/M) O_m (principal complex root, so their product carries lambda)."""
+    root = complex(lam) ** (1.0 / len(o))
+    return [root * x for x in o]
+
+
+def sparse_decomposition(geom: dict, probe, shifts, i_meas, iterations: int, matrix_steps: int = 1, o0=None):
+    """Algorithm 2 from slices o0 (default: all ones) and lambda^0 = 1: per iteration, `matrix_steps`
+    gradient steps on Eq. (Opt_Prob_Matrix), then the decomposition update.  Returns
+    (slices lambda^(1/M) O_m, lambda, matrix-objective history, decomposition-objective history)."""
+    n = np.asarray(probe).shape[0]
+    M = geom["n_slices"]
+    F = dft_matrix_2d(n)
+    G = propagator_matrix(geom, n)
+    P = probe_matrix(probe, shifts)
+    I = measurement_matrix(i_meas)
+    mu = matrix_step_size(probe)
+    o = [np.ones(n * n, dtype=complex) for _ in range(M)] if o0 is None else [np.asarray(x, dtype=complex).ravel() for x in o0]
+    lam = 1.0
+    A = lam * transfer_matrix(G, o)
+    hist_m, hist_d = [], []
+    for _ in range(iterations):
+        for _ in range(matrix_steps):
+            A, obj = matrix_step(A, F, P, I, mu)
+            hist_m.append(obj)
+        o, lam, A, obj = decomposition_update(A, G, o, lam)
+        hist_d.append(obj)
+    return final_slices(o, lam), lam, hist_m, hist_d
+
+
+# ----------------------------------------------------------------------------
 # Error metrics, Sec. 5.1
 # ----------------------------------------------------------------------------
 
