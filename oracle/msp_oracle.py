@@ -408,7 +408,7 @@ def matrix_objective_residual(A, F, P, I):
     """U = F A P, the objective 1/2 sum (sqrt(I) - |U|)^2 of Eq. (Opt_Prob_Matrix) and
     R = (|U| - sqrt(I)) o U/|U| = U - sqrt(I) U/|U|, the fraction taken as 0 where
     |U| <= 1e-5 times the RMS measured amplitude sqrt(mean I)."""
-    U = F @ A @ P
+    U = F @ (A @ P)
     amp = np.abs(U)
     root = np.sqrt(I)
     objective = 0.5 * float(np.sum((root - amp) ** 2))

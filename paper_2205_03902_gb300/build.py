@@ -1,6 +1,6 @@
 """In-tree build of libmsp.so for sm_103a (nvcc, no CMake).
 
-The two translation units compile in parallel; the shared library lands in
+The translation units compile in parallel; the shared library lands in
 `paper_2205_03902_gb300/lib/`, object files in `_build/` at the repository root.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libmsp.so")
-SOURCES = ["msp_position.cu", "msp_position_cluster.cu", "msp_api.cu", "msp_noalloc.cu"]
+SOURCES = ["msp_position.cu", "msp_position_cluster.cu", "msp_api.cu", "msp_noalloc.cu", "msp_smd.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -31,7 +31,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "msp.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -1,0 +1,1120 @@
+// msp_smd.cu -- Sparse Matrix Decomposition (Sec. 3.4, Algorithm 2) on sm_103a.
+//
+// Algorithm 2 alternates two problems on the paper's full-field model (an N x N
+// object, the probe shifted cyclically, dense N^2 x N^2 matrices):
+//
+//   matrix estimate   A <- A - mu F^H ((|FAP| - sqrt I) o FAP/|FAP|) P^H
+//                     Two dense complex contractions (A P and the rank-S update by P^H)
+//                     run in `cgemm_kernel`; between them `farfield_kernel` takes every
+//                     column of A P through the 2-D DFT, forms the amplitude-flow
+//                     residual and takes it back (F^H), one CTA per column.
+//   decomposition     The proximal step of every slice needs diag(R_l^H M S_l^H) with
+//                     M = lambda A(o) - Ahat.  Column j of A(o) is the multislice exit
+//                     wave of a unit impulse at object pixel j, S_l e_j is the wave that
+//                     impulse makes incident on slice l and R_l^H m_j is the adjoint wave
+//                     at slice l, so the diagonal is sum_j (R_l^H m_j) o conj(S_l e_j):
+//                     one forward and one adjoint multislice pass per column, with the
+//                     per-slice products summed over columns (`grad_kernel`).  No dense
+//                     R_l or S_l is formed.  `transfer_kernel` rebuilds A(o) column by
+//                     column for the lambda update (Eq. Update Lambda) and for A^{t+1}.
+//
+// N is not a power of two in the paper's own setting (40 x 40 detector and scan,
+// Table 1), so the 2-D DFT of an N x N image is computed directly, as two products
+// with the N x N twiddle matrix W (Y = W X W), in shared memory: each thread owns a
+// 2 x 4 block of the product and reads rows of the left operand and four-wide rows of
+// W.  Every pass stores its result transposed, so after the two passes of a 2-D DFT
+// the image is back in row-major order and every elementwise step (propagator, slice,
+// residual) works on the same 8 pixels per thread, held in registers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "msp.h"
+#include "msp_smd.h"
+
+namespace msp {
+
+msp_status set_last_error(msp_status s, const std::string& m);   // shown by msp_last_error_message()
+void count_launches(int n);
+
+namespace smd {
+
+constexpr double kZeroTau = 1e-5;   // zero rule: |U| <= 1e-5 sqrt(mean I) counts as U = 0
+constexpr int kMaxSlices = 5;
+constexpr int kPartSlots = 4096;    // FP64 partial sums per reduction
+
+// scalar slots in the workspace
+enum { S_OBJ = 0, S_MU = 1, S_SPEC = 2, S_SUMI = 3, S_THR2 = 4, S_DOBJ = 5, S_MAXO = 8 };
+
+__host__ __device__ constexpr int ld_of(int N) { return N + 2; }   // padded row of an image buffer
+__host__ __device__ constexpr int threads_of(int N) { return N * N / 8; }
+__host__ __device__ constexpr int max_slices(int N) { return N == 64 ? 3 : kMaxSlices; }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+
+// acc += d * w (CONJ: d * conj(w))
+template <bool CONJ>
+__device__ __forceinline__ void cmac(float2& acc, float2 d, float2 w) {
+  if (!CONJ) {
+    acc.x = fmaf(d.x, w.x, acc.x);
+    acc.x = fmaf(-d.y, w.y, acc.x);
+    acc.y = fmaf(d.x, w.y, acc.y);
+    acc.y = fmaf(d.y, w.x, acc.y);
+  } else {
+    acc.x = fmaf(d.x, w.x, acc.x);
+    acc.x = fmaf(d.y, w.y, acc.x);
+    acc.y = fmaf(d.y, w.x, acc.y);
+    acc.y = fmaf(-d.x, w.y, acc.y);
+  }
+}
+
+// W[k][c] = exp(-2 pi i (k c mod N) / N), unpadded rows, computed in double and rounded once.
+template <int N>
+__device__ void fill_twiddles(float2* Wt) {
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const int m = ((e / N) * (e % N)) % N;
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)N, &s, &c);
+    Wt[e] = make_float2((float)c, (float)s);
+  }
+}
+
+// One pass: a = rows r0, r0+1 and columns c0..c0+3 of D W (CONJ: D conj(W)).
+template <int N, bool CONJ>
+__device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const float2* __restrict__ Wt,
+                                         float2 (&a)[2][4], int r0, int c0) {
+  constexpr int LD = ld_of(N);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) a[i][j] = make_float2(0.f, 0.f);
+  const float2* d0 = D + r0 * LD;
+  const float2* d1 = d0 + LD;
+  const float2* wp = Wt + c0;
+#pragma unroll 4
+  for (int k = 0; k < N; k += 2) {
+    const float4 x0 = *reinterpret_cast<const float4*>(d0 + k);
+    const float4 x1 = *reinterpret_cast<const float4*>(d1 + k);
+    const float4 wa = *reinterpret_cast<const float4*>(wp + k * N);
+    const float4 wb = *reinterpret_cast<const float4*>(wp + k * N + 2);
+    const float4 wc = *reinterpret_cast<const float4*>(wp + (k + 1) * N);
+    const float4 wd = *reinterpret_cast<const float4*>(wp + (k + 1) * N + 2);
+    const float2 w0[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                          make_float2(wb.z, wb.w)};
+    const float2 w1[4] = {make_float2(wc.x, wc.y), make_float2(wc.z, wc.w), make_float2(wd.x, wd.y),
+                          make_float2(wd.z, wd.w)};
+    const float2 l00 = make_float2(x0.x, x0.y), l01 = make_float2(x0.z, x0.w);
+    const float2 l10 = make_float2(x1.x, x1.y), l11 = make_float2(x1.z, x1.w);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      cmac<CONJ>(a[0][j], l00, w0[j]);
+      cmac<CONJ>(a[1][j], l10, w0[j]);
+      cmac<CONJ>(a[0][j], l01, w1[j]);
+      cmac<CONJ>(a[1][j], l11, w1[j]);
+    }
+  }
+}
+
+// O[c0 + j][r0 + i] = a[i][j]: the transposed store that follows every pass.
+template <int N>
+__device__ __forceinline__ void store_t(float2* O, const float2 (&a)[2][4], int r0, int c0) {
+  constexpr int LD = ld_of(N);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    *reinterpret_cast<float4*>(O + (c0 + j) * LD + r0) = make_float4(a[0][j].x, a[0][j].y, a[1][j].x, a[1][j].y);
+}
+
+// 2-D DFT of the image whose pixels (y, x) = (c0 + j, r0 + i) are held in v (the pixels
+// this thread owns); the result comes back in v at the same pixels.  INV: conjugate kernel
+// (F^H, unnormalised).  Uses X and Y as scratch; begins and ends with all threads free to
+// overwrite X.
+template <int N, bool INV>
+__device__ __forceinline__ void dft2(float2 (&v)[2][4], float2* X, float2* Y, const float2* Wt, int r0, int c0) {
+  store_t<N>(X, v, r0, c0);
+  __syncthreads();
+  dft_pass<N, INV>(X, Wt, v, r0, c0);
+  store_t<N>(Y, v, r0, c0);
+  __syncthreads();
+  dft_pass<N, INV>(Y, Wt, v, r0, c0);
+}
+
+__device__ __forceinline__ int owned(int N, int r0, int c0, int i, int j) { return (c0 + j) * N + r0 + i; }
+
+// v <- G v (ADJ: G^H v), G = F^-1 diag(h) F; h carries the 1/N^2 of F^-1.
+template <int N, bool ADJ>
+__device__ __forceinline__ void propagate(float2 (&v)[2][4], float2* X, float2* Y, const float2* Wt,
+                                          const float2* __restrict__ h, int r0, int c0) {
+  dft2<N, false>(v, X, Y, Wt, r0, c0);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 hv = __ldg(&h[owned(N, r0, c0, i, j)]);
+      v[i][j] = ADJ ? cmulc(v[i][j], hv) : cmul(v[i][j], hv);
+    }
+  dft2<N, true>(v, X, Y, Wt, r0, c0);
+}
+
+// Fixed-order FP64 block sum (any block size); every thread receives the total.
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += sh[i];
+    sh[blockDim.x] = t;
+  }
+  __syncthreads();
+  const double t = sh[blockDim.x];
+  __syncthreads();
+  return t;
+}
+
+template <int N>
+constexpr size_t image_bytes() { return (size_t)N * ld_of(N) * sizeof(float2); }
+
+// ---------------------------------------------------------------------------
+// per-column kernels
+// ---------------------------------------------------------------------------
+
+// Matrix step, between the two contractions: for every column s of A P (summed over its
+// `splits` partial products), U = F (A P)_s, the objective term and R = U - sqrt(I) U/|U|
+// (U where |U|^2 <= thr2), then C_s = F^H R written over partial 0.
+template <int N>
+__global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int splits, size_t split_stride,
+                                                                 const float* __restrict__ I, int S,
+                                                                 const double* __restrict__ scal,
+                                                                 double* __restrict__ obj_part) {
+  extern __shared__ float4 smem4[];
+  float2* X = reinterpret_cast<float2*>(smem4);
+  float2* Y = X + N * ld_of(N);
+  float2* Wt = Y + N * ld_of(N);
+  double* red = reinterpret_cast<double*>(Wt + N * N);
+  constexpr int n2 = N * N;
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
+  fill_twiddles<N>(Wt);
+  const float thr2 = (float)scal[S_THR2];
+  double obj = 0.0;
+  for (int s = blockIdx.x; s < S; s += gridDim.x) {
+    float2 v[2][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const size_t e = (size_t)s * n2 + owned(N, r0, c0, 0, j);
+      float4 acc = *reinterpret_cast<const float4*>(BC + e);
+      for (int z = 1; z < splits; ++z) {
+        const float4 q = *reinterpret_cast<const float4*>(BC + z * split_stride + e);
+        acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
+      }
+      v[0][j] = make_float2(acc.x, acc.y);
+      v[1][j] = make_float2(acc.z, acc.w);
+    }
+    dft2<N, false>(v, X, Y, Wt, r0, c0);
+    float o = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float meas = __ldg(&I[(size_t)s * n2 + owned(N, r0, c0, i, j)]);
+        const float2 u = v[i][j];
+        const float a2 = fmaf(u.x, u.x, u.y * u.y);
+        const float a = sqrtf(a2);
+        const float rt = sqrtf(meas);
+        o = fmaf(rt - a, rt - a, o);
+        const float f = (a2 > thr2) ? 1.f - rt / a : 1.f;
+        v[i][j] = make_float2(u.x * f, u.y * f);
+      }
+    obj += (double)o;
+    dft2<N, true>(v, X, Y, Wt, r0, c0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      *reinterpret_cast<float4*>(BC + (size_t)s * n2 + owned(N, r0, c0, 0, j)) =
+          make_float4(v[0][j].x, v[0][j].y, v[1][j].x, v[1][j].y);
+  }
+  const double tot = block_sum(obj, red);
+  if (threadIdx.x == 0) obj_part[blockIdx.x] = 0.5 * tot;
+}
+
+// Multislice pass of a unit impulse at object pixel `col` through the slices o (M of them):
+// v ends as column col of A(o) = O_M G ... G O_1; incident waves on slices 1..M-1 go to stash.
+template <int N, bool STASH>
+__device__ __forceinline__ void impulse_forward(float2 (&v)[2][4], int col, int M, const float2* __restrict__ o,
+                                                const float2* __restrict__ h, float2* X, float2* Y, const float2* Wt,
+                                                float2* stash, int r0, int c0) {
+  constexpr int n2 = N * N;
+  const float2 o0 = __ldg(&o[col]);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[i][j] = owned(N, r0, c0, i, j) == col ? o0 : make_float2(0.f, 0.f);
+  for (int m = 1; m < M; ++m) {
+    propagate<N, false>(v, X, Y, Wt, h, r0, c0);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = owned(N, r0, c0, i, j);
+        if (STASH) stash[(m - 1) * n2 + e] = v[i][j];
+        v[i][j] = cmul(v[i][j], __ldg(&o[(size_t)m * n2 + e]));
+      }
+  }
+}
+
+// Decomposition gradient: for every column j, m_j = lambda A(o)_j - Ahat_j and, for every
+// slice l, the column's share (R_l^H m_j) o conj(S_l e_j) of diag(R_l^H M S_l^H).  The
+// per-CTA sums go to gpart[cta][l][k]; the objective 1/2 sum |m_j|^2 to obj_part[cta].
+template <int N, int MAXM>
+__global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __restrict__ A,
+                                                             const float2* __restrict__ o,
+                                                             const float2* __restrict__ h,
+                                                             const double* __restrict__ lam_p, int M,
+                                                             float2* __restrict__ gpart,
+                                                             double* __restrict__ obj_part) {
+  extern __shared__ float4 smem4[];
+  float2* X = reinterpret_cast<float2*>(smem4);
+  float2* Y = X + N * ld_of(N);
+  float2* Wt = Y + N * ld_of(N);
+  float2* stash = Wt + N * N;                                      // [M-1][N^2], thread-owned pixels
+  double* red = reinterpret_cast<double*>(stash + (MAXM - 1) * N * N);
+  constexpr int n2 = N * N;
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
+  fill_twiddles<N>(Wt);
+  const float lam = (float)lam_p[0];
+  float2 acc[MAXM][2][4];
+#pragma unroll
+  for (int q = 0; q < MAXM; ++q)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[q][i][j] = make_float2(0.f, 0.f);
+  double obj = 0.0;
+  for (int col = blockIdx.x; col < n2; col += gridDim.x) {
+    float2 v[2][4];
+    impulse_forward<N, true>(v, col, M, o, h, X, Y, Wt, stash, r0, c0);
+    const float2* Aj = A + (size_t)col * n2;
+    float ob = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float4 a = *reinterpret_cast<const float4*>(Aj + owned(N, r0, c0, 0, j));
+      const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
+      v[0][j] = make_float2(fmaf(lam, v[0][j].x, -a0.x), fmaf(lam, v[0][j].y, -a0.y));
+      v[1][j] = make_float2(fmaf(lam, v[1][j].x, -a1.x), fmaf(lam, v[1][j].y, -a1.y));
+      ob = fmaf(v[0][j].x, v[0][j].x, fmaf(v[0][j].y, v[0][j].y, ob));
+      ob = fmaf(v[1][j].x, v[1][j].x, fmaf(v[1][j].y, v[1][j].y, ob));
+    }
+    obj += (double)ob;
+    for (int l = M - 1;; --l) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = owned(N, r0, c0, i, j);
+          float2 g;
+          if (l > 0)
+            g = cmulc(v[i][j], stash[(l - 1) * n2 + e]);
+          else
+            g = (e == col) ? v[i][j] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < MAXM; ++q)
+            if (q == l) {
+              acc[q][i][j].x += g.x;
+              acc[q][i][j].y += g.y;
+            }
+        }
+      if (l == 0) break;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[i][j] = cmulc(v[i][j], __ldg(&o[(size_t)l * n2 + owned(N, r0, c0, i, j)]));
+      propagate<N, true>(v, X, Y, Wt, h, r0, c0);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < MAXM; ++q)
+    if (q < M)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<float4*>(gpart + ((size_t)blockIdx.x * M + q) * n2 + owned(N, r0, c0, 0, j)) =
+            make_float4(acc[q][0][j].x, acc[q][0][j].y, acc[q][1][j].x, acc[q][1][j].y);
+  const double tot = block_sum(obj, red);
+  if (threadIdx.x == 0) obj_part[blockIdx.x] = 0.5 * tot;
+}
+
+// A(o) column by column, written as scale * A(o) into A.  HAVE_AHAT: A holds Ahat on entry;
+// per CTA, Re <Ahat_j, A(o)_j> and ||A(o)_j||^2 are summed for the lambda update.
+template <int N, bool HAVE_AHAT>
+__global__ void __launch_bounds__(threads_of(N)) transfer_kernel(float2* A, const float2* __restrict__ o,
+                                                                 const float2* __restrict__ h, int M, float scale,
+                                                                 double* __restrict__ dot_part,
+                                                                 double* __restrict__ nrm_part) {
+  extern __shared__ float4 smem4[];
+  float2* X = reinterpret_cast<float2*>(smem4);
+  float2* Y = X + N * ld_of(N);
+  float2* Wt = Y + N * ld_of(N);
+  double* red = reinterpret_cast<double*>(Wt + N * N);
+  constexpr int n2 = N * N;
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
+  fill_twiddles<N>(Wt);
+  double dot = 0.0, nrm = 0.0;
+  for (int col = blockIdx.x; col < n2; col += gridDim.x) {
+    float2 v[2][4];
+    impulse_forward<N, false>(v, col, M, o, h, X, Y, Wt, nullptr, r0, c0);
+    float2* Aj = A + (size_t)col * n2;
+    float d = 0.f, q = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float4* p = reinterpret_cast<float4*>(Aj + owned(N, r0, c0, 0, j));
+      if (HAVE_AHAT) {
+        const float4 a = *p;
+        d = fmaf(a.x, v[0][j].x, fmaf(a.y, v[0][j].y, d));
+        d = fmaf(a.z, v[1][j].x, fmaf(a.w, v[1][j].y, d));
+        q = fmaf(v[0][j].x, v[0][j].x, fmaf(v[0][j].y, v[0][j].y, q));
+        q = fmaf(v[1][j].x, v[1][j].x, fmaf(v[1][j].y, v[1][j].y, q));
+      }
+      *p = make_float4(scale * v[0][j].x, scale * v[0][j].y, scale * v[1][j].x, scale * v[1][j].y);
+    }
+    dot += (double)d;
+    nrm += (double)q;
+  }
+  if (HAVE_AHAT) {
+    const double td = block_sum(dot, red);
+    const double tn = block_sum(nrm, red);
+    if (threadIdx.x == 0) {
+      dot_part[blockIdx.x] = td;
+      nrm_part[blockIdx.x] = tn;
+    }
+  }
+}
+
+// Matrix-step set-up (one CTA): max_k |(F p)_k|^2, the sum of I from its partials, the
+// squared zero-rule threshold and mu.
+template <int N>
+__global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __restrict__ probe,
+                                                              const double* __restrict__ sum_part, int n_part,
+                                                              double count, double step, double* scal,
+                                                              double* mu_out) {
+  extern __shared__ float4 smem4[];
+  float2* X = reinterpret_cast<float2*>(smem4);
+  float2* Y = X + N * ld_of(N);
+  float2* Wt = Y + N * ld_of(N);
+  double* red = reinterpret_cast<double*>(Wt + N * N);
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
+  fill_twiddles<N>(Wt);
+  float2 v[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[i][j] = probe[owned(N, r0, c0, i, j)];
+  dft2<N, false>(v, X, Y, Wt, r0, c0);
+  double mx = 0.0;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mx = fmax(mx, (double)v[i][j].x * v[i][j].x + (double)v[i][j].y * v[i][j].y);
+  red[t] = mx;
+  __syncthreads();
+  if (t == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) m = fmax(m, red[i]);
+    double s = 0.0;
+    for (int i = 0; i < n_part; ++i) s += sum_part[i];
+    scal[S_SPEC] = m;
+    scal[S_SUMI] = s;
+    scal[S_THR2] = kZeroTau * kZeroTau * s / count;
+    const double mu = step > 0.0 ? step : (m > 0.0 ? 1.0 / ((double)(N * N) * m) : 0.0);
+    scal[S_MU] = mu;
+    if (mu_out) mu_out[0] = mu;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// dense complex contraction (FP32, SIMT)
+// ---------------------------------------------------------------------------
+// C_z = A[:, K_z] op(B)[K_z, :] for the K-range K_z of blockIdx.z.  A: M x K column-major.
+// op(B) = B (K x N column-major) or, with B_CONJ_T, B^H for B stored N x K column-major.
+// C: M x N column-major, partial z at C + z * c_stride.  64 x 64 tile per CTA, 256 threads,
+// each a 4 x 4 block (rows ty*4.., columns tx + 16 c); K in steps of 8, double-buffered.
+constexpr int GBM = 64, GBN = 64, GBK = 8;
+
+template <bool B_CONJ_T>
+__global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K, int k_chunk, const float2* __restrict__ A,
+                                                    size_t lda, const float2* __restrict__ B, size_t ldb,
+                                                    float2* __restrict__ C, size_t ldc, size_t c_stride) {
+  __shared__ __align__(16) float2 As[2][GBK][GBM];
+  __shared__ __align__(16) float2 Bs[2][GBK][GBN];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int i0 = blockIdx.x * GBM, j0 = blockIdx.y * GBN;
+  const int kb = blockIdx.z * k_chunk;
+  const int ke = min(K, kb + k_chunk);
+  // loader coordinates
+  const int la_k = t >> 5, la_i = (t & 31) * 2;                                   // A: (i, k), 2 rows
+  const int lb_k = B_CONJ_T ? (t >> 5) : (t & 3) * 2, lb_j = B_CONJ_T ? (t & 31) * 2 : (t >> 2);
+  float4 ra, rb;
+  auto load = [&](int k0) {
+    {
+      const int k = k0 + la_k, i = i0 + la_i;
+      if (k < ke && i + 1 < M) {
+        ra = *reinterpret_cast<const float4*>(A + (size_t)k * lda + i);
+      } else {
+        float2 p = make_float2(0.f, 0.f), q = p;
+        if (k < ke && i < M) p = A[(size_t)k * lda + i];
+        ra = make_float4(p.x, p.y, q.x, q.y);
+      }
+    }
+    if (B_CONJ_T) {
+      const int k = k0 + lb_k, j = j0 + lb_j;
+      if (k < ke && j + 1 < N) {
+        rb = *reinterpret_cast<const float4*>(B + (size_t)k * ldb + j);
+      } else {
+        float2 p = make_float2(0.f, 0.f), q = p;
+        if (k < ke && j < N) p = B[(size_t)k * ldb + j];
+        rb = make_float4(p.x, p.y, q.x, q.y);
+      }
+    } else {
+      const int k = k0 + lb_k, j = j0 + lb_j;
+      if (j < N && k + 1 < ke) {
+        rb = *reinterpret_cast<const float4*>(B + (size_t)j * ldb + k);
+      } else {
+        float2 p = make_float2(0.f, 0.f), q = p;
+        if (j < N && k < ke) p = B[(size_t)j * ldb + k];
+        rb = make_float4(p.x, p.y, q.x, q.y);
+      }
+    }
+  };
+  auto store = [&](int buf) {
+    *reinterpret_cast<float4*>(&As[buf][la_k][la_i]) = ra;
+    if (B_CONJ_T) {
+      *reinterpret_cast<float4*>(&Bs[buf][lb_k][lb_j]) = make_float4(rb.x, -rb.y, rb.z, -rb.w);
+    } else {
+      Bs[buf][lb_k][lb_j] = make_float2(rb.x, rb.y);
+      Bs[buf][lb_k + 1][lb_j] = make_float2(rb.z, rb.w);
+    }
+  };
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  if (kb < ke) {
+    load(kb);
+    store(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = kb; k0 < ke; k0 += GBK) {
+    const bool more = k0 + GBK < ke;
+    if (more) load(k0 + GBK);
+#pragma unroll
+    for (int k = 0; k < GBK; ++k) {
+      const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
+      const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4 + 2]);
+      const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
+                           make_float2(a23.z, a23.w)};
+      float2 b[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][k][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac<false>(acc[r][c], a[r], b[c]);
+    }
+    if (more) store(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float2* Cz = C + (size_t)blockIdx.z * c_stride;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = j0 + tx + 16 * c;
+    if (j >= N) continue;
+    const int i = i0 + ty * 4;
+    float2* p = Cz + (size_t)j * ldc + i;
+    if (i + 3 < M) {
+      reinterpret_cast<float4*>(p)[0] = make_float4(acc[0][c].x, acc[0][c].y, acc[1][c].x, acc[1][c].y);
+      reinterpret_cast<float4*>(p)[1] = make_float4(acc[2][c].x, acc[2][c].y, acc[3][c].x, acc[3][c].y);
+    } else {
+      for (int r = 0; r < 4; ++r)
+        if (i + r < M) p[r] = acc[r][c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+// P[:, s] = vec of the probe shifted cyclically by shifts[s] (Sec. 2.1).
+__global__ void probe_matrix_kernel(const float2* __restrict__ probe, const int2* __restrict__ shifts, int N, int S,
+                                    float2* __restrict__ P) {
+  const size_t n2 = (size_t)N * N, total = n2 * S;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n2), k = (int)(e % n2);
+    const int y = k / N, x = k % N;
+    const int2 sh = shifts[s];
+    const int ys = ((sh.x % N) + N) % N, xs = ((sh.y % N) + N) % N;
+    P[e] = probe[((y - ys + N) % N) * N + (x - xs + N) % N];
+  }
+}
+
+// h[ky][kx] = exp(-i pi dz lambda (qy^2 + qx^2)) / N^2, in double, rounded once.
+__global__ void propagator_kernel(float2* __restrict__ h, int N, double dzlam, double dq) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const int ky = e / N, kx = e % N;
+  const double qy = (ky < N / 2 ? ky : ky - N) * dq, qx = (kx < N / 2 ? kx : kx - N) * dq;
+  double s, c;
+  sincospi(-dzlam * (qy * qy + qx * qx), &s, &c);
+  const double inv = 1.0 / ((double)N * N);
+  h[e] = make_float2((float)(c * inv), (float)(s * inv));
+}
+
+// Block partial sums (FP64) of a float array over fixed chunks.
+__global__ void __launch_bounds__(256) sum_part_kernel(const float* __restrict__ x, size_t n, double* __restrict__ part) {
+  __shared__ double sh[257];
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
+  double a = 0.0;
+  for (size_t i = b0 + threadIdx.x; i < b1; i += 256) a += (double)x[i];
+  const double tot = block_sum(a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// out = sum of part[0..n) in order, written to scal[slot] and, if given, to copy.
+__global__ void finish_sum_kernel(const double* __restrict__ part, int n, double* scal, int slot, double* copy) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += part[i];
+  scal[slot] = s;
+  if (copy) copy[0] = s;
+}
+
+// A += -mu * sum_z part_z (the rank-S update of the matrix step), float4 over element pairs.
+__global__ void combine_kernel(float2* __restrict__ A, const float2* __restrict__ part, int splits, size_t stride,
+                               size_t n_pairs, const double* __restrict__ scal) {
+  const float a = (float)(-scal[S_MU]);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n_pairs; e += (size_t)gridDim.x * blockDim.x) {
+    float4 s = reinterpret_cast<const float4*>(part)[e];
+    for (int z = 1; z < splits; ++z) {
+      const float4 q = reinterpret_cast<const float4*>(part + z * stride)[e];
+      s.x += q.x; s.y += q.y; s.z += q.z; s.w += q.w;
+    }
+    float4 v = reinterpret_cast<float4*>(A)[e];
+    v.x = fmaf(a, s.x, v.x);
+    v.y = fmaf(a, s.y, v.y);
+    v.z = fmaf(a, s.z, v.z);
+    v.w = fmaf(a, s.w, v.w);
+    reinterpret_cast<float4*>(A)[e] = v;
+  }
+}
+
+// max_k |o_m[k]| per slice into scal[S_MAXO + m]; the decomposition objective from its
+// partials into scal[S_DOBJ] (and obj_out).
+__global__ void __launch_bounds__(1024) slice_max_kernel(const float2* __restrict__ o, int M, int n2,
+                                                         const double* __restrict__ obj_part, int n_part,
+                                                         double* scal, double* obj_out) {
+  __shared__ float sh[1024];
+  const int t = threadIdx.x;
+  for (int m = 0; m < M; ++m) {
+    float a = 0.f;
+    for (int k = t; k < n2; k += 1024) {
+      const float2 v = o[(size_t)m * n2 + k];
+      a = fmaxf(a, fmaf(v.x, v.x, v.y * v.y));
+    }
+    sh[t] = a;
+    __syncthreads();
+    for (int s = 512; s > 0; s >>= 1) {
+      if (t < s) sh[t] = fmaxf(sh[t], sh[t + s]);
+      __syncthreads();
+    }
+    if (t == 0) scal[S_MAXO + m] = sqrt((double)sh[0]);
+    __syncthreads();
+  }
+  if (t == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n_part; ++i) s += obj_part[i];
+    scal[S_DOBJ] = s;
+    if (obj_out) obj_out[0] = s;
+  }
+}
+
+// g[l][k] = sum_cta gpart[cta][l][k] in CTA order (FP64).
+__global__ void grad_reduce_kernel(const float2* __restrict__ gpart, int n_cta, int Mn2, double2* __restrict__ g) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Mn2) return;
+  double re = 0.0, im = 0.0;
+  for (int c = 0; c < n_cta; ++c) {
+    const float2 v = gpart[(size_t)c * Mn2 + e];
+    re += v.x;
+    im += v.y;
+  }
+  g[e] = make_double2(re, im);
+}
+
+// Proximal step of slice l = blockIdx.x (Eq. Prox_Min): x = o_l - mu_l lambda g_l with
+// mu_l = 1 / (lambda prod_{m != l} max|o_m|)^2, then o_l = x / ||x||_F.
+__global__ void __launch_bounds__(1024) prox_kernel(float2* o, const double2* __restrict__ g, const double* scal,
+                                                    const double* __restrict__ lam_p, int M, int n2) {
+  __shared__ double sh[1025];
+  const int l = blockIdx.x, t = threadIdx.x;
+  const double lam = lam_p[0];
+  double bound = fabs(lam);
+  for (int m = 0; m < M; ++m)
+    if (m != l) bound *= scal[S_MAXO + m];
+  const double mu = bound > 0.0 ? 1.0 / (bound * bound) : 0.0;
+  const double c = mu * lam;
+  float2* ol = o + (size_t)l * n2;
+  const double2* gl = g + (size_t)l * n2;
+  double ss = 0.0;
+  for (int k = t; k < n2; k += blockDim.x) {
+    const double xr = (double)ol[k].x - c * gl[k].x, xi = (double)ol[k].y - c * gl[k].y;
+    ss += xr * xr + xi * xi;
+  }
+  const double nrm2 = block_sum(ss, sh);
+  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 1.0;
+  for (int k = t; k < n2; k += blockDim.x) {
+    const double xr = (double)ol[k].x - c * gl[k].x, xi = (double)ol[k].y - c * gl[k].y;
+    ol[k] = make_float2((float)(xr * inv), (float)(xi * inv));
+  }
+}
+
+// lambda = sum dot / sum nrm (Eq. Update Lambda, real part), partials in CTA order.
+__global__ void lambda_kernel(const double* __restrict__ dot_part, const double* __restrict__ nrm_part, int n,
+                              double* lam) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double d = 0.0, q = 0.0;
+  for (int i = 0; i < n; ++i) {
+    d += dot_part[i];
+    q += nrm_part[i];
+  }
+  lam[0] = q > 0.0 ? d / q : 0.0;
+}
+
+__global__ void scale_kernel(float4* __restrict__ A, size_t n4, const double* __restrict__ lam) {
+  const float s = (float)lam[0];
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n4; e += (size_t)gridDim.x * blockDim.x) {
+    float4 v = A[e];
+    v.x *= s; v.y *= s; v.z *= s; v.w *= s;
+    A[e] = v;
+  }
+}
+
+// out_m = lambda^(1/M) o_m, principal root.
+__global__ void final_slices_kernel(const float2* o, const double* __restrict__ lam, int M, size_t n, float2* out) {
+  const double l = lam[0];
+  const double r = pow(fabs(l), 1.0 / M);
+  double s = 0.0, c = 1.0;
+  if (l < 0.0) sincospi(1.0 / M, &s, &c);
+  const float2 root = make_float2((float)(r * c), (float)(r * s));
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    out[e] = cmul(o[e], root);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+static msp_status fail(msp_status s, const std::string& m) { return set_last_error(s, m); }
+
+#define SMD_CK(call)                                                                                  \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) return fail(MSP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define SMD_LAUNCHED(n)                                                                                    \
+  do {                                                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                                                   \
+    if (e_ != cudaSuccess) return fail(MSP_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    count_launches(n);                                                                                     \
+  } while (0)
+#define SMD_TRY(expr)            \
+  do {                           \
+    msp_status s_ = (expr);      \
+    if (s_ != MSP_OK) return s_; \
+  } while (0)
+
+static bool supported_n(int n) { return n == 16 || n == 24 || n == 32 || n == 40 || n == 48 || n == 64; }
+
+static msp_status check(const msp_smd_geometry* g) {
+  if (!g) return fail(MSP_EINVAL, "geometry is NULL");
+  if (!supported_n(g->n)) return fail(MSP_EUNSUPPORTED, "N = " + std::to_string(g->n) + " (supported: 16, 24, 32, 40, 48, 64)");
+  if (g->n_slices < 1) return fail(MSP_EINVAL, "n_slices < 1");
+  if (g->n_slices > max_slices(g->n))
+    return fail(MSP_EUNSUPPORTED, "at most " + std::to_string(max_slices(g->n)) + " slices for N = " + std::to_string(g->n));
+  if (g->n_pos < 1) return fail(MSP_EINVAL, "n_pos < 1");
+  if (!(std::isfinite(g->wavelength_A) && g->wavelength_A > 0)) return fail(MSP_EINVAL, "wavelength must be > 0");
+  if (!(std::isfinite(g->pixel_A) && g->pixel_A > 0)) return fail(MSP_EINVAL, "pixel size must be > 0");
+  if (!(std::isfinite(g->dz_A) && g->dz_A >= 0)) return fail(MSP_EINVAL, "propagation distance must be >= 0");
+  if ((double)g->n * g->n * g->n_pos > 2.0e9) return fail(MSP_EUNSUPPORTED, "N^2 S too large");
+  return MSP_OK;
+}
+
+// Dynamic shared memory of the per-column kernels.
+static size_t image_smem(int N, int stash_planes, int threads) {
+  return 2 * (size_t)N * ld_of(N) * sizeof(float2) + (size_t)N * N * sizeof(float2) +
+         (size_t)stash_planes * N * N * sizeof(float2) + (size_t)(threads + 1) * sizeof(double);
+}
+
+struct Dev {
+  bool init = false;
+  int sms = 0;
+  int gemm_per_sm = 1;
+};
+static Dev g_dev[64];
+static std::mutex g_mu;
+
+template <int N>
+struct Kernels {
+  static constexpr int T = threads_of(N);
+  static constexpr int MM = max_slices(N);
+  static size_t smem_plain() { return image_smem(N, 0, T); }
+  static size_t smem_grad() { return image_smem(N, MM - 1, T); }
+  static cudaError_t attrs() {
+    cudaError_t e = cudaFuncSetAttribute(farfield_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(grad_kernel<N, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_grad());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transfer_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(transfer_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(setup_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
+    return e;
+  }
+  static int per_sm_plain() {
+    int k = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, farfield_kernel<N>, T, smem_plain());
+    int k2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k2, transfer_kernel<N, true>, T, smem_plain());
+    return std::max(1, std::min(k, k2));
+  }
+  static int per_sm_grad() {
+    int k = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, grad_kernel<N, MM>, T, smem_grad());
+    return std::max(1, k);
+  }
+};
+
+struct PerN {
+  bool init = false;
+  int plain = 1, grad = 1;   // resident CTAs per SM
+};
+static PerN g_pern[64][65];
+
+template <int N>
+static msp_status init_n(int dev, PerN* out) {
+  PerN& p = g_pern[dev][N];
+  if (!p.init) {
+    SMD_CK(Kernels<N>::attrs());
+    p.plain = Kernels<N>::per_sm_plain();
+    p.grad = Kernels<N>::per_sm_grad();
+    p.init = true;
+  }
+  *out = p;
+  return MSP_OK;
+}
+
+static msp_status device(Dev* d, PerN* pn, int N) {
+  int dev = 0;
+  SMD_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(MSP_EUNSUPPORTED, "device index beyond 63");
+  std::lock_guard<std::mutex> lk(g_mu);
+  Dev& D = g_dev[dev];
+  if (!D.init) {
+    SMD_CK(cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev));
+    int k = 0;
+    SMD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, cgemm_kernel<false>, 256, 0));
+    int k2 = 0;
+    SMD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k2, cgemm_kernel<true>, 256, 0));
+    D.gemm_per_sm = std::max(1, std::min(k, k2));
+    D.init = true;
+  }
+  *d = D;
+  switch (N) {
+    case 16: return init_n<16>(dev, pn);
+    case 24: return init_n<24>(dev, pn);
+    case 32: return init_n<32>(dev, pn);
+    case 40: return init_n<40>(dev, pn);
+    case 48: return init_n<48>(dev, pn);
+    case 64: return init_n<64>(dev, pn);
+  }
+  return fail(MSP_EUNSUPPORTED, "N");
+}
+
+// Split of the K range of a contraction over `tiles` output tiles: the split count that
+// minimises waves x K-chunk (the time of the slowest slot), fewest splits on ties.
+struct Split {
+  int splits = 1, chunk = 0;
+};
+static Split choose_split(int tiles, int K, int slots, int max_splits) {
+  Split best;
+  long long best_cost = -1;
+  for (int s = 1; s <= max_splits; ++s) {
+    int chunk = (K + s - 1) / s;
+    chunk = (chunk + GBK - 1) / GBK * GBK;
+    const int real = (K + chunk - 1) / chunk;
+    if (real != s) continue;
+    const long long waves = ((long long)tiles * s + slots - 1) / slots;
+    const long long cost = waves * chunk;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best.splits = s;
+      best.chunk = chunk;
+    }
+  }
+  return best;
+}
+
+static int tiles_of(int M, int N) { return ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN); }
+
+struct Layout {
+  double* scal = nullptr;
+  double* part = nullptr;    // kPartSlots
+  double* part2 = nullptr;   // kPartSlots
+  float2* h = nullptr;
+  float2* P = nullptr;
+  float2* BC = nullptr;      // splits1 * n2 * S
+  float2* U = nullptr;       // splits2 * n2 * n2 (rank-S update partials)
+  float2* gpart = nullptr;   // grid_grad * M * n2
+  double2* gsum = nullptr;   // M * n2
+  Split s1, s2;
+  int grid_plain = 1, grid_grad = 1, grid_ff = 1;
+  size_t bytes = 0;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, char* base) {
+  Layout w;
+  const size_t n2 = (size_t)g->n * g->n, S = g->n_pos, M = g->n_slices;
+  const int slots = d.gemm_per_sm * d.sms;
+  w.s1 = choose_split(tiles_of((int)n2, (int)S), (int)n2, slots, 16);
+  w.s2 = choose_split(tiles_of((int)n2, (int)n2), (int)S, slots, 4);
+  const size_t cap = kPartSlots;
+  w.grid_plain = (int)std::min({n2, (size_t)pn.plain * d.sms, cap});
+  w.grid_grad = (int)std::min({n2, (size_t)pn.grad * d.sms, cap});
+  w.grid_ff = (int)std::min({S, (size_t)pn.plain * d.sms, cap});
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+  w.scal = (double*)take(32 * sizeof(double));
+  w.part = (double*)take(kPartSlots * sizeof(double));
+  w.part2 = (double*)take(kPartSlots * sizeof(double));
+  w.h = (float2*)take(n2 * sizeof(float2));
+  w.P = (float2*)take(n2 * S * sizeof(float2));
+  w.BC = (float2*)take((size_t)w.s1.splits * n2 * S * sizeof(float2));
+  w.U = (float2*)take(w.s2.splits > 1 ? (size_t)w.s2.splits * n2 * n2 * sizeof(float2) : n2 * n2 * sizeof(float2));
+  w.gpart = (float2*)take((size_t)w.grid_grad * M * n2 * sizeof(float2));
+  w.gsum = (double2*)take(M * n2 * sizeof(double2));
+  w.bytes = off;
+  return w;
+}
+
+struct Call {
+  Dev dev;
+  PerN pn;
+  Layout w;
+  cudaStream_t st = nullptr;
+};
+
+static bool misaligned(const void* p, size_t a) { return ((uintptr_t)p) % a != 0; }
+
+static msp_status need(const void* p, const char* name) {
+  if (!p) return fail(MSP_EINVAL, std::string(name) + " is NULL");
+  if (misaligned(p, 16)) return fail(MSP_EINVAL, std::string(name) + " must be 16-byte aligned");
+  return MSP_OK;
+}
+
+static msp_status begin(const msp_smd_geometry* g, void* ws, size_t ws_bytes, void* stream, Call* c) {
+  SMD_TRY(check(g));
+  SMD_TRY(device(&c->dev, &c->pn, g->n));
+  const size_t need_b = layout(g, c->dev, c->pn, nullptr).bytes;
+  if (!ws) return fail(MSP_EINVAL, "workspace is NULL");
+  if (misaligned(ws, 256)) return fail(MSP_EINVAL, "workspace must be 256-byte aligned");
+  if (ws_bytes < need_b)
+    return fail(MSP_EINVAL, "workspace too small: " + std::to_string(ws_bytes) + " < " + std::to_string(need_b));
+  c->w = layout(g, c->dev, c->pn, (char*)ws);
+  c->st = (cudaStream_t)stream;
+  return MSP_OK;
+}
+
+static msp_status launch_propagator(const msp_smd_geometry* g, Call& c) {
+  const int N = g->n;
+  propagator_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.h, N, g->dz_A * g->wavelength_A,
+                                                           1.0 / ((double)N * g->pixel_A));
+  SMD_LAUNCHED(1);
+  return MSP_OK;
+}
+
+template <int N>
+static msp_status launch_transfer(const msp_smd_geometry* g, Call& c, float2* A, const float2* o, float scale,
+                                  bool have_ahat) {
+  const size_t sm = Kernels<N>::smem_plain();
+  if (have_ahat)
+    transfer_kernel<N, true><<<c.w.grid_plain, threads_of(N), sm, c.st>>>(A, o, c.w.h, g->n_slices, scale,
+                                                                          c.w.part, c.w.part2);
+  else
+    transfer_kernel<N, false><<<c.w.grid_plain, threads_of(N), sm, c.st>>>(A, o, c.w.h, g->n_slices, scale,
+                                                                           nullptr, nullptr);
+  SMD_LAUNCHED(1);
+  return MSP_OK;
+}
+
+template <int N>
+static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, const float2* probe,
+                                const int2* shifts, const float* I, double step, double* obj_out) {
+  const size_t n2 = (size_t)N * N, S = g->n_pos;
+  const Layout& w = c.w;
+  const int blocks = (int)std::min<size_t>((n2 * S + 255) / 256, (size_t)c.dev.sms * 16);
+  probe_matrix_kernel<<<blocks, 256, 0, c.st>>>(probe, shifts, N, (int)S, w.P);
+  SMD_LAUNCHED(1);
+  const int nsum = 256;
+  sum_part_kernel<<<nsum, 256, 0, c.st>>>(I, n2 * S, w.part2);
+  SMD_LAUNCHED(1);
+  setup_kernel<N><<<1, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(probe, w.part2, nsum, (double)(n2 * S), step,
+                                                                        w.scal, nullptr);
+  SMD_LAUNCHED(1);
+  // A P: M = N^2, N = S, K = N^2
+  dim3 g1((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((S + GBN - 1) / GBN), (unsigned)w.s1.splits);
+  cgemm_kernel<false><<<g1, 256, 0, c.st>>>((int)n2, (int)S, (int)n2, w.s1.chunk, A, n2, w.P, n2, w.BC, n2, n2 * S);
+  SMD_LAUNCHED(1);
+  farfield_kernel<N><<<w.grid_ff, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(w.BC, w.s1.splits, n2 * S, I,
+                                                                                   (int)S, w.scal, w.part);
+  SMD_LAUNCHED(1);
+  finish_sum_kernel<<<1, 32, 0, c.st>>>(w.part, w.grid_ff, w.scal, S_OBJ, obj_out);
+  SMD_LAUNCHED(1);
+  // C P^H: M = N^2, N = N^2, K = S
+  dim3 g2((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((n2 + GBN - 1) / GBN), (unsigned)w.s2.splits);
+  cgemm_kernel<true><<<g2, 256, 0, c.st>>>((int)n2, (int)n2, (int)S, w.s2.chunk, w.BC, n2, w.P, n2, w.U, n2, n2 * n2);
+  SMD_LAUNCHED(1);
+  const size_t pairs = n2 * n2 / 2;
+  combine_kernel<<<(int)std::min<size_t>((pairs + 255) / 256, (size_t)c.dev.sms * 16), 256, 0, c.st>>>(
+      A, w.U, w.s2.splits, n2 * n2, pairs, w.scal);
+  SMD_LAUNCHED(1);
+  return MSP_OK;
+}
+
+template <int N>
+static msp_status decompose_n(const msp_smd_geometry* g, Call& c, float2* A, float2* o, double* lam, double* obj_out) {
+  const size_t n2 = (size_t)N * N;
+  const int M = g->n_slices;
+  const Layout& w = c.w;
+  SMD_TRY(launch_propagator(g, c));
+  grad_kernel<N, max_slices(N)><<<w.grid_grad, threads_of(N), Kernels<N>::smem_grad(), c.st>>>(A, o, w.h, lam, M,
+                                                                                               w.gpart, w.part);
+  SMD_LAUNCHED(1);
+  slice_max_kernel<<<1, 1024, 0, c.st>>>(o, M, (int)n2, w.part, w.grid_grad, w.scal, obj_out);
+  SMD_LAUNCHED(1);
+  const int mn2 = (int)(M * n2);
+  grad_reduce_kernel<<<(mn2 + 255) / 256, 256, 0, c.st>>>(w.gpart, w.grid_grad, mn2, w.gsum);
+  SMD_LAUNCHED(1);
+  prox_kernel<<<M, 1024, 0, c.st>>>(o, w.gsum, w.scal, lam, M, (int)n2);
+  SMD_LAUNCHED(1);
+  SMD_TRY(launch_transfer<N>(g, c, A, o, 1.f, true));
+  lambda_kernel<<<1, 32, 0, c.st>>>(w.part, w.part2, w.grid_plain, lam);
+  SMD_LAUNCHED(1);
+  const size_t n4 = n2 * n2 / 2;
+  scale_kernel<<<(int)std::min<size_t>((n4 + 255) / 256, (size_t)c.dev.sms * 16), 256, 0, c.st>>>((float4*)A, n4, lam);
+  SMD_LAUNCHED(1);
+  return MSP_OK;
+}
+
+}  // namespace smd
+}  // namespace msp
+
+using namespace msp;
+using namespace msp::smd;
+
+#define SMD_DISPATCH(N_, CALL)          \
+  switch (N_) {                         \
+    case 16: { constexpr int N = 16; return CALL; } \
+    case 24: { constexpr int N = 24; return CALL; } \
+    case 32: { constexpr int N = 32; return CALL; } \
+    case 40: { constexpr int N = 40; return CALL; } \
+    case 48: { constexpr int N = 48; return CALL; } \
+    case 64: { constexpr int N = 64; return CALL; } \
+  }                                     \
+  return fail(MSP_EUNSUPPORTED, "N");
+
+extern "C" {
+
+msp_status msp_smd_validate_geometry(const msp_smd_geometry* g) {
+  set_last_error(MSP_OK, "");
+  return check(g);
+}
+
+size_t msp_smd_workspace_bytes(const msp_smd_geometry* g) {
+  if (check(g) != MSP_OK) return 0;
+  Dev d;
+  PerN pn;
+  if (device(&d, &pn, g->n) != MSP_OK) return 0;
+  return layout(g, d, pn, nullptr).bytes;
+}
+
+msp_status msp_smd_transfer(const msp_smd_geometry* g, const float* o, double lambda, float* A, void* ws,
+                            size_t ws_bytes, void* stream) {
+  set_last_error(MSP_OK, "");
+  Call c;
+  SMD_TRY(begin(g, ws, ws_bytes, stream, &c));
+  SMD_TRY(need(o, "o"));
+  SMD_TRY(need(A, "A"));
+  if (!std::isfinite(lambda)) return fail(MSP_EINVAL, "lambda must be finite");
+  SMD_TRY(launch_propagator(g, c));
+  SMD_DISPATCH(g->n, (launch_transfer<N>(g, c, (float2*)A, (const float2*)o, (float)lambda, false)));
+}
+
+msp_status msp_smd_matrix_step(const msp_smd_geometry* g, float* A, const float* probe, const int32_t* shifts,
+                               const float* I, double step, double* objective_before, double* mu_out, void* ws,
+                               size_t ws_bytes, void* stream) {
+  set_last_error(MSP_OK, "");
+  Call c;
+  SMD_TRY(begin(g, ws, ws_bytes, stream, &c));
+  SMD_TRY(need(A, "A"));
+  SMD_TRY(need(probe, "probe"));
+  SMD_TRY(need(shifts, "shifts"));
+  SMD_TRY(need(I, "I"));
+  if (objective_before && misaligned(objective_before, 8)) return fail(MSP_EINVAL, "objective_before must be 8-byte aligned");
+  if (mu_out && misaligned(mu_out, 8)) return fail(MSP_EINVAL, "mu_out must be 8-byte aligned");
+  if (!std::isfinite(step)) return fail(MSP_EINVAL, "step must be finite");
+  msp_status s = MSP_OK;
+  switch (g->n) {
+    case 16: s = matrix_step_n<16>(g, c, (float2*)A, (const float2*)probe, (const int2*)shifts, I, step, objective_before); break;
+    case 24: s = matrix_step_n<24>(g, c, (float2*)A, (const float2*)probe, (const int2*)shifts, I, step, objective_before); break;
+    case 32: s = matrix_step_n<32>(g, c, (float2*)A, (const float2*)probe, (const int2*)shifts, I, step, objective_before); break;
+    case 40: s = matrix_step_n<40>(g, c, (float2*)A, (const float2*)probe, (const int2*)shifts, I, step, objective_before); break;
+    case 48: s = matrix_step_n<48>(g, c, (float2*)A, (const float2*)probe, (const int2*)shifts, I, step, objective_before); break;
+    case 64: s = matrix_step_n<64>(g, c, (float2*)A, (const float2*)probe, (const int2*)shifts, I, step, objective_before); break;
+  }
+  if (s != MSP_OK) return s;
+  if (mu_out) SMD_CK(cudaMemcpyAsync(mu_out, c.w.scal + S_MU, sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  return MSP_OK;
+}
+
+msp_status msp_smd_decompose(const msp_smd_geometry* g, float* A, float* o, double* lambda, double* objective_before,
+                             void* ws, size_t ws_bytes, void* stream) {
+  set_last_error(MSP_OK, "");
+  Call c;
+  SMD_TRY(begin(g, ws, ws_bytes, stream, &c));
+  SMD_TRY(need(A, "A"));
+  SMD_TRY(need(o, "o"));
+  if (!lambda || misaligned(lambda, 8)) return fail(MSP_EINVAL, "lambda must be a non-NULL 8-byte aligned device double");
+  if (objective_before && misaligned(objective_before, 8)) return fail(MSP_EINVAL, "objective_before must be 8-byte aligned");
+  SMD_DISPATCH(g->n, (decompose_n<N>(g, c, (float2*)A, (float2*)o, lambda, objective_before)));
+}
+
+msp_status msp_smd_final_slices(const msp_smd_geometry* g, const float* o, const double* lambda, float* out,
+                                void* stream) {
+  set_last_error(MSP_OK, "");
+  SMD_TRY(check(g));
+  SMD_TRY(need(o, "o"));
+  SMD_TRY(need(out, "out"));
+  if (!lambda || misaligned(lambda, 8)) return fail(MSP_EINVAL, "lambda must be a non-NULL 8-byte aligned device double");
+  const size_t n = (size_t)g->n_slices * g->n * g->n;
+  final_slices_kernel<<<(int)std::min<size_t>((n + 255) / 256, 4096), 256, 0, (cudaStream_t)stream>>>(
+      (const float2*)o, lambda, g->n_slices, n, (float2*)out);
+  SMD_LAUNCHED(1);
+  return MSP_OK;
+}
+
+}  // extern "C"

@@ -52,9 +52,26 @@ def geometry(n_slices, obj_ny, obj_nx, win, n_pos, wavelength_A, sigma, dz_A, pi
                     float(wavelength_A), float(sigma), float(dz_A), float(pixel_A))
 
 
+class SmdGeometry(ctypes.Structure):
+    """msp_smd_geometry (include/msp_smd.h): Algorithm 2 on the N x N full-field model (Sec. 3.4)."""
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("n_slices", ctypes.c_int32),
+        ("n_pos", ctypes.c_int32),
+        ("wavelength_A", ctypes.c_double),
+        ("dz_A", ctypes.c_double),
+        ("pixel_A", ctypes.c_double),
+    ]
+
+
+def smd_geometry(n, n_slices, n_pos, wavelength_A, dz_A, pixel_A, **_ignored) -> SmdGeometry:
+    return SmdGeometry(int(n), int(n_slices), int(n_pos), float(wavelength_A), float(dz_A), float(pixel_A))
+
+
 _lib = None
 _P = ctypes.c_void_p
 _G = ctypes.POINTER(Geometry)
+_GS = ctypes.POINTER(SmdGeometry)
 _SIGS = {
     "msp_validate_geometry": ([_G], ctypes.c_int),
     "msp_workspace_bytes": ([_G], ctypes.c_size_t),
@@ -69,6 +86,12 @@ _SIGS = {
     "msp_profile_enable": ([ctypes.c_int32], ctypes.c_int),
     "msp_profile_read": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int32], ctypes.c_int),
+    "msp_smd_validate_geometry": ([_GS], ctypes.c_int),
+    "msp_smd_workspace_bytes": ([_GS], ctypes.c_size_t),
+    "msp_smd_transfer": ([_GS, _P, ctypes.c_double, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_smd_matrix_step": ([_GS, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_smd_decompose": ([_GS, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_smd_final_slices": ([_GS, _P, _P, _P, _P], ctypes.c_int),
     "msp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "msp_last_error_message": ([], ctypes.c_char_p),
 }
@@ -263,6 +286,116 @@ def validate_geometry(g: Geometry) -> int:
 
 def status_string(status: int) -> str:
     return lib().msp_status_string(int(status)).decode()
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2, Sparse Matrix Decomposition (include/msp_smd.h)
+# ---------------------------------------------------------------------------
+
+def smd_validate_geometry(g: SmdGeometry) -> int:
+    return int(lib().msp_smd_validate_geometry(ctypes.byref(g)))
+
+
+def smd_make_workspace(g: SmdGeometry, device=None) -> Workspace:
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n = int(lib().msp_smd_workspace_bytes(ctypes.byref(g)))
+    if n == 0:
+        _check(lib().msp_smd_validate_geometry(ctypes.byref(g)), "msp_smd_workspace_bytes")
+        raise MspError(MSP_ECUDA, "msp_smd_workspace_bytes", "no CUDA device")
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return Workspace(buf[off:off + n])
+
+
+def _smd_ws(g, ws, device):
+    return smd_make_workspace(g, device) if ws is None else ws
+
+
+def _smd_slices(g: SmdGeometry, o, name="o"):
+    _need(o, name, torch.complex64, (g.n_slices, g.n, g.n), o.device)
+
+
+def _smd_matrix(g: SmdGeometry, A, device):
+    n2 = g.n * g.n
+    _need(A, "A", torch.complex64, (n2, n2), device)   # A[j] is column j of the N^2 x N^2 matrix
+
+
+def smd_transfer(g: SmdGeometry, o, lam: float = 1.0, A=None, ws=None, stream=None):
+    """lambda * O_M prod G O_m as an [N^2][N^2] complex64 tensor whose row j is column j of the
+    matrix (the exit wave of an impulse at pixel j) (msp_smd_transfer)."""
+    _smd_slices(g, o)
+    n2 = g.n * g.n
+    if A is None:
+        A = torch.empty((n2, n2), dtype=torch.complex64, device=o.device)
+    _smd_matrix(g, A, o.device)
+    ws = _smd_ws(g, ws, o.device)
+    _check(lib().msp_smd_transfer(ctypes.byref(g), _ptr(o), float(lam), _ptr(A), ws.ptr(), ws.nbytes,
+                                  _stream(stream)), "msp_smd_transfer")
+    return A
+
+
+def smd_matrix_step(g: SmdGeometry, A, probe, shifts, I, step: float = 0.0, ws=None, stream=None,
+                    objective=None, mu=None):
+    """One gradient step of Eq. (Opt_Prob_Matrix) on A in place; returns (objective_before, mu)."""
+    device = A.device
+    _smd_matrix(g, A, device)
+    _need(probe, "probe", torch.complex64, (g.n, g.n), device)
+    _need(shifts, "shifts", torch.int32, (g.n_pos, 2), device)
+    _need(I, "I", torch.float32, (g.n_pos, g.n, g.n), device)
+    if objective is None:
+        objective = torch.empty(1, dtype=torch.float64, device=device)
+    if mu is None:
+        mu = torch.empty(1, dtype=torch.float64, device=device)
+    ws = _smd_ws(g, ws, device)
+    _check(lib().msp_smd_matrix_step(ctypes.byref(g), _ptr(A), _ptr(probe), _ptr(shifts), _ptr(I), float(step),
+                                     _ptr(objective), _ptr(mu), ws.ptr(), ws.nbytes, _stream(stream)),
+           "msp_smd_matrix_step")
+    return objective, mu
+
+
+def smd_decompose(g: SmdGeometry, A, o, lam, ws=None, stream=None, objective=None):
+    """Proximal slice updates, lambda update and A = lambda A(o) (Algorithm 2); A, o and the
+    float64 [1] tensor lam are updated in place; returns the decomposition objective before."""
+    device = A.device
+    _smd_matrix(g, A, device)
+    _smd_slices(g, o)
+    _need(lam, "lam", torch.float64, (1,), device)
+    if objective is None:
+        objective = torch.empty(1, dtype=torch.float64, device=device)
+    ws = _smd_ws(g, ws, device)
+    _check(lib().msp_smd_decompose(ctypes.byref(g), _ptr(A), _ptr(o), _ptr(lam), _ptr(objective), ws.ptr(),
+                                   ws.nbytes, _stream(stream)), "msp_smd_decompose")
+    return objective
+
+
+def smd_final_slices(g: SmdGeometry, o, lam, out=None, stream=None):
+    """lambda^(1/M) o_m (msp_smd_final_slices)."""
+    _smd_slices(g, o)
+    _need(lam, "lam", torch.float64, (1,), o.device)
+    if out is None:
+        out = torch.empty_like(o)
+    _check(lib().msp_smd_final_slices(ctypes.byref(g), _ptr(o), _ptr(lam), _ptr(out), _stream(stream)),
+           "msp_smd_final_slices")
+    return out
+
+
+def sparse_decomposition(g: SmdGeometry, probe, shifts, I, iterations: int, matrix_steps: int = 1, o0=None,
+                         ws=None, stream=None):
+    """Algorithm 2 from slices o0 (default all ones) and lambda = 1.  Returns
+    (slices lambda^(1/M) o_m, lambda [1] float64, matrix objectives [iterations*matrix_steps],
+    decomposition objectives [iterations]) -- all on the device."""
+    device = probe.device
+    o = torch.ones((g.n_slices, g.n, g.n), dtype=torch.complex64, device=device) if o0 is None else o0.clone()
+    lam = torch.ones(1, dtype=torch.float64, device=device)
+    ws = _smd_ws(g, ws, device)
+    A = smd_transfer(g, o, 1.0, ws=ws, stream=stream)
+    hm = torch.empty(iterations * matrix_steps, dtype=torch.float64, device=device)
+    hd = torch.empty(iterations, dtype=torch.float64, device=device)
+    for t in range(iterations):
+        for k in range(matrix_steps):
+            smd_matrix_step(g, A, probe, shifts, I, ws=ws, stream=stream, objective=hm[t * matrix_steps + k:][:1])
+        smd_decompose(g, A, o, lam, ws=ws, stream=stream, objective=hd[t:][:1])
+    return smd_final_slices(g, o, lam, stream=stream), lam, hm, hd
 
 
 class MultisliceLoss(torch.autograd.Function):

@@ -20,14 +20,21 @@ def lib():
 
 
 def declared_symbols():
-    text = open(os.path.join(ROOT, "include", "msp.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(msp_\w+)\s*\(", text, flags=re.M)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if not h.endswith(".h"):
+            continue
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(msp_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     syms = declared_symbols()
-    for name in ["msp_forward", "msp_loss_grad", "msp_layer_step", "msp_probe_step", "msp_workspace_bytes"]:
+    for name in ["msp_forward", "msp_loss_grad", "msp_layer_step", "msp_probe_step", "msp_workspace_bytes",
+                 "msp_smd_transfer", "msp_smd_matrix_step", "msp_smd_decompose", "msp_smd_final_slices",
+                 "msp_smd_workspace_bytes"]:
         assert name in syms
 
 
@@ -79,3 +86,39 @@ def test_compute_calls_reject_bad_geometry_before_touching_the_device(lib):
     st = lib.msp_loss_grad(ctypes.byref(g), None, None, None, None, None, None, None, None, 0, None)
     assert st == msp.MSP_EINVAL
     assert lib.msp_workspace_bytes(ctypes.byref(g)) == 0
+
+
+def smd_geom(**kw):
+    base = dict(n=40, n_slices=3, n_pos=1600, wavelength_A=0.02508, dz_A=20.0, pixel_A=0.2827)
+    base.update(kw)
+    return msp.smd_geometry(**base)
+
+
+@pytest.mark.parametrize("kw,status", [
+    ({}, msp.MSP_OK),
+    (dict(n=16, n_pos=1), msp.MSP_OK),
+    (dict(n=64, n_slices=3), msp.MSP_OK),
+    (dict(n=64, n_slices=4), msp.MSP_EUNSUPPORTED),
+    (dict(n=48, n_slices=5), msp.MSP_OK),
+    (dict(n=48, n_slices=6), msp.MSP_EUNSUPPORTED),
+    (dict(n=36), msp.MSP_EUNSUPPORTED),
+    (dict(n=128), msp.MSP_EUNSUPPORTED),
+    (dict(n_slices=0), msp.MSP_EINVAL),
+    (dict(n_pos=0), msp.MSP_EINVAL),
+    (dict(wavelength_A=-1.0), msp.MSP_EINVAL),
+    (dict(pixel_A=float("nan")), msp.MSP_EINVAL),
+    (dict(dz_A=-2.0), msp.MSP_EINVAL),
+    (dict(dz_A=0.0), msp.MSP_OK),
+])
+def test_smd_geometry_validation(lib, kw, status):
+    assert msp.smd_validate_geometry(smd_geom(**kw)) == status
+
+
+def test_smd_calls_reject_bad_geometry_before_touching_the_device(lib):
+    g = smd_geom(n=36)
+    assert lib.msp_smd_transfer(ctypes.byref(g), None, 1.0, None, None, 0, None) == msp.MSP_EUNSUPPORTED
+    g = smd_geom(n_slices=0)
+    assert lib.msp_smd_decompose(ctypes.byref(g), None, None, None, None, None, 0, None) == msp.MSP_EINVAL
+    assert lib.msp_smd_final_slices(ctypes.byref(g), None, None, None, None) == msp.MSP_EINVAL
+    assert lib.msp_smd_workspace_bytes(ctypes.byref(g)) == 0
+    assert lib.msp_smd_validate_geometry(None) == msp.MSP_EINVAL

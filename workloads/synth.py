@@ -66,6 +66,41 @@ C4 = Workload("c4_L16_obj640_W256_S2304", 16, 640, 0.1, 1.0, 30, 256, (48, 48), 
               lattice_A=3.9, species_vnm=None, seed=3)
 CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c4": C4}
 
+# Algorithm 2 on the paper's own setting (Table 1, GaAs): a 2 x 2 supercell of the
+# 5.6533 A cubic cell on a 40 x 40 grid, every one of the 40 x 40 cyclic probe shifts,
+# 200 kV, 32 mrad, three slices 2 nm apart (the distance at which the paper's sparse
+# decomposition separates the slices, Sec. 5.3).  Atomic columns every a/2; a 2 nm slice
+# holds several atoms per column, so each column is given 40-45 V nm (about 0.3 rad).
+GAAS_CELL_A = 5.6533
+SMD_GAAS = Workload("smd_gaas_N40_M3_S1600", 3, 40, 2 * GAAS_CELL_A / 40, 20.0, 200, 40, (40, 40), 1,
+                    32.0, 0.0, None, lattice_A=GAAS_CELL_A / 2, species_vnm=(40.0, 45.0), seed=5)
+SMD_CONFIGS = {"smd_gaas": SMD_GAAS}
+
+
+def smd_geometry(cfg: Workload, n_pos: int | None = None) -> dict:
+    """Scalar statement of the full-field problem of Algorithm 2 (N = object = probe = detector side)."""
+    return dict(n=cfg.obj, n_slices=cfg.n_slices, n_pos=cfg.n_pos if n_pos is None else n_pos,
+                wavelength_A=physics.wavelength_A(cfg.volts), sigma=physics.interaction_constant(cfg.volts),
+                dz_A=cfg.dz_A, pixel_A=cfg.pixel_A, obj_ny=cfg.obj, obj_nx=cfg.obj, win=cfg.obj)
+
+
+def cyclic_shifts(n: int, step: int = 1, count: int | None = None, seed: int | None = None) -> np.ndarray:
+    """Probe shifts (ys, xs) of a cyclic raster with the given step (step 1: all n^2 shifts,
+    the paper's full scan); `count` draws that many distinct shifts at random instead."""
+    if count is not None:
+        rng = np.random.default_rng([0 if seed is None else seed, 41])
+        flat = rng.choice(n * n, size=count, replace=False)
+        return np.stack([flat // n, flat % n], axis=1).astype(np.int32)
+    g = np.arange(0, n, step)
+    yy, xx = np.meshgrid(g, g, indexing="ij")
+    return np.stack([yy.ravel(), xx.ravel()], axis=1).astype(np.int32)
+
+
+def random_phase_slices(M: int, n: int, seed: int, amp: float = 0.5) -> np.ndarray:
+    """Unimodular slices exp(i amp g) with Gaussian g, complex128 [M][n][n]."""
+    rng = np.random.default_rng([seed, 43])
+    return np.exp(1j * amp * rng.standard_normal((M, n, n)))
+
 
 def geometry(cfg: Workload, n_pos: int | None = None) -> dict:
     """Scalar problem statement shared by the oracle and the library."""
