@@ -7,10 +7,15 @@ through every slice, the atomic-free overlap-add of the slice gradient and of
 the illumination map, the FP64 step-size reduction and the update of V_0.
 value = S * L / (time per step).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference] [--config c2|smd_gaas]
 
 --impl reference times the FP64 CPU oracle on the host cores (a bounded sample
 of the same workload); it is a reported baseline, not the target.
+
+--config smd_gaas times the paper's second method instead: one iteration of
+Algorithm 2 (Sec. 3.4: one matrix step of Eq. Opt_Prob_Matrix, the proximal step
+of every slice, the lambda update and A = lambda A(o)) on the Table 1 setting,
+N = 40, all 1600 cyclic probe shifts, M = 3; value = iterations / s.
 Under torchrun (N > 1) every rank runs an independent replica (the method's
 positions could be sharded, but this build is single-GPU): weak scaling.
 """
@@ -202,6 +207,255 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Algorithm 2 (sparse matrix decomposition)
+# ---------------------------------------------------------------------------
+
+SMD_METRIC = "Algorithm 2 iterations/s"
+SMD_UNIT = "iterations/s"
+
+
+def smd_flops(n, S, M):
+    """Algorithmic FLOPs of one Algorithm 2 iteration, split as (contractions, DFTs): the two
+    complex contractions N^2 x N^2 x S of the matrix step (8 flops per complex multiply-add),
+    and direct DFT passes of 8 N^3 flops each -- 4 per column of A P (S columns), 8 (M - 1)
+    per column of the decomposition gradient and 4 (M - 1) per column of the transfer pass
+    (N^2 columns each)."""
+    n2 = n * n
+    return 2 * 8.0 * n2 * n2 * S, 8.0 * n ** 3 * (4 * S + 12 * (M - 1) * n2)
+
+
+def smd_inputs(msp, torch, dev, cfg):
+    """Table 1 stand-in: lattice slices exp(i sigma V), the aperture probe, every cyclic shift,
+    noise-free intensities |F A P|^2 (A from the library's transfer matrix; P and F applied
+    with torch, as input synthesis only)."""
+    gd = synth.smd_geometry(cfg)
+    n, M = cfg.obj, cfg.n_slices
+    g = msp.smd_geometry(**gd)
+    V = synth.potential_slices(cfg)
+    truth = np.exp(1j * gd["sigma"] * V).astype(np.complex64)
+    probe = synth.probe(cfg).astype(np.complex64)
+    shifts = synth.cyclic_shifts(n)
+    ws = msp.smd_make_workspace(g, dev)
+    A_true = msp.smd_transfer(g, torch.from_numpy(truth).to(dev), 1.0, ws=ws)      # row j = column j
+    p = torch.from_numpy(probe).to(dev)
+    P = torch.stack([torch.roll(p, (int(a), int(b)), dims=(0, 1)).reshape(-1) for a, b in shifts], dim=1)
+    B = A_true.transpose(0, 1) @ P                                                  # exit waves, N^2 x S
+    I = (torch.fft.fft2(B.transpose(0, 1).reshape(-1, n, n)).abs() ** 2).float()
+    torch.cuda.synchronize()
+    return g, gd, ws, probe, shifts, I.cpu().numpy()
+
+
+def smd_cpu_iteration(cfg, probe, shifts, I):
+    """One Algorithm 2 iteration of the FP64 oracle, as it stands (dense N^2 x N^2 matrices)."""
+    from oracle import msp_oracle as O
+    gd = synth.smd_geometry(cfg)
+    n, M = cfg.obj, cfg.n_slices
+    t0 = time.perf_counter()
+    F = O.dft_matrix_2d(n)
+    G = O.propagator_matrix(gd, n)
+    P = O.probe_matrix(probe.astype(np.complex128), shifts)
+    Im = O.measurement_matrix(I.astype(np.float64))
+    o = [np.ones(n * n, complex) for _ in range(M)]
+    A = O.transfer_matrix(G, o)
+    t1 = time.perf_counter()
+    A, _ = O.matrix_step(A, F, P, Im, O.matrix_step_size(probe.astype(np.complex128)))
+    O.decomposition_update(A, G, o, 1.0)
+    return time.perf_counter() - t1, t1 - t0
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        return int(max(n)) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def smd_cpu_baseline(cfg, probe, shifts, I, budget_s=60.0, max_iter=3):
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_iter and (not times or time.perf_counter() - t_start < budget_s):
+        dt, _ = smd_cpu_iteration(cfg, probe, shifts, I)
+        times.append(dt)
+    t = float(np.median(times))
+    return {"value": 1.0 / t, "unit": SMD_UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": f"{len(times)} full Algorithm 2 iteration(s) of {cfg.name} (N = {cfg.obj}, S = {cfg.n_pos}, "
+                      f"M = {cfg.n_slices}), FP64 numpy oracle with dense N^2 x N^2 matrices, multithreaded BLAS, "
+                      f"median {t:.2f} s"}
+
+
+def run_smd_reference(args, rank, world):
+    if rank != 0:
+        return
+    cfg = CFG
+    import torch
+    from paper_2205_03902_gb300 import msp
+    if torch.cuda.is_available():
+        import __graft_entry__
+        __graft_entry__.build()
+        _, _, _, probe, shifts, I = smd_inputs(msp, torch, torch.device("cuda", 0), cfg)
+    else:
+        probe = synth.probe(cfg).astype(np.complex64)
+        shifts = synth.cyclic_shifts(cfg.obj)
+        I = np.ones((len(shifts), cfg.obj, cfg.obj), np.float32)
+    base = smd_cpu_baseline(cfg, probe, shifts, I, budget_s=60.0, max_iter=max(1, min(args.steps, 3)))
+    value = base["value"]
+    line = {"impl": "reference", "metric": SMD_METRIC, "value": value, "unit": SMD_UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "call": "oracle.matrix_step + oracle.decomposition_update",
+                       "parallelism": f"cpu, {base['cores']} BLAS threads"},
+            "cpu_baseline": base,
+            "e2e": {"value": value, "unit": SMD_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_smd(args, rank, world, local_rank):
+    import torch
+    from paper_2205_03902_gb300 import msp
+    import __graft_entry__
+    __graft_entry__.build()
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist = dist_mod
+        dist.init_process_group("nccl", device_id=dev)
+
+    cfg = CFG
+    g, gd, ws, probe_h, shifts_h, I_h = smd_inputs(msp, torch, dev, cfg)
+    n, M, S = cfg.obj, cfg.n_slices, cfg.n_pos
+    probe = torch.from_numpy(probe_h).to(dev)
+    shifts = torch.from_numpy(shifts_h).to(dev)
+    I = torch.from_numpy(I_h).to(dev)
+    o = torch.ones((M, n, n), dtype=torch.complex64, device=dev)     # Algorithm 2 starts at O^0 = I, lambda = 1
+    lam = torch.ones(1, dtype=torch.float64, device=dev)
+    A = msp.smd_transfer(g, o, 1.0, ws=ws)
+    obj = torch.empty(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(A, o, lam, probe, shifts, I, obj):
+        msp.smd_matrix_step(g, A, probe, shifts, I, ws=ws, objective=obj[0:1])
+        msp.smd_decompose(g, A, o, lam, ws=ws, objective=obj[1:2])
+
+    for _ in range(args.warmup):
+        step(A, o, lam, probe, shifts, I, obj)
+    torch.cuda.synchronize()
+    obj_first = obj.cpu().tolist()
+
+    msp.profile_read(reset=True)
+    msp.profile_enable(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step(A, o, lam, probe, shifts, I, obj)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = msp.profile_read(reset=True)
+    msp.profile_enable(False)
+    ms_per_step = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)), dist, dev) / args.steps
+    value = job_throughput(world, 1.0, ms_per_step)
+    obj_last = obj.cpu().tolist()
+
+    # ---- end to end with host buffers: the step's inputs (probe, shifts, I) copied from pinned
+    # memory on a copy stream (two input sets), the slices, lambda and objectives read back ----
+    h_I = torch.from_numpy(I_h).pin_memory()
+    h_p = torch.from_numpy(probe_h).pin_memory()
+    h_s = torch.from_numpy(shifts_h).pin_memory()
+    h_o = [torch.empty((M, n, n), dtype=torch.complex64).pin_memory() for _ in range(2)]
+    h_scal = [torch.empty(3, dtype=torch.float64).pin_memory() for _ in range(2)]
+    sets = [dict(I=torch.empty_like(I), p=torch.empty_like(probe), s=torch.empty_like(shifts),
+                 scal=torch.empty(3, dtype=torch.float64, device=dev)) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    ev_copy = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    h2d = h_I.numel() * 4 + h_p.numel() * 8 + h_s.numel() * 4
+    d2h = h_o[0].numel() * 8 + h_scal[0].numel() * 8
+
+    def issue_copy(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(ev_done[k % 2])
+            b["I"].copy_(h_I, non_blocking=True)
+            b["p"].copy_(h_p, non_blocking=True)
+            b["s"].copy_(h_s, non_blocking=True)
+            ev_copy[k % 2].record(copy_stream)
+
+    def issue_step(k):
+        b = sets[k % 2]
+        stream.wait_event(ev_copy[k % 2])
+        step(A, o, lam, b["p"], b["s"], b["I"], b["scal"])
+        b["scal"][2:3].copy_(lam)
+        h_o[k % 2].copy_(o, non_blocking=True)
+        h_scal[k % 2].copy_(b["scal"], non_blocking=True)
+        ev_done[k % 2].record(stream)
+
+    e_steps = max(3, min(args.steps, 50))
+    issue_copy(0)
+    issue_step(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    issue_copy(1)
+    for k in range(1, e_steps + 1):
+        if k < e_steps:
+            issue_copy(k + 1)
+        issue_step(k)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    assert np.isfinite(h_scal[e_steps % 2].numpy()).all()
+    e2e_value = job_throughput(world, 1.0, 1e3 * max_over_ranks(e2e_s, dist, dev))
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = read_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12
+    gemm_flops, dft_flops = smd_flops(n, S, M)
+    gemm_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
+    achieved = (gemm_flops / 2) / (gemm_ms * 1e-3) / 1e12
+    line = {
+        "metric": SMD_METRIC, "value": value, "unit": SMD_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg.name, "call": "msp_smd_matrix_step + msp_smd_decompose (auto steps)",
+                   "N": n, "shifts": S, "slices": M,
+                   "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "cgemm_kernel (FP32 complex contraction, A P and C P^H)", "kernel_ms": gemm_ms,
+                     "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"},
+        "step_tflops": (gemm_flops + dft_flops) / (ms_per_step * 1e-3) / 1e12,
+        "e2e": {"value": e2e_value, "unit": SMD_UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["all_launches"]),
+        "clocks": clocks,
+        "objectives_first_timed_step": obj_first, "objectives_last_timed_step": obj_last,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = smd_cpu_baseline(cfg, probe_h, shifts_h, I_h, budget_s=30.0, max_iter=2)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def run_msp(args, rank, world, local_rank):
     import torch
     from paper_2205_03902_gb300 import msp
@@ -358,18 +612,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=sorted(synth.CONFIGS),
-                    help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration)")
+    ap.add_argument("--config", default="c2", choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS),
+                    help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration; "
+                         "smd_gaas: Algorithm 2 on the Table 1 setting)")
     args = ap.parse_args()
     global CFG
-    CFG = synth.CONFIGS[args.config]
+    smd = args.config in synth.SMD_CONFIGS
+    CFG = synth.SMD_CONFIGS[args.config] if smd else synth.CONFIGS[args.config]
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
-        run_reference(args, rank, world)
+        (run_smd_reference if smd else run_reference)(args, rank, world)
     else:
-        run_msp(args, rank, world, local_rank)
+        (run_smd if smd else run_msp)(args, rank, world, local_rank)
 
 
 if __name__ == "__main__":

@@ -164,13 +164,14 @@ msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const 
  * (every compute call clears the flag when it starts): MSP_OK or MSP_EINVAL. */
 msp_status msp_check_workspace(void* ws, void* stream);
 
-/* Profiling hooks, off by default.  While enabled, every launch of the fused
- * per-position kernel (the forward / adjoint of all positions) is bracketed by
- * CUDA events recorded on its stream. */
+/* Profiling hooks, off by default.  While enabled, every launch of the dominant
+ * kernel of a call is bracketed by CUDA events recorded on its stream: the fused
+ * per-position kernel (the forward / adjoint of all positions) of the calls above,
+ * and the two dense complex contractions of msp_smd_matrix_step (msp_smd.h). */
 msp_status msp_profile_enable(int32_t on);
 
 /* Waits for the recorded events and returns, since the last reset: the summed
- * duration in ms and the number of fused-kernel launches timed, and the number of
+ * duration in ms and the number of dominant-kernel launches timed, and the number of
  * kernels libmsp launched in total (counted whether or not timing is enabled).
  * Any output pointer may be NULL (host pointers); reset != 0 starts a new interval. */
 msp_status msp_profile_read(double* fused_ms, int64_t* fused_launches, int64_t* all_launches,

@@ -16,6 +16,7 @@
 #include <vector>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 
@@ -512,8 +513,10 @@ static PosParams base_params(const msp_geometry* g, const float* probe, const fl
   return p;
 }
 
-static msp_status run_position(const msp_geometry* g, int mode, const PosParams& p, Call& c) {
-  if (g->n_pos == 0) return MSP_OK;
+// Launches one kernel through `launch`; while profiling is on, brackets it with an event
+// pair on `st` (the dominant kernel of each call: the fused per-position kernel here, the
+// dense contraction of the sparse-decomposition matrix step).
+msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& launch) {
   std::unique_lock<std::mutex> lk(g_prof_mu);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (g_prof_on) {
@@ -530,15 +533,20 @@ static msp_status run_position(const msp_geometry* g, int mode, const PosParams&
     }
     e0 = g_ev_pool[2 * g_ev_used];
     e1 = g_ev_pool[2 * g_ev_used + 1];
-    MSP_CK(cudaEventRecord(e0, c.st));
+    MSP_CK(cudaEventRecord(e0, st));
   }
-  MSP_CK(launch_position_kernel(g->win, mode, p, c.grid, c.st));
+  MSP_CK(launch());
   counted();
   if (g_prof_on) {
-    MSP_CK(cudaEventRecord(e1, c.st));
+    MSP_CK(cudaEventRecord(e1, st));
     ++g_ev_used;
   }
   return MSP_OK;
+}
+
+static msp_status run_position(const msp_geometry* g, int mode, const PosParams& p, Call& c) {
+  if (g->n_pos == 0) return MSP_OK;
+  return profiled_launch(c.st, [&] { return launch_position_kernel(g->win, mode, p, c.grid, c.st); });
 }
 
 static msp_status reduce_loss(const msp_geometry* g, Call& c, double* extra) {

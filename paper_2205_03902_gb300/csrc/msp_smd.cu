@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 #include <mutex>
 #include <string>
 
@@ -39,6 +40,7 @@ namespace msp {
 
 msp_status set_last_error(msp_status s, const std::string& m);   // shown by msp_last_error_message()
 void count_launches(int n);
+msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& launch);
 
 namespace smd {
 
@@ -977,8 +979,10 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   SMD_LAUNCHED(1);
   // A P: M = N^2, N = S, K = N^2
   dim3 g1((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((S + GBN - 1) / GBN), (unsigned)w.s1.splits);
-  cgemm_kernel<false><<<g1, 256, 0, c.st>>>((int)n2, (int)S, (int)n2, w.s1.chunk, A, n2, w.P, n2, w.BC, n2, n2 * S);
-  SMD_LAUNCHED(1);
+  SMD_TRY(profiled_launch(c.st, [&] {
+    cgemm_kernel<false><<<g1, 256, 0, c.st>>>((int)n2, (int)S, (int)n2, w.s1.chunk, A, n2, w.P, n2, w.BC, n2, n2 * S);
+    return cudaGetLastError();
+  }));
   farfield_kernel<N><<<w.grid_ff, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(w.BC, w.s1.splits, n2 * S, I,
                                                                                    (int)S, w.scal, w.part);
   SMD_LAUNCHED(1);
@@ -986,8 +990,10 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   SMD_LAUNCHED(1);
   // C P^H: M = N^2, N = N^2, K = S
   dim3 g2((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((n2 + GBN - 1) / GBN), (unsigned)w.s2.splits);
-  cgemm_kernel<true><<<g2, 256, 0, c.st>>>((int)n2, (int)n2, (int)S, w.s2.chunk, w.BC, n2, w.P, n2, w.U, n2, n2 * n2);
-  SMD_LAUNCHED(1);
+  SMD_TRY(profiled_launch(c.st, [&] {
+    cgemm_kernel<true><<<g2, 256, 0, c.st>>>((int)n2, (int)n2, (int)S, w.s2.chunk, w.BC, n2, w.P, n2, w.U, n2, n2 * n2);
+    return cudaGetLastError();
+  }));
   const size_t pairs = n2 * n2 / 2;
   combine_kernel<<<(int)std::min<size_t>((pairs + 255) / 256, (size_t)c.dev.sms * 16), 256, 0, c.st>>>(
       A, w.U, w.s2.splits, n2 * n2, pairs, w.scal);
