@@ -218,11 +218,12 @@ SMD_UNIT = "iterations/s"
 def smd_flops(n, S, M):
     """Algorithmic FLOPs of one Algorithm 2 iteration, split as (contractions, DFTs): the two
     complex contractions N^2 x N^2 x S of the matrix step (8 flops per complex multiply-add),
-    and direct DFT passes of 8 N^3 flops each -- 4 per column of A P (S columns), 8 (M - 1)
-    per column of the decomposition gradient and 4 (M - 1) per column of the transfer pass
-    (N^2 columns each)."""
+    and direct DFT passes of 8 N^3 flops each -- 4 per column of A P (S columns), and, per
+    column of the N^2 x N^2 matrices, 8 (M - 2) for the decomposition gradient and 4 (M - 2)
+    for the transfer pass (a unit impulse needs no DFT for its first propagation, and the
+    adjoint wave on the first slice is needed at one pixel only)."""
     n2 = n * n
-    return 2 * 8.0 * n2 * n2 * S, 8.0 * n ** 3 * (4 * S + 12 * (M - 1) * n2)
+    return 2 * 8.0 * n2 * n2 * S, 8.0 * n ** 3 * (4 * S + 12 * max(M - 2, 0) * n2)
 
 
 def smd_inputs(msp, torch, dev, cfg):

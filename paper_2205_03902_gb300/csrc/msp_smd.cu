@@ -78,18 +78,22 @@ __device__ __forceinline__ void cmac(float2& acc, float2 d, float2 w) {
   }
 }
 
-// W[k][c] = exp(-2 pi i (k c mod N) / N), unpadded rows, computed in double and rounded once.
+// W[k][c] = exp(-2 pi i (k c mod N) / N), unpadded rows: the N distinct values are computed
+// in double and rounded once (into `scratch`, N float2), then spread.  Ends with a barrier.
 template <int N>
-__device__ void fill_twiddles(float2* Wt) {
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const int m = ((e / N) * (e % N)) % N;
+__device__ void fill_twiddles(float2* Wt, float2* scratch) {
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
     double s, c;
     sincospi(-2.0 * (double)m / (double)N, &s, &c);
-    Wt[e] = make_float2((float)c, (float)s);
+    scratch[m] = make_float2((float)c, (float)s);
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) Wt[e] = scratch[((e / N) * (e % N)) % N];
+  __syncthreads();
 }
 
-// One pass: a = rows r0, r0+1 and columns c0..c0+3 of D W (CONJ: D conj(W)).
+// One pass: a[i][j] = element (r0 + i, c0 + j N/4) of D W (CONJ: D conj(W)).  The four
+// columns of a thread are N/4 apart, so a quarter warp reads consecutive twiddles.
 template <int N, bool CONJ>
 __device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const float2* __restrict__ Wt,
                                          float2 (&a)[2][4], int r0, int c0) {
@@ -101,18 +105,17 @@ __device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const flo
   const float2* d0 = D + r0 * LD;
   const float2* d1 = d0 + LD;
   const float2* wp = Wt + c0;
+  constexpr int Q = N / 4;
 #pragma unroll 4
   for (int k = 0; k < N; k += 2) {
     const float4 x0 = *reinterpret_cast<const float4*>(d0 + k);
     const float4 x1 = *reinterpret_cast<const float4*>(d1 + k);
-    const float4 wa = *reinterpret_cast<const float4*>(wp + k * N);
-    const float4 wb = *reinterpret_cast<const float4*>(wp + k * N + 2);
-    const float4 wc = *reinterpret_cast<const float4*>(wp + (k + 1) * N);
-    const float4 wd = *reinterpret_cast<const float4*>(wp + (k + 1) * N + 2);
-    const float2 w0[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
-                          make_float2(wb.z, wb.w)};
-    const float2 w1[4] = {make_float2(wc.x, wc.y), make_float2(wc.z, wc.w), make_float2(wd.x, wd.y),
-                          make_float2(wd.z, wd.w)};
+    float2 w0[4], w1[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      w0[j] = wp[k * N + Q * j];
+      w1[j] = wp[(k + 1) * N + Q * j];
+    }
     const float2 l00 = make_float2(x0.x, x0.y), l01 = make_float2(x0.z, x0.w);
     const float2 l10 = make_float2(x1.x, x1.y), l11 = make_float2(x1.z, x1.w);
 #pragma unroll
@@ -125,16 +128,17 @@ __device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const flo
   }
 }
 
-// O[c0 + j][r0 + i] = a[i][j]: the transposed store that follows every pass.
+// O[c0 + j N/4][r0 + i] = a[i][j]: the transposed store that follows every pass.
 template <int N>
 __device__ __forceinline__ void store_t(float2* O, const float2 (&a)[2][4], int r0, int c0) {
   constexpr int LD = ld_of(N);
 #pragma unroll
   for (int j = 0; j < 4; ++j)
-    *reinterpret_cast<float4*>(O + (c0 + j) * LD + r0) = make_float4(a[0][j].x, a[0][j].y, a[1][j].x, a[1][j].y);
+    *reinterpret_cast<float4*>(O + (c0 + (N / 4) * j) * LD + r0) =
+        make_float4(a[0][j].x, a[0][j].y, a[1][j].x, a[1][j].y);
 }
 
-// 2-D DFT of the image whose pixels (y, x) = (c0 + j, r0 + i) are held in v (the pixels
+// 2-D DFT of the image whose pixels (y, x) = (c0 + j N/4, r0 + i) are held in v (the pixels
 // this thread owns); the result comes back in v at the same pixels.  INV: conjugate kernel
 // (F^H, unnormalised).  Uses X and Y as scratch; begins and ends with all threads free to
 // overwrite X.
@@ -148,7 +152,7 @@ __device__ __forceinline__ void dft2(float2 (&v)[2][4], float2* X, float2* Y, co
   dft_pass<N, INV>(Y, Wt, v, r0, c0);
 }
 
-__device__ __forceinline__ int owned(int N, int r0, int c0, int i, int j) { return (c0 + j) * N + r0 + i; }
+__device__ __forceinline__ int owned(int N, int r0, int c0, int i, int j) { return (c0 + (N / 4) * j) * N + r0 + i; }
 
 // v <- G v (ADJ: G^H v), G = F^-1 diag(h) F; h carries the 1/N^2 of F^-1.
 template <int N, bool ADJ>
@@ -165,14 +169,21 @@ __device__ __forceinline__ void propagate(float2 (&v)[2][4], float2* X, float2* 
   dft2<N, true>(v, X, Y, Wt, r0, c0);
 }
 
-// Fixed-order FP64 block sum (any block size); every thread receives the total.
+// Fixed-order FP64 block sum (at least 32 threads): the first warp adds strided values in
+// order, then a butterfly; every thread receives the total.  sh: blockDim.x + 1 doubles.
+template <bool MAX = false>
 __device__ double block_sum(double v, double* sh) {
   sh[threadIdx.x] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) t += sh[i];
-    sh[blockDim.x] = t;
+  if (threadIdx.x < 32) {
+    double s = MAX ? sh[threadIdx.x] : 0.0;
+    for (int i = threadIdx.x + (MAX ? 32 : 0); i < (int)blockDim.x; i += 32) s = MAX ? fmax(s, sh[i]) : s + sh[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double o = __shfl_xor_sync(0xffffffffu, s, off);
+      s = MAX ? fmax(s, o) : s + o;
+    }
+    if (threadIdx.x == 0) sh[blockDim.x] = s;
   }
   __syncthreads();
   const double t = sh[blockDim.x];
@@ -201,8 +212,8 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
   float2* Wt = Y + N * ld_of(N);
   double* red = reinterpret_cast<double*>(Wt + N * N);
   constexpr int n2 = N * N;
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
-  fill_twiddles<N>(Wt);
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
+  fill_twiddles<N>(Wt, X);
   const float thr2 = (float)scal[S_THR2];
   double obj = 0.0;
   for (int s = blockIdx.x; s < S; s += gridDim.x) {
@@ -244,20 +255,54 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
   if (threadIdx.x == 0) obj_part[blockIdx.x] = 0.5 * tot;
 }
 
+// Fixed-order sum of one complex value per thread (block of at least 32 threads); every
+// thread receives the total.  red: blockDim.x + 1 float2.
+__device__ float2 block_sum2(float2 v, float2* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float2 s = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) {
+      s.x += red[i].x;
+      s.y += red[i].y;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+    }
+    if (threadIdx.x == 0) red[blockDim.x] = s;
+  }
+  __syncthreads();
+  return red[blockDim.x];
+}
+
+// Index of pixel e = (y, x) relative to pixel col, cyclically: (y - yc) mod N, (x - xc) mod N.
+__device__ __forceinline__ int rel_index(int N, int e, int col) {
+  const int y = e / N - col / N, x = e % N - col % N;
+  return (y < 0 ? y + N : y) * N + (x < 0 ? x + N : x);
+}
+
 // Multislice pass of a unit impulse at object pixel `col` through the slices o (M of them):
-// v ends as column col of A(o) = O_M G ... G O_1; incident waves on slices 1..M-1 go to stash.
+// v ends as column col of A(o) = O_M G ... G O_1.  The first propagation needs no DFT:
+// G (o_1[col] e_col) = o_1[col] gk(. - col), gk = G e_0 the propagator's real-space kernel.
+// Incident waves on slices 1..M-1 go to stash.
 template <int N, bool STASH>
 __device__ __forceinline__ void impulse_forward(float2 (&v)[2][4], int col, int M, const float2* __restrict__ o,
-                                                const float2* __restrict__ h, float2* X, float2* Y, const float2* Wt,
-                                                float2* stash, int r0, int c0) {
+                                                const float2* __restrict__ gk, const float2* __restrict__ h,
+                                                float2* X, float2* Y, const float2* Wt, float2* stash, int r0,
+                                                int c0) {
   constexpr int n2 = N * N;
   const float2 o0 = __ldg(&o[col]);
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[i][j] = owned(N, r0, c0, i, j) == col ? o0 : make_float2(0.f, 0.f);
+    for (int j = 0; j < 4; ++j) {
+      const int e = owned(N, r0, c0, i, j);
+      v[i][j] = M == 1 ? (e == col ? o0 : make_float2(0.f, 0.f)) : cmul(o0, __ldg(&gk[rel_index(N, e, col)]));
+    }
   for (int m = 1; m < M; ++m) {
-    propagate<N, false>(v, X, Y, Wt, h, r0, c0);
+    if (m > 1) propagate<N, false>(v, X, Y, Wt, h, r0, c0);
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -270,28 +315,34 @@ __device__ __forceinline__ void impulse_forward(float2 (&v)[2][4], int col, int 
 }
 
 // Decomposition gradient: for every column j, m_j = lambda A(o)_j - Ahat_j and, for every
-// slice l, the column's share (R_l^H m_j) o conj(S_l e_j) of diag(R_l^H M S_l^H).  The
-// per-CTA sums go to gpart[cta][l][k]; the objective 1/2 sum |m_j|^2 to obj_part[cta].
-template <int N, int MAXM>
+// slice l, the column's share (R_l^H m_j) o conj(S_l e_j) of diag(R_l^H M S_l^H).  Slice 0
+// (S_0 = I) receives from column j one value only, at pixel j: it is written to g0[j].  The
+// per-CTA sums of slices 1..M-1 go to gpart[cta][l-1][k]; the objective 1/2 sum |m_j|^2 to
+// obj_part[cta].
+template <int N, int M>
 __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __restrict__ A,
                                                              const float2* __restrict__ o,
+                                                             const float2* __restrict__ gk,
                                                              const float2* __restrict__ h,
-                                                             const double* __restrict__ lam_p, int M,
+                                                             const double* __restrict__ lam_p,
+                                                             float2* __restrict__ g0,
                                                              float2* __restrict__ gpart,
                                                              double* __restrict__ obj_part) {
+  constexpr int NA = M > 1 ? M - 1 : 1;   // accumulated slices 1..M-1
   extern __shared__ float4 smem4[];
   float2* X = reinterpret_cast<float2*>(smem4);
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
   float2* stash = Wt + N * N;                                      // [M-1][N^2], thread-owned pixels
-  double* red = reinterpret_cast<double*>(stash + (MAXM - 1) * N * N);
+  double* red = reinterpret_cast<double*>(stash + (M - 1) * N * N);
+  float2* red2 = reinterpret_cast<float2*>(red);
   constexpr int n2 = N * N;
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
-  fill_twiddles<N>(Wt);
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
+  fill_twiddles<N>(Wt, X);
   const float lam = (float)lam_p[0];
-  float2 acc[MAXM][2][4];
+  float2 acc[NA][2][4];
 #pragma unroll
-  for (int q = 0; q < MAXM; ++q)
+  for (int q = 0; q < NA; ++q)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -299,7 +350,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
   double obj = 0.0;
   for (int col = blockIdx.x; col < n2; col += gridDim.x) {
     float2 v[2][4];
-    impulse_forward<N, true>(v, col, M, o, h, X, Y, Wt, stash, r0, c0);
+    impulse_forward<N, true>(v, col, M, o, gk, h, X, Y, Wt, stash, r0, c0);
     const float2* Aj = A + (size_t)col * n2;
     float ob = 0.f;
 #pragma unroll
@@ -312,39 +363,49 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
       ob = fmaf(v[1][j].x, v[1][j].x, fmaf(v[1][j].y, v[1][j].y, ob));
     }
     obj += (double)ob;
-    for (int l = M - 1;; --l) {
+    // adjoint: chi_l = R_l^H m_j, from slice M-1 down to slice 1
+#pragma unroll
+    for (int l = M - 1; l >= 1; --l) {
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int e = owned(N, r0, c0, i, j);
-          float2 g;
-          if (l > 0)
-            g = cmulc(v[i][j], stash[(l - 1) * n2 + e]);
-          else
-            g = (e == col) ? v[i][j] : make_float2(0.f, 0.f);
-#pragma unroll
-          for (int q = 0; q < MAXM; ++q)
-            if (q == l) {
-              acc[q][i][j].x += g.x;
-              acc[q][i][j].y += g.y;
-            }
+          const float2 g = cmulc(v[i][j], stash[(l - 1) * n2 + e]);
+          acc[l - 1][i][j].x += g.x;
+          acc[l - 1][i][j].y += g.y;
+          v[i][j] = cmulc(v[i][j], __ldg(&o[(size_t)l * n2 + e]));
         }
-      if (l == 0) break;
+      if (l > 1) propagate<N, true>(v, X, Y, Wt, h, r0, c0);
+    }
+    // slice 0: (G^H conj(o_1) chi_1)[col] = <G e_col, conj(o_1) chi_1>, or m_j[col] when M = 1
+    float2 chi0 = make_float2(0.f, 0.f);
+    if (M > 1) {
+      float2 d = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[i][j] = cmulc(v[i][j], __ldg(&o[(size_t)l * n2 + owned(N, r0, c0, i, j)]));
-      propagate<N, true>(v, X, Y, Wt, h, r0, c0);
+        for (int j = 0; j < 4; ++j) {
+          const float2 p = cmulc(v[i][j], __ldg(&gk[rel_index(N, owned(N, r0, c0, i, j), col)]));
+          d.x += p.x;
+          d.y += p.y;
+        }
+      chi0 = block_sum2(d, red2);
     }
-  }
 #pragma unroll
-  for (int q = 0; q < MAXM; ++q)
-    if (q < M)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        *reinterpret_cast<float4*>(gpart + ((size_t)blockIdx.x * M + q) * n2 + owned(N, r0, c0, 0, j)) =
+        if (owned(N, r0, c0, i, j) == col) g0[col] = M > 1 ? chi0 : v[i][j];
+  }
+  if (M > 1) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<float4*>(gpart + ((size_t)blockIdx.x * NA + q) * n2 + owned(N, r0, c0, 0, j)) =
             make_float4(acc[q][0][j].x, acc[q][0][j].y, acc[q][1][j].x, acc[q][1][j].y);
+  }
   const double tot = block_sum(obj, red);
   if (threadIdx.x == 0) obj_part[blockIdx.x] = 0.5 * tot;
 }
@@ -353,6 +414,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
 // per CTA, Re <Ahat_j, A(o)_j> and ||A(o)_j||^2 are summed for the lambda update.
 template <int N, bool HAVE_AHAT>
 __global__ void __launch_bounds__(threads_of(N)) transfer_kernel(float2* A, const float2* __restrict__ o,
+                                                                 const float2* __restrict__ gk,
                                                                  const float2* __restrict__ h, int M, float scale,
                                                                  double* __restrict__ dot_part,
                                                                  double* __restrict__ nrm_part) {
@@ -362,12 +424,12 @@ __global__ void __launch_bounds__(threads_of(N)) transfer_kernel(float2* A, cons
   float2* Wt = Y + N * ld_of(N);
   double* red = reinterpret_cast<double*>(Wt + N * N);
   constexpr int n2 = N * N;
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
-  fill_twiddles<N>(Wt);
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
+  fill_twiddles<N>(Wt, X);
   double dot = 0.0, nrm = 0.0;
   for (int col = blockIdx.x; col < n2; col += gridDim.x) {
     float2 v[2][4];
-    impulse_forward<N, false>(v, col, M, o, h, X, Y, Wt, nullptr, r0, c0);
+    impulse_forward<N, false>(v, col, M, o, gk, h, X, Y, Wt, nullptr, r0, c0);
     float2* Aj = A + (size_t)col * n2;
     float d = 0.f, q = 0.f;
 #pragma unroll
@@ -407,8 +469,8 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
   double* red = reinterpret_cast<double*>(Wt + N * N);
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = 4 * (t % (N / 4));
-  fill_twiddles<N>(Wt);
+  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
+  fill_twiddles<N>(Wt, X);
   float2 v[2][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
@@ -420,13 +482,11 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) mx = fmax(mx, (double)v[i][j].x * v[i][j].x + (double)v[i][j].y * v[i][j].y);
-  red[t] = mx;
-  __syncthreads();
+  const double m = block_sum<true>(mx, red);
+  double a = 0.0;
+  for (int i = t; i < n_part; i += blockDim.x) a += sum_part[i];
+  const double s = block_sum(a, red);
   if (t == 0) {
-    double m = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) m = fmax(m, red[i]);
-    double s = 0.0;
-    for (int i = 0; i < n_part; ++i) s += sum_part[i];
     scal[S_SPEC] = m;
     scal[S_SUMI] = s;
     scal[S_THR2] = kZeroTau * kZeroTau * s / count;
@@ -577,6 +637,28 @@ __global__ void propagator_kernel(float2* __restrict__ h, int N, double dzlam, d
   h[e] = make_float2((float)(c * inv), (float)(s * inv));
 }
 
+// gk = G e_0, the real-space kernel of the propagator: with h = h1(ky) h1(kx) separable,
+// gk[y][x] = g1(y) g1(x), g1(y) = (1/N) sum_k h1(k) exp(2 pi i k y / N); in double, rounded once.
+__global__ void __launch_bounds__(256) kernel_column_kernel(float2* __restrict__ gk, int N, double dzlam, double dq) {
+  __shared__ double2 g1[64];
+  for (int y = threadIdx.x; y < N; y += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < N; ++k) {
+      const double q = (k < N / 2 ? k : k - N) * dq;
+      double s, c;
+      sincospi(-dzlam * q * q + 2.0 * (double)((k * y) % N) / N, &s, &c);
+      re += c;
+      im += s;
+    }
+    g1[y] = make_double2(re / N, im / N);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+    const double2 a = g1[e / N], b = g1[e % N];
+    gk[e] = make_float2((float)(a.x * b.x - a.y * b.y), (float)(a.x * b.y + a.y * b.x));
+  }
+}
+
 // Block partial sums (FP64) of a float array over fixed chunks.
 __global__ void __launch_bounds__(256) sum_part_kernel(const float* __restrict__ x, size_t n, double* __restrict__ part) {
   __shared__ double sh[257];
@@ -588,13 +670,17 @@ __global__ void __launch_bounds__(256) sum_part_kernel(const float* __restrict__
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// out = sum of part[0..n) in order, written to scal[slot] and, if given, to copy.
-__global__ void finish_sum_kernel(const double* __restrict__ part, int n, double* scal, int slot, double* copy) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = 0; i < n; ++i) s += part[i];
-  scal[slot] = s;
-  if (copy) copy[0] = s;
+// out = sum of part[0..n) in a fixed order (one block of 256), written to scal[slot] and copy.
+__global__ void __launch_bounds__(256) finish_sum_kernel(const double* __restrict__ part, int n, double* scal,
+                                                         int slot, double* copy) {
+  __shared__ double sh[257];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) a += part[i];
+  const double s = block_sum(a, sh);
+  if (threadIdx.x == 0) {
+    scal[slot] = s;
+    if (copy) copy[0] = s;
+  }
 }
 
 // A += -mu * sum_z part_z (the rank-S update of the matrix step), float4 over element pairs.
@@ -646,17 +732,34 @@ __global__ void __launch_bounds__(1024) slice_max_kernel(const float2* __restric
   }
 }
 
-// g[l][k] = sum_cta gpart[cta][l][k] in CTA order (FP64).
-__global__ void grad_reduce_kernel(const float2* __restrict__ gpart, int n_cta, int Mn2, double2* __restrict__ g) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= Mn2) return;
+// g[0][k] = g0[k]; g[l][k] = sum over CTAs of gpart[cta][l-1][k] (l >= 1), FP64, in a fixed
+// order: 32 consecutive k per block, 8 groups of CTAs (cta mod 8), then the groups in order.
+__global__ void __launch_bounds__(256) grad_reduce_kernel(const float2* __restrict__ g0,
+                                                          const float2* __restrict__ gpart, int n_cta, int M,
+                                                          int n2, double2* __restrict__ g) {
+  __shared__ double2 sh[8][32];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;          // index into slices 1..M-1: (l - 1) * n2 + k
+  const int na = (M - 1) * n2;
   double re = 0.0, im = 0.0;
-  for (int c = 0; c < n_cta; ++c) {
-    const float2 v = gpart[(size_t)c * Mn2 + e];
-    re += v.x;
-    im += v.y;
+  if (e < na)
+    for (int c = grp; c < n_cta; c += 8) {
+      const float2 v = gpart[(size_t)c * na + e];
+      re += v.x;
+      im += v.y;
+    }
+  sh[grp][lane] = make_double2(re, im);
+  __syncthreads();
+  if (grp == 0 && e < na) {
+    double2 t = sh[0][lane];
+    for (int k = 1; k < 8; ++k) {
+      t.x += sh[k][lane].x;
+      t.y += sh[k][lane].y;
+    }
+    g[n2 + e] = t;
   }
-  g[e] = make_double2(re, im);
+  const int k = blockIdx.x * 256 + threadIdx.x;
+  if (k < n2) g[k] = make_double2(g0[k].x, g0[k].y);
 }
 
 // Proximal step of slice l = blockIdx.x (Eq. Prox_Min): x = o_l - mu_l lambda g_l with
@@ -687,15 +790,17 @@ __global__ void __launch_bounds__(1024) prox_kernel(float2* o, const double2* __
 }
 
 // lambda = sum dot / sum nrm (Eq. Update Lambda, real part), partials in CTA order.
-__global__ void lambda_kernel(const double* __restrict__ dot_part, const double* __restrict__ nrm_part, int n,
-                              double* lam) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__global__ void __launch_bounds__(256) lambda_kernel(const double* __restrict__ dot_part,
+                                                     const double* __restrict__ nrm_part, int n, double* lam) {
+  __shared__ double sh[257];
   double d = 0.0, q = 0.0;
-  for (int i = 0; i < n; ++i) {
+  for (int i = threadIdx.x; i < n; i += 256) {
     d += dot_part[i];
     q += nrm_part[i];
   }
-  lam[0] = q > 0.0 ? d / q : 0.0;
+  d = block_sum(d, sh);
+  q = block_sum(q, sh);
+  if (threadIdx.x == 0) lam[0] = q > 0.0 ? d / q : 0.0;
 }
 
 __global__ void scale_kernel(float4* __restrict__ A, size_t n4, const double* __restrict__ lam) {
@@ -776,13 +881,27 @@ struct Kernels {
   static constexpr int T = threads_of(N);
   static constexpr int MM = max_slices(N);
   static size_t smem_plain() { return image_smem(N, 0, T); }
-  static size_t smem_grad() { return image_smem(N, MM - 1, T); }
-  static cudaError_t attrs() {
+  static size_t smem_grad(int M) { return image_smem(N, M - 1, T); }
+  template <int M>
+  static cudaError_t grad_attr(int* per_sm) {
+    if constexpr (M <= max_slices(N)) {
+      cudaError_t e = cudaFuncSetAttribute(grad_kernel<N, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem_grad(M));
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, grad_kernel<N, M>, T, smem_grad(M));
+      return e;
+    }
+    return cudaSuccess;
+  }
+  static cudaError_t attrs(int* grad_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(farfield_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(grad_kernel<N, MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_grad());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(transfer_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(transfer_kernel<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(setup_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_plain());
+    if (e == cudaSuccess) e = grad_attr<1>(&grad_per_sm[1]);
+    if (e == cudaSuccess) e = grad_attr<2>(&grad_per_sm[2]);
+    if (e == cudaSuccess) e = grad_attr<3>(&grad_per_sm[3]);
+    if (e == cudaSuccess) e = grad_attr<4>(&grad_per_sm[4]);
+    if (e == cudaSuccess) e = grad_attr<5>(&grad_per_sm[5]);
     return e;
   }
   static int per_sm_plain() {
@@ -792,16 +911,12 @@ struct Kernels {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k2, transfer_kernel<N, true>, T, smem_plain());
     return std::max(1, std::min(k, k2));
   }
-  static int per_sm_grad() {
-    int k = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, grad_kernel<N, MM>, T, smem_grad());
-    return std::max(1, k);
-  }
 };
 
 struct PerN {
   bool init = false;
-  int plain = 1, grad = 1;   // resident CTAs per SM
+  int plain = 1;                       // resident CTAs per SM of the plain per-column kernels
+  int grad[kMaxSlices + 1] = {};       // ... of grad_kernel<N, M>
 };
 static PerN g_pern[64][65];
 
@@ -809,9 +924,9 @@ template <int N>
 static msp_status init_n(int dev, PerN* out) {
   PerN& p = g_pern[dev][N];
   if (!p.init) {
-    SMD_CK(Kernels<N>::attrs());
+    SMD_CK(Kernels<N>::attrs(p.grad));
     p.plain = Kernels<N>::per_sm_plain();
-    p.grad = Kernels<N>::per_sm_grad();
+    for (int m = 1; m <= kMaxSlices; ++m) p.grad[m] = std::max(1, p.grad[m]);
     p.init = true;
   }
   *out = p;
@@ -876,10 +991,12 @@ struct Layout {
   double* part = nullptr;    // kPartSlots
   double* part2 = nullptr;   // kPartSlots
   float2* h = nullptr;
+  float2* gk = nullptr;      // G e_0
   float2* P = nullptr;
   float2* BC = nullptr;      // splits1 * n2 * S
   float2* U = nullptr;       // splits2 * n2 * n2 (rank-S update partials)
-  float2* gpart = nullptr;   // grid_grad * M * n2
+  float2* g0 = nullptr;      // n2: slice-0 gradient, one value per column
+  float2* gpart = nullptr;   // grid_grad * (M - 1) * n2
   double2* gsum = nullptr;   // M * n2
   Split s1, s2;
   int grid_plain = 1, grid_grad = 1, grid_ff = 1;
@@ -896,7 +1013,7 @@ static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, ch
   w.s2 = choose_split(tiles_of((int)n2, (int)n2), (int)S, slots, 4);
   const size_t cap = kPartSlots;
   w.grid_plain = (int)std::min({n2, (size_t)pn.plain * d.sms, cap});
-  w.grid_grad = (int)std::min({n2, (size_t)pn.grad * d.sms, cap});
+  w.grid_grad = (int)std::min({n2, (size_t)pn.grad[M] * d.sms, cap});
   w.grid_ff = (int)std::min({S, (size_t)pn.plain * d.sms, cap});
   size_t off = 0;
   auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
@@ -904,10 +1021,12 @@ static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, ch
   w.part = (double*)take(kPartSlots * sizeof(double));
   w.part2 = (double*)take(kPartSlots * sizeof(double));
   w.h = (float2*)take(n2 * sizeof(float2));
+  w.gk = (float2*)take(n2 * sizeof(float2));
   w.P = (float2*)take(n2 * S * sizeof(float2));
   w.BC = (float2*)take((size_t)w.s1.splits * n2 * S * sizeof(float2));
   w.U = (float2*)take(w.s2.splits > 1 ? (size_t)w.s2.splits * n2 * n2 * sizeof(float2) : n2 * n2 * sizeof(float2));
-  w.gpart = (float2*)take((size_t)w.grid_grad * M * n2 * sizeof(float2));
+  w.g0 = (float2*)take(n2 * sizeof(float2));
+  w.gpart = (float2*)take((size_t)w.grid_grad * std::max<size_t>(M - 1, 1) * n2 * sizeof(float2));
   w.gsum = (double2*)take(M * n2 * sizeof(double2));
   w.bytes = off;
   return w;
@@ -946,6 +1065,9 @@ static msp_status launch_propagator(const msp_smd_geometry* g, Call& c) {
   propagator_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.h, N, g->dz_A * g->wavelength_A,
                                                            1.0 / ((double)N * g->pixel_A));
   SMD_LAUNCHED(1);
+  kernel_column_kernel<<<1, 256, 0, c.st>>>(c.w.gk, N, g->dz_A * g->wavelength_A,
+                                                              1.0 / ((double)N * g->pixel_A));
+  SMD_LAUNCHED(1);
   return MSP_OK;
 }
 
@@ -954,10 +1076,10 @@ static msp_status launch_transfer(const msp_smd_geometry* g, Call& c, float2* A,
                                   bool have_ahat) {
   const size_t sm = Kernels<N>::smem_plain();
   if (have_ahat)
-    transfer_kernel<N, true><<<c.w.grid_plain, threads_of(N), sm, c.st>>>(A, o, c.w.h, g->n_slices, scale,
+    transfer_kernel<N, true><<<c.w.grid_plain, threads_of(N), sm, c.st>>>(A, o, c.w.gk, c.w.h, g->n_slices, scale,
                                                                           c.w.part, c.w.part2);
   else
-    transfer_kernel<N, false><<<c.w.grid_plain, threads_of(N), sm, c.st>>>(A, o, c.w.h, g->n_slices, scale,
+    transfer_kernel<N, false><<<c.w.grid_plain, threads_of(N), sm, c.st>>>(A, o, c.w.gk, c.w.h, g->n_slices, scale,
                                                                            nullptr, nullptr);
   SMD_LAUNCHED(1);
   return MSP_OK;
@@ -986,7 +1108,7 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   farfield_kernel<N><<<w.grid_ff, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(w.BC, w.s1.splits, n2 * S, I,
                                                                                    (int)S, w.scal, w.part);
   SMD_LAUNCHED(1);
-  finish_sum_kernel<<<1, 32, 0, c.st>>>(w.part, w.grid_ff, w.scal, S_OBJ, obj_out);
+  finish_sum_kernel<<<1, 256, 0, c.st>>>(w.part, w.grid_ff, w.scal, S_OBJ, obj_out);
   SMD_LAUNCHED(1);
   // C P^H: M = N^2, N = N^2, K = S
   dim3 g2((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((n2 + GBN - 1) / GBN), (unsigned)w.s2.splits);
@@ -1001,24 +1123,49 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   return MSP_OK;
 }
 
+template <int N, int M>
+static cudaError_t launch_grad_m(Call& c, const float2* A, const float2* o, const double* lam) {
+  if constexpr (M <= max_slices(N)) {
+    const Layout& w = c.w;
+    grad_kernel<N, M><<<w.grid_grad, threads_of(N), Kernels<N>::smem_grad(M), c.st>>>(A, o, w.gk, w.h, lam, w.g0,
+                                                                                      w.gpart, w.part);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int N>
+static msp_status launch_grad(int M, Call& c, const float2* A, const float2* o, const double* lam) {
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (M) {
+    case 1: e = launch_grad_m<N, 1>(c, A, o, lam); break;
+    case 2: e = launch_grad_m<N, 2>(c, A, o, lam); break;
+    case 3: e = launch_grad_m<N, 3>(c, A, o, lam); break;
+    case 4: e = launch_grad_m<N, 4>(c, A, o, lam); break;
+    case 5: e = launch_grad_m<N, 5>(c, A, o, lam); break;
+  }
+  if (e != cudaSuccess) return fail(MSP_ECUDA, std::string("grad_kernel: ") + cudaGetErrorString(e));
+  return MSP_OK;
+}
+
 template <int N>
 static msp_status decompose_n(const msp_smd_geometry* g, Call& c, float2* A, float2* o, double* lam, double* obj_out) {
   const size_t n2 = (size_t)N * N;
   const int M = g->n_slices;
   const Layout& w = c.w;
   SMD_TRY(launch_propagator(g, c));
-  grad_kernel<N, max_slices(N)><<<w.grid_grad, threads_of(N), Kernels<N>::smem_grad(), c.st>>>(A, o, w.h, lam, M,
-                                                                                               w.gpart, w.part);
+  SMD_TRY(launch_grad<N>(M, c, A, o, lam));
   SMD_LAUNCHED(1);
   slice_max_kernel<<<1, 1024, 0, c.st>>>(o, M, (int)n2, w.part, w.grid_grad, w.scal, obj_out);
   SMD_LAUNCHED(1);
-  const int mn2 = (int)(M * n2);
-  grad_reduce_kernel<<<(mn2 + 255) / 256, 256, 0, c.st>>>(w.gpart, w.grid_grad, mn2, w.gsum);
+  const int na = (int)((M - 1) * n2);
+  const int rgrid = std::max({(na + 31) / 32, (int)((n2 + 255) / 256), 1});
+  grad_reduce_kernel<<<rgrid, 256, 0, c.st>>>(w.g0, w.gpart, w.grid_grad, M, (int)n2, w.gsum);
   SMD_LAUNCHED(1);
   prox_kernel<<<M, 1024, 0, c.st>>>(o, w.gsum, w.scal, lam, M, (int)n2);
   SMD_LAUNCHED(1);
   SMD_TRY(launch_transfer<N>(g, c, A, o, 1.f, true));
-  lambda_kernel<<<1, 32, 0, c.st>>>(w.part, w.part2, w.grid_plain, lam);
+  lambda_kernel<<<1, 256, 0, c.st>>>(w.part, w.part2, w.grid_plain, lam);
   SMD_LAUNCHED(1);
   const size_t n4 = n2 * n2 / 2;
   scale_kernel<<<(int)std::min<size_t>((n4 + 255) / 256, (size_t)c.dev.sms * 16), 256, 0, c.st>>>((float4*)A, n4, lam);
