@@ -63,7 +63,7 @@ typedef enum {
   MSP_ENOMEM = 2,        /* reserved: the library never allocates */
   MSP_ECUDA = 3,         /* a CUDA launch or runtime call failed */
   MSP_EUNSUPPORTED = 4,  /* valid but not implemented here (window size, parametrisation) */
-  MSP_ETIMEOUT = 5       /* reserved for bounded device-side waits */
+  MSP_ETIMEOUT = 5       /* a bounded device-side wait ran out (msp_check_workspace) */
 } msp_status;
 
 /* Slice parametrisation: real potentials (X_m = exp(i sigma V_m)) or complex
@@ -159,9 +159,10 @@ msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const 
                                const int32_t* pos, float* I_out, int32_t* window_error,
                                void* stream);
 
-/* Synchronises `stream`, then reports (and clears) the workspace flag raised when
- * a scan window of the most recent compute call on `ws` lay outside the object
- * (every compute call clears the flag when it starts): MSP_OK or MSP_EINVAL. */
+/* Synchronises `stream`, then reports (and clears) the workspace flag raised by the
+ * most recent compute call on `ws` (every call that can raise it clears it when it
+ * starts): MSP_OK; MSP_EINVAL when a scan window lay outside the object; MSP_ETIMEOUT
+ * when a bounded wait for the tensor core ran out (msp_smd_matrix_step). */
 msp_status msp_check_workspace(void* ws, void* stream);
 
 /* Profiling hooks, off by default.  While enabled, every launch of the dominant

@@ -80,7 +80,10 @@ msp_status msp_smd_transfer(const msp_smd_geometry* g, const float* o, double la
  * A: in/out; probe [N][N] complex; shifts [S][2] int32; I [S][N][N] float.
  * step > 0 sets mu, step <= 0 takes mu = 1 / (N^2 ||P||^2).  objective_before (device
  * double, or NULL) receives the objective at the incoming A; mu_out (device double or
- * NULL) the step used. */
+ * NULL) the step used.  The two contractions run on the tensor cores (tcgen05, operands
+ * split into tf32 pairs); their waits are bounded, and a wait that runs out leaves A
+ * invalid and raises the workspace flag, which msp_check_workspace(ws, stream) reports
+ * as MSP_ETIMEOUT. */
 msp_status msp_smd_matrix_step(const msp_smd_geometry* g, float* A, const float* probe,
                                const int32_t* shifts, const float* I, double step,
                                double* objective_before, double* mu_out,

@@ -787,6 +787,7 @@ msp_status msp_check_workspace(void* ws, void* stream) {
   MSP_CK(cudaMemcpy(&flag, ws, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     MSP_CK(cudaMemset(ws, 0, sizeof(int)));
+    if (flag == 2) return fail(MSP_ETIMEOUT, "a wait for the tensor core timed out; the call's results are not valid");
     return fail(MSP_EINVAL, "a scan window lies outside the object (position skipped)");
   }
   return MSP_OK;

@@ -35,6 +35,7 @@
 
 #include "msp.h"
 #include "msp_smd.h"
+#include "msp_tc.cuh"
 
 namespace msp {
 
@@ -497,115 +498,263 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
 }
 
 // ---------------------------------------------------------------------------
-// dense complex contraction (FP32, SIMT)
+// dense complex contraction on the tensor cores (tcgen05, 3xTF32)
 // ---------------------------------------------------------------------------
-// C_z = A[:, K_z] op(B)[K_z, :] for the K-range K_z of blockIdx.z.  A: M x K column-major.
+// C_z = A[:, K_z] op(B)[K_z, :] for the K range K_z of blockIdx.z.  A: M x K column-major.
 // op(B) = B (K x N column-major) or, with B_CONJ_T, B^H for B stored N x K column-major.
-// C: M x N column-major, partial z at C + z * c_stride.  64 x 64 tile per CTA, 256 threads,
-// each a 4 x 4 block (rows ty*4.., columns tx + 16 c); K in steps of 8, double-buffered.
-constexpr int GBM = 64, GBN = 64, GBK = 8;
+// C: M x N column-major, partial z at C + z * c_stride.
+//
+// One CTA computes a 128 x 64 complex tile.  The complex product is the real product
+//   D (128 x 128) = A_re B_re^T,  A_re = [Ar, Ai],  B_re rows n: [Br, -Bi], rows 64 + n: [Bi, Br]
+// so columns n of D hold Re C and columns 64 + n hold Im C.  Every real operand x is split
+// into tf32 parts x = big + small and D accumulates big*big + big*small + small*big, which
+// keeps the product error near FP32's.  The tensor core's FP32 accumulation does not round
+// to nearest, so D accumulates over groups of GROUP K-tiles only, alternating between two
+// TMEM halves; each finished group is added into FP32 registers.
+//
+// Warps 0..7 are producers: they load K-tiles of A and B (one tile ahead, in registers),
+// split them and write them in the canonical no-swizzle K-major layout into a 3-stage
+// shared-memory ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
+// TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
+// mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded: on
+// timeout the CTA raises *err = 2, stops and frees its TMEM.
+namespace gemm {
+constexpr int TM = 128, TN = 64, TK = 16;                   // complex tile and K-tile
+constexpr int KR = 2 * TK;                                  // real K per tile
+constexpr uint32_t A_BYTES = 128 * KR * 4;                  // one tf32 part of A_re: 16 KB
+constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 16 KB
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES; // 64 KB
+constexpr int STAGES = 3;
+constexpr int GROUP = 8;
+constexpr int NPROD = 256;
+constexpr int NTHREADS = NPROD + 32;
+constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of one accumulator
+constexpr uint32_t TMEM_COLS = 2 * DCOLS;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
+constexpr int kWaitLimit = 1 << 20;                         // polls (with 32 ns pauses) per wait
+
+// Bounded wait; gives up early once another thread has raised the abort flag.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (int i = 0; i < kWaitLimit; ++i) {
+    if (tc::mbar_test(bar, parity)) return true;
+    if ((i & 255) == 255 && *abort_flag) return false;
+    if (i > 64) __nanosleep(32);
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+// Warp-uniform wait: lane 0 waits, every lane gets the verdict.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(bar, parity, abort_flag) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Byte offset of real element (row, k) in a K-major operand: core matrices of 8 rows x 4
+// tf32, 128 bytes apart along K, KR/4 * 128 bytes apart along rows.
+__device__ __forceinline__ uint32_t kmaj(int row, int k) {
+  return (uint32_t)((k >> 2) * 128 + (row >> 3) * (KR / 4) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+struct Split4 {
+  uint4 big, small;
+};
+
+__device__ __forceinline__ Split4 split4(float x0, float x1, float x2, float x3) {
+  Split4 r;
+  r.big = make_uint4(tc::to_tf32(x0), tc::to_tf32(x1), tc::to_tf32(x2), tc::to_tf32(x3));
+  r.small = make_uint4(tc::to_tf32(x0 - __uint_as_float(r.big.x)), tc::to_tf32(x1 - __uint_as_float(r.big.y)),
+                       tc::to_tf32(x2 - __uint_as_float(r.big.z)), tc::to_tf32(x3 - __uint_as_float(r.big.w)));
+  return r;
+}
+
+__device__ __forceinline__ Split4 neg(const Split4& v) {   // rounding is symmetric: split(-x) = -split(x)
+  Split4 r;
+  r.big = make_uint4(v.big.x ^ 0x80000000u, v.big.y ^ 0x80000000u, v.big.z ^ 0x80000000u, v.big.w ^ 0x80000000u);
+  r.small = make_uint4(v.small.x ^ 0x80000000u, v.small.y ^ 0x80000000u, v.small.z ^ 0x80000000u,
+                       v.small.w ^ 0x80000000u);
+  return r;
+}
+
+__device__ __forceinline__ void put(uint8_t* big, uint8_t* small, uint32_t off, const Split4& v) {
+  *reinterpret_cast<uint4*>(big + off) = v.big;
+  *reinterpret_cast<uint4*>(small + off) = v.small;
+}
+
+// Adds accumulator half h into this thread's registers: TMEM lane (row) 32 (warp & 3) + lane,
+// columns 32 (warp >> 2) + q (Re) and TN + 32 (warp >> 2) + q (Im), q < 32.
+__device__ __forceinline__ void flush(uint32_t tmem, int h, int warp, float (&re)[32], float (&im)[32]) {
+  const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(h * DCOLS + 32 * (warp >> 2));
+  uint32_t r[16];
+#pragma unroll
+  for (int part = 0; part < 4; ++part) {
+    tc::tmem_ld16(base + (part < 2 ? 16 * part : TN + 16 * (part - 2)), r);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (part < 2)
+        re[16 * part + q] += __uint_as_float(r[q]);
+      else
+        im[16 * (part - 2) + q] += __uint_as_float(r[q]);
+    }
+  }
+}
+}  // namespace gemm
 
 template <bool B_CONJ_T>
-__global__ void __launch_bounds__(256) cgemm_kernel(int M, int N, int K, int k_chunk, const float2* __restrict__ A,
-                                                    size_t lda, const float2* __restrict__ B, size_t ldb,
-                                                    float2* __restrict__ C, size_t ldc, size_t c_stride) {
-  __shared__ __align__(16) float2 As[2][GBK][GBM];
-  __shared__ __align__(16) float2 Bs[2][GBK][GBN];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int i0 = blockIdx.x * GBM, j0 = blockIdx.y * GBN;
+__global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, int K, int k_chunk,
+                                                                  const float2* __restrict__ A, size_t lda,
+                                                                  const float2* __restrict__ B, size_t ldb,
+                                                                  float2* __restrict__ C, size_t ldc,
+                                                                  size_t c_stride, int* err) {
+  using namespace gemm;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + STAGES);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
   const int kb = blockIdx.z * k_chunk;
   const int ke = min(K, kb + k_chunk);
-  // loader coordinates
-  const int la_k = t >> 5, la_i = (t & 31) * 2;                                   // A: (i, k), 2 rows
-  const int lb_k = B_CONJ_T ? (t >> 5) : (t & 3) * 2, lb_j = B_CONJ_T ? (t & 31) * 2 : (t >> 2);
-  float4 ra, rb;
-  auto load = [&](int k0) {
-    {
-      const int k = k0 + la_k, i = i0 + la_i;
-      if (k < ke && i + 1 < M) {
-        ra = *reinterpret_cast<const float4*>(A + (size_t)k * lda + i);
-      } else {
-        float2 p = make_float2(0.f, 0.f), q = p;
-        if (k < ke && i < M) p = A[(size_t)k * lda + i];
-        ra = make_float4(p.x, p.y, q.x, q.y);
-      }
+  const int ntiles = max(0, (ke - kb + TK - 1) / TK);
+
+  if (t == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], NPROD);
+      tc::mbar_init(&empty[s], 1);
     }
-    if (B_CONJ_T) {
-      const int k = k0 + lb_k, j = j0 + lb_j;
-      if (k < ke && j + 1 < N) {
-        rb = *reinterpret_cast<const float4*>(B + (size_t)k * ldb + j);
-      } else {
-        float2 p = make_float2(0.f, 0.f), q = p;
-        if (k < ke && j < N) p = B[(size_t)k * ldb + j];
-        rb = make_float4(p.x, p.y, q.x, q.y);
-      }
-    } else {
-      const int k = k0 + lb_k, j = j0 + lb_j;
-      if (j < N && k + 1 < ke) {
-        rb = *reinterpret_cast<const float4*>(B + (size_t)j * ldb + k);
-      } else {
-        float2 p = make_float2(0.f, 0.f), q = p;
-        if (j < N && k < ke) p = B[(size_t)j * ldb + k];
-        rb = make_float4(p.x, p.y, q.x, q.y);
-      }
-    }
-  };
-  auto store = [&](int buf) {
-    *reinterpret_cast<float4*>(&As[buf][la_k][la_i]) = ra;
-    if (B_CONJ_T) {
-      *reinterpret_cast<float4*>(&Bs[buf][lb_k][lb_j]) = make_float4(rb.x, -rb.y, rb.z, -rb.w);
-    } else {
-      Bs[buf][lb_k][lb_j] = make_float2(rb.x, rb.y);
-      Bs[buf][lb_k + 1][lb_j] = make_float2(rb.z, rb.w);
-    }
-  };
-  float2 acc[4][4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
-  if (kb < ke) {
-    load(kb);
-    store(0);
+    tc::fence_mbar_init();
+    *abort_flag = 0;
   }
+  if (warp == 8) tc::tmem_alloc(tslot, TMEM_COLS);
+  tc::fence_before();
   __syncthreads();
-  int buf = 0;
-  for (int k0 = kb; k0 < ke; k0 += GBK) {
-    const bool more = k0 + GBK < ke;
-    if (more) load(k0 + GBK);
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 8) {
+    if ((t & 31) == 0) {   // MMA issuer
+      constexpr uint32_t idesc = tc::idesc_tf32(128, 2 * TN);
+      for (int it = 0; it < ntiles; ++it) {
+        const int s = it % STAGES;
+        if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag)) break;
+        tc::fence_after();
+        const uint32_t ab = tc::smem_u32(smem + s * STAGE_BYTES), as = ab + A_BYTES, bb = ab + 2 * A_BYTES,
+                       bs = bb + B_BYTES;
+        const uint32_t dcol = tmem + (uint32_t)(((it / GROUP) & 1) * DCOLS);
 #pragma unroll
-    for (int k = 0; k < GBK; ++k) {
-      const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4]);
-      const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][k][ty * 4 + 2]);
-      const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
-                           make_float2(a23.z, a23.w)};
-      float2 b[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[buf][k][tx + 16 * c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cmac<false>(acc[r][c], a[r], b[c]);
+        for (int kk = 0; kk < KR / 8; ++kk) {   // K = 8 tf32 (two core matrices) per MMA
+          const uint32_t koff = kk * 256;
+          const uint64_t dab = tc::smem_desc(ab + koff, 128, (KR / 4) * 128);
+          const uint64_t das = tc::smem_desc(as + koff, 128, (KR / 4) * 128);
+          const uint64_t dbb = tc::smem_desc(bb + koff, 128, (KR / 4) * 128);
+          const uint64_t dbs = tc::smem_desc(bs + koff, 128, (KR / 4) * 128);
+          tc::mma_tf32(dcol, dab, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_tf32(dcol, dab, dbs, idesc, 1u);
+          tc::mma_tf32(dcol, das, dbb, idesc, 1u);
+        }
+        tc::commit(&empty[s]);
+      }
     }
-    if (more) store(buf ^ 1);
-    __syncthreads();
-    buf ^= 1;
-  }
-  float2* Cz = C + (size_t)blockIdx.z * c_stride;
+  } else {
+    float re[32], im[32];
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int j = j0 + tx + 16 * c;
-    if (j >= N) continue;
-    const int i = i0 + ty * 4;
-    float2* p = Cz + (size_t)j * ldc + i;
-    if (i + 3 < M) {
-      reinterpret_cast<float4*>(p)[0] = make_float4(acc[0][c].x, acc[0][c].y, acc[1][c].x, acc[1][c].y);
-      reinterpret_cast<float4*>(p)[1] = make_float4(acc[2][c].x, acc[2][c].y, acc[3][c].x, acc[3][c].y);
-    } else {
-      for (int r = 0; r < 4; ++r)
-        if (i + r < M) p[r] = acc[r][c];
+    for (int q = 0; q < 32; ++q) re[q] = im[q] = 0.f;
+    int flushed = 0;
+    const int am = t & 127, aq = t >> 7;   // A: row am, complex K 8 aq .. 8 aq + 7 of the tile
+    const int bn = t & 63, bq = t >> 6;    // B: column bn, complex K 4 bq .. 4 bq + 3
+    float2 a[8], b[4];
+    auto load = [&](int it) {
+      const int ka = kb + it * TK + 8 * aq, kq = kb + it * TK + 4 * bq;
+      const int i = i0 + am, j = j0 + bn;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = ka + q;
+        a[q] = (k < ke && i < M) ? A[(size_t)k * lda + i] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = kq + q;
+        if (k < ke && j < N) {
+          if (B_CONJ_T) {
+            const float2 v = B[(size_t)k * ldb + j];
+            b[q] = make_float2(v.x, -v.y);
+          } else {
+            b[q] = B[(size_t)j * ldb + k];
+          }
+        } else {
+          b[q] = make_float2(0.f, 0.f);
+        }
+      }
+    };
+    bool ok = true;
+    if (ntiles > 0) load(0);
+    for (int it = 0; it < ntiles && ok; ++it) {
+      const int s = it % STAGES;
+      if (it >= STAGES) {
+        ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag);
+        if (!ok) break;
+        tc::fence_after();
+        // every group whose last tile is it - STAGES or earlier is complete: fold it in
+        const int done_groups = (it - STAGES + 1) / GROUP;
+        while (flushed < done_groups) {
+          flush(tmem, flushed & 1, warp, re, im);
+          ++flushed;
+        }
+      }
+      uint8_t* Ab = smem + s * STAGE_BYTES;
+      uint8_t* As = Ab + A_BYTES;
+      uint8_t* Bb = Ab + 2 * A_BYTES;
+      uint8_t* Bs = Bb + B_BYTES;
+      {
+        const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
+        const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
+        put(Ab, As, kmaj(am, 8 * aq), r0);
+        put(Ab, As, kmaj(am, 8 * aq + 4), r1);
+        put(Ab, As, kmaj(am, TK + 8 * aq), m0);
+        put(Ab, As, kmaj(am, TK + 8 * aq + 4), m1);
+        const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
+        const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
+        put(Bb, Bs, kmaj(bn, 4 * bq), br);              // row n:      Br
+        put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
+        put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
+        put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
+      }
+      if (it + 1 < ntiles) load(it + 1);
+      tc::fence_proxy_async();
+      tc::fence_before();
+      tc::mbar_arrive(&full[s]);
+    }
+    // the last tile's commit covers every MMA of the CTA
+    if (ok && ntiles > 0) ok = warp_wait(&empty[(ntiles - 1) % STAGES], ((ntiles - 1) / STAGES) & 1, abort_flag);
+    tc::fence_after();
+    if (ok) {
+      const int groups = (ntiles + GROUP - 1) / GROUP;
+      while (flushed < groups) {
+        flush(tmem, flushed & 1, warp, re, im);
+        ++flushed;
+      }
+    }
+    const int i = i0 + 32 * (warp & 3) + (t & 31);
+    float2* Cz = C + (size_t)blockIdx.z * c_stride;
+    if (i < M) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = j0 + 32 * (warp >> 2) + q;
+        if (j < N) Cz[(size_t)j * ldc + i] = make_float2(re[q], im[q]);
+      }
     }
   }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 8) {
+    tc::fence_after();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (t == 0 && *abort_flag) atomicExch(err, 2);
 }
 
 // ---------------------------------------------------------------------------
@@ -941,11 +1090,16 @@ static msp_status device(Dev* d, PerN* pn, int N) {
   Dev& D = g_dev[dev];
   if (!D.init) {
     SMD_CK(cudaDeviceGetAttribute(&D.sms, cudaDevAttrMultiProcessorCount, dev));
-    int k = 0;
-    SMD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, cgemm_kernel<false>, 256, 0));
-    int k2 = 0;
-    SMD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k2, cgemm_kernel<true>, 256, 0));
+    SMD_CK(cudaFuncSetAttribute(cgemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm::SMEM_BYTES));
+    SMD_CK(cudaFuncSetAttribute(cgemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm::SMEM_BYTES));
+    int k = 0, k2 = 0;
+    SMD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, cgemm_kernel<false>, gemm::NTHREADS, gemm::SMEM_BYTES));
+    SMD_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k2, cgemm_kernel<true>, gemm::NTHREADS, gemm::SMEM_BYTES));
     D.gemm_per_sm = std::max(1, std::min(k, k2));
+    // resident CTAs must never ask for more than the 512 TMEM columns of an SM (an allocation
+    // that cannot be met waits)
+    if (std::max(k, k2) * (int)gemm::TMEM_COLS > 512)
+      return fail(MSP_EUNSUPPORTED, "tensor-memory budget: more resident contraction CTAs than TMEM allows");
     D.init = true;
   }
   *d = D;
@@ -961,7 +1115,8 @@ static msp_status device(Dev* d, PerN* pn, int N) {
 }
 
 // Split of the K range of a contraction over `tiles` output tiles: the split count that
-// minimises waves x K-chunk (the time of the slowest slot), fewest splits on ties.
+// minimises waves x (K-chunk + the cost of writing one partial tile, counted as 64 K),
+// fewest splits on ties.
 struct Split {
   int splits = 1, chunk = 0;
 };
@@ -970,11 +1125,11 @@ static Split choose_split(int tiles, int K, int slots, int max_splits) {
   long long best_cost = -1;
   for (int s = 1; s <= max_splits; ++s) {
     int chunk = (K + s - 1) / s;
-    chunk = (chunk + GBK - 1) / GBK * GBK;
+    chunk = (chunk + gemm::TK - 1) / gemm::TK * gemm::TK;
     const int real = (K + chunk - 1) / chunk;
     if (real != s) continue;
     const long long waves = ((long long)tiles * s + slots - 1) / slots;
-    const long long cost = waves * chunk;
+    const long long cost = waves * (chunk + 64);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best.splits = s;
@@ -984,9 +1139,10 @@ static Split choose_split(int tiles, int K, int slots, int max_splits) {
   return best;
 }
 
-static int tiles_of(int M, int N) { return ((M + GBM - 1) / GBM) * ((N + GBN - 1) / GBN); }
+static int tiles_of(int M, int N) { return ((M + gemm::TM - 1) / gemm::TM) * ((N + gemm::TN - 1) / gemm::TN); }
 
 struct Layout {
+  int* err = nullptr;        // first word of the workspace: 2 = a tensor-core wait timed out
   double* scal = nullptr;
   double* part = nullptr;    // kPartSlots
   double* part2 = nullptr;   // kPartSlots
@@ -1017,6 +1173,7 @@ static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, ch
   w.grid_ff = (int)std::min({S, (size_t)pn.plain * d.sms, cap});
   size_t off = 0;
   auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+  w.err = (int*)take(sizeof(int));
   w.scal = (double*)take(32 * sizeof(double));
   w.part = (double*)take(kPartSlots * sizeof(double));
   w.part2 = (double*)take(kPartSlots * sizeof(double));
@@ -1090,6 +1247,7 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
                                 const int2* shifts, const float* I, double step, double* obj_out) {
   const size_t n2 = (size_t)N * N, S = g->n_pos;
   const Layout& w = c.w;
+  SMD_CK(cudaMemsetAsync(w.err, 0, sizeof(int), c.st));   // the call's own error word
   const int blocks = (int)std::min<size_t>((n2 * S + 255) / 256, (size_t)c.dev.sms * 16);
   probe_matrix_kernel<<<blocks, 256, 0, c.st>>>(probe, shifts, N, (int)S, w.P);
   SMD_LAUNCHED(1);
@@ -1100,9 +1258,10 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
                                                                         w.scal, nullptr);
   SMD_LAUNCHED(1);
   // A P: M = N^2, N = S, K = N^2
-  dim3 g1((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((S + GBN - 1) / GBN), (unsigned)w.s1.splits);
+  dim3 g1((unsigned)((n2 + gemm::TM - 1) / gemm::TM), (unsigned)((S + gemm::TN - 1) / gemm::TN), (unsigned)w.s1.splits);
   SMD_TRY(profiled_launch(c.st, [&] {
-    cgemm_kernel<false><<<g1, 256, 0, c.st>>>((int)n2, (int)S, (int)n2, w.s1.chunk, A, n2, w.P, n2, w.BC, n2, n2 * S);
+    cgemm_kernel<false><<<g1, gemm::NTHREADS, gemm::SMEM_BYTES, c.st>>>((int)n2, (int)S, (int)n2, w.s1.chunk, A, n2,
+                                                                         w.P, n2, w.BC, n2, n2 * S, w.err);
     return cudaGetLastError();
   }));
   farfield_kernel<N><<<w.grid_ff, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(w.BC, w.s1.splits, n2 * S, I,
@@ -1111,9 +1270,10 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   finish_sum_kernel<<<1, 256, 0, c.st>>>(w.part, w.grid_ff, w.scal, S_OBJ, obj_out);
   SMD_LAUNCHED(1);
   // C P^H: M = N^2, N = N^2, K = S
-  dim3 g2((unsigned)((n2 + GBM - 1) / GBM), (unsigned)((n2 + GBN - 1) / GBN), (unsigned)w.s2.splits);
+  dim3 g2((unsigned)((n2 + gemm::TM - 1) / gemm::TM), (unsigned)((n2 + gemm::TN - 1) / gemm::TN), (unsigned)w.s2.splits);
   SMD_TRY(profiled_launch(c.st, [&] {
-    cgemm_kernel<true><<<g2, 256, 0, c.st>>>((int)n2, (int)n2, (int)S, w.s2.chunk, w.BC, n2, w.P, n2, w.U, n2, n2 * n2);
+    cgemm_kernel<true><<<g2, gemm::NTHREADS, gemm::SMEM_BYTES, c.st>>>((int)n2, (int)n2, (int)S, w.s2.chunk, w.BC, n2,
+                                                                        w.P, n2, w.U, n2, n2 * n2, w.err);
     return cudaGetLastError();
   }));
   const size_t pairs = n2 * n2 / 2;
