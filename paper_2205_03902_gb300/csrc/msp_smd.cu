@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
 // to nearest, so D accumulates over groups of GROUP K-tiles only, alternating between two
 // TMEM halves; each finished group is added into FP32 registers.
 //
-// Warps 0..7 are producers: they load K-tiles of A and B (one tile ahead, in registers),
+// Warps 0..7 are producers: they load K-tiles of A and B (two tiles ahead, in registers),
 // split them and write them in the canonical no-swizzle K-major layout into a 3-stage
 // shared-memory ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
 // TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
@@ -561,11 +561,17 @@ struct Split4 {
   uint4 big, small;
 };
 
+// big = x rounded to tf32 (nearest, ties away: add half a tf32 ulp, clear the 13 low bits, two
+// integer operations instead of the conversion unit); small = x - big, exact in FP32, handed
+// over unrounded (the tensor core reads the 19 high bits of a tf32 operand, so small loses at
+// most 2^-10 of itself, 2^-21 of x).
+__device__ __forceinline__ uint32_t tf32_big(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
+
 __device__ __forceinline__ Split4 split4(float x0, float x1, float x2, float x3) {
   Split4 r;
-  r.big = make_uint4(tc::to_tf32(x0), tc::to_tf32(x1), tc::to_tf32(x2), tc::to_tf32(x3));
-  r.small = make_uint4(tc::to_tf32(x0 - __uint_as_float(r.big.x)), tc::to_tf32(x1 - __uint_as_float(r.big.y)),
-                       tc::to_tf32(x2 - __uint_as_float(r.big.z)), tc::to_tf32(x3 - __uint_as_float(r.big.w)));
+  r.big = make_uint4(tf32_big(x0), tf32_big(x1), tf32_big(x2), tf32_big(x3));
+  r.small = make_uint4(__float_as_uint(x0 - __uint_as_float(r.big.x)), __float_as_uint(x1 - __uint_as_float(r.big.y)),
+                       __float_as_uint(x2 - __uint_as_float(r.big.z)), __float_as_uint(x3 - __uint_as_float(r.big.w)));
   return r;
 }
 
@@ -666,19 +672,20 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     int flushed = 0;
     const int am = t & 127, aq = t >> 7;   // A: row am, complex K 8 aq .. 8 aq + 7 of the tile
     const int bn = t & 63, bq = t >> 6;    // B: column bn, complex K 4 bq .. 4 bq + 3
-    float2 a[8], b[4];
-    auto load = [&](int it) {
+    // operands of the next two K-tiles in flight, in two register sets
+    float2 a0[8], b0[4], a1[8], b1[4];
+    auto load = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
       const int ka = kb + it * TK + 8 * aq, kq = kb + it * TK + 4 * bq;
       const int i = i0 + am, j = j0 + bn;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int k = ka + q;
-        a[q] = (k < ke && i < M) ? A[(size_t)k * lda + i] : make_float2(0.f, 0.f);
+        a[q] = (it < ntiles && k < ke && i < M) ? A[(size_t)k * lda + i] : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int k = kq + q;
-        if (k < ke && j < N) {
+        if (it < ntiles && k < ke && j < N) {
           if (B_CONJ_T) {
             const float2 v = B[(size_t)k * ldb + j];
             b[q] = make_float2(v.x, -v.y);
@@ -691,12 +698,12 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       }
     };
     bool ok = true;
-    if (ntiles > 0) load(0);
-    for (int it = 0; it < ntiles && ok; ++it) {
+    // fills the stage of tile it from (a, b), then starts the loads of tile it + 2 into them
+    auto produce = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
       const int s = it % STAGES;
       if (it >= STAGES) {
         ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag);
-        if (!ok) break;
+        if (!ok) return;
         tc::fence_after();
         // every group whose last tile is it - STAGES or earlier is complete: fold it in
         const int done_groups = (it - STAGES + 1) / GROUP;
@@ -709,24 +716,28 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       uint8_t* As = Ab + A_BYTES;
       uint8_t* Bb = Ab + 2 * A_BYTES;
       uint8_t* Bs = Bb + B_BYTES;
-      {
-        const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
-        const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
-        put(Ab, As, kmaj(am, 8 * aq), r0);
-        put(Ab, As, kmaj(am, 8 * aq + 4), r1);
-        put(Ab, As, kmaj(am, TK + 8 * aq), m0);
-        put(Ab, As, kmaj(am, TK + 8 * aq + 4), m1);
-        const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
-        const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
-        put(Bb, Bs, kmaj(bn, 4 * bq), br);              // row n:      Br
-        put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
-        put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
-        put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
-      }
-      if (it + 1 < ntiles) load(it + 1);
+      const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
+      const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
+      put(Ab, As, kmaj(am, 8 * aq), r0);
+      put(Ab, As, kmaj(am, 8 * aq + 4), r1);
+      put(Ab, As, kmaj(am, TK + 8 * aq), m0);
+      put(Ab, As, kmaj(am, TK + 8 * aq + 4), m1);
+      const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
+      const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
+      put(Bb, Bs, kmaj(bn, 4 * bq), br);              // row n:      Br
+      put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
+      put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
+      put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
+      if (it + 2 < ntiles) load(it + 2, a, b);
       tc::fence_proxy_async();
       tc::fence_before();
       tc::mbar_arrive(&full[s]);
+    };
+    load(0, a0, b0);
+    load(1, a1, b1);
+    for (int it = 0; it < ntiles && ok; it += 2) {
+      produce(it, a0, b0);
+      if (ok && it + 1 < ntiles) produce(it + 1, a1, b1);
     }
     // the last tile's commit covers every MMA of the CTA
     if (ok && ntiles > 0) ok = warp_wait(&empty[(ntiles - 1) % STAGES], ((ntiles - 1) / STAGES) & 1, abort_flag);
@@ -788,18 +799,24 @@ __global__ void propagator_kernel(float2* __restrict__ h, int N, double dzlam, d
 
 // gk = G e_0, the real-space kernel of the propagator: with h = h1(ky) h1(kx) separable,
 // gk[y][x] = g1(y) g1(x), g1(y) = (1/N) sum_k h1(k) exp(2 pi i k y / N); in double, rounded once.
-__global__ void __launch_bounds__(256) kernel_column_kernel(float2* __restrict__ gk, int N, double dzlam, double dq) {
+__global__ void __launch_bounds__(1024) kernel_column_kernel(float2* __restrict__ gk, int N, double dzlam, double dq) {
   __shared__ double2 g1[64];
-  for (int y = threadIdx.x; y < N; y += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int y = warp; y < N; y += 32) {   // one warp per y: lanes take k = lane, lane + 32; butterfly sum
     double re = 0.0, im = 0.0;
-    for (int k = 0; k < N; ++k) {
+    for (int k = lane; k < N; k += 32) {
       const double q = (k < N / 2 ? k : k - N) * dq;
       double s, c;
       sincospi(-dzlam * q * q + 2.0 * (double)((k * y) % N) / N, &s, &c);
       re += c;
       im += s;
     }
-    g1[y] = make_double2(re / N, im / N);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0) g1[y] = make_double2(re / N, im / N);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
@@ -873,9 +890,11 @@ __global__ void __launch_bounds__(1024) slice_max_kernel(const float2* __restric
     if (t == 0) scal[S_MAXO + m] = sqrt((double)sh[0]);
     __syncthreads();
   }
+  __shared__ double shd[1025];
+  double a = 0.0;
+  for (int i = t; i < n_part; i += 1024) a += obj_part[i];
+  const double s = block_sum(a, shd);
   if (t == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n_part; ++i) s += obj_part[i];
     scal[S_DOBJ] = s;
     if (obj_out) obj_out[0] = s;
   }
@@ -1222,7 +1241,7 @@ static msp_status launch_propagator(const msp_smd_geometry* g, Call& c) {
   propagator_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.h, N, g->dz_A * g->wavelength_A,
                                                            1.0 / ((double)N * g->pixel_A));
   SMD_LAUNCHED(1);
-  kernel_column_kernel<<<1, 256, 0, c.st>>>(c.w.gk, N, g->dz_A * g->wavelength_A,
+  kernel_column_kernel<<<1, 1024, 0, c.st>>>(c.w.gk, N, g->dz_A * g->wavelength_A,
                                                               1.0 / ((double)N * g->pixel_A));
   SMD_LAUNCHED(1);
   return MSP_OK;
