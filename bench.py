@@ -461,6 +461,122 @@ def run_smd(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# DFT as a matrix product on the tensor cores, against the fused shared-memory FFT
+# ---------------------------------------------------------------------------
+
+DFT_METRIC = "2-D DFTs/s (W = 128, tensor-core contraction)"
+DFT_UNIT = "transforms/s"
+
+
+def run_dft(args, rank, world, local_rank):
+    """The batched 2-D DFT of msp_dft2_tc on c3's shape (S = 4096 images of 128 x 128), and, in the
+    same run, the fused kernel's own FFT rate in the c3 layer step ((4L - 2) 2-D FFTs per position)."""
+    import torch
+    from paper_2205_03902_gb300 import msp
+    import __graft_entry__
+    __graft_entry__.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    cfg = synth.C3
+    S, W = cfg.n_pos, cfg.win
+    x_h = synth.random_complex((S, W, W), 7).astype(np.complex64)
+    x = torch.from_numpy(x_h).to(dev)
+    y = torch.empty_like(x)
+    n = int(msp.lib().msp_dft2_tc_workspace_bytes(W, S))
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=dev)
+    off = (-buf.data_ptr()) % 256
+    ws = msp.Workspace(buf[off:off + n])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        msp.dft2_tc(x, out=y, ws=ws)
+    torch.cuda.synchronize()
+    msp.profile_read(reset=True)
+    msp.profile_enable(True)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        msp.dft2_tc(x, out=y, ws=ws)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = msp.profile_read(reset=True)
+    msp.profile_enable(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    value = S / (ms * 1e-3)
+    pass_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
+    tc_flops = 24.0 * S * W ** 3                      # one pass: 24 M N K with M = K = W, N = S W
+    peaks = read_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    tf32_peak = bf16 * 1.1 / 2.25
+    # end to end: host -> device, transform, device -> host (pinned buffers)
+    x_pin = torch.from_numpy(x_h).pin_memory()
+    y_pin = torch.empty_like(x_pin).pin_memory()
+    e_steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        x.copy_(x_pin, non_blocking=True)
+        msp.dft2_tc(x, out=y, ws=ws)
+        y_pin.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e = S / ((time.perf_counter() - t0) / e_steps)
+    # the fused kernel's FFT rate on the c3 layer step
+    g, gd, pos, d_pos, ws3, V_true, p_guess, I_meas = make_inputs(msp, torch, dev, cfg)
+    probe = torch.from_numpy(p_guess).to(dev)
+    V = torch.zeros((cfg.n_slices, cfg.obj, cfg.obj), dtype=torch.float32, device=dev)
+    Im = torch.from_numpy(I_meas).to(dev)
+    for _ in range(2):
+        msp.layer_step(g, probe, V, d_pos, Im, 0, ws=ws3)
+    torch.cuda.synchronize()
+    msp.profile_read(reset=True)
+    msp.profile_enable(True)
+    for _ in range(5):
+        msp.layer_step(g, probe, V, d_pos, Im, 0, ws=ws3)
+    torch.cuda.synchronize()
+    p3 = msp.profile_read(reset=True)
+    msp.profile_enable(False)
+    fused_ms = p3["fused_ms"] / max(1, p3["fused_launches"])
+    fft_rate = (4 * cfg.n_slices - 2) * S / (fused_ms * 1e-3)
+    line = {
+        "metric": DFT_METRIC, "value": value, "unit": DFT_UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"dft2_W{W}_S{S} (c3 shape)", "call": "msp_dft2_tc (two tensor-core passes)",
+                   "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "parallelism": "single GPU"},
+        "roofline": {"bound": "tensor", "achieved": tc_flops / (pass_ms * 1e-3) / 1e12, "peak": tf32_peak,
+                     "unit": "TFLOP/s", "frac": tc_flops / (pass_ms * 1e-3) / 1e12 / tf32_peak, "traffic": None,
+                     "kernel": "cgemm_kernel<false, true> (one DFT pass, tcgen05 kind::tf32, split operands)",
+                     "kernel_ms": pass_ms,
+                     "peak_source": f"measured bf16 burst {bf16:.1f} TFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"},
+        "smem_fft_comparison": {"fused_kernel": "position_kernel<128, LAYER> on the c3 layer step",
+                                "fused_kernel_ms": fused_ms, "fft_transforms_per_s": fft_rate,
+                                "tensor_dft_over_smem_fft": value / fft_rate},
+        "e2e": {"value": e2e, "unit": DFT_UNIT, "h2d_bytes_per_step": S * W * W * 8, "d2h_bytes_per_step": S * W * W * 8},
+        "gpu_launches": int(prof["all_launches"]),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        sub = x_h[:64].astype(np.complex128)
+        from oracle import msp_oracle as O
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 5.0:
+            for v in sub:
+                O.dft2(v)
+            reps += 1
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": reps * len(sub) / dt, "unit": DFT_UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{reps * len(sub)} transforms of 128 x 128 with the oracle's numpy FFT, one thread, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
 def run_msp(args, rank, world, local_rank):
     import torch
     from paper_2205_03902_gb300 import msp
@@ -617,12 +733,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS),
+    ap.add_argument("--config", default="c2", choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3"],
                     help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration; "
                          "smd_gaas: Algorithm 2 on the Table 1 setting)")
     args = ap.parse_args()
     global CFG
     smd = args.config in synth.SMD_CONFIGS
+    if args.config == "dft_c3":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the DFT study has no reference arm; see --config c3"}))
+            return
+        run_dft(args, int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+                int(os.environ.get("LOCAL_RANK", 0)))
+        return
     CFG = synth.SMD_CONFIGS[args.config] if smd else synth.CONFIGS[args.config]
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -35,7 +35,7 @@
 
 #include "msp.h"
 #include "msp_smd.h"
-#include "msp_tc.cuh"
+#include "msp_cgemm.cuh"
 
 namespace msp {
 
@@ -495,277 +495,6 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
     scal[S_MU] = mu;
     if (mu_out) mu_out[0] = mu;
   }
-}
-
-// ---------------------------------------------------------------------------
-// dense complex contraction on the tensor cores (tcgen05, 3xTF32)
-// ---------------------------------------------------------------------------
-// C_z = A[:, K_z] op(B)[K_z, :] for the K range K_z of blockIdx.z.  A: M x K column-major.
-// op(B) = B (K x N column-major) or, with B_CONJ_T, B^H for B stored N x K column-major.
-// C: M x N column-major, partial z at C + z * c_stride.
-//
-// One CTA computes a 128 x 64 complex tile.  The complex product is the real product
-//   D (128 x 128) = A_re B_re^T,  A_re = [Ar, Ai],  B_re rows n: [Br, -Bi], rows 64 + n: [Bi, Br]
-// so columns n of D hold Re C and columns 64 + n hold Im C.  Every real operand x is split
-// into tf32 parts x = big + small and D accumulates big*big + big*small + small*big, which
-// keeps the product error near FP32's.  The tensor core's FP32 accumulation does not round
-// to nearest, so D accumulates over groups of GROUP K-tiles only, alternating between two
-// TMEM halves; each finished group is added into FP32 registers.
-//
-// Warps 0..7 are producers: they load K-tiles of A and B (two tiles ahead, in registers),
-// split them and write them in the canonical no-swizzle K-major layout into a 3-stage
-// shared-memory ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
-// TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
-// mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded: on
-// timeout the CTA raises *err = 2, stops and frees its TMEM.
-namespace gemm {
-constexpr int TM = 128, TN = 64, TK = 16;                   // complex tile and K-tile
-constexpr int KR = 2 * TK;                                  // real K per tile
-constexpr uint32_t A_BYTES = 128 * KR * 4;                  // one tf32 part of A_re: 16 KB
-constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 16 KB
-constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES; // 64 KB
-constexpr int STAGES = 3;
-constexpr int GROUP = 8;
-constexpr int NPROD = 256;
-constexpr int NTHREADS = NPROD + 32;
-constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of one accumulator
-constexpr uint32_t TMEM_COLS = 2 * DCOLS;
-constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
-constexpr int kWaitLimit = 1 << 20;                         // polls (with 32 ns pauses) per wait
-
-// Bounded wait; gives up early once another thread has raised the abort flag.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (int i = 0; i < kWaitLimit; ++i) {
-    if (tc::mbar_test(bar, parity)) return true;
-    if ((i & 255) == 255 && *abort_flag) return false;
-    if (i > 64) __nanosleep(32);
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-// Warp-uniform wait: lane 0 waits, every lane gets the verdict.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(bar, parity, abort_flag) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-// Byte offset of real element (row, k) in a K-major operand: core matrices of 8 rows x 4
-// tf32, 128 bytes apart along K, KR/4 * 128 bytes apart along rows.
-__device__ __forceinline__ uint32_t kmaj(int row, int k) {
-  return (uint32_t)((k >> 2) * 128 + (row >> 3) * (KR / 4) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
-
-struct Split4 {
-  uint4 big, small;
-};
-
-// big = x rounded to tf32 (nearest, ties away: add half a tf32 ulp, clear the 13 low bits, two
-// integer operations instead of the conversion unit); small = x - big, exact in FP32, handed
-// over unrounded (the tensor core reads the 19 high bits of a tf32 operand, so small loses at
-// most 2^-10 of itself, 2^-21 of x).
-__device__ __forceinline__ uint32_t tf32_big(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
-
-__device__ __forceinline__ Split4 split4(float x0, float x1, float x2, float x3) {
-  Split4 r;
-  r.big = make_uint4(tf32_big(x0), tf32_big(x1), tf32_big(x2), tf32_big(x3));
-  r.small = make_uint4(__float_as_uint(x0 - __uint_as_float(r.big.x)), __float_as_uint(x1 - __uint_as_float(r.big.y)),
-                       __float_as_uint(x2 - __uint_as_float(r.big.z)), __float_as_uint(x3 - __uint_as_float(r.big.w)));
-  return r;
-}
-
-__device__ __forceinline__ Split4 neg(const Split4& v) {   // rounding is symmetric: split(-x) = -split(x)
-  Split4 r;
-  r.big = make_uint4(v.big.x ^ 0x80000000u, v.big.y ^ 0x80000000u, v.big.z ^ 0x80000000u, v.big.w ^ 0x80000000u);
-  r.small = make_uint4(v.small.x ^ 0x80000000u, v.small.y ^ 0x80000000u, v.small.z ^ 0x80000000u,
-                       v.small.w ^ 0x80000000u);
-  return r;
-}
-
-__device__ __forceinline__ void put(uint8_t* big, uint8_t* small, uint32_t off, const Split4& v) {
-  *reinterpret_cast<uint4*>(big + off) = v.big;
-  *reinterpret_cast<uint4*>(small + off) = v.small;
-}
-
-// Adds accumulator half h into this thread's registers: TMEM lane (row) 32 (warp & 3) + lane,
-// columns 32 (warp >> 2) + q (Re) and TN + 32 (warp >> 2) + q (Im), q < 32.
-__device__ __forceinline__ void flush(uint32_t tmem, int h, int warp, float (&re)[32], float (&im)[32]) {
-  const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(h * DCOLS + 32 * (warp >> 2));
-  uint32_t r[16];
-#pragma unroll
-  for (int part = 0; part < 4; ++part) {
-    tc::tmem_ld16(base + (part < 2 ? 16 * part : TN + 16 * (part - 2)), r);
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      if (part < 2)
-        re[16 * part + q] += __uint_as_float(r[q]);
-      else
-        im[16 * (part - 2) + q] += __uint_as_float(r[q]);
-    }
-  }
-}
-}  // namespace gemm
-
-template <bool B_CONJ_T>
-__global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, int K, int k_chunk,
-                                                                  const float2* __restrict__ A, size_t lda,
-                                                                  const float2* __restrict__ B, size_t ldb,
-                                                                  float2* __restrict__ C, size_t ldc,
-                                                                  size_t c_stride, int* err) {
-  using namespace gemm;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + STAGES);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
-  const int t = threadIdx.x, warp = t >> 5;
-  const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
-  const int kb = blockIdx.z * k_chunk;
-  const int ke = min(K, kb + k_chunk);
-  const int ntiles = max(0, (ke - kb + TK - 1) / TK);
-
-  if (t == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(&full[s], NPROD);
-      tc::mbar_init(&empty[s], 1);
-    }
-    tc::fence_mbar_init();
-    *abort_flag = 0;
-  }
-  if (warp == 8) tc::tmem_alloc(tslot, TMEM_COLS);
-  tc::fence_before();
-  __syncthreads();
-  tc::fence_after();
-  const uint32_t tmem = *tslot;
-
-  if (warp == 8) {
-    if ((t & 31) == 0) {   // MMA issuer
-      constexpr uint32_t idesc = tc::idesc_tf32(128, 2 * TN);
-      for (int it = 0; it < ntiles; ++it) {
-        const int s = it % STAGES;
-        if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag)) break;
-        tc::fence_after();
-        const uint32_t ab = tc::smem_u32(smem + s * STAGE_BYTES), as = ab + A_BYTES, bb = ab + 2 * A_BYTES,
-                       bs = bb + B_BYTES;
-        const uint32_t dcol = tmem + (uint32_t)(((it / GROUP) & 1) * DCOLS);
-#pragma unroll
-        for (int kk = 0; kk < KR / 8; ++kk) {   // K = 8 tf32 (two core matrices) per MMA
-          const uint32_t koff = kk * 256;
-          const uint64_t dab = tc::smem_desc(ab + koff, 128, (KR / 4) * 128);
-          const uint64_t das = tc::smem_desc(as + koff, 128, (KR / 4) * 128);
-          const uint64_t dbb = tc::smem_desc(bb + koff, 128, (KR / 4) * 128);
-          const uint64_t dbs = tc::smem_desc(bs + koff, 128, (KR / 4) * 128);
-          tc::mma_tf32(dcol, dab, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_tf32(dcol, dab, dbs, idesc, 1u);
-          tc::mma_tf32(dcol, das, dbb, idesc, 1u);
-        }
-        tc::commit(&empty[s]);
-      }
-    }
-  } else {
-    float re[32], im[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) re[q] = im[q] = 0.f;
-    int flushed = 0;
-    const int am = t & 127, aq = t >> 7;   // A: row am, complex K 8 aq .. 8 aq + 7 of the tile
-    const int bn = t & 63, bq = t >> 6;    // B: column bn, complex K 4 bq .. 4 bq + 3
-    // operands of the next two K-tiles in flight, in two register sets
-    float2 a0[8], b0[4], a1[8], b1[4];
-    auto load = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
-      const int ka = kb + it * TK + 8 * aq, kq = kb + it * TK + 4 * bq;
-      const int i = i0 + am, j = j0 + bn;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = ka + q;
-        a[q] = (it < ntiles && k < ke && i < M) ? A[(size_t)k * lda + i] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = kq + q;
-        if (it < ntiles && k < ke && j < N) {
-          if (B_CONJ_T) {
-            const float2 v = B[(size_t)k * ldb + j];
-            b[q] = make_float2(v.x, -v.y);
-          } else {
-            b[q] = B[(size_t)j * ldb + k];
-          }
-        } else {
-          b[q] = make_float2(0.f, 0.f);
-        }
-      }
-    };
-    bool ok = true;
-    // fills the stage of tile it from (a, b), then starts the loads of tile it + 2 into them
-    auto produce = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
-      const int s = it % STAGES;
-      if (it >= STAGES) {
-        ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag);
-        if (!ok) return;
-        tc::fence_after();
-        // every group whose last tile is it - STAGES or earlier is complete: fold it in
-        const int done_groups = (it - STAGES + 1) / GROUP;
-        while (flushed < done_groups) {
-          flush(tmem, flushed & 1, warp, re, im);
-          ++flushed;
-        }
-      }
-      uint8_t* Ab = smem + s * STAGE_BYTES;
-      uint8_t* As = Ab + A_BYTES;
-      uint8_t* Bb = Ab + 2 * A_BYTES;
-      uint8_t* Bs = Bb + B_BYTES;
-      const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
-      const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
-      put(Ab, As, kmaj(am, 8 * aq), r0);
-      put(Ab, As, kmaj(am, 8 * aq + 4), r1);
-      put(Ab, As, kmaj(am, TK + 8 * aq), m0);
-      put(Ab, As, kmaj(am, TK + 8 * aq + 4), m1);
-      const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
-      const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
-      put(Bb, Bs, kmaj(bn, 4 * bq), br);              // row n:      Br
-      put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
-      put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
-      put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
-      if (it + 2 < ntiles) load(it + 2, a, b);
-      tc::fence_proxy_async();
-      tc::fence_before();
-      tc::mbar_arrive(&full[s]);
-    };
-    load(0, a0, b0);
-    load(1, a1, b1);
-    for (int it = 0; it < ntiles && ok; it += 2) {
-      produce(it, a0, b0);
-      if (ok && it + 1 < ntiles) produce(it + 1, a1, b1);
-    }
-    // the last tile's commit covers every MMA of the CTA
-    if (ok && ntiles > 0) ok = warp_wait(&empty[(ntiles - 1) % STAGES], ((ntiles - 1) / STAGES) & 1, abort_flag);
-    tc::fence_after();
-    if (ok) {
-      const int groups = (ntiles + GROUP - 1) / GROUP;
-      while (flushed < groups) {
-        flush(tmem, flushed & 1, warp, re, im);
-        ++flushed;
-      }
-    }
-    const int i = i0 + 32 * (warp & 3) + (t & 31);
-    float2* Cz = C + (size_t)blockIdx.z * c_stride;
-    if (i < M) {
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = j0 + 32 * (warp >> 2) + q;
-        if (j < N) Cz[(size_t)j * ldc + i] = make_float2(re[q], im[q]);
-      }
-    }
-  }
-  tc::fence_before();
-  __syncthreads();
-  if (warp == 8) {
-    tc::fence_after();
-    tc::tmem_dealloc(tmem, TMEM_COLS);
-  }
-  if (t == 0 && *abort_flag) atomicExch(err, 2);
 }
 
 // ---------------------------------------------------------------------------

@@ -92,6 +92,8 @@ _SIGS = {
     "msp_smd_matrix_step": ([_GS, _P, _P, _P, _P, ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "msp_smd_decompose": ([_GS, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "msp_smd_final_slices": ([_GS, _P, _P, _P, _P], ctypes.c_int),
+    "msp_dft2_tc_workspace_bytes": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_size_t),
+    "msp_dft2_tc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "msp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "msp_last_error_message": ([], ctypes.c_char_p),
 }
@@ -396,6 +398,32 @@ def sparse_decomposition(g: SmdGeometry, probe, shifts, I, iterations: int, matr
             smd_matrix_step(g, A, probe, shifts, I, ws=ws, stream=stream, objective=hm[t * matrix_steps + k:][:1])
         smd_decompose(g, A, o, lam, ws=ws, stream=stream, objective=hd[t:][:1])
     return smd_final_slices(g, o, lam, stream=stream), lam, hm, hd
+
+
+# ---------------------------------------------------------------------------
+# Batched 2-D DFT on the tensor cores (include/msp_dft.h)
+# ---------------------------------------------------------------------------
+
+def dft2_tc(x, inverse: bool = False, out=None, ws=None, stream=None):
+    """F x_s F for a batch x [S][W][W] complex64 (inverse: the conjugate kernel, unnormalised),
+    as two tensor-core contractions (msp_dft2_tc)."""
+    if not isinstance(x, torch.Tensor) or x.dim() != 3 or x.shape[1] != x.shape[2]:
+        raise ValueError("x must be a [S][W][W] tensor")
+    S, W = int(x.shape[0]), int(x.shape[1])
+    _need(x, "x", torch.complex64, (S, W, W), x.device)
+    if out is None:
+        out = torch.empty_like(x)
+    _need(out, "out", torch.complex64, (S, W, W), x.device)
+    n = int(lib().msp_dft2_tc_workspace_bytes(W, S))
+    if n == 0:
+        raise MspError(MSP_EUNSUPPORTED, "msp_dft2_tc", f"W = {W}, S = {S} not supported")
+    if ws is None or ws.nbytes < n:
+        buf = torch.empty(n + 256, dtype=torch.uint8, device=x.device)
+        off = (-buf.data_ptr()) % 256
+        ws = Workspace(buf[off:off + n])
+    _check(lib().msp_dft2_tc(W, S, 1 if inverse else 0, _ptr(x), _ptr(out), ws.ptr(), ws.nbytes, _stream(stream)),
+           "msp_dft2_tc")
+    return out
 
 
 class MultisliceLoss(torch.autograd.Function):
