@@ -165,6 +165,14 @@ msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const 
  * when a bounded wait for the tensor core ran out (msp_smd_matrix_step). */
 msp_status msp_check_workspace(void* ws, void* stream);
 
+/* Failure-detection hook: the number of polls after which a wait of the tensor-core
+ * kernels (msp_smd_matrix_step, msp_dft2_tc) for their own pipeline gives up, for every
+ * later call of this process.  The default (polls < 1 restores it) is 2^20 polls, well
+ * under a second; a tiny bound makes the waits run out on purpose, which the kernels
+ * report through the workspace flag (msp_check_workspace: MSP_ETIMEOUT) after freeing
+ * their tensor memory, leaving the device usable. */
+msp_status msp_set_wait_limit(int32_t polls);
+
 /* Profiling hooks, off by default.  While enabled, every launch of the dominant
  * kernel of a call is bracketed by CUDA events recorded on its stream: the fused
  * per-position kernel (the forward / adjoint of all positions) of the calls above,

@@ -347,6 +347,10 @@ static msp_status fail(msp_status s, const std::string& m) {
 msp_status set_last_error(msp_status s, const std::string& m) { return fail(s, m); }
 void count_launches(int n) { counted(n); }
 
+// Poll bound of the tensor-core kernels' mbarrier waits (msp_set_wait_limit).
+static std::atomic<int> g_wait_limit{1 << 20};
+int tc_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
 #define MSP_CK(call)                                                                      \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
@@ -754,6 +758,12 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, c
                                             (normalize && S > 0) ? 1 : 0, 0.0, c.ws.scal + 3, S, mu_out);
   MSP_CK(cudaGetLastError());
   counted();
+  return MSP_OK;
+}
+
+msp_status msp_set_wait_limit(int32_t polls) {
+  g_err.clear();
+  g_wait_limit.store(polls >= 1 ? polls : (1 << 20), std::memory_order_relaxed);
   return MSP_OK;
 }
 

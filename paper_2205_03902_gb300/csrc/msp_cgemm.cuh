@@ -28,8 +28,9 @@ namespace msp {
 // split them and write them in the canonical no-swizzle K-major layout into a 3-stage
 // shared-memory ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
 // TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
-// mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded: on
-// timeout the CTA raises *err = 2, stops and frees its TMEM.
+// mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded (by
+// `wait_limit` polls): on timeout the CTA raises *err = 2 and stops; the MMA thread still
+// waits, bounded, for the MMAs it issued before the TMEM is freed.
 namespace gemm {
 constexpr int TM = 128, TN = 64, TK = 16;                   // complex tile and K-tile
 constexpr int KR = 2 * TK;                                  // real K per tile
@@ -43,11 +44,12 @@ constexpr int NTHREADS = NPROD + 32;
 constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of one accumulator
 constexpr uint32_t TMEM_COLS = 2 * DCOLS;
 constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
-constexpr int kWaitLimit = 1 << 20;                         // polls (with 32 ns pauses) per wait
+constexpr int kWaitLimit = 1 << 20;   // default polls (with 32 ns pauses) per wait: well under a second
 
-// Bounded wait; gives up early once another thread has raised the abort flag.
-__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (int i = 0; i < kWaitLimit; ++i) {
+// Bounded wait of at most `limit` polls; gives up early once another thread has raised the
+// abort flag, and raises it when the limit runs out.
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int limit) {
+  for (int i = 0; i < limit; ++i) {
     if (tc::mbar_test(bar, parity)) return true;
     if ((i & 255) == 255 && *abort_flag) return false;
     if (i > 64) __nanosleep(32);
@@ -57,10 +59,20 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 }
 
 // Warp-uniform wait: lane 0 waits, every lane gets the verdict.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int limit) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(bar, parity, abort_flag) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = wait_or_abort(bar, parity, abort_flag, limit) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Bounded wait that ignores the abort flag: the MMA thread's wait for its own last commit,
+// so that no MMA is still writing tensor memory when it is freed.
+__device__ __forceinline__ bool drain_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i) {
+    if (tc::mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
 }
 
 // Byte offset of real element (row, k) in a K-major operand: core matrices of 8 rows x 4
@@ -128,7 +140,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
                                                                   const float2* __restrict__ A, size_t lda,
                                                                   const float2* __restrict__ B, size_t ldb,
                                                                   float2* __restrict__ C, size_t ldc,
-                                                                  size_t c_stride, int* err) {
+                                                                  size_t c_stride, int* err, int wait_limit) {
   using namespace gemm;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -159,9 +171,10 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
   if (warp == 8) {
     if ((t & 31) == 0) {   // MMA issuer
       constexpr uint32_t idesc = tc::idesc_tf32(128, 2 * TN);
+      int last = -1;   // last tile whose MMAs were committed
       for (int it = 0; it < ntiles; ++it) {
         const int s = it % STAGES;
-        if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag)) break;
+        if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag, wait_limit)) break;
         tc::fence_after();
         const uint32_t ab = tc::smem_u32(smem + s * STAGE_BYTES), as = ab + A_BYTES, bb = ab + 2 * A_BYTES,
                        bs = bb + B_BYTES;
@@ -178,7 +191,10 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
           tc::mma_tf32(dcol, das, dbb, idesc, 1u);
         }
         tc::commit(&empty[s]);
+        last = it;
       }
+      // every MMA issued must be done before tensor memory is freed, aborted or not
+      if (last >= 0 && !drain_wait(&empty[last % STAGES], (last / STAGES) & 1)) *abort_flag = 1;
     }
   } else {
     float re[32], im[32];
@@ -217,7 +233,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     auto produce = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
       const int s = it % STAGES;
       if (it >= STAGES) {
-        ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag);
+        ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag, wait_limit);
         if (!ok) return;
         tc::fence_after();
         // every group whose last tile is it - STAGES or earlier is complete: fold it in
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       if (ok && it + 1 < ntiles) produce(it + 1, a1, b1);
     }
     // the last tile's commit covers every MMA of the CTA
-    if (ok && ntiles > 0) ok = warp_wait(&empty[(ntiles - 1) % STAGES], ((ntiles - 1) / STAGES) & 1, abort_flag);
+    if (ok && ntiles > 0) ok = warp_wait(&empty[(ntiles - 1) % STAGES], ((ntiles - 1) / STAGES) & 1, abort_flag, wait_limit);
     tc::fence_after();
     if (ok) {
       const int groups = (ntiles + GROUP - 1) / GROUP;

@@ -14,6 +14,7 @@ namespace msp {
 
 msp_status set_last_error(msp_status s, const std::string& m);
 void count_launches(int n);
+int tc_wait_limit();
 msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& launch);
 
 namespace {
@@ -107,7 +108,8 @@ msp_status msp_dft2_tc(int32_t W, int32_t S, int32_t inverse, const float* in, f
   for (int pass = 0; pass < 2; ++pass) {
     msp_status s = profiled_launch(st, [&] {
       cgemm_kernel<false, true><<<grid, gemm::NTHREADS, gemm::SMEM_BYTES, st>>>(W, N, W, W, l.F, (size_t)W, src[pass],
-                                                                               (size_t)W, dst[pass], (size_t)W, 0, l.err);
+                                                                               (size_t)W, dst[pass], (size_t)W, 0, l.err,
+                                                                               tc_wait_limit());
       return cudaGetLastError();
     });
     if (s != MSP_OK) return s;

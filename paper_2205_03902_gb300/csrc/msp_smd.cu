@@ -41,6 +41,7 @@ namespace msp {
 
 msp_status set_last_error(msp_status s, const std::string& m);   // shown by msp_last_error_message()
 void count_launches(int n);
+int tc_wait_limit();
 msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& launch);
 
 namespace smd {
@@ -1009,7 +1010,7 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   dim3 g1((unsigned)((n2 + gemm::TM - 1) / gemm::TM), (unsigned)((S + gemm::TN - 1) / gemm::TN), (unsigned)w.s1.splits);
   SMD_TRY(profiled_launch(c.st, [&] {
     cgemm_kernel<false><<<g1, gemm::NTHREADS, gemm::SMEM_BYTES, c.st>>>((int)n2, (int)S, (int)n2, w.s1.chunk, A, n2,
-                                                                         w.P, n2, w.BC, n2, n2 * S, w.err);
+                                                                         w.P, n2, w.BC, n2, n2 * S, w.err, tc_wait_limit());
     return cudaGetLastError();
   }));
   farfield_kernel<N><<<w.grid_ff, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(w.BC, w.s1.splits, n2 * S, I,
@@ -1021,7 +1022,7 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   dim3 g2((unsigned)((n2 + gemm::TM - 1) / gemm::TM), (unsigned)((n2 + gemm::TN - 1) / gemm::TN), (unsigned)w.s2.splits);
   SMD_TRY(profiled_launch(c.st, [&] {
     cgemm_kernel<true><<<g2, gemm::NTHREADS, gemm::SMEM_BYTES, c.st>>>((int)n2, (int)n2, (int)S, w.s2.chunk, w.BC, n2,
-                                                                        w.P, n2, w.U, n2, n2 * n2, w.err);
+                                                                        w.P, n2, w.U, n2, n2 * n2, w.err, tc_wait_limit());
     return cudaGetLastError();
   }));
   const size_t pairs = n2 * n2 / 2;

@@ -84,6 +84,7 @@ _SIGS = {
     "msp_check_workspace": ([_P, _P], ctypes.c_int),
     "msp_forward_noalloc": ([_G, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "msp_profile_enable": ([ctypes.c_int32], ctypes.c_int),
+    "msp_set_wait_limit": ([ctypes.c_int32], ctypes.c_int),
     "msp_profile_read": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int32], ctypes.c_int),
     "msp_smd_validate_geometry": ([_GS], ctypes.c_int),
@@ -265,6 +266,11 @@ def probe_step(g: Geometry, probe, V, pos, I_meas, step: float = 0.0, normalize:
 def check_workspace(ws: Workspace, stream=None) -> None:
     """Raises MspError(MSP_EINVAL) if the last call on `ws` skipped a window outside the object."""
     _check(lib().msp_check_workspace(ws.ptr(), _stream(stream)), "msp_check_workspace")
+
+
+def set_wait_limit(polls: int = 0) -> None:
+    """Poll bound of the tensor-core kernels' waits (0: the default); a test hook for failure detection."""
+    _check(lib().msp_set_wait_limit(int(polls)), "msp_set_wait_limit")
 
 
 def profile_enable(on: bool = True) -> None:
