@@ -57,13 +57,14 @@ __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, 
 }
 
 // Overlap-add of per-position window arrays into object-frame maps.  One CTA of 256
-// threads owns a 16 x 16 object tile of one slice (one pixel per thread).  Positions
+// threads owns a 32 x 8 object tile of one slice (one pixel per thread, one warp per tile
+// row, so a warp reads 128 contiguous bytes of a window per position).  Positions
 // are taken in chunks of 256: the chunk's positions whose window overlaps the tile are
 // compacted (ballot, order kept) into a shared list, and the CTA adds their window
-// values in ascending scan order, eight positions in flight per thread.  Every pixel
+// values in ascending scan order, sixteen positions in flight per thread.  Every pixel
 // therefore sums its covering positions in a fixed order (bit-reproducible, no atomics)
 // and no thread spends time on positions that miss its tile.
-constexpr int kGatherTile = 16;
+constexpr int kGatherTX = 32, kGatherTY = 8;   // object tile of one CTA: one warp per tile row
 
 // CPLX: the gathered channel is complex (float2, transmission mode); ILLUM: a second, real
 // channel (the illumination windows of a layer step) is gathered too and its per-tile
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
                                                      int nl_src, const int2* __restrict__ pos, int S, int W,
                                                      int Ny, int Nx, float* __restrict__ out0,
                                                      float* __restrict__ out1, double* __restrict__ blockmax) {
-  constexpr int T = kGatherTile;
-  constexpr int U = 8;
+  constexpr int TX = kGatherTX, TY = kGatherTY;
+  constexpr int U = 16;
   __shared__ int2 spos[256];
   __shared__ int sidx[256];
   __shared__ int wcount[8];
@@ -82,8 +83,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   const int tid = threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
   const int l = blockIdx.z;
-  const int tx0 = blockIdx.x * T, ty0 = blockIdx.y * T;
-  const int px = tx0 + (tid % T), py = ty0 + (tid / T);
+  const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+  const int px = tx0 + (tid % TX), py = ty0 + (tid / TX);
   const size_t WW = (size_t)W * W;
   float2 acc0 = make_float2(0.f, 0.f);
   float acc1 = 0.f;
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
     bool ov = false;
     if (tid < n) {
       ps = pos[base + tid];
-      ov = ps.x < ty0 + T && ps.x + W > ty0 && ps.y < tx0 + T && ps.y + W > tx0;
+      ov = ps.x < ty0 + TY && ps.x + W > ty0 && ps.y < tx0 + TX && ps.y + W > tx0;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, ov);
     __syncthreads();                      // the previous chunk's list is no longer read
@@ -257,6 +258,93 @@ __global__ void dprobe_reduce_kernel(const float2* __restrict__ part, int G, int
 
 // Step size of a layer step: mu = step, or 1 / (c W^2 max illumination) with c = 2 sigma^2
 // (potential mode) or c = prod_{m > l} max |o_m|^2 (scal[6], transmission mode).
+// Set-up of every pass in one launch.  Block 0 clears the error word, forms the squared
+// zero-rule threshold tau^2 ||p||^2 (fixed-order sums) and the propagator factor
+// h1 (as propagator_kernel); every block converts its share of the potentials into
+// transmissions exp(i sigma V) (potential mode; n = 0 in transmission mode).
+__global__ void __launch_bounds__(1024) prepare_kernel(const float2* __restrict__ probe, int W, double tau2,
+                                                       double* __restrict__ zthr2, float2* __restrict__ h1,
+                                                       double dzlam, double dq, int* __restrict__ err,
+                                                       const float* __restrict__ V, float2* __restrict__ T, size_t n,
+                                                       float sigma) {
+  if (blockIdx.x == 0) {
+    // the threshold's arithmetic of zero_threshold_kernel: FP32 partials per thread and warp,
+    // the 32 warp sums in FP64 (FP64 throughput is low; a threshold needs no more)
+    __shared__ float wsum[32];
+    const int tid = threadIdx.x;
+    float a = 0.f;
+    for (int i = tid; i < W * W; i += 1024) {
+      const float2 v = probe[i];
+      a = fmaf(v.x, v.x, fmaf(v.y, v.y, a));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((tid & 31) == 0) wsum[tid >> 5] = a;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < 32; ++i) t += (double)wsum[i];
+      zthr2[0] = tau2 * t;
+      err[0] = 0;
+    }
+    for (int k = tid; k < W; k += 1024) {
+      const double q = (double)(k < W / 2 ? k : k - W) * dq;
+      double t = dzlam * q * q;   // phase / pi
+      t = t - 2.0 * floor(t * 0.5);
+      double sn, cs;
+      sincospi(t, &sn, &cs);
+      h1[k] = make_float2((float)(cs / W), (float)(-sn / W));
+    }
+  }
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float sn, cs;
+    sincosf(sigma * V[i], &sn, &cs);
+    T[i] = make_float2(cs, sn);
+  }
+}
+
+// End of a layer step's reductions in one launch, each in the fixed order of reduce_kernel:
+// the illumination maximum (scal[2]) from the gather's per-tile maxima, the loss (scal[0],
+// loss_out) from the per-position partials, and the step mu (scal[1], mu_out) as
+// layer_mu_kernel forms it.
+__global__ void __launch_bounds__(1024) layer_finish_kernel(const double* __restrict__ blockmax, int nblk,
+                                                            const double* __restrict__ loss_part, int nloss,
+                                                            double step, double c_w2, int cplx, double* scal,
+                                                            double* mu_out, double* loss_out) {
+  __shared__ double sh[1024];
+  const int tid = threadIdx.x;
+  double m = 0.0;
+  for (int i = tid; i < nblk; i += 1024) m = fmax(m, blockmax[i]);
+  sh[tid] = m;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] = fmax(sh[tid], sh[tid + s]);
+    __syncthreads();
+  }
+  const double illum = sh[0];
+  __syncthreads();
+  double a = 0.0;
+  for (int i = tid; i < nloss; i += 1024) a += loss_part[i];
+  sh[tid] = a;
+  __syncthreads();
+  for (int s = 512; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] += sh[tid + s];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    scal[2] = illum;
+    scal[0] = sh[0];
+    if (loss_out) loss_out[0] = sh[0];
+    double mu = step;
+    if (!(step > 0.0)) {
+      const double mm = illum * (cplx ? scal[6] : 1.0);
+      mu = (mm > 0.0) ? 1.0 / (c_w2 * mm) : 0.0;
+    }
+    scal[1] = mu;
+    if (mu_out) mu_out[0] = mu;
+  }
+}
+
 __global__ void layer_mu_kernel(double* scal, double step, double two_sig2_w2, double* mu_out, int cplx) {
   double mu = step;
   if (!(step > 0.0)) {
@@ -396,7 +484,7 @@ static msp_status check_geometry(const msp_geometry* g) {
   if (!std::isfinite(g->sigma)) return fail(MSP_EINVAL, "sigma must be finite");
   const double cells = (double)g->n_slices * g->obj_ny * g->obj_nx;
   if (cells > 4.0e9) return fail(MSP_EUNSUPPORTED, "object too large");
-  if ((size_t)((g->obj_nx + 15) / 16) * ((g->obj_ny + 15) / 16) > (size_t)kRedSlots)
+  if ((size_t)((g->obj_nx + kGatherTX - 1) / kGatherTX) * ((g->obj_ny + kGatherTY - 1) / kGatherTY) > (size_t)kRedSlots)
     return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
   return MSP_OK;
 }
@@ -476,19 +564,12 @@ static msp_status need_ptr(const void* p, const char* name) {
 
 static msp_status prepare(const msp_geometry* g, const float* probe, const float* V, Call& c) {
   const int W = g->win;
-  MSP_CK(cudaMemsetAsync(c.ws.err, 0, sizeof(int), c.st));
-  zero_threshold_kernel<<<1, 1024, 0, c.st>>>((const float2*)probe, W * W, kZeroRuleTau * kZeroRuleTau,
-                                              c.ws.scal + 5);
-  MSP_CK(cudaGetLastError());
-  counted();
-  propagator_kernel<<<(W + 255) / 256, 256, 0, c.st>>>(c.ws.h1, W, g->dz_A * g->wavelength_A,
-                                                      1.0 / ((double)W * g->pixel_A));
-  MSP_CK(cudaGetLastError());
-  counted();
-  if (g->param == MSP_PARAM_TRANSMISSION) return MSP_OK;   // the caller's slices are used as given
-  const size_t n = (size_t)g->n_slices * g->obj_ny * g->obj_nx;
-  const int blocks = (int)std::min<size_t>((n + 255) / 256, (size_t)c.dev.sms * 16);
-  transmission_kernel<<<blocks, 256, 0, c.st>>>(V, c.ws.T, n, (float)g->sigma);
+  const bool pot = g->param != MSP_PARAM_TRANSMISSION;   // transmission mode uses the caller's slices as given
+  const size_t n = pot ? (size_t)g->n_slices * g->obj_ny * g->obj_nx : 0;
+  const int blocks = (int)std::max<size_t>(1, std::min<size_t>((n + 1023) / 1024, (size_t)c.dev.sms * 4));
+  prepare_kernel<<<blocks, 1024, 0, c.st>>>((const float2*)probe, W, kZeroRuleTau * kZeroRuleTau, c.ws.scal + 5,
+                                            c.ws.h1, g->dz_A * g->wavelength_A, 1.0 / ((double)W * g->pixel_A),
+                                            c.ws.err, V, c.ws.T, n, (float)g->sigma);
   MSP_CK(cudaGetLastError());
   counted();
   return MSP_OK;
@@ -629,7 +710,7 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   }
   MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
   if (dV) {
-    dim3 grid((g->obj_nx + kGatherTile - 1) / kGatherTile, (g->obj_ny + kGatherTile - 1) / kGatherTile, g->n_slices);
+    dim3 grid((g->obj_nx + kGatherTX - 1) / kGatherTX, (g->obj_ny + kGatherTY - 1) / kGatherTY, g->n_slices);
     if (p.cplx)
       gather_kernel<true, false><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos,
                                                          W, g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
@@ -678,7 +759,7 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   p.I_meas = I_meas;
   p.layer = layer;
   MSP_TRY(run_position(g, MODE_LAYER, p, c));
-  dim3 grid((g->obj_nx + kGatherTile - 1) / kGatherTile, (g->obj_ny + kGatherTile - 1) / kGatherTile, 1);
+  dim3 grid((g->obj_nx + kGatherTX - 1) / kGatherTX, (g->obj_ny + kGatherTY - 1) / kGatherTY, 1);
   const int nblk = (int)(grid.x * grid.y);
   if (nblk > kRedSlots) return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
   if (p.cplx)
@@ -689,9 +770,6 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
                                                        g->obj_ny, g->obj_nx, c.ws.map0, c.ws.map1, c.ws.red);
   MSP_CK(cudaGetLastError());
   counted();
-  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nblk, 1, c.ws.scal + 2, nullptr);
-  MSP_CK(cudaGetLastError());
-  counted();
   if (p.cplx) {
     later_slices_gain_kernel<<<1, 1024, 0, c.st>>>((const float2*)V, g->n_slices, plane, layer, c.ws.scal + 6);
     MSP_CK(cudaGetLastError());
@@ -699,10 +777,10 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   }
   // potential mode: mu = 1 / (2 sigma^2 W^2 max illum); transmission: 1 / (W^2 max illum prod max|o_m|^2)
   const double c_w2 = (p.cplx ? 1.0 : 2.0 * g->sigma * g->sigma) * (double)W * (double)W;
-  layer_mu_kernel<<<1, 1, 0, c.st>>>(c.ws.scal, step, c_w2, mu_out, p.cplx);
+  layer_finish_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nblk, c.ws.loss_part, g->n_pos * loss_slots(W), step, c_w2,
+                                            p.cplx, c.ws.scal, mu_out, loss_before);
   MSP_CK(cudaGetLastError());
   counted();
-  MSP_TRY(reduce_loss(g, c, loss_before));
   // V_l (or the complex o_l, as interleaved floats) -= mu * gradient map
   const size_t nupd = plane * (p.cplx ? 2 : 1);
   const int blocks = (int)std::min<size_t>((nupd + 255) / 256, (size_t)c.dev.sms * 8);
