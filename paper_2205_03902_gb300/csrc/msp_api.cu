@@ -303,38 +303,38 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const float2* __restrict_
   }
 }
 
-// End of a layer step's reductions in one launch, each in the fixed order of reduce_kernel:
-// the illumination maximum (scal[2]) from the gather's per-tile maxima, the loss (scal[0],
-// loss_out) from the per-position partials, and the step mu (scal[1], mu_out) as
-// layer_mu_kernel forms it.
+// End of a layer step's reductions in one launch, each in a fixed order (strided partials per
+// thread, a butterfly within each warp, the 32 warp values in order): the illumination
+// maximum (scal[2]) from the gather's per-tile maxima, the loss (scal[0], loss_out) from the
+// per-position partials, and the step mu (scal[1], mu_out) as layer_mu_kernel forms it.
 __global__ void __launch_bounds__(1024) layer_finish_kernel(const double* __restrict__ blockmax, int nblk,
                                                             const double* __restrict__ loss_part, int nloss,
                                                             double step, double c_w2, int cplx, double* scal,
                                                             double* mu_out, double* loss_out) {
-  __shared__ double sh[1024];
-  const int tid = threadIdx.x;
-  double m = 0.0;
+  __shared__ double wm[32], ws[32];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  double m = 0.0, a = 0.0;
   for (int i = tid; i < nblk; i += 1024) m = fmax(m, blockmax[i]);
-  sh[tid] = m;
-  __syncthreads();
-  for (int s = 512; s > 0; s >>= 1) {
-    if (tid < s) sh[tid] = fmax(sh[tid], sh[tid + s]);
-    __syncthreads();
-  }
-  const double illum = sh[0];
-  __syncthreads();
-  double a = 0.0;
   for (int i = tid; i < nloss; i += 1024) a += loss_part[i];
-  sh[tid] = a;
-  __syncthreads();
-  for (int s = 512; s > 0; s >>= 1) {
-    if (tid < s) sh[tid] += sh[tid + s];
-    __syncthreads();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    a += __shfl_xor_sync(0xffffffffu, a, o);
   }
+  if (lane == 0) {
+    wm[w] = m;
+    ws[w] = a;
+  }
+  __syncthreads();
   if (tid == 0) {
+    double illum = 0.0, loss = 0.0;
+    for (int i = 0; i < 32; ++i) {
+      illum = fmax(illum, wm[i]);
+      loss += ws[i];
+    }
     scal[2] = illum;
-    scal[0] = sh[0];
-    if (loss_out) loss_out[0] = sh[0];
+    scal[0] = loss;
+    if (loss_out) loss_out[0] = loss;
     double mu = step;
     if (!(step > 0.0)) {
       const double mm = illum * (cplx ? scal[6] : 1.0);
