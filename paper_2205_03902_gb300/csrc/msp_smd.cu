@@ -529,30 +529,31 @@ __global__ void propagator_kernel(float2* __restrict__ h, int N, double dzlam, d
 
 // gk = G e_0, the real-space kernel of the propagator: with h = h1(ky) h1(kx) separable,
 // gk[y][x] = g1(y) g1(x), g1(y) = (1/N) sum_k h1(k) exp(2 pi i k y / N); in double, rounded once.
-__global__ void __launch_bounds__(1024) kernel_column_kernel(float2* __restrict__ gk, int N, double dzlam, double dq) {
-  __shared__ double2 g1[64];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int y = warp; y < N; y += 32) {   // one warp per y: lanes take k = lane, lane + 32; butterfly sum
-    double re = 0.0, im = 0.0;
-    for (int k = lane; k < N; k += 32) {
-      const double q = (k < N / 2 ? k : k - N) * dq;
-      double s, c;
-      sincospi(-dzlam * q * q + 2.0 * (double)((k * y) % N) / N, &s, &c);
-      re += c;
-      im += s;
-    }
+// g1[y], one block of one warp per y (the FP64 work spread over N SMs): lanes take
+// k = lane, lane + 32, then a butterfly sum.
+__global__ void __launch_bounds__(32) kernel_row_kernel(double2* __restrict__ g1, int N, double dzlam, double dq) {
+  const int y = blockIdx.x, lane = threadIdx.x;
+  double re = 0.0, im = 0.0;
+  for (int k = lane; k < N; k += 32) {
+    const double q = (k < N / 2 ? k : k - N) * dq;
+    double s, c;
+    sincospi(-dzlam * q * q + 2.0 * (double)((k * y) % N) / N, &s, &c);
+    re += c;
+    im += s;
+  }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, off);
-      im += __shfl_xor_sync(0xffffffffu, im, off);
-    }
-    if (lane == 0) g1[y] = make_double2(re / N, im / N);
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-    const double2 a = g1[e / N], b = g1[e % N];
-    gk[e] = make_float2((float)(a.x * b.x - a.y * b.y), (float)(a.x * b.y + a.y * b.x));
-  }
+  if (lane == 0) g1[y] = make_double2(re / N, im / N);
+}
+
+__global__ void kernel_column_kernel(float2* __restrict__ gk, const double2* __restrict__ g1, int N) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  const double2 a = g1[e / N], b = g1[e % N];
+  gk[e] = make_float2((float)(a.x * b.x - a.y * b.y), (float)(a.x * b.y + a.y * b.x));
 }
 
 // Block partial sums (FP64) of a float array over fixed chunks.
@@ -897,6 +898,7 @@ struct Layout {
   double* part2 = nullptr;   // kPartSlots
   float2* h = nullptr;
   float2* gk = nullptr;      // G e_0
+  double2* g1 = nullptr;     // its separable factor, N values
   float2* P = nullptr;
   float2* BC = nullptr;      // splits1 * n2 * S
   float2* U = nullptr;       // splits2 * n2 * n2 (rank-S update partials)
@@ -928,6 +930,7 @@ static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, ch
   w.part2 = (double*)take(kPartSlots * sizeof(double));
   w.h = (float2*)take(n2 * sizeof(float2));
   w.gk = (float2*)take(n2 * sizeof(float2));
+  w.g1 = (double2*)take(64 * sizeof(double2));
   w.P = (float2*)take(n2 * S * sizeof(float2));
   w.BC = (float2*)take((size_t)w.s1.splits * n2 * S * sizeof(float2));
   w.U = (float2*)take(w.s2.splits > 1 ? (size_t)w.s2.splits * n2 * n2 * sizeof(float2) : n2 * n2 * sizeof(float2));
@@ -971,8 +974,9 @@ static msp_status launch_propagator(const msp_smd_geometry* g, Call& c) {
   propagator_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.h, N, g->dz_A * g->wavelength_A,
                                                            1.0 / ((double)N * g->pixel_A));
   SMD_LAUNCHED(1);
-  kernel_column_kernel<<<1, 1024, 0, c.st>>>(c.w.gk, N, g->dz_A * g->wavelength_A,
-                                                              1.0 / ((double)N * g->pixel_A));
+  kernel_row_kernel<<<N, 32, 0, c.st>>>(c.w.g1, N, g->dz_A * g->wavelength_A, 1.0 / ((double)N * g->pixel_A));
+  SMD_LAUNCHED(1);
+  kernel_column_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.gk, c.w.g1, N);
   SMD_LAUNCHED(1);
   return MSP_OK;
 }
