@@ -122,3 +122,20 @@ def test_smd_calls_reject_bad_geometry_before_touching_the_device(lib):
     assert lib.msp_smd_final_slices(ctypes.byref(g), None, None, None, None) == msp.MSP_EINVAL
     assert lib.msp_smd_workspace_bytes(ctypes.byref(g)) == 0
     assert lib.msp_smd_validate_geometry(None) == msp.MSP_EINVAL
+
+
+@pytest.mark.parametrize("W,S,ok", [(32, 1, True), (64, 37, True), (128, 4096, True), (256, 3, True),
+                                    (48, 4, False), (512, 1, False), (128, 0, False), (128, 40000, False)])
+def test_dft_workspace_sizes_and_host_validation(lib, W, S, ok):
+    n = lib.msp_dft2_tc_workspace_bytes(W, S)
+    if ok:
+        # error word, the DFT matrix and the intermediate batch, each 256-byte aligned
+        assert n >= W * W * 8 + S * W * W * 8
+    else:
+        assert n == 0
+        assert lib.msp_dft2_tc(W, S, 0, None, None, None, 0, None) == msp.MSP_EUNSUPPORTED
+
+
+def test_wait_limit_hook_needs_no_device(lib):
+    assert lib.msp_set_wait_limit(5) == msp.MSP_OK
+    assert lib.msp_set_wait_limit(0) == msp.MSP_OK
