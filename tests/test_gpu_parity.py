@@ -479,3 +479,45 @@ def test_transmission_mode_probe_step(msp, c2_strong):
     pn, loss_ref, mu_ref = O.probe_step(c.gd, c.probe, c.pos, c.I, T=T)
     assert abs(loss.item() - loss_ref) / loss_ref <= TOL
     assert rel(p.cpu().numpy() - c.probe, pn - c.probe) <= TOL
+
+
+# --------------------------------------------------------------------------- full c3 and c4 sizes
+
+@pytest.mark.parametrize("cfg_name,samples", [("c3", 24), ("c4", 10)])
+def test_full_size_sampled_intensities_and_gradient_property(msp, cfg_name, samples):
+    """Every position of the 8-slice W = 128 (4096 positions) and 16-slice W = 256 (2304 positions,
+    four-CTA clusters) workloads in one launch, as bench.py times them: the intensities of
+    sampled positions against the oracle, position by position, and the full-size potential
+    gradient against central differences of the library's own loss (a property at any size)."""
+    cfg = synth.CONFIGS[cfg_name]
+    pos = synth.scan_positions(cfg)
+    gd = synth.geometry(cfg, n_pos=len(pos))
+    g = msp.geometry(**gd)
+    V_true = f32(synth.potential_slices(cfg))
+    p_true = synth.probe(cfg).astype(np.complex64).astype(np.complex128)
+    dpos = to_dev(pos, np.int32)
+    I_gpu = msp.forward(g, to_dev(p_true, np.complex64), to_dev(V_true, np.float32), dpos).cpu().numpy()
+    X = O.transmission(V_true.astype(np.float64), gd["sigma"])
+    h = O.fresnel_propagator(cfg.win, gd["pixel_A"], gd["wavelength_A"], gd["dz_A"])
+    pick = np.random.default_rng(5).choice(len(pos), size=samples, replace=False)
+    pick[0], pick[1] = 0, len(pos) - 1                       # first and last CTA's last position
+    for s in pick:
+        _, _, far = O.position_forward(p_true, X, int(pos[s][0]), int(pos[s][1]), h)
+        assert rel(I_gpu[s], np.abs(far) ** 2) <= TOL, s
+    # gradient property: (L(V + eps D) - L(V - eps D)) / (2 eps) = <dV, D>, on measurements that
+    # do not come from the library: the probe's own pattern, scaled by a seeded factor per position
+    base = (np.abs(np.fft.fft2(p_true)) ** 2).astype(np.float32)
+    scale = (1.0 + 0.2 * np.random.default_rng(9).random(len(pos))).astype(np.float32)
+    I_meas = base[None] * scale[:, None, None]
+    dI = to_dev(I_meas, np.float32)
+    V0 = f32(0.5 * V_true)
+    dp = to_dev(p_true, np.complex64)
+    loss, dV, _ = msp.loss_grad(g, dp, to_dev(V0, np.float32), dpos, dI, want_dprobe=False)
+    D = f32(synth.random_real(V0.shape, 11))
+    eps = 1e-2 * float(np.abs(V0).max()) / float(np.abs(D).max())
+    lp, _, _ = msp.loss_grad(g, dp, to_dev(f32(V0 + eps * D), np.float32), dpos, dI, want_dV=False, want_dprobe=False)
+    lm, _, _ = msp.loss_grad(g, dp, to_dev(f32(V0 - eps * D), np.float32), dpos, dI, want_dV=False, want_dprobe=False)
+    fd = (lp.item() - lm.item()) / (2 * eps)
+    an = float(np.sum(dV.cpu().numpy().astype(np.float64) * D))
+    print(cfg_name, "fd", fd, "analytic", an)
+    assert abs(fd - an) <= 2e-2 * abs(an)
