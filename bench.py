@@ -192,7 +192,8 @@ def run_reference(args, rank, world):
     per_step = []
     base = None
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(CFG, budget_s=max(2.0, 20.0 / max(1, args.steps + args.warmup)))
+        # the whole run stays near 90 s: each step times a bounded sample of positions
+        r = cpu_baseline(CFG, budget_s=max(0.05, 90.0 / max(1, args.steps + args.warmup)))
         if i >= args.warmup:
             per_step.append(r["value"])
             base = r
