@@ -24,9 +24,10 @@ namespace msp {
 // to nearest, so D accumulates over groups of GROUP K-tiles only, alternating between two
 // TMEM halves; each finished group is added into FP32 registers.
 //
-// Warps 0..7 are producers: they load K-tiles of A and B (two tiles ahead, in registers),
-// split them and write them in the canonical no-swizzle K-major layout into a 3-stage
-// shared-memory ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
+// Warps 0..7 are producers: they copy the raw complex K-tiles of A and B into shared memory
+// with cp.async, two tiles ahead of the one they convert, so that no register waits on a
+// global load; they then split each tile and write it in the canonical no-swizzle K-major
+// layout into a 2-stage ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
 // TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
 // mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded (by
 // `wait_limit` polls): on timeout the CTA raises *err = 2 and stops; the MMA thread still
@@ -37,13 +38,20 @@ constexpr int KR = 2 * TK;                                  // real K per tile
 constexpr uint32_t A_BYTES = 128 * KR * 4;                  // one tf32 part of A_re: 16 KB
 constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 16 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES; // 64 KB
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int GROUP = 8;
 constexpr int NPROD = 256;
 constexpr int NTHREADS = NPROD + 32;
 constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of one accumulator
 constexpr uint32_t TMEM_COLS = 2 * DCOLS;
-constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
+// raw complex K-tiles as they come from global memory, RAW of them in flight
+constexpr int RAW = 3;
+constexpr int RB_LD = TK + 2;                               // padded row of a raw B tile [j][k]
+constexpr uint32_t RAW_A_BYTES = TK * TM * 8;               // [k][i] float2: 16 KB
+constexpr uint32_t RAW_B_BYTES = (TN * RB_LD > TK * TN ? TN * RB_LD : TK * TN) * 8;
+constexpr uint32_t RAW_BYTES = RAW_A_BYTES + RAW_B_BYTES;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + RAW * RAW_BYTES + 1024 + 128;
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
 constexpr int kWaitLimit = 1 << 20;   // default polls (with 32 ns pauses) per wait: well under a second
 
 // Bounded wait of at most `limit` polls; gives up early once another thread has raised the
@@ -112,6 +120,29 @@ __device__ __forceinline__ void put(uint8_t* big, uint8_t* small, uint32_t off, 
   *reinterpret_cast<uint4*>(small + off) = v.small;
 }
 
+// Copies `bytes` (0, 8 or 16) from global src into 16 bytes at shared dst, zero-filling the
+// rest; vec16: one 16-byte copy (src and dst 16-byte aligned), else two 8-byte copies.
+__device__ __forceinline__ void copy_pair(uint8_t* dst, const float2* src, const float2* safe, int bytes, bool vec16) {
+  const uint32_t d = tc::smem_u32(dst);
+  if (vec16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(bytes > 0 ? src : safe), "r"(bytes)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(bytes >= 8 ? src : safe),
+                 "r"(bytes >= 8 ? 8 : 0)
+                 : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d + 8), "l"(bytes >= 16 ? src + 1 : safe),
+                 "r"(bytes >= 16 ? 8 : 0)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void copy_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// this thread's copies of all but the newest group are complete
+__device__ __forceinline__ void copy_wait_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void copy_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// barrier of the NPROD producer threads only (the MMA warp never joins it)
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory"); }
+
 // Adds accumulator half h into this thread's registers: TMEM lane (row) 32 (warp & 3) + lane,
 // columns 32 (warp >> 2) + q (Re) and TN + 32 (warp >> 2) + q (Im), q < 32.
 __device__ __forceinline__ void flush(uint32_t tmem, int h, int warp, float (&re)[32], float (&im)[32]) {
@@ -144,7 +175,8 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
   using namespace gemm;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint8_t* raw = smem + STAGES * STAGE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(raw + RAW * RAW_BYTES);
   uint64_t* empty = full + STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + STAGES);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
@@ -203,38 +235,52 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     int flushed = 0;
     const int am = t & 127, aq = t >> 7;   // A: row am, complex K 8 aq .. 8 aq + 7 of the tile
     const int bn = t & 63, bq = t >> 6;    // B: column bn, complex K 4 bq .. 4 bq + 3
-    // operands of the next two K-tiles in flight, in two register sets
-    float2 a0[8], b0[4], a1[8], b1[4];
-    auto load = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
-      const int ka = kb + it * TK + 8 * aq, kq = kb + it * TK + 4 * bq;
-      const int i = i0 + am, j = j0 + bn;
+    // 16-byte copies need 16-byte aligned rows and even offsets of every copied pair
+    const bool vec16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0 &&
+                       (lda & 1) == 0 && (ldb & 1) == 0 && (kb & 1) == 0;
+    // starts the copies of K-tile it into raw slot it % RAW (one commit group, empty past the end)
+    auto issue = [&](int it) {
+      if (it < ntiles) {
+        uint8_t* ra = raw + (it % RAW) * RAW_BYTES;
+        uint8_t* rb = ra + RAW_A_BYTES;
+        const int k0 = kb + it * TK;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int k = ka + q;
-        a[q] = (it < ntiles && k < ke && i < M) ? A[(size_t)k * lda + i] : make_float2(0.f, 0.f);
-      }
+        for (int u = 0; u < 4; ++u) {   // A: TK rows k x TM / 2 pairs of i, stored [k][i]
+          const int q = t + NPROD * u, k = q >> 6, p = q & 63;
+          const int kk = k0 + k, i = i0 + 2 * p;
+          const int n = kk < ke ? max(0, min(2, M - i)) : 0;
+          copy_pair(ra + (k * TM + 2 * p) * 8, A + (n > 0 ? (size_t)kk * lda + i : 0), A, 8 * n, vec16);
+        }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = kq + q;
-        if (it < ntiles && k < ke && j < N) {
-          if (B_CONJ_T) {
-            const float2 v = B[(size_t)k * ldb + j];
-            b[q] = make_float2(v.x, -v.y);
-          } else {
-            b[q] = B[(size_t)j * ldb + k];
+        for (int u = 0; u < 2; ++u) {
+          const int q = t + NPROD * u;
+          if (B_CONJ_T) {   // B[k][j] rows of TN / 2 pairs of j, stored [k][j]
+            const int k = q >> 5, p = q & 31, kk = k0 + k, j = j0 + 2 * p;
+            const int n = kk < ke ? max(0, min(2, N - j)) : 0;
+            copy_pair(rb + (k * TN + 2 * p) * 8, B + (n > 0 ? (size_t)kk * ldb + j : 0), B, 8 * n, vec16);
+          } else {          // B[j][k] columns of TK / 2 pairs of k, stored [j][k] with row RB_LD
+            const int j = q >> 3, p = q & 7, kk = k0 + 2 * p, jj = j0 + j;
+            const int n = jj < N ? max(0, min(2, ke - kk)) : 0;
+            copy_pair(rb + (j * RB_LD + 2 * p) * 8, B + (n > 0 ? (size_t)jj * ldb + kk : 0), B, 8 * n, vec16);
           }
-        } else {
-          b[q] = make_float2(0.f, 0.f);
         }
       }
+      copy_commit();
     };
     bool ok = true;
-    // fills the stage of tile it from (a, b), then starts the loads of tile it + 2 into them
-    auto produce = [&](int it, float2 (&a)[8], float2 (&b)[4]) {
+    issue(0);
+    issue(1);
+    // Every producer passes producers_sync once per tile, aborted or not, so that none waits
+    // at it for a warp that has left.
+    for (int it = 0; it < ntiles; ++it) {
+      copy_wait_but_one();   // this thread's copies of tile it have landed
+      producers_sync();      // everyone's have; everyone has converted tile it - 1
+      issue(it + 2);         // into the slot tile it - 1 came from
+      if (!ok) continue;
       const int s = it % STAGES;
       if (it >= STAGES) {
         ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag, wait_limit);
-        if (!ok) return;
+        if (!ok) continue;
         tc::fence_after();
         // every group whose last tile is it - STAGES or earlier is complete: fold it in
         const int done_groups = (it - STAGES + 1) / GROUP;
@@ -242,6 +288,25 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
           flush(tmem, flushed & 1, warp, re, im);
           ++flushed;
         }
+      }
+      const float2* ra = reinterpret_cast<const float2*>(raw + (it % RAW) * RAW_BYTES);
+      const float2* rb = reinterpret_cast<const float2*>(raw + (it % RAW) * RAW_BYTES + RAW_A_BYTES);
+      float2 a[8], b[4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) a[q] = ra[(8 * aq + q) * TM + am];
+      if (B_CONJ_T) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 v = rb[(4 * bq + q) * TN + bn];
+          b[q] = make_float2(v.x, -v.y);
+        }
+      } else {
+        const float4 v0 = *reinterpret_cast<const float4*>(rb + bn * RB_LD + 4 * bq);
+        const float4 v1 = *reinterpret_cast<const float4*>(rb + bn * RB_LD + 4 * bq + 2);
+        b[0] = make_float2(v0.x, v0.y);
+        b[1] = make_float2(v0.z, v0.w);
+        b[2] = make_float2(v1.x, v1.y);
+        b[3] = make_float2(v1.z, v1.w);
       }
       uint8_t* Ab = smem + s * STAGE_BYTES;
       uint8_t* As = Ab + A_BYTES;
@@ -259,17 +324,11 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
       put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
       put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
-      if (it + 2 < ntiles) load(it + 2, a, b);
       tc::fence_proxy_async();
       tc::fence_before();
       tc::mbar_arrive(&full[s]);
-    };
-    load(0, a0, b0);
-    load(1, a1, b1);
-    for (int it = 0; it < ntiles && ok; it += 2) {
-      produce(it, a0, b0);
-      if (ok && it + 1 < ntiles) produce(it + 1, a1, b1);
     }
+    copy_wait_all();   // no copy may still be writing shared memory when the CTA ends
     // the last tile's commit covers every MMA of the CTA
     if (ok && ntiles > 0) ok = warp_wait(&empty[(ntiles - 1) % STAGES], ((ntiles - 1) / STAGES) & 1, abort_flag, wait_limit);
     tc::fence_after();
