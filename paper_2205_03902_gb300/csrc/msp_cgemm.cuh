@@ -26,8 +26,11 @@ namespace msp {
 //
 // Warps 0..7 are producers: they copy the raw complex K-tiles of A and B into shared memory
 // with cp.async, two tiles ahead of the one they convert, so that no register waits on a
-// global load; they then split each tile and write it in the canonical no-swizzle K-major
-// layout into a 2-stage ring (`full` mbarriers, one arrival per producer thread).  Warp 8 allocates
+// global load.  They split each tile and write A_re into tensor memory (row m in lane m, its
+// real K in consecutive columns; tcgen05.st) and B_re in the canonical no-swizzle K-major
+// layout into shared memory: a 4-stage ring (`full` mbarriers, one arrival per producer
+// thread).  A read from tensor memory costs no shared-memory bandwidth, which the MMAs'
+// B reads and the producers' stores share.  Warp 8 allocates
 // TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
 // mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded (by
 // `wait_limit` polls): on timeout the CTA raises *err = 2 and stops; the MMA thread still
@@ -35,15 +38,16 @@ namespace msp {
 namespace gemm {
 constexpr int TM = 128, TN = 64, TK = 16;                   // complex tile and K-tile
 constexpr int KR = 2 * TK;                                  // real K per tile
-constexpr uint32_t A_BYTES = 128 * KR * 4;                  // one tf32 part of A_re: 16 KB
 constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 16 KB
-constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES; // 64 KB
-constexpr int STAGES = 2;
+constexpr uint32_t STAGE_BYTES = 2 * B_BYTES;               // 32 KB of shared memory
+constexpr int STAGES = 4;
 constexpr int GROUP = 8;
 constexpr int NPROD = 256;
 constexpr int NTHREADS = NPROD + 32;
 constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of one accumulator
-constexpr uint32_t TMEM_COLS = 2 * DCOLS;
+constexpr uint32_t ACOL = 2 * DCOLS;                        // first TMEM column of the A stages
+constexpr uint32_t TMEM_COLS = 512;                         // two accumulators + STAGES x (big, small) A
+static_assert(ACOL + STAGES * 2 * KR <= TMEM_COLS, "tensor memory of one CTA");
 // raw complex K-tiles as they come from global memory, RAW of them in flight
 constexpr int RAW = 3;
 constexpr int RB_LD = TK + 2;                               // padded row of a raw B tile [j][k]
@@ -208,19 +212,17 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         const int s = it % STAGES;
         if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag, wait_limit)) break;
         tc::fence_after();
-        const uint32_t ab = tc::smem_u32(smem + s * STAGE_BYTES), as = ab + A_BYTES, bb = ab + 2 * A_BYTES,
-                       bs = bb + B_BYTES;
+        const uint32_t bb = tc::smem_u32(smem + s * STAGE_BYTES), bs = bb + B_BYTES;
+        const uint32_t ab = tmem + ACOL + (uint32_t)(s * 2 * KR), as = ab + KR;   // A big, small
         const uint32_t dcol = tmem + (uint32_t)(((it / GROUP) & 1) * DCOLS);
 #pragma unroll
         for (int kk = 0; kk < KR / 8; ++kk) {   // K = 8 tf32 (two core matrices) per MMA
           const uint32_t koff = kk * 256;
-          const uint64_t dab = tc::smem_desc(ab + koff, 128, (KR / 4) * 128);
-          const uint64_t das = tc::smem_desc(as + koff, 128, (KR / 4) * 128);
           const uint64_t dbb = tc::smem_desc(bb + koff, 128, (KR / 4) * 128);
           const uint64_t dbs = tc::smem_desc(bs + koff, 128, (KR / 4) * 128);
-          tc::mma_tf32(dcol, dab, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_tf32(dcol, dab, dbs, idesc, 1u);
-          tc::mma_tf32(dcol, das, dbb, idesc, 1u);
+          tc::mma_tf32_ta(dcol, ab + 8 * kk, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_tf32_ta(dcol, ab + 8 * kk, dbs, idesc, 1u);
+          tc::mma_tf32_ta(dcol, as + 8 * kk, dbb, idesc, 1u);
         }
         tc::commit(&empty[s]);
         last = it;
@@ -308,22 +310,23 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         b[2] = make_float2(v1.x, v1.y);
         b[3] = make_float2(v1.z, v1.w);
       }
-      uint8_t* Ab = smem + s * STAGE_BYTES;
-      uint8_t* As = Ab + A_BYTES;
-      uint8_t* Bb = Ab + 2 * A_BYTES;
+      uint8_t* Bb = smem + s * STAGE_BYTES;
       uint8_t* Bs = Bb + B_BYTES;
       const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
       const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
-      put(Ab, As, kmaj(am, 8 * aq), r0);
-      put(Ab, As, kmaj(am, 8 * aq + 4), r1);
-      put(Ab, As, kmaj(am, TK + 8 * aq), m0);
-      put(Ab, As, kmaj(am, TK + 8 * aq + 4), m1);
+      // row am of A_re = [Ar, Ai]: this warp's TMEM lanes are 32 (warp & 3) .. + 31
+      const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + ACOL + (uint32_t)(s * 2 * KR);
+      tc::tmem_st8(ta + 8 * aq, r0.big, r1.big);
+      tc::tmem_st8(ta + TK + 8 * aq, m0.big, m1.big);
+      tc::tmem_st8(ta + KR + 8 * aq, r0.small, r1.small);
+      tc::tmem_st8(ta + KR + TK + 8 * aq, m0.small, m1.small);
       const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
       const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
       put(Bb, Bs, kmaj(bn, 4 * bq), br);              // row n:      Br
       put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
       put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
       put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
+      tc::tmem_wait_st();
       tc::fence_proxy_async();
       tc::fence_before();
       tc::mbar_arrive(&full[s]);
