@@ -25,10 +25,10 @@ namespace msp {
 // TMEM halves; each finished group is added into FP32 registers.
 //
 // Warps 0..7 are producers: they copy the raw complex K-tiles of A and B into shared memory
-// with cp.async, two tiles ahead of the one they convert, so that no register waits on a
+// with cp.async, RAW - 1 tiles ahead of the one they convert, so that no register waits on a
 // global load.  They split each tile and write A_re into tensor memory (row m in lane m, its
 // real K in consecutive columns; tcgen05.st) and B_re in the canonical no-swizzle K-major
-// layout into shared memory: a 4-stage ring (`full` mbarriers, one arrival per producer
+// layout into shared memory: a 3-stage ring (`full` mbarriers, one arrival per producer
 // thread).  A read from tensor memory costs no shared-memory bandwidth, which the MMAs'
 // B reads and the producers' stores share.  Warp 8 allocates
 // TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
@@ -40,7 +40,7 @@ constexpr int TM = 128, TN = 64, TK = 16;                   // complex tile and 
 constexpr int KR = 2 * TK;                                  // real K per tile
 constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 16 KB
 constexpr uint32_t STAGE_BYTES = 2 * B_BYTES;               // 32 KB of shared memory
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int GROUP = 8;
 constexpr int NPROD = 256;
 constexpr int NTHREADS = NPROD + 32;
@@ -48,8 +48,8 @@ constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of on
 constexpr uint32_t ACOL = 2 * DCOLS;                        // first TMEM column of the A stages
 constexpr uint32_t TMEM_COLS = 512;                         // two accumulators + STAGES x (big, small) A
 static_assert(ACOL + STAGES * 2 * KR <= TMEM_COLS, "tensor memory of one CTA");
-// raw complex K-tiles as they come from global memory, RAW of them in flight
-constexpr int RAW = 3;
+// raw complex K-tiles as they come from global memory: RAW slots, RAW - 1 tiles in flight
+constexpr int RAW = 5;
 constexpr int RB_LD = TK + 2;                               // padded row of a raw B tile [j][k]
 constexpr uint32_t RAW_A_BYTES = TK * TM * 8;               // [k][i] float2: 16 KB
 constexpr uint32_t RAW_B_BYTES = (TN * RB_LD > TK * TN ? TN * RB_LD : TK * TN) * 8;
@@ -141,8 +141,9 @@ __device__ __forceinline__ void copy_pair(uint8_t* dst, const float2* src, const
   }
 }
 __device__ __forceinline__ void copy_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// this thread's copies of all but the newest group are complete
-__device__ __forceinline__ void copy_wait_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// this thread's copies of all but the newest `pending` groups are complete
+template <int pending>
+__device__ __forceinline__ void copy_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(pending) : "memory"); }
 __device__ __forceinline__ void copy_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 // barrier of the NPROD producer threads only (the MMA warp never joins it)
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory"); }
@@ -240,6 +241,17 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     // 16-byte copies need 16-byte aligned rows and even offsets of every copied pair
     const bool vec16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0 &&
                        (lda & 1) == 0 && (ldb & 1) == 0 && (kb & 1) == 0;
+    // copies: A row pair ia, ia + 1 at K rows ka + 4 u of each tile; B pairs u = 0, 1
+    const int ka = t >> 6, ia = i0 + 2 * (t & 63);
+    const int na = max(0, min(2, M - ia));
+    const float2* a_src = A + (na > 0 ? (size_t)(kb + ka) * lda + ia : 0);
+    const uint32_t a_dst = (uint32_t)(ka * TM + 2 * (t & 63)) * 8;
+    // B^H: K rows kbk + 8 u, columns jb, jb + 1 (nb of them);  B: columns jb + 32 u, K pair kbk
+    const int kbk = B_CONJ_T ? (t >> 5) : 2 * (t & 7);
+    const int jb = B_CONJ_T ? j0 + 2 * (t & 31) : j0 + (t >> 3);
+    const int nb = B_CONJ_T ? max(0, min(2, N - jb)) : 0;
+    const float2* b_src = B_CONJ_T ? B + (nb > 0 ? (size_t)(kb + kbk) * ldb + jb : 0) : B + (size_t)jb * ldb + kb + kbk;
+    const uint32_t b_dst = B_CONJ_T ? (uint32_t)(kbk * TN + 2 * (t & 31)) * 8 : (uint32_t)((t >> 3) * RB_LD + kbk) * 8;
     // starts the copies of K-tile it into raw slot it % RAW (one commit group, empty past the end)
     auto issue = [&](int it) {
       if (it < ntiles) {
@@ -247,37 +259,35 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         uint8_t* rb = ra + RAW_A_BYTES;
         const int k0 = kb + it * TK;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {   // A: TK rows k x TM / 2 pairs of i, stored [k][i]
-          const int q = t + NPROD * u, k = q >> 6, p = q & 63;
-          const int kk = k0 + k, i = i0 + 2 * p;
-          const int n = kk < ke ? max(0, min(2, M - i)) : 0;
-          copy_pair(ra + (k * TM + 2 * p) * 8, A + (n > 0 ? (size_t)kk * lda + i : 0), A, 8 * n, vec16);
+        for (int u = 0; u < 4; ++u) {
+          const int n = k0 + ka + 4 * u < ke ? na : 0;
+          copy_pair(ra + a_dst + u * 4 * TM * 8, n > 0 ? a_src + (size_t)(it * TK + 4 * u) * lda : A, A, 8 * n,
+                    vec16);
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-          const int q = t + NPROD * u;
-          if (B_CONJ_T) {   // B[k][j] rows of TN / 2 pairs of j, stored [k][j]
-            const int k = q >> 5, p = q & 31, kk = k0 + k, j = j0 + 2 * p;
-            const int n = kk < ke ? max(0, min(2, N - j)) : 0;
-            copy_pair(rb + (k * TN + 2 * p) * 8, B + (n > 0 ? (size_t)kk * ldb + j : 0), B, 8 * n, vec16);
-          } else {          // B[j][k] columns of TK / 2 pairs of k, stored [j][k] with row RB_LD
-            const int j = q >> 3, p = q & 7, kk = k0 + 2 * p, jj = j0 + j;
-            const int n = jj < N ? max(0, min(2, ke - kk)) : 0;
-            copy_pair(rb + (j * RB_LD + 2 * p) * 8, B + (n > 0 ? (size_t)jj * ldb + kk : 0), B, 8 * n, vec16);
+          if (B_CONJ_T) {
+            const int n = k0 + kbk + 8 * u < ke ? nb : 0;
+            copy_pair(rb + b_dst + u * 8 * TN * 8, n > 0 ? b_src + (size_t)(it * TK + 8 * u) * ldb : B, B, 8 * n,
+                      vec16);
+          } else {
+            const int n = jb + 32 * u < N ? max(0, min(2, ke - (k0 + kbk))) : 0;
+            copy_pair(rb + b_dst + u * 32 * RB_LD * 8, n > 0 ? b_src + (size_t)32 * u * ldb + it * TK : B, B, 8 * n,
+                      vec16);
           }
         }
       }
       copy_commit();
     };
     bool ok = true;
-    issue(0);
-    issue(1);
+#pragma unroll
+    for (int it = 0; it < RAW - 1; ++it) issue(it);
     // Every producer passes producers_sync once per tile, aborted or not, so that none waits
     // at it for a warp that has left.
     for (int it = 0; it < ntiles; ++it) {
-      copy_wait_but_one();   // this thread's copies of tile it have landed
+      copy_wait<RAW - 2>();  // this thread's copies of tile it have landed
       producers_sync();      // everyone's have; everyone has converted tile it - 1
-      issue(it + 2);         // into the slot tile it - 1 came from
+      issue(it + RAW - 1);   // into the slot tile it - 1 came from
       if (!ok) continue;
       const int s = it % STAGES;
       if (it >= STAGES) {
