@@ -19,12 +19,15 @@
 //                     column for the lambda update (Eq. Update Lambda) and for A^{t+1}.
 //
 // N is not a power of two in the paper's own setting (40 x 40 detector and scan,
-// Table 1), so the 2-D DFT of an N x N image is computed directly, as two products
-// with the N x N twiddle matrix W (Y = W X W), in shared memory: each thread owns a
-// 2 x 4 block of the product and reads rows of the left operand and four-wide rows of
-// W.  Every pass stores its result transposed, so after the two passes of a 2-D DFT
-// the image is back in row-major order and every elementwise step (propagator, slice,
-// residual) works on the same 8 pixels per thread, held in registers.
+// Table 1).  The 2-D DFT of an N x N image is two passes over its rows in shared memory,
+// each the product with the N-point DFT matrix (Y = W X W), factored once as N = N1 N2
+// (Cooley-Tukey): a length-N1 DFT over the N2 decimated sub-sequences, a twiddle, then a
+// length-N2 DFT, N1 + N2 + 1 complex multiply-adds per output instead of N.  A thread owns
+// two rows and one bin c0 < N1 of the short DFT, i.e. the N2 columns c0 + N1 j: every step
+// of the factored pass stays in its registers.  Every pass stores its result transposed,
+// so after the two passes of a 2-D DFT the image is back in row-major order and every
+// elementwise step (propagator, slice, residual) works on the same 2 N2 pixels per
+// thread, held in registers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,7 +57,12 @@ constexpr int kPartSlots = 4096;    // FP64 partial sums per reduction
 enum { S_OBJ = 0, S_MU = 1, S_SPEC = 2, S_SUMI = 3, S_THR2 = 4, S_DOBJ = 5, S_MAXO = 8 };
 
 __host__ __device__ constexpr int ld_of(int N) { return N + 2; }   // padded row of an image buffer
-__host__ __device__ constexpr int threads_of(int N) { return N * N / 8; }
+// N = N1 N2 with N1 = 8 (4 at N = 16); the kernels' images need N in {16, 24, 32, 40, 48, 64}
+__host__ __device__ constexpr int fac1(int N) { return N == 16 ? 4 : 8; }
+__host__ __device__ constexpr int fac2(int N) { return N / fac1(N); }
+__host__ __device__ constexpr int threads_of(int N) { return (N / 2) * fac1(N); }
+// float2 slots of the twiddle tables: N base values, then the N2 x N2 matrix (N2 <= 8)
+__host__ __device__ constexpr int tw_elems(int N) { return N + 64; }
 __host__ __device__ constexpr int max_slices(int N) { return N == 64 ? 3 : kMaxSlices; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -80,95 +88,119 @@ __device__ __forceinline__ void cmac(float2& acc, float2 d, float2 w) {
   }
 }
 
-// W[k][c] = exp(-2 pi i (k c mod N) / N), unpadded rows: the N distinct values are computed
-// in double and rounded once (into `scratch`, N float2), then spread.  Ends with a barrier.
+// Wt[m] = exp(-2 pi i m / N) for m < N, computed in double and rounded once; then
+// Wt[N + k2 N2 + c2] = Wt[(N1 k2 c2) mod N], the N2-point DFT matrix.  Ends with a barrier.
 template <int N>
-__device__ void fill_twiddles(float2* Wt, float2* scratch) {
+__device__ void fill_twiddles(float2* Wt) {
+  constexpr int N1 = fac1(N), N2 = fac2(N);
   for (int m = threadIdx.x; m < N; m += blockDim.x) {
     double s, c;
     sincospi(-2.0 * (double)m / (double)N, &s, &c);
-    scratch[m] = make_float2((float)c, (float)s);
+    Wt[m] = make_float2((float)c, (float)s);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) Wt[e] = scratch[((e / N) * (e % N)) % N];
+  for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) Wt[N + e] = Wt[(N1 * (e / N2) * (e % N2)) % N];
   __syncthreads();
 }
 
-// One pass: a[i][j] = element (r0 + i, c0 + j N/4) of D W (CONJ: D conj(W)).  The four
-// columns of a thread are N/4 apart, so a quarter warp reads consecutive twiddles.
+// The twiddles of one thread's bin c0: its row of the N1-point DFT and the twiddles between
+// the two short DFTs in registers, the N2-point DFT matrix (the same for every thread) in
+// shared memory.
+template <int N>
+struct Twiddles {
+  float2 w1[fac1(N)];   // exp(-2 pi i N2 k1 c0 / N), k1 < N1
+  float2 tw[fac2(N)];   // exp(-2 pi i k2 c0 / N), k2 < N2
+  const float2* w2;     // [k2][c2]: exp(-2 pi i N1 k2 c2 / N)
+  __device__ Twiddles(const float2* Wt, int c0) {
+#pragma unroll
+    for (int k1 = 0; k1 < fac1(N); ++k1) w1[k1] = Wt[(fac2(N) * k1 * c0) % N];
+#pragma unroll
+    for (int k2 = 0; k2 < fac2(N); ++k2) tw[k2] = Wt[(k2 * c0) % N];
+    w2 = Wt + N;
+  }
+};
+
+// One pass: a[i][j] = element (r0 + i, c0 + N1 j) of D W (CONJ: D conj(W)), through
+// X[c0 + N1 c2] = sum_k2 W_N2^(k2 c2) W_N^(k2 c0) sum_k1 W_N1^(k1 c0) x[N2 k1 + k2],
+// with W_n = exp(-2 pi i / n).  The threads of a bin read the same row words (broadcast).
 template <int N, bool CONJ>
-__device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const float2* __restrict__ Wt,
-                                         float2 (&a)[2][4], int r0, int c0) {
-  constexpr int LD = ld_of(N);
+__device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const Twiddles<N>& tw,
+                                         float2 (&a)[2][fac2(N)], int r0) {
+  constexpr int LD = ld_of(N), N2 = fac2(N);
+  float2 y[2][N2];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) a[i][j] = make_float2(0.f, 0.f);
+    for (int q = 0; q < N2; ++q) y[i][q] = make_float2(0.f, 0.f);
   const float2* d0 = D + r0 * LD;
   const float2* d1 = d0 + LD;
-  const float2* wp = Wt + c0;
-  constexpr int Q = N / 4;
-#pragma unroll 4
-  for (int k = 0; k < N; k += 2) {
+#pragma unroll
+  for (int k = 0; k < N; k += 2) {   // x[k] = x[N2 k1 + k2]: k1 = k / N2, k2 = k % N2
     const float4 x0 = *reinterpret_cast<const float4*>(d0 + k);
     const float4 x1 = *reinterpret_cast<const float4*>(d1 + k);
-    float2 w0[4], w1[4];
+    cmac<CONJ>(y[0][k % N2], make_float2(x0.x, x0.y), tw.w1[k / N2]);
+    cmac<CONJ>(y[1][k % N2], make_float2(x1.x, x1.y), tw.w1[k / N2]);
+    cmac<CONJ>(y[0][(k + 1) % N2], make_float2(x0.z, x0.w), tw.w1[(k + 1) / N2]);
+    cmac<CONJ>(y[1][(k + 1) % N2], make_float2(x1.z, x1.w), tw.w1[(k + 1) / N2]);
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      w0[j] = wp[k * N + Q * j];
-      w1[j] = wp[(k + 1) * N + Q * j];
-    }
-    const float2 l00 = make_float2(x0.x, x0.y), l01 = make_float2(x0.z, x0.w);
-    const float2 l10 = make_float2(x1.x, x1.y), l11 = make_float2(x1.z, x1.w);
+  for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      cmac<CONJ>(a[0][j], l00, w0[j]);
-      cmac<CONJ>(a[1][j], l10, w0[j]);
-      cmac<CONJ>(a[0][j], l01, w1[j]);
-      cmac<CONJ>(a[1][j], l11, w1[j]);
+    for (int q = 0; q < N2; ++q) y[i][q] = CONJ ? cmulc(y[i][q], tw.tw[q]) : cmul(y[i][q], tw.tw[q]);
+#pragma unroll
+  for (int c2 = 0; c2 < N2; ++c2) {
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < N2; ++q) {
+      const float2 w = tw.w2[q * N2 + c2];
+      cmac<CONJ>(s0, y[0][q], w);
+      cmac<CONJ>(s1, y[1][q], w);
     }
+    a[0][c2] = s0;
+    a[1][c2] = s1;
   }
 }
 
-// O[c0 + j N/4][r0 + i] = a[i][j]: the transposed store that follows every pass.
+// O[c0 + N1 j][r0 + i] = a[i][j]: the transposed store that follows every pass.
 template <int N>
-__device__ __forceinline__ void store_t(float2* O, const float2 (&a)[2][4], int r0, int c0) {
+__device__ __forceinline__ void store_t(float2* O, const float2 (&a)[2][fac2(N)], int r0, int c0) {
   constexpr int LD = ld_of(N);
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    *reinterpret_cast<float4*>(O + (c0 + (N / 4) * j) * LD + r0) =
+  for (int j = 0; j < fac2(N); ++j)
+    *reinterpret_cast<float4*>(O + (c0 + fac1(N) * j) * LD + r0) =
         make_float4(a[0][j].x, a[0][j].y, a[1][j].x, a[1][j].y);
 }
 
-// 2-D DFT of the image whose pixels (y, x) = (c0 + j N/4, r0 + i) are held in v (the pixels
+// 2-D DFT of the image whose pixels (y, x) = (c0 + N1 j, r0 + i) are held in v (the pixels
 // this thread owns); the result comes back in v at the same pixels.  INV: conjugate kernel
 // (F^H, unnormalised).  Uses X and Y as scratch; begins and ends with all threads free to
 // overwrite X.
 template <int N, bool INV>
-__device__ __forceinline__ void dft2(float2 (&v)[2][4], float2* X, float2* Y, const float2* Wt, int r0, int c0) {
+__device__ __forceinline__ void dft2(float2 (&v)[2][fac2(N)], float2* X, float2* Y, const Twiddles<N>& tw, int r0,
+                                     int c0) {
   store_t<N>(X, v, r0, c0);
   __syncthreads();
-  dft_pass<N, INV>(X, Wt, v, r0, c0);
+  dft_pass<N, INV>(X, tw, v, r0);
   store_t<N>(Y, v, r0, c0);
   __syncthreads();
-  dft_pass<N, INV>(Y, Wt, v, r0, c0);
+  dft_pass<N, INV>(Y, tw, v, r0);
 }
 
-__device__ __forceinline__ int owned(int N, int r0, int c0, int i, int j) { return (c0 + (N / 4) * j) * N + r0 + i; }
+__host__ __device__ constexpr int owned(int N, int r0, int c0, int i, int j) { return (c0 + fac1(N) * j) * N + r0 + i; }
 
 // v <- G v (ADJ: G^H v), G = F^-1 diag(h) F; h carries the 1/N^2 of F^-1.
 template <int N, bool ADJ>
-__device__ __forceinline__ void propagate(float2 (&v)[2][4], float2* X, float2* Y, const float2* Wt,
+__device__ __forceinline__ void propagate(float2 (&v)[2][fac2(N)], float2* X, float2* Y, const Twiddles<N>& tw,
                                           const float2* __restrict__ h, int r0, int c0) {
-  dft2<N, false>(v, X, Y, Wt, r0, c0);
+  dft2<N, false>(v, X, Y, tw, r0, c0);
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < fac2(N); ++j) {
       const float2 hv = __ldg(&h[owned(N, r0, c0, i, j)]);
       v[i][j] = ADJ ? cmulc(v[i][j], hv) : cmul(v[i][j], hv);
     }
-  dft2<N, true>(v, X, Y, Wt, r0, c0);
+  dft2<N, true>(v, X, Y, tw, r0, c0);
 }
 
 // Fixed-order FP64 block sum (at least 32 threads): the first warp adds strided values in
@@ -212,16 +244,17 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
   float2* X = reinterpret_cast<float2*>(smem4);
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
-  double* red = reinterpret_cast<double*>(Wt + N * N);
+  double* red = reinterpret_cast<double*>(Wt + tw_elems(N));
   constexpr int n2 = N * N;
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
-  fill_twiddles<N>(Wt, X);
+  const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
+  fill_twiddles<N>(Wt);
+  const Twiddles<N> tw(Wt, c0);
   const float thr2 = (float)scal[S_THR2];
   double obj = 0.0;
   for (int s = blockIdx.x; s < S; s += gridDim.x) {
-    float2 v[2][4];
+    float2 v[2][fac2(N)];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < fac2(N); ++j) {
       const size_t e = (size_t)s * n2 + owned(N, r0, c0, 0, j);
       float4 acc = *reinterpret_cast<const float4*>(BC + e);
       for (int z = 1; z < splits; ++z) {
@@ -231,12 +264,12 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
       v[0][j] = make_float2(acc.x, acc.y);
       v[1][j] = make_float2(acc.z, acc.w);
     }
-    dft2<N, false>(v, X, Y, Wt, r0, c0);
+    dft2<N, false>(v, X, Y, tw, r0, c0);
     float o = 0.f;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < fac2(N); ++j) {
         const float meas = __ldg(&I[(size_t)s * n2 + owned(N, r0, c0, i, j)]);
         const float2 u = v[i][j];
         const float a2 = fmaf(u.x, u.x, u.y * u.y);
@@ -247,9 +280,9 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
         v[i][j] = make_float2(u.x * f, u.y * f);
       }
     obj += (double)o;
-    dft2<N, true>(v, X, Y, Wt, r0, c0);
+    dft2<N, true>(v, X, Y, tw, r0, c0);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < fac2(N); ++j)
       *reinterpret_cast<float4*>(BC + (size_t)s * n2 + owned(N, r0, c0, 0, j)) =
           make_float4(v[0][j].x, v[0][j].y, v[1][j].x, v[1][j].y);
   }
@@ -290,25 +323,25 @@ __device__ __forceinline__ int rel_index(int N, int e, int col) {
 // G (o_1[col] e_col) = o_1[col] gk(. - col), gk = G e_0 the propagator's real-space kernel.
 // Incident waves on slices 1..M-1 go to stash.
 template <int N, bool STASH>
-__device__ __forceinline__ void impulse_forward(float2 (&v)[2][4], int col, int M, const float2* __restrict__ o,
+__device__ __forceinline__ void impulse_forward(float2 (&v)[2][fac2(N)], int col, int M, const float2* __restrict__ o,
                                                 const float2* __restrict__ gk, const float2* __restrict__ h,
-                                                float2* X, float2* Y, const float2* Wt, float2* stash, int r0,
-                                                int c0) {
+                                                float2* X, float2* Y, const Twiddles<N>& tw, float2* stash,
+                                                int r0, int c0) {
   constexpr int n2 = N * N;
   const float2 o0 = __ldg(&o[col]);
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < fac2(N); ++j) {
       const int e = owned(N, r0, c0, i, j);
       v[i][j] = M == 1 ? (e == col ? o0 : make_float2(0.f, 0.f)) : cmul(o0, __ldg(&gk[rel_index(N, e, col)]));
     }
   for (int m = 1; m < M; ++m) {
-    if (m > 1) propagate<N, false>(v, X, Y, Wt, h, r0, c0);
+    if (m > 1) propagate<N, false>(v, X, Y, tw, h, r0, c0);
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < fac2(N); ++j) {
         const int e = owned(N, r0, c0, i, j);
         if (STASH) stash[(m - 1) * n2 + e] = v[i][j];
         v[i][j] = cmul(v[i][j], __ldg(&o[(size_t)m * n2 + e]));
@@ -335,28 +368,29 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
   float2* X = reinterpret_cast<float2*>(smem4);
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
-  float2* stash = Wt + N * N;                                      // [M-1][N^2], thread-owned pixels
+  float2* stash = Wt + tw_elems(N);                                      // [M-1][N^2], thread-owned pixels
   double* red = reinterpret_cast<double*>(stash + (M - 1) * N * N);
   float2* red2 = reinterpret_cast<float2*>(red);
   constexpr int n2 = N * N;
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
-  fill_twiddles<N>(Wt, X);
+  const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
+  fill_twiddles<N>(Wt);
+  const Twiddles<N> tw(Wt, c0);
   const float lam = (float)lam_p[0];
-  float2 acc[NA][2][4];
+  float2 acc[NA][2][fac2(N)];
 #pragma unroll
   for (int q = 0; q < NA; ++q)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[q][i][j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < fac2(N); ++j) acc[q][i][j] = make_float2(0.f, 0.f);
   double obj = 0.0;
   for (int col = blockIdx.x; col < n2; col += gridDim.x) {
-    float2 v[2][4];
-    impulse_forward<N, true>(v, col, M, o, gk, h, X, Y, Wt, stash, r0, c0);
+    float2 v[2][fac2(N)];
+    impulse_forward<N, true>(v, col, M, o, gk, h, X, Y, tw, stash, r0, c0);
     const float2* Aj = A + (size_t)col * n2;
     float ob = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < fac2(N); ++j) {
       const float4 a = *reinterpret_cast<const float4*>(Aj + owned(N, r0, c0, 0, j));
       const float2 a0 = make_float2(a.x, a.y), a1 = make_float2(a.z, a.w);
       v[0][j] = make_float2(fmaf(lam, v[0][j].x, -a0.x), fmaf(lam, v[0][j].y, -a0.y));
@@ -371,14 +405,14 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < fac2(N); ++j) {
           const int e = owned(N, r0, c0, i, j);
           const float2 g = cmulc(v[i][j], stash[(l - 1) * n2 + e]);
           acc[l - 1][i][j].x += g.x;
           acc[l - 1][i][j].y += g.y;
           v[i][j] = cmulc(v[i][j], __ldg(&o[(size_t)l * n2 + e]));
         }
-      if (l > 1) propagate<N, true>(v, X, Y, Wt, h, r0, c0);
+      if (l > 1) propagate<N, true>(v, X, Y, tw, h, r0, c0);
     }
     // slice 0: (G^H conj(o_1) chi_1)[col] = <G e_col, conj(o_1) chi_1>, or m_j[col] when M = 1
     float2 chi0 = make_float2(0.f, 0.f);
@@ -387,7 +421,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < fac2(N); ++j) {
           const float2 p = cmulc(v[i][j], __ldg(&gk[rel_index(N, owned(N, r0, c0, i, j), col)]));
           d.x += p.x;
           d.y += p.y;
@@ -397,14 +431,14 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < fac2(N); ++j)
         if (owned(N, r0, c0, i, j) == col) g0[col] = M > 1 ? chi0 : v[i][j];
   }
   if (M > 1) {
 #pragma unroll
     for (int q = 0; q < NA; ++q)
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < fac2(N); ++j)
         *reinterpret_cast<float4*>(gpart + ((size_t)blockIdx.x * NA + q) * n2 + owned(N, r0, c0, 0, j)) =
             make_float4(acc[q][0][j].x, acc[q][0][j].y, acc[q][1][j].x, acc[q][1][j].y);
   }
@@ -424,18 +458,19 @@ __global__ void __launch_bounds__(threads_of(N)) transfer_kernel(float2* A, cons
   float2* X = reinterpret_cast<float2*>(smem4);
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
-  double* red = reinterpret_cast<double*>(Wt + N * N);
+  double* red = reinterpret_cast<double*>(Wt + tw_elems(N));
   constexpr int n2 = N * N;
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
-  fill_twiddles<N>(Wt, X);
+  const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
+  fill_twiddles<N>(Wt);
+  const Twiddles<N> tw(Wt, c0);
   double dot = 0.0, nrm = 0.0;
   for (int col = blockIdx.x; col < n2; col += gridDim.x) {
-    float2 v[2][4];
-    impulse_forward<N, false>(v, col, M, o, gk, h, X, Y, Wt, nullptr, r0, c0);
+    float2 v[2][fac2(N)];
+    impulse_forward<N, false>(v, col, M, o, gk, h, X, Y, tw, nullptr, r0, c0);
     float2* Aj = A + (size_t)col * n2;
     float d = 0.f, q = 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < fac2(N); ++j) {
       float4* p = reinterpret_cast<float4*>(Aj + owned(N, r0, c0, 0, j));
       if (HAVE_AHAT) {
         const float4 a = *p;
@@ -470,20 +505,21 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
   float2* X = reinterpret_cast<float2*>(smem4);
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
-  double* red = reinterpret_cast<double*>(Wt + N * N);
-  const int t = threadIdx.x, r0 = 2 * (t / (N / 4)), c0 = t % (N / 4);
-  fill_twiddles<N>(Wt, X);
-  float2 v[2][4];
+  double* red = reinterpret_cast<double*>(Wt + tw_elems(N));
+  const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
+  fill_twiddles<N>(Wt);
+  const Twiddles<N> tw(Wt, c0);
+  float2 v[2][fac2(N)];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[i][j] = probe[owned(N, r0, c0, i, j)];
-  dft2<N, false>(v, X, Y, Wt, r0, c0);
+    for (int j = 0; j < fac2(N); ++j) v[i][j] = probe[owned(N, r0, c0, i, j)];
+  dft2<N, false>(v, X, Y, tw, r0, c0);
   double mx = 0.0;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) mx = fmax(mx, (double)v[i][j].x * v[i][j].x + (double)v[i][j].y * v[i][j].y);
+    for (int j = 0; j < fac2(N); ++j) mx = fmax(mx, (double)v[i][j].x * v[i][j].x + (double)v[i][j].y * v[i][j].y);
   const double m = block_sum<true>(mx, red);
   double a = 0.0;
   for (int i = t; i < n_part; i += blockDim.x) a += sum_part[i];
@@ -763,7 +799,7 @@ static msp_status check(const msp_smd_geometry* g) {
 
 // Dynamic shared memory of the per-column kernels.
 static size_t image_smem(int N, int stash_planes, int threads) {
-  return 2 * (size_t)N * ld_of(N) * sizeof(float2) + (size_t)N * N * sizeof(float2) +
+  return 2 * (size_t)N * ld_of(N) * sizeof(float2) + (size_t)tw_elems(N) * sizeof(float2) +
          (size_t)stash_planes * N * N * sizeof(float2) + (size_t)(threads + 1) * sizeof(double);
 }
 

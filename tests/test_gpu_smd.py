@@ -10,7 +10,8 @@ contractions run on the tensor cores with every operand split into a pair of tf3
 values and FP32 accumulation over groups of 128 K (then round-to-nearest FP32 sums):
 their error is at most max(sqrt(K), 32) 2^-24 (32 2^-24 = 1.9e-6, the measured level
 at any K).  So one matrix step carries e = (max(N, 32) + max(sqrt(S), 32) + 4 sqrt(N))
-2^-24 (A P over N^2 terms, C P^H over S terms, four direct-DFT passes of N terms), and a
+2^-24 (A P over N^2 terms, C P^H over S terms, four DFT passes of at most N terms: the
+kernels factor the N-point DFT, N1 + N2 + 1 terms per output), and a
 multislice impulse pass through M slices e = 8 (M - 1) sqrt(N) 2^-24 (four passes per
 propagator, forward and adjoint).  The
 residual R = U - sqrt(I) U/|U| and the decomposition residual lambda A(o) - Ahat
@@ -250,6 +251,26 @@ def test_decomposition_table1_size(msp):
     At = O.transfer_matrix(case.G, slices_list(case.truth))
     Ahat = c64((At + 0.02 * synth.random_complex(At.shape, 6) / 40).T)
     decompose_check(msp, case, Ahat, c64(np.ones((3, 40, 40))), 1.0)
+
+
+def test_transfer_columns_at_the_largest_grid(msp):
+    """N = 64 (N1 = N2 = 8), M = 3: sampled columns of A(o), each the oracle's multislice pass
+    of an impulse (Eq. exit_wave_mslices with p = e_j) through its FFT propagator."""
+    n, M = 64, 3
+    case = Case(n, M, seed=64, count=4)
+    o = c64(synth.random_complex((M, n, n), 9))
+    A = msp.smd_transfer(case.sg(msp), dev(o), 1.0).cpu().numpy()
+    g = case.geom
+    h = O.fresnel_propagator(n, g["pixel_A"], g["wavelength_A"], g["dz_A"])
+    oc = o.astype(np.complex128)
+    rng = np.random.default_rng(5)
+    cols = [0, 1, n - 1, n, n * n - 1] + list(rng.choice(n * n, 7, replace=False))
+    for j in cols:
+        e = np.zeros((n, n), np.complex128)
+        e.flat[j] = oc[0].flat[j]
+        for m in range(1, M):
+            e = oc[m] * O.propagate(e, h)
+        assert rel(A[j].reshape(n, n), e) <= bar(e_chain(n, M)), j
 
 
 def test_one_slice_decomposition_at_the_largest_grid(msp):
