@@ -253,26 +253,6 @@ def test_decomposition_table1_size(msp):
     decompose_check(msp, case, Ahat, c64(np.ones((3, 40, 40))), 1.0)
 
 
-def test_transfer_columns_at_the_largest_grid(msp):
-    """N = 64 (N1 = N2 = 8), M = 3: sampled columns of A(o), each the oracle's multislice pass
-    of an impulse (Eq. exit_wave_mslices with p = e_j) through its FFT propagator."""
-    n, M = 64, 3
-    case = Case(n, M, seed=64, count=4)
-    o = c64(synth.random_complex((M, n, n), 9))
-    A = msp.smd_transfer(case.sg(msp), dev(o), 1.0).cpu().numpy()
-    g = case.geom
-    h = O.fresnel_propagator(n, g["pixel_A"], g["wavelength_A"], g["dz_A"])
-    oc = o.astype(np.complex128)
-    rng = np.random.default_rng(5)
-    cols = [0, 1, n - 1, n, n * n - 1] + list(rng.choice(n * n, 7, replace=False))
-    for j in cols:
-        e = np.zeros((n, n), np.complex128)
-        e.flat[j] = oc[0].flat[j]
-        for m in range(1, M):
-            e = oc[m] * O.propagate(e, h)
-        assert rel(A[j].reshape(n, n), e) <= bar(e_chain(n, M)), j
-
-
 def test_one_slice_decomposition_at_the_largest_grid(msp):
     """N = 64, M = 1: R = S = I, so the slice becomes diag(Ahat)/||diag(Ahat)||, lambda
     ||diag(Ahat)|| and A the diagonal part of Ahat (the closed form of the one-slice case)."""
