@@ -61,8 +61,8 @@ __host__ __device__ constexpr int ld_of(int N) { return N + 2; }   // padded row
 __host__ __device__ constexpr int fac1(int N) { return N == 16 ? 4 : 8; }
 __host__ __device__ constexpr int fac2(int N) { return N / fac1(N); }
 __host__ __device__ constexpr int threads_of(int N) { return (N / 2) * fac1(N); }
-// float2 slots of the twiddle tables: N base values, then the N2 x N2 matrix (N2 <= 8)
-__host__ __device__ constexpr int tw_elems(int N) { return N + 64; }
+// float2 slots of the twiddle tables: N base values, the N2 x N2 matrix and its conjugate (N2 <= 8)
+__host__ __device__ constexpr int tw_elems(int N) { return N + 128; }
 __host__ __device__ constexpr int max_slices(int N) { return N == 64 ? 3 : kMaxSlices; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -89,7 +89,8 @@ __device__ __forceinline__ void cmac(float2& acc, float2 d, float2 w) {
 }
 
 // Wt[m] = exp(-2 pi i m / N) for m < N, computed in double and rounded once; then
-// Wt[N + k2 N2 + c2] = Wt[(N1 k2 c2) mod N], the N2-point DFT matrix.  Ends with a barrier.
+// Wt[N + k2 N2 + c2] = Wt[(N1 k2 c2) mod N], the N2-point DFT matrix, and at Wt[N + 64 + ...]
+// its conjugate.  Ends with a barrier.
 template <int N>
 __device__ void fill_twiddles(float2* Wt) {
   constexpr int N1 = fac1(N), N2 = fac2(N);
@@ -99,31 +100,47 @@ __device__ void fill_twiddles(float2* Wt) {
     Wt[m] = make_float2((float)c, (float)s);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) Wt[N + e] = Wt[(N1 * (e / N2) * (e % N2)) % N];
+  for (int e = threadIdx.x; e < N2 * N2; e += blockDim.x) {
+    const float2 w = Wt[(N1 * (e / N2) * (e % N2)) % N];
+    Wt[N + e] = w;
+    Wt[N + 64 + e] = make_float2(w.x, -w.y);
+  }
   __syncthreads();
 }
 
 // The twiddles of one thread's bin c0: its row of the N1-point DFT and the twiddles between
 // the two short DFTs in registers, the N2-point DFT matrix (the same for every thread) in
-// shared memory.
+// shared memory.  conjugate() turns them into those of F^H (and back).
 template <int N>
 struct Twiddles {
   float2 w1[fac1(N)];   // exp(-2 pi i N2 k1 c0 / N), k1 < N1
   float2 tw[fac2(N)];   // exp(-2 pi i k2 c0 / N), k2 < N2
   const float2* w2;     // [k2][c2]: exp(-2 pi i N1 k2 c2 / N)
+  const float2* w2c;    // its conjugate
   __device__ Twiddles(const float2* Wt, int c0) {
 #pragma unroll
     for (int k1 = 0; k1 < fac1(N); ++k1) w1[k1] = Wt[(fac2(N) * k1 * c0) % N];
 #pragma unroll
     for (int k2 = 0; k2 < fac2(N); ++k2) tw[k2] = Wt[(k2 * c0) % N];
     w2 = Wt + N;
+    w2c = Wt + N + 64;
+  }
+  __device__ __forceinline__ void conjugate() {
+#pragma unroll
+    for (int k1 = 0; k1 < fac1(N); ++k1) w1[k1].y = -w1[k1].y;
+#pragma unroll
+    for (int k2 = 0; k2 < fac2(N); ++k2) tw[k2].y = -tw[k2].y;
+    const float2* t = w2;
+    w2 = w2c;
+    w2c = t;
   }
 };
 
-// One pass: a[i][j] = element (r0 + i, c0 + N1 j) of D W (CONJ: D conj(W)), through
+// One pass: a[i][j] = element (r0 + i, c0 + N1 j) of D W, through
 // X[c0 + N1 c2] = sum_k2 W_N2^(k2 c2) W_N^(k2 c0) sum_k1 W_N1^(k1 c0) x[N2 k1 + k2],
-// with W_n = exp(-2 pi i / n).  The threads of a bin read the same row words (broadcast).
-template <int N, bool CONJ>
+// with W_n = exp(-2 pi i / n) (conjugated twiddles: D conj(W)).  The threads of a bin read
+// the same row words (broadcast).
+template <int N>
 __device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const Twiddles<N>& tw,
                                          float2 (&a)[2][fac2(N)], int r0) {
   constexpr int LD = ld_of(N), N2 = fac2(N);
@@ -138,23 +155,23 @@ __device__ __forceinline__ void dft_pass(const float2* __restrict__ D, const Twi
   for (int k = 0; k < N; k += 2) {   // x[k] = x[N2 k1 + k2]: k1 = k / N2, k2 = k % N2
     const float4 x0 = *reinterpret_cast<const float4*>(d0 + k);
     const float4 x1 = *reinterpret_cast<const float4*>(d1 + k);
-    cmac<CONJ>(y[0][k % N2], make_float2(x0.x, x0.y), tw.w1[k / N2]);
-    cmac<CONJ>(y[1][k % N2], make_float2(x1.x, x1.y), tw.w1[k / N2]);
-    cmac<CONJ>(y[0][(k + 1) % N2], make_float2(x0.z, x0.w), tw.w1[(k + 1) / N2]);
-    cmac<CONJ>(y[1][(k + 1) % N2], make_float2(x1.z, x1.w), tw.w1[(k + 1) / N2]);
+    cmac<false>(y[0][k % N2], make_float2(x0.x, x0.y), tw.w1[k / N2]);
+    cmac<false>(y[1][k % N2], make_float2(x1.x, x1.y), tw.w1[k / N2]);
+    cmac<false>(y[0][(k + 1) % N2], make_float2(x0.z, x0.w), tw.w1[(k + 1) / N2]);
+    cmac<false>(y[1][(k + 1) % N2], make_float2(x1.z, x1.w), tw.w1[(k + 1) / N2]);
   }
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int q = 0; q < N2; ++q) y[i][q] = CONJ ? cmulc(y[i][q], tw.tw[q]) : cmul(y[i][q], tw.tw[q]);
+    for (int q = 0; q < N2; ++q) y[i][q] = cmul(y[i][q], tw.tw[q]);
 #pragma unroll
   for (int c2 = 0; c2 < N2; ++c2) {
     float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
 #pragma unroll
     for (int q = 0; q < N2; ++q) {
       const float2 w = tw.w2[q * N2 + c2];
-      cmac<CONJ>(s0, y[0][q], w);
-      cmac<CONJ>(s1, y[1][q], w);
+      cmac<false>(s0, y[0][q], w);
+      cmac<false>(s1, y[1][q], w);
     }
     a[0][c2] = s0;
     a[1][c2] = s1;
@@ -172,35 +189,46 @@ __device__ __forceinline__ void store_t(float2* O, const float2 (&a)[2][fac2(N)]
 }
 
 // 2-D DFT of the image whose pixels (y, x) = (c0 + N1 j, r0 + i) are held in v (the pixels
-// this thread owns); the result comes back in v at the same pixels.  INV: conjugate kernel
-// (F^H, unnormalised).  Uses X and Y as scratch; begins and ends with all threads free to
-// overwrite X.
-template <int N, bool INV>
-__device__ __forceinline__ void dft2(float2 (&v)[2][fac2(N)], float2* X, float2* Y, const Twiddles<N>& tw, int r0,
-                                     int c0) {
-  store_t<N>(X, v, r0, c0);
-  __syncthreads();
-  dft_pass<N, INV>(X, tw, v, r0);
-  store_t<N>(Y, v, r0, c0);
-  __syncthreads();
-  dft_pass<N, INV>(Y, tw, v, r0);
+// this thread owns); the result comes back in v at the same pixels.  inv: conjugate kernel
+// (F^H, unnormalised).  Uses X (first pass) and Y (second) as scratch; begins and ends with
+// all threads free to overwrite X.  The two passes share one copy of the pass code and the
+// direction is a run-time flag: a kernel inlines this a few times only, which keeps its
+// code within the instruction cache.
+template <int N>
+__device__ __forceinline__ void dft2(float2 (&v)[2][fac2(N)], float2* X, float2* Y, Twiddles<N>& tw, bool inv,
+                                     int r0, int c0) {
+  if (inv) tw.conjugate();
+#pragma unroll 1
+  for (int p = 0; p < 2; ++p) {
+    float2* B = p ? Y : X;
+    store_t<N>(B, v, r0, c0);
+    __syncthreads();
+    dft_pass<N>(B, tw, v, r0);
+  }
+  if (inv) tw.conjugate();
 }
 
 __host__ __device__ constexpr int owned(int N, int r0, int c0, int i, int j) { return (c0 + fac1(N) * j) * N + r0 + i; }
 
-// v <- G v (ADJ: G^H v), G = F^-1 diag(h) F; h carries the 1/N^2 of F^-1.
-template <int N, bool ADJ>
-__device__ __forceinline__ void propagate(float2 (&v)[2][fac2(N)], float2* X, float2* Y, const Twiddles<N>& tw,
-                                          const float2* __restrict__ h, int r0, int c0) {
-  dft2<N, false>(v, X, Y, tw, r0, c0);
+// v <- G v (adj: G^H v), G = F^-1 diag(h) F; h carries the 1/N^2 of F^-1.  One inlined
+// 2-D DFT, run forward, then (after diag(h), or diag(conj h)) inverse.
+template <int N>
+__device__ __forceinline__ void propagate(float2 (&v)[2][fac2(N)], float2* X, float2* Y, Twiddles<N>& tw,
+                                          const float2* __restrict__ h, bool adj, int r0, int c0) {
+  const float hs = adj ? -1.f : 1.f;
+#pragma unroll 1
+  for (int d = 0; d < 2; ++d) {
+    dft2<N>(v, X, Y, tw, d == 1, r0, c0);
+    if (d == 0) {
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < 2; ++i)
 #pragma unroll
-    for (int j = 0; j < fac2(N); ++j) {
-      const float2 hv = __ldg(&h[owned(N, r0, c0, i, j)]);
-      v[i][j] = ADJ ? cmulc(v[i][j], hv) : cmul(v[i][j], hv);
+        for (int j = 0; j < fac2(N); ++j) {
+          const float2 hv = __ldg(&h[owned(N, r0, c0, i, j)]);
+          v[i][j] = cmul(v[i][j], make_float2(hv.x, hs * hv.y));
+        }
     }
-  dft2<N, true>(v, X, Y, tw, r0, c0);
+  }
 }
 
 // Fixed-order FP64 block sum (at least 32 threads): the first warp adds strided values in
@@ -248,7 +276,7 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
   constexpr int n2 = N * N;
   const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
   fill_twiddles<N>(Wt);
-  const Twiddles<N> tw(Wt, c0);
+  Twiddles<N> tw(Wt, c0);
   const float thr2 = (float)scal[S_THR2];
   double obj = 0.0;
   for (int s = blockIdx.x; s < S; s += gridDim.x) {
@@ -264,7 +292,7 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
       v[0][j] = make_float2(acc.x, acc.y);
       v[1][j] = make_float2(acc.z, acc.w);
     }
-    dft2<N, false>(v, X, Y, tw, r0, c0);
+    dft2<N>(v, X, Y, tw, false, r0, c0);
     float o = 0.f;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -280,7 +308,7 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
         v[i][j] = make_float2(u.x * f, u.y * f);
       }
     obj += (double)o;
-    dft2<N, true>(v, X, Y, tw, r0, c0);
+    dft2<N>(v, X, Y, tw, true, r0, c0);
 #pragma unroll
     for (int j = 0; j < fac2(N); ++j)
       *reinterpret_cast<float4*>(BC + (size_t)s * n2 + owned(N, r0, c0, 0, j)) =
@@ -325,7 +353,7 @@ __device__ __forceinline__ int rel_index(int N, int e, int col) {
 template <int N, bool STASH>
 __device__ __forceinline__ void impulse_forward(float2 (&v)[2][fac2(N)], int col, int M, const float2* __restrict__ o,
                                                 const float2* __restrict__ gk, const float2* __restrict__ h,
-                                                float2* X, float2* Y, const Twiddles<N>& tw, float2* stash,
+                                                float2* X, float2* Y, Twiddles<N>& tw, float2* stash,
                                                 int r0, int c0) {
   constexpr int n2 = N * N;
   const float2 o0 = __ldg(&o[col]);
@@ -337,7 +365,7 @@ __device__ __forceinline__ void impulse_forward(float2 (&v)[2][fac2(N)], int col
       v[i][j] = M == 1 ? (e == col ? o0 : make_float2(0.f, 0.f)) : cmul(o0, __ldg(&gk[rel_index(N, e, col)]));
     }
   for (int m = 1; m < M; ++m) {
-    if (m > 1) propagate<N, false>(v, X, Y, tw, h, r0, c0);
+    if (m > 1) propagate<N>(v, X, Y, tw, h, false, r0, c0);
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -374,7 +402,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
   constexpr int n2 = N * N;
   const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
   fill_twiddles<N>(Wt);
-  const Twiddles<N> tw(Wt, c0);
+  Twiddles<N> tw(Wt, c0);
   const float lam = (float)lam_p[0];
   float2 acc[NA][2][fac2(N)];
 #pragma unroll
@@ -412,7 +440,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
           acc[l - 1][i][j].y += g.y;
           v[i][j] = cmulc(v[i][j], __ldg(&o[(size_t)l * n2 + e]));
         }
-      if (l > 1) propagate<N, true>(v, X, Y, tw, h, r0, c0);
+      if (l > 1) propagate<N>(v, X, Y, tw, h, true, r0, c0);
     }
     // slice 0: (G^H conj(o_1) chi_1)[col] = <G e_col, conj(o_1) chi_1>, or m_j[col] when M = 1
     float2 chi0 = make_float2(0.f, 0.f);
@@ -462,7 +490,7 @@ __global__ void __launch_bounds__(threads_of(N)) transfer_kernel(float2* A, cons
   constexpr int n2 = N * N;
   const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
   fill_twiddles<N>(Wt);
-  const Twiddles<N> tw(Wt, c0);
+  Twiddles<N> tw(Wt, c0);
   double dot = 0.0, nrm = 0.0;
   for (int col = blockIdx.x; col < n2; col += gridDim.x) {
     float2 v[2][fac2(N)];
@@ -508,13 +536,13 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
   double* red = reinterpret_cast<double*>(Wt + tw_elems(N));
   const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
   fill_twiddles<N>(Wt);
-  const Twiddles<N> tw(Wt, c0);
+  Twiddles<N> tw(Wt, c0);
   float2 v[2][fac2(N)];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < fac2(N); ++j) v[i][j] = probe[owned(N, r0, c0, i, j)];
-  dft2<N, false>(v, X, Y, tw, r0, c0);
+  dft2<N>(v, X, Y, tw, false, r0, c0);
   double mx = 0.0;
 #pragma unroll
   for (int i = 0; i < 2; ++i)
