@@ -54,7 +54,7 @@ constexpr int kMaxSlices = 5;
 constexpr int kPartSlots = 4096;    // FP64 partial sums per reduction
 
 // scalar slots in the workspace
-enum { S_OBJ = 0, S_MU = 1, S_SPEC = 2, S_SUMI = 3, S_THR2 = 4, S_DOBJ = 5, S_MAXO = 8 };
+enum { S_OBJ = 0, S_MU = 1, S_SPEC = 2, S_SUMI = 3, S_THR2 = 4, S_DOBJ = 5 };
 
 __host__ __device__ constexpr int ld_of(int N) { return N + 2; }   // padded row of an image buffer
 // N = N1 N2 with N1 = 8 (4 at N = 16); the kernels' images need N in {16, 24, 32, 40, 48, 64}
@@ -381,7 +381,8 @@ __device__ __forceinline__ void impulse_forward(float2 (&v)[2][fac2(N)], int col
 // slice l, the column's share (R_l^H m_j) o conj(S_l e_j) of diag(R_l^H M S_l^H).  Slice 0
 // (S_0 = I) receives from column j one value only, at pixel j: it is written to g0[j].  The
 // per-CTA sums of slices 1..M-1 go to gpart[cta][l-1][k]; the objective 1/2 sum |m_j|^2 to
-// obj_part[cta].
+// obj_part[cta].  Each CTA also writes max |o_m|^2 over its share of the pixels to
+// maxpart[cta][m], for the proximal step sizes.
 template <int N, int M>
 __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __restrict__ A,
                                                              const float2* __restrict__ o,
@@ -390,7 +391,8 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
                                                              const double* __restrict__ lam_p,
                                                              float2* __restrict__ g0,
                                                              float2* __restrict__ gpart,
-                                                             double* __restrict__ obj_part) {
+                                                             double* __restrict__ obj_part,
+                                                             float* __restrict__ maxpart) {
   constexpr int NA = M > 1 ? M - 1 : 1;   // accumulated slices 1..M-1
   extern __shared__ float4 smem4[];
   float2* X = reinterpret_cast<float2*>(smem4);
@@ -403,6 +405,19 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
   const int t = threadIdx.x, r0 = 2 * (t / fac1(N)), c0 = t % fac1(N);
   fill_twiddles<N>(Wt);
   Twiddles<N> tw(Wt, c0);
+  {
+    const int chunk = (n2 + gridDim.x - 1) / gridDim.x;
+    const int k0 = blockIdx.x * chunk, k1 = min(n2, k0 + chunk);
+    for (int m = 0; m < M; ++m) {
+      float a = 0.f;
+      for (int k = k0 + t; k < k1; k += blockDim.x) {
+        const float2 v = __ldg(&o[(size_t)m * n2 + k]);
+        a = fmaxf(a, fmaf(v.x, v.x, v.y * v.y));
+      }
+      const double mx = block_sum<true>((double)a, red);
+      if (t == 0) maxpart[blockIdx.x * M + m] = (float)mx;
+    }
+  }
   const float lam = (float)lam_p[0];
   float2 acc[NA][2][fac2(N)];
 #pragma unroll
@@ -567,15 +582,21 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
 // ---------------------------------------------------------------------------
 
 // P[:, s] = vec of the probe shifted cyclically by shifts[s] (Sec. 2.1).
+// Grid: x over the pixels k of a column, y over the shifts s (each thread takes every
+// gridDim.y-th shift).
 __global__ void probe_matrix_kernel(const float2* __restrict__ probe, const int2* __restrict__ shifts, int N, int S,
                                     float2* __restrict__ P) {
-  const size_t n2 = (size_t)N * N, total = n2 * S;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int s = (int)(e / n2), k = (int)(e % n2);
-    const int y = k / N, x = k % N;
+  const int n2 = N * N, k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n2) return;
+  const int y = k / N, x = k - y * N;
+#pragma unroll 4
+  for (int s = blockIdx.y; s < S; s += gridDim.y) {
     const int2 sh = shifts[s];
     const int ys = ((sh.x % N) + N) % N, xs = ((sh.y % N) + N) % N;
-    P[e] = probe[((y - ys + N) % N) * N + (x - xs + N) % N];
+    int yy = y - ys, xx = x - xs;
+    if (yy < 0) yy += N;
+    if (xx < 0) xx += N;
+    P[(size_t)s * n2 + k] = __ldg(&probe[yy * N + xx]);
   }
 }
 
@@ -620,14 +641,16 @@ __global__ void kernel_column_kernel(float2* __restrict__ gk, const double2* __r
   gk[e] = make_float2((float)(a.x * b.x - a.y * b.y), (float)(a.x * b.y + a.y * b.x));
 }
 
-// Block partial sums (FP64) of a float array over fixed chunks.
+// Block partial sums of a float array over fixed chunks: FP32 within a thread (a few dozen
+// terms), FP64 across the block.  Only the zero-rule threshold uses the total.
 __global__ void __launch_bounds__(256) sum_part_kernel(const float* __restrict__ x, size_t n, double* __restrict__ part) {
   __shared__ double sh[257];
   const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const size_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-  double a = 0.0;
-  for (size_t i = b0 + threadIdx.x; i < b1; i += 256) a += (double)x[i];
-  const double tot = block_sum(a, sh);
+  float a = 0.f;
+#pragma unroll 8
+  for (size_t i = b0 + threadIdx.x; i < b1; i += 256) a += __ldg(&x[i]);
+  const double tot = block_sum((double)a, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
@@ -663,92 +686,92 @@ __global__ void combine_kernel(float2* __restrict__ A, const float2* __restrict_
   }
 }
 
-// max_k |o_m[k]| per slice into scal[S_MAXO + m]; the decomposition objective from its
-// partials into scal[S_DOBJ] (and obj_out).
-__global__ void __launch_bounds__(1024) slice_max_kernel(const float2* __restrict__ o, int M, int n2,
-                                                         const double* __restrict__ obj_part, int n_part,
-                                                         double* scal, double* obj_out) {
-  __shared__ float sh[1024];
-  const int t = threadIdx.x;
+// The proximal step (Eq. Prox_Min) before its normalisation.  Element e = l n2 + k of the
+// slices (a block: 32 elements of one slice; n2 is a multiple of 32):
+//   g_l[k]: slice 0 from g0, slices 1..M-1 summed in FP64 over the CTAs' partials in a fixed
+//           order (8 groups of CTAs, cta mod 8, then the groups in order);
+//   x = o_l[k] - mu_l lambda g_l[k] in FP64, mu_l = 1 / (lambda prod_{m != l} max|o_m|)^2,
+//       written over o_l[k];
+//   normpart[block] = sum of |x|^2 over the block's 32 elements (fixed order).
+// max|o_m| comes from the CTAs' maxima (every block reduces them alike).  Block 0 also sums the
+// decomposition objective into scal[S_DOBJ] (and obj_out).
+__global__ void __launch_bounds__(256) grad_step_kernel(float2* __restrict__ o, const float2* __restrict__ g0,
+                                                        const float2* __restrict__ gpart,
+                                                        const float* __restrict__ maxpart, int n_cta, int M, int n2,
+                                                        const double* __restrict__ lam_p,
+                                                        const double* __restrict__ obj_part,
+                                                        double* __restrict__ normpart, double* scal,
+                                                        double* obj_out) {
+  __shared__ double2 sh[8][32];
+  __shared__ double red[257];
+  __shared__ double maxo[kMaxSlices];
+  const int t = threadIdx.x, lane = t & 31, grp = t >> 5;
   for (int m = 0; m < M; ++m) {
     float a = 0.f;
-    for (int k = t; k < n2; k += 1024) {
-      const float2 v = o[(size_t)m * n2 + k];
-      a = fmaxf(a, fmaf(v.x, v.x, v.y * v.y));
-    }
-    sh[t] = a;
-    __syncthreads();
-    for (int s = 512; s > 0; s >>= 1) {
-      if (t < s) sh[t] = fmaxf(sh[t], sh[t + s]);
-      __syncthreads();
-    }
-    if (t == 0) scal[S_MAXO + m] = sqrt((double)sh[0]);
-    __syncthreads();
+    for (int c = t; c < n_cta; c += 256) a = fmaxf(a, maxpart[c * M + m]);
+    const double mx = block_sum<true>((double)a, red);
+    if (t == 0) maxo[m] = sqrt(mx);
   }
-  __shared__ double shd[1025];
-  double a = 0.0;
-  for (int i = t; i < n_part; i += 1024) a += obj_part[i];
-  const double s = block_sum(a, shd);
-  if (t == 0) {
-    scal[S_DOBJ] = s;
-    if (obj_out) obj_out[0] = s;
-  }
-}
-
-// g[0][k] = g0[k]; g[l][k] = sum over CTAs of gpart[cta][l-1][k] (l >= 1), FP64, in a fixed
-// order: 32 consecutive k per block, 8 groups of CTAs (cta mod 8), then the groups in order.
-__global__ void __launch_bounds__(256) grad_reduce_kernel(const float2* __restrict__ g0,
-                                                          const float2* __restrict__ gpart, int n_cta, int M,
-                                                          int n2, double2* __restrict__ g) {
-  __shared__ double2 sh[8][32];
-  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  const int e = blockIdx.x * 32 + lane;          // index into slices 1..M-1: (l - 1) * n2 + k
-  const int na = (M - 1) * n2;
+  const int l = (blockIdx.x * 32) / n2, k = blockIdx.x * 32 - l * n2 + lane;
+  const size_t na = (size_t)(M - 1) * n2;
   double re = 0.0, im = 0.0;
-  if (e < na)
+  if (l > 0)
+#pragma unroll 4
     for (int c = grp; c < n_cta; c += 8) {
-      const float2 v = gpart[(size_t)c * na + e];
+      const float2 v = gpart[(size_t)c * na + (size_t)(l - 1) * n2 + k];
       re += v.x;
       im += v.y;
     }
   sh[grp][lane] = make_double2(re, im);
   __syncthreads();
-  if (grp == 0 && e < na) {
-    double2 t = sh[0][lane];
-    for (int k = 1; k < 8; ++k) {
-      t.x += sh[k][lane].x;
-      t.y += sh[k][lane].y;
+  if (grp == 0) {
+    double2 g;
+    if (l == 0) {
+      g = make_double2(g0[k].x, g0[k].y);
+    } else {
+      g = sh[0][lane];
+      for (int q = 1; q < 8; ++q) {
+        g.x += sh[q][lane].x;
+        g.y += sh[q][lane].y;
+      }
     }
-    g[n2 + e] = t;
+    const double lam = lam_p[0];
+    double bound = fabs(lam);
+    for (int m = 0; m < M; ++m)
+      if (m != l) bound *= maxo[m];
+    const double cstep = (bound > 0.0 ? 1.0 / (bound * bound) : 0.0) * lam;
+    float2* p = o + (size_t)l * n2 + k;
+    const double xr = (double)p->x - cstep * g.x, xi = (double)p->y - cstep * g.y;
+    *p = make_float2((float)xr, (float)xi);
+    double ss = xr * xr + xi * xi;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
+    if (lane == 0) normpart[blockIdx.x] = ss;
   }
-  const int k = blockIdx.x * 256 + threadIdx.x;
-  if (k < n2) g[k] = make_double2(g0[k].x, g0[k].y);
+  if (blockIdx.x == 0) {
+    double a = 0.0;
+    for (int i = t; i < n_cta; i += 256) a += obj_part[i];
+    const double tot = block_sum(a, red);
+    if (t == 0) {
+      scal[S_DOBJ] = tot;
+      if (obj_out) obj_out[0] = tot;
+    }
+  }
 }
 
-// Proximal step of slice l = blockIdx.x (Eq. Prox_Min): x = o_l - mu_l lambda g_l with
-// mu_l = 1 / (lambda prod_{m != l} max|o_m|)^2, then o_l = x / ||x||_F.
-__global__ void __launch_bounds__(1024) prox_kernel(float2* o, const double2* __restrict__ g, const double* scal,
-                                                    const double* __restrict__ lam_p, int M, int n2) {
-  __shared__ double sh[1025];
-  const int l = blockIdx.x, t = threadIdx.x;
-  const double lam = lam_p[0];
-  double bound = fabs(lam);
-  for (int m = 0; m < M; ++m)
-    if (m != l) bound *= scal[S_MAXO + m];
-  const double mu = bound > 0.0 ? 1.0 / (bound * bound) : 0.0;
-  const double c = mu * lam;
-  float2* ol = o + (size_t)l * n2;
-  const double2* gl = g + (size_t)l * n2;
-  double ss = 0.0;
-  for (int k = t; k < n2; k += blockDim.x) {
-    const double xr = (double)ol[k].x - c * gl[k].x, xi = (double)ol[k].y - c * gl[k].y;
-    ss += xr * xr + xi * xi;
-  }
-  const double nrm2 = block_sum(ss, sh);
-  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 1.0;
-  for (int k = t; k < n2; k += blockDim.x) {
-    const double xr = (double)ol[k].x - c * gl[k].x, xi = (double)ol[k].y - c * gl[k].y;
-    ol[k] = make_float2((float)(xr * inv), (float)(xi * inv));
+// o_l = x_l / ||x_l||_F (Eq. Prox_Min) for slice l = blockIdx.y, ||x_l||^2 the fixed-order sum
+// of its blocks' partials.
+__global__ void __launch_bounds__(256) prox_kernel(float2* __restrict__ o, const double* __restrict__ normpart,
+                                                   int n2) {
+  __shared__ double red[257];
+  const int l = blockIdx.y, nb = n2 / 32;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) a += normpart[l * nb + i];
+  const double nrm2 = block_sum(a, red);
+  const float inv = nrm2 > 0.0 ? (float)(1.0 / sqrt(nrm2)) : 1.f;
+  for (int k = blockIdx.x * 256 + threadIdx.x; k < n2; k += gridDim.x * 256) {
+    float2* p = o + (size_t)l * n2 + k;
+    *p = make_float2(p->x * inv, p->y * inv);
   }
 }
 
@@ -968,7 +991,8 @@ struct Layout {
   float2* U = nullptr;       // splits2 * n2 * n2 (rank-S update partials)
   float2* g0 = nullptr;      // n2: slice-0 gradient, one value per column
   float2* gpart = nullptr;   // grid_grad * (M - 1) * n2
-  double2* gsum = nullptr;   // M * n2
+  float* maxpart = nullptr;  // grid_grad * M: per-CTA max |o_m|^2
+  double* normpart = nullptr;  // M * n2 / 32: per-block |x|^2 of the proximal step
   Split s1, s2;
   int grid_plain = 1, grid_grad = 1, grid_ff = 1;
   size_t bytes = 0;
@@ -1000,7 +1024,8 @@ static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, ch
   w.U = (float2*)take(w.s2.splits > 1 ? (size_t)w.s2.splits * n2 * n2 * sizeof(float2) : n2 * n2 * sizeof(float2));
   w.g0 = (float2*)take(n2 * sizeof(float2));
   w.gpart = (float2*)take((size_t)w.grid_grad * std::max<size_t>(M - 1, 1) * n2 * sizeof(float2));
-  w.gsum = (double2*)take(M * n2 * sizeof(double2));
+  w.maxpart = (float*)take((size_t)w.grid_grad * M * sizeof(float));
+  w.normpart = (double*)take(M * n2 / 32 * sizeof(double));
   w.bytes = off;
   return w;
 }
@@ -1065,10 +1090,10 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   const size_t n2 = (size_t)N * N, S = g->n_pos;
   const Layout& w = c.w;
   SMD_CK(cudaMemsetAsync(w.err, 0, sizeof(int), c.st));   // the call's own error word
-  const int blocks = (int)std::min<size_t>((n2 * S + 255) / 256, (size_t)c.dev.sms * 16);
-  probe_matrix_kernel<<<blocks, 256, 0, c.st>>>(probe, shifts, N, (int)S, w.P);
+  probe_matrix_kernel<<<dim3((unsigned)((n2 + 255) / 256), (unsigned)std::min<size_t>(S, 128)), 256, 0, c.st>>>(
+      probe, shifts, N, (int)S, w.P);
   SMD_LAUNCHED(1);
-  const int nsum = 256;
+  const int nsum = std::min(kPartSlots, 4 * c.dev.sms);
   sum_part_kernel<<<nsum, 256, 0, c.st>>>(I, n2 * S, w.part2);
   SMD_LAUNCHED(1);
   setup_kernel<N><<<1, threads_of(N), Kernels<N>::smem_plain(), c.st>>>(probe, w.part2, nsum, (double)(n2 * S), step,
@@ -1105,7 +1130,7 @@ static cudaError_t launch_grad_m(Call& c, const float2* A, const float2* o, cons
   if constexpr (M <= max_slices(N)) {
     const Layout& w = c.w;
     grad_kernel<N, M><<<w.grid_grad, threads_of(N), Kernels<N>::smem_grad(M), c.st>>>(A, o, w.gk, w.h, lam, w.g0,
-                                                                                      w.gpart, w.part);
+                                                                                      w.gpart, w.part, w.maxpart);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -1133,13 +1158,10 @@ static msp_status decompose_n(const msp_smd_geometry* g, Call& c, float2* A, flo
   SMD_TRY(launch_propagator(g, c));
   SMD_TRY(launch_grad<N>(M, c, A, o, lam));
   SMD_LAUNCHED(1);
-  slice_max_kernel<<<1, 1024, 0, c.st>>>(o, M, (int)n2, w.part, w.grid_grad, w.scal, obj_out);
+  grad_step_kernel<<<(int)(M * n2 / 32), 256, 0, c.st>>>(o, w.g0, w.gpart, w.maxpart, w.grid_grad, M, (int)n2, lam,
+                                                        w.part, w.normpart, w.scal, obj_out);
   SMD_LAUNCHED(1);
-  const int na = (int)((M - 1) * n2);
-  const int rgrid = std::max({(na + 31) / 32, (int)((n2 + 255) / 256), 1});
-  grad_reduce_kernel<<<rgrid, 256, 0, c.st>>>(w.g0, w.gpart, w.grid_grad, M, (int)n2, w.gsum);
-  SMD_LAUNCHED(1);
-  prox_kernel<<<M, 1024, 0, c.st>>>(o, w.gsum, w.scal, lam, M, (int)n2);
+  prox_kernel<<<dim3((unsigned)((n2 + 255) / 256), (unsigned)M), 256, 0, c.st>>>(o, w.normpart, (int)n2);
   SMD_LAUNCHED(1);
   SMD_TRY(launch_transfer<N>(g, c, A, o, 1.f, true));
   lambda_kernel<<<1, 256, 0, c.st>>>(w.part, w.part2, w.grid_plain, lam);
