@@ -16,40 +16,42 @@ namespace msp {
 // op(B) = B (K x N column-major) or, with B_CONJ_T, B^H for B stored N x K column-major.
 // C: M x N column-major, partial z at C + z * c_stride.
 //
-// One CTA computes a 128 x 64 complex tile.  The complex product is the real product
-//   D (128 x 128) = A_re B_re^T,  A_re = [Ar, Ai],  B_re rows n: [Br, -Bi], rows 64 + n: [Bi, Br]
-// so columns n of D hold Re C and columns 64 + n hold Im C.  Every real operand x is split
-// into tf32 parts x = big + small and D accumulates big*big + big*small + small*big, which
-// keeps the product error near FP32's.  The tensor core's FP32 accumulation does not round
-// to nearest, so D accumulates over groups of GROUP K-tiles only, alternating between two
-// TMEM halves; each finished group is added into FP32 registers.
+// One CTA computes a 128 x 128 complex tile.  The complex product is the real product
+//   D (128 x 256) = A_re B_re^T,  A_re = [Ar, Ai],  B_re rows n: [Br, -Bi], rows 128 + n: [Bi, Br]
+// so columns n of D hold Re C and columns 128 + n hold Im C: one M = 128, N = 256 MMA per
+// 8 real K, the widest tcgen05 shape of one SM.  Every real operand x is split into tf32
+// parts x = big + small and D accumulates big*big + big*small + small*big, which keeps the
+// product error near FP32's.  The tensor core's FP32 accumulation does not round to
+// nearest, so D accumulates over groups of GROUP K-tiles only; after each group the
+// producers add D into FP32 registers (128 per thread) and release it (`dfree` mbarrier)
+// before the next group overwrites it.
 //
-// Warps 0..7 are producers: they copy the raw complex K-tiles of A and B into shared memory
-// with cp.async, RAW - 1 tiles ahead of the one they convert, so that no register waits on a
-// global load.  They split each tile and write A_re into tensor memory (row m in lane m, its
-// real K in consecutive columns; tcgen05.st) and B_re in the canonical no-swizzle K-major
-// layout into shared memory: a 3-stage ring (`full` mbarriers, one arrival per producer
-// thread).  A read from tensor memory costs no shared-memory bandwidth, which the MMAs'
-// B reads and the producers' stores share.  Warp 8 allocates
-// TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's `empty`
-// mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded (by
-// `wait_limit` polls): on timeout the CTA raises *err = 2 and stops; the MMA thread still
-// waits, bounded, for the MMAs it issued before the TMEM is freed.
+// Warps 0..7 are producers.  They copy the raw complex K-tiles of A and B into shared
+// memory with cp.async, one tile ahead of the one they convert, so that no register waits
+// on a global load.  They split each tile and write A_re into tensor memory (row m in lane
+// m, its real K in consecutive columns; tcgen05.st) and B_re in the canonical no-swizzle
+// K-major layout into shared memory: a 2-stage ring (`full` mbarriers, one arrival per
+// producer thread).  A read from tensor memory costs no shared-memory bandwidth.  Warp 8
+// allocates TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's
+// `empty` mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded
+// (by `wait_limit` polls): on timeout the CTA raises *err = 2 and stops; the MMA thread
+// still waits, bounded, for the MMAs it issued before the TMEM is freed.
 namespace gemm {
-constexpr int TM = 128, TN = 64, TK = 16;                   // complex tile and K-tile
+constexpr int TM = 128, TN = 128, TK = 16;                  // complex tile and K-tile
 constexpr int KR = 2 * TK;                                  // real K per tile
-constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 16 KB
-constexpr uint32_t STAGE_BYTES = 2 * B_BYTES;               // 32 KB of shared memory
-constexpr int STAGES = 3;
+constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 32 KB
+constexpr uint32_t STAGE_BYTES = 2 * B_BYTES;               // 64 KB of shared memory
+constexpr int STAGES = 2;
 constexpr int GROUP = 8;
 constexpr int NPROD = 256;
 constexpr int NTHREADS = NPROD + 32;
-constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of one accumulator
-constexpr uint32_t ACOL = 2 * DCOLS;                        // first TMEM column of the A stages
-constexpr uint32_t TMEM_COLS = 512;                         // two accumulators + STAGES x (big, small) A
+constexpr int CPT = TN / 2;                                 // complex columns of C per producer thread
+constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of the accumulator
+constexpr uint32_t ACOL = DCOLS;                            // first TMEM column of the A stages
+constexpr uint32_t TMEM_COLS = 512;                         // accumulator + STAGES x (big, small) A
 static_assert(ACOL + STAGES * 2 * KR <= TMEM_COLS, "tensor memory of one CTA");
 // raw complex K-tiles as they come from global memory: RAW slots, RAW - 1 tiles in flight
-constexpr int RAW = 5;
+constexpr int RAW = 2;
 constexpr int RB_LD = TK + 2;                               // padded row of a raw B tile [j][k]
 constexpr uint32_t RAW_A_BYTES = TK * TM * 8;               // [k][i] float2: 16 KB
 constexpr uint32_t RAW_B_BYTES = (TN * RB_LD > TK * TN ? TN * RB_LD : TK * TN) * 8;
@@ -148,21 +150,20 @@ __device__ __forceinline__ void copy_wait_all() { asm volatile("cp.async.wait_gr
 // barrier of the NPROD producer threads only (the MMA warp never joins it)
 __device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory"); }
 
-// Adds accumulator half h into this thread's registers: TMEM lane (row) 32 (warp & 3) + lane,
-// columns 32 (warp >> 2) + q (Re) and TN + 32 (warp >> 2) + q (Im), q < 32.
-__device__ __forceinline__ void flush(uint32_t tmem, int h, int warp, float (&re)[32], float (&im)[32]) {
-  const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(h * DCOLS + 32 * (warp >> 2));
-  uint32_t r[16];
+// Adds the accumulator into this thread's registers: TMEM lane (row) 32 (warp & 3) + lane,
+// columns CPT (warp >> 2) + q (Re) and TN + CPT (warp >> 2) + q (Im), q < CPT.
+__device__ __forceinline__ void flush(uint32_t tmem, int warp, float (&re)[CPT], float (&im)[CPT]) {
+  const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(CPT * (warp >> 2));
 #pragma unroll
-  for (int part = 0; part < 4; ++part) {
-    tc::tmem_ld16(base + (part < 2 ? 16 * part : TN + 16 * (part - 2)), r);
+  for (int part = 0; part < CPT / 16; ++part) {
+    uint32_t r[16], u[16];
+    tc::tmem_ld16(base + 16 * part, r);
+    tc::tmem_ld16(base + TN + 16 * part, u);
     tc::tmem_wait_ld();
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      if (part < 2)
-        re[16 * part + q] += __uint_as_float(r[q]);
-      else
-        im[16 * (part - 2) + q] += __uint_as_float(r[q]);
+      re[16 * part + q] += __uint_as_float(r[q]);
+      im[16 * part + q] += __uint_as_float(u[q]);
     }
   }
 }
@@ -183,7 +184,8 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
   uint8_t* raw = smem + STAGES * STAGE_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(raw + RAW * RAW_BYTES);
   uint64_t* empty = full + STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + STAGES);
+  uint64_t* dfree = empty + STAGES;   // the producers have read the accumulator out
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(dfree + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int t = threadIdx.x, warp = t >> 5;
   const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       tc::mbar_init(&full[s], NPROD);
       tc::mbar_init(&empty[s], 1);
     }
+    tc::mbar_init(dfree, NPROD);
     tc::fence_mbar_init();
     *abort_flag = 0;
   }
@@ -211,19 +214,22 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       int last = -1;   // last tile whose MMAs were committed
       for (int it = 0; it < ntiles; ++it) {
         const int s = it % STAGES;
+        // a new group overwrites the accumulator: wait until the last one has been read out
+        if (it >= GROUP && it % GROUP == 0 &&
+            !wait_or_abort(dfree, ((it / GROUP) - 1) & 1, abort_flag, wait_limit))
+          break;
         if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag, wait_limit)) break;
         tc::fence_after();
         const uint32_t bb = tc::smem_u32(smem + s * STAGE_BYTES), bs = bb + B_BYTES;
         const uint32_t ab = tmem + ACOL + (uint32_t)(s * 2 * KR), as = ab + KR;   // A big, small
-        const uint32_t dcol = tmem + (uint32_t)(((it / GROUP) & 1) * DCOLS);
 #pragma unroll
         for (int kk = 0; kk < KR / 8; ++kk) {   // K = 8 tf32 (two core matrices) per MMA
           const uint32_t koff = kk * 256;
           const uint64_t dbb = tc::smem_desc(bb + koff, 128, (KR / 4) * 128);
           const uint64_t dbs = tc::smem_desc(bs + koff, 128, (KR / 4) * 128);
-          tc::mma_tf32_ta(dcol, ab + 8 * kk, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_tf32_ta(dcol, ab + 8 * kk, dbs, idesc, 1u);
-          tc::mma_tf32_ta(dcol, as + 8 * kk, dbb, idesc, 1u);
+          tc::mma_tf32_ta(tmem, ab + 8 * kk, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
+          tc::mma_tf32_ta(tmem, ab + 8 * kk, dbs, idesc, 1u);
+          tc::mma_tf32_ta(tmem, as + 8 * kk, dbb, idesc, 1u);
         }
         tc::commit(&empty[s]);
         last = it;
@@ -232,26 +238,26 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
       if (last >= 0 && !drain_wait(&empty[last % STAGES], (last / STAGES) & 1)) *abort_flag = 1;
     }
   } else {
-    float re[32], im[32];
+    float re[CPT], im[CPT];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) re[q] = im[q] = 0.f;
+    for (int q = 0; q < CPT; ++q) re[q] = im[q] = 0.f;
     int flushed = 0;
     const int am = t & 127, aq = t >> 7;   // A: row am, complex K 8 aq .. 8 aq + 7 of the tile
-    const int bn = t & 63, bq = t >> 6;    // B: column bn, complex K 4 bq .. 4 bq + 3
+    const int bn = t & 127, bq = t >> 7;   // B: column bn, complex K 8 bq .. 8 bq + 7
     // 16-byte copies need 16-byte aligned rows and even offsets of every copied pair
     const bool vec16 = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0 &&
                        (lda & 1) == 0 && (ldb & 1) == 0 && (kb & 1) == 0;
-    // copies: A row pair ia, ia + 1 at K rows ka + 4 u of each tile; B pairs u = 0, 1
+    // copies: A row pair ia, ia + 1 at K rows ka + 4 u of each tile; B four pairs u = 0..3
     const int ka = t >> 6, ia = i0 + 2 * (t & 63);
     const int na = max(0, min(2, M - ia));
     const float2* a_src = A + (na > 0 ? (size_t)(kb + ka) * lda + ia : 0);
     const uint32_t a_dst = (uint32_t)(ka * TM + 2 * (t & 63)) * 8;
-    // B^H: K rows kbk + 8 u, columns jb, jb + 1 (nb of them);  B: columns jb + 32 u, K pair kbk
-    const int kbk = B_CONJ_T ? (t >> 5) : 2 * (t & 7);
-    const int jb = B_CONJ_T ? j0 + 2 * (t & 31) : j0 + (t >> 3);
+    // B^H: K rows kbk + 4 u, columns jb, jb + 1 (nb of them);  B: columns jb + 32 u, K pair kbk
+    const int kbk = B_CONJ_T ? (t >> 6) : 2 * (t & 7);
+    const int jb = B_CONJ_T ? j0 + 2 * (t & 63) : j0 + (t >> 3);
     const int nb = B_CONJ_T ? max(0, min(2, N - jb)) : 0;
     const float2* b_src = B_CONJ_T ? B + (nb > 0 ? (size_t)(kb + kbk) * ldb + jb : 0) : B + (size_t)jb * ldb + kb + kbk;
-    const uint32_t b_dst = B_CONJ_T ? (uint32_t)(kbk * TN + 2 * (t & 31)) * 8 : (uint32_t)((t >> 3) * RB_LD + kbk) * 8;
+    const uint32_t b_dst = B_CONJ_T ? (uint32_t)(kbk * TN + 2 * (t & 63)) * 8 : (uint32_t)((t >> 3) * RB_LD + kbk) * 8;
     // starts the copies of K-tile it into raw slot it % RAW (one commit group, empty past the end)
     auto issue = [&](int it) {
       if (it < ntiles) {
@@ -265,10 +271,10 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
                     vec16);
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
           if (B_CONJ_T) {
-            const int n = k0 + kbk + 8 * u < ke ? nb : 0;
-            copy_pair(rb + b_dst + u * 8 * TN * 8, n > 0 ? b_src + (size_t)(it * TK + 8 * u) * ldb : B, B, 8 * n,
+            const int n = k0 + kbk + 4 * u < ke ? nb : 0;
+            copy_pair(rb + b_dst + u * 4 * TN * 8, n > 0 ? b_src + (size_t)(it * TK + 4 * u) * ldb : B, B, 8 * n,
                       vec16);
           } else {
             const int n = jb + 32 * u < N ? max(0, min(2, ke - (k0 + kbk))) : 0;
@@ -294,52 +300,65 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         ok = warp_wait(&empty[s], ((it / STAGES) - 1) & 1, abort_flag, wait_limit);
         if (!ok) continue;
         tc::fence_after();
-        // every group whose last tile is it - STAGES or earlier is complete: fold it in
-        const int done_groups = (it - STAGES + 1) / GROUP;
-        while (flushed < done_groups) {
-          flush(tmem, flushed & 1, warp, re, im);
-          ++flushed;
-        }
       }
       const float2* ra = reinterpret_cast<const float2*>(raw + (it % RAW) * RAW_BYTES);
       const float2* rb = reinterpret_cast<const float2*>(raw + (it % RAW) * RAW_BYTES + RAW_A_BYTES);
-      float2 a[8], b[4];
+      {
+        float2 a[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) a[q] = ra[(8 * aq + q) * TM + am];
-      if (B_CONJ_T) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 v = rb[(4 * bq + q) * TN + bn];
-          b[q] = make_float2(v.x, -v.y);
-        }
-      } else {
-        const float4 v0 = *reinterpret_cast<const float4*>(rb + bn * RB_LD + 4 * bq);
-        const float4 v1 = *reinterpret_cast<const float4*>(rb + bn * RB_LD + 4 * bq + 2);
-        b[0] = make_float2(v0.x, v0.y);
-        b[1] = make_float2(v0.z, v0.w);
-        b[2] = make_float2(v1.x, v1.y);
-        b[3] = make_float2(v1.z, v1.w);
+        for (int q = 0; q < 8; ++q) a[q] = ra[(8 * aq + q) * TM + am];
+        const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
+        const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
+        // row am of A_re = [Ar, Ai]: this warp's TMEM lanes are 32 (warp & 3) .. + 31
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + ACOL + (uint32_t)(s * 2 * KR);
+        tc::tmem_st8(ta + 8 * aq, r0.big, r1.big);
+        tc::tmem_st8(ta + TK + 8 * aq, m0.big, m1.big);
+        tc::tmem_st8(ta + KR + 8 * aq, r0.small, r1.small);
+        tc::tmem_st8(ta + KR + TK + 8 * aq, m0.small, m1.small);
       }
       uint8_t* Bb = smem + s * STAGE_BYTES;
       uint8_t* Bs = Bb + B_BYTES;
-      const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
-      const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
-      // row am of A_re = [Ar, Ai]: this warp's TMEM lanes are 32 (warp & 3) .. + 31
-      const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + ACOL + (uint32_t)(s * 2 * KR);
-      tc::tmem_st8(ta + 8 * aq, r0.big, r1.big);
-      tc::tmem_st8(ta + TK + 8 * aq, m0.big, m1.big);
-      tc::tmem_st8(ta + KR + 8 * aq, r0.small, r1.small);
-      tc::tmem_st8(ta + KR + TK + 8 * aq, m0.small, m1.small);
-      const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
-      const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
-      put(Bb, Bs, kmaj(bn, 4 * bq), br);              // row n:      Br
-      put(Bb, Bs, kmaj(bn, TK + 4 * bq), neg(bi));    //             -Bi
-      put(Bb, Bs, kmaj(TN + bn, 4 * bq), bi);         // row TN + n: Bi
-      put(Bb, Bs, kmaj(TN + bn, TK + 4 * bq), br);    //             Br
+#pragma unroll
+      for (int hq = 0; hq < 2; ++hq) {   // complex K 8 bq + 4 hq .. + 3
+        float2 b[4];
+        if (B_CONJ_T) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = rb[(8 * bq + 4 * hq + q) * TN + bn];
+            b[q] = make_float2(v.x, -v.y);
+          }
+        } else {
+          const float4 v0 = *reinterpret_cast<const float4*>(rb + bn * RB_LD + 8 * bq + 4 * hq);
+          const float4 v1 = *reinterpret_cast<const float4*>(rb + bn * RB_LD + 8 * bq + 4 * hq + 2);
+          b[0] = make_float2(v0.x, v0.y);
+          b[1] = make_float2(v0.z, v0.w);
+          b[2] = make_float2(v1.x, v1.y);
+          b[3] = make_float2(v1.z, v1.w);
+        }
+        const int k4 = 8 * bq + 4 * hq;
+        const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
+        const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
+        put(Bb, Bs, kmaj(bn, k4), br);              // row n:      Br
+        put(Bb, Bs, kmaj(bn, TK + k4), neg(bi));    //             -Bi
+        put(Bb, Bs, kmaj(TN + bn, k4), bi);         // row TN + n: Bi
+        put(Bb, Bs, kmaj(TN + bn, TK + k4), br);    //             Br
+      }
       tc::tmem_wait_st();
       tc::fence_proxy_async();
       tc::fence_before();
       tc::mbar_arrive(&full[s]);
+      // tile it opens a new group: once the MMAs of the last group are done (the commit of
+      // tile it - 1), fold the accumulator in and hand it back to the MMAs of tile it
+      if (it >= GROUP && it % GROUP == 0) {
+        const int lt = it - 1;
+        ok = warp_wait(&empty[lt % STAGES], (lt / STAGES) & 1, abort_flag, wait_limit);
+        if (!ok) continue;
+        tc::fence_after();
+        flush(tmem, warp, re, im);
+        tc::fence_before();
+        tc::mbar_arrive(dfree);
+        ++flushed;
+      }
     }
     copy_wait_all();   // no copy may still be writing shared memory when the CTA ends
     // the last tile's commit covers every MMA of the CTA
@@ -348,7 +367,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     if (ok) {
       const int groups = (ntiles + GROUP - 1) / GROUP;
       while (flushed < groups) {
-        flush(tmem, flushed & 1, warp, re, im);
+        flush(tmem, warp, re, im);
         ++flushed;
       }
     }
@@ -356,8 +375,8 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     float2* Cz = C + (size_t)blockIdx.z * c_stride;
     if (i < M) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        const int j = j0 + 32 * (warp >> 2) + q;
+      for (int q = 0; q < CPT; ++q) {
+        const int j = j0 + CPT * (warp >> 2) + q;
         if (j < N) {
           const size_t e = STORE_T ? ((size_t)(j / ldc) * ldc + i) * ldc + (size_t)(j % ldc) : (size_t)j * ldc + i;
           Cz[e] = make_float2(re[q], im[q]);
