@@ -16,10 +16,11 @@ namespace msp {
 // op(B) = B (K x N column-major) or, with B_CONJ_T, B^H for B stored N x K column-major.
 // C: M x N column-major, partial z at C + z * c_stride.
 //
-// One CTA computes a 128 x 128 complex tile.  The complex product is the real product
-//   D (128 x 256) = A_re B_re^T,  A_re = [Ar, Ai],  B_re rows n: [Br, -Bi], rows 128 + n: [Bi, Br]
-// so columns n of D hold Re C and columns 128 + n hold Im C: one M = 128, N = 256 MMA per
-// 8 real K, the widest tcgen05 shape of one SM.  Every real operand x is split into tf32
+// One CTA computes a 128 x 128 complex tile as two real products sharing one B operand,
+//   Re C = [Ar, -Ai] B'^T,  Im C = [Ai, Ar] B'^T,  B' rows n: [Br, Bi],
+// each an M = 128, N = 128 MMA per 8 real K into its own TMEM accumulator (columns 0..127 Re,
+// 128..255 Im).  Both A operands are windows of one TMEM layout per row, [Ai | Ar | -Ai], so B
+// is split and stored once, without duplicates.  Every real operand x is split into tf32
 // parts x = big + small and D accumulates big*big + big*small + small*big, which keeps the
 // product error near FP32's.  The tensor core's FP32 accumulation does not round to
 // nearest, so D accumulates over groups of GROUP K-tiles only; after each group the
@@ -29,7 +30,7 @@ namespace msp {
 // Warps 0..7 are producers.  They copy the raw complex K-tiles of A and B into shared
 // memory with cp.async, one tile ahead of the one they convert, so that no register waits
 // on a global load.  They split each tile and write A_re into tensor memory (row m in lane
-// m, its real K in consecutive columns; tcgen05.st) and B_re in the canonical no-swizzle
+// m, its real K in consecutive columns; tcgen05.st) and B' in the canonical no-swizzle
 // K-major layout into shared memory: a 2-stage ring (`full` mbarriers, one arrival per
 // producer thread).  A read from tensor memory costs no shared-memory bandwidth.  Warp 8
 // allocates TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's
@@ -39,17 +40,18 @@ namespace msp {
 namespace gemm {
 constexpr int TM = 128, TN = 128, TK = 16;                  // complex tile and K-tile
 constexpr int KR = 2 * TK;                                  // real K per tile
-constexpr uint32_t B_BYTES = 2 * TN * KR * 4;               // one tf32 part of B_re: 32 KB
-constexpr uint32_t STAGE_BYTES = 2 * B_BYTES;               // 64 KB of shared memory
+constexpr uint32_t B_BYTES = TN * KR * 4;                   // one tf32 part of B': 16 KB
+constexpr uint32_t STAGE_BYTES = 2 * B_BYTES;               // 32 KB of shared memory
 constexpr int STAGES = 2;
 constexpr int GROUP = 8;
 constexpr int NPROD = 256;
 constexpr int NTHREADS = NPROD + 32;
 constexpr int CPT = TN / 2;                                 // complex columns of C per producer thread
-constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of the accumulator
+constexpr uint32_t DCOLS = 2 * TN;                          // f32 columns of the accumulators (Re, Im)
 constexpr uint32_t ACOL = DCOLS;                            // first TMEM column of the A stages
-constexpr uint32_t TMEM_COLS = 512;                         // accumulator + STAGES x (big, small) A
-static_assert(ACOL + STAGES * 2 * KR <= TMEM_COLS, "tensor memory of one CTA");
+constexpr uint32_t APART = 3 * TK;                          // columns of one tf32 part: [Ai | Ar | -Ai]
+constexpr uint32_t TMEM_COLS = 512;                         // accumulators + STAGES x (big, small) A
+static_assert(ACOL + STAGES * 2 * APART <= TMEM_COLS, "tensor memory of one CTA");
 // raw complex K-tiles as they come from global memory: RAW slots, RAW - 1 tiles in flight
 constexpr int RAW = 2;
 constexpr int RB_LD = TK + 2;                               // padded row of a raw B tile [j][k]
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
 
   if (warp == 8) {
     if ((t & 31) == 0) {   // MMA issuer
-      constexpr uint32_t idesc = tc::idesc_tf32(128, 2 * TN);
+      constexpr uint32_t idesc = tc::idesc_tf32(128, TN);
       int last = -1;   // last tile whose MMAs were committed
       for (int it = 0; it < ntiles; ++it) {
         const int s = it % STAGES;
@@ -221,15 +223,21 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         if (!wait_or_abort(&full[s], (it / STAGES) & 1, abort_flag, wait_limit)) break;
         tc::fence_after();
         const uint32_t bb = tc::smem_u32(smem + s * STAGE_BYTES), bs = bb + B_BYTES;
-        const uint32_t ab = tmem + ACOL + (uint32_t)(s * 2 * KR), as = ab + KR;   // A big, small
+        // A big and small parts, each [Ai | Ar | -Ai]: Re uses columns TK.., Im columns 0..
+        const uint32_t ab = tmem + ACOL + (uint32_t)(s * 2 * APART), as = ab + APART;
+        const uint32_t dre = tmem, dim = tmem + TN;
 #pragma unroll
         for (int kk = 0; kk < KR / 8; ++kk) {   // K = 8 tf32 (two core matrices) per MMA
           const uint32_t koff = kk * 256;
           const uint64_t dbb = tc::smem_desc(bb + koff, 128, (KR / 4) * 128);
           const uint64_t dbs = tc::smem_desc(bs + koff, 128, (KR / 4) * 128);
-          tc::mma_tf32_ta(tmem, ab + 8 * kk, dbb, idesc, (it % GROUP > 0 || kk > 0) ? 1u : 0u);
-          tc::mma_tf32_ta(tmem, ab + 8 * kk, dbs, idesc, 1u);
-          tc::mma_tf32_ta(tmem, as + 8 * kk, dbb, idesc, 1u);
+          const uint32_t acc = (it % GROUP > 0 || kk > 0) ? 1u : 0u;
+          tc::mma_tf32_ta(dre, ab + TK + 8 * kk, dbb, idesc, acc);
+          tc::mma_tf32_ta(dre, ab + TK + 8 * kk, dbs, idesc, 1u);
+          tc::mma_tf32_ta(dre, as + TK + 8 * kk, dbb, idesc, 1u);
+          tc::mma_tf32_ta(dim, ab + 8 * kk, dbb, idesc, acc);
+          tc::mma_tf32_ta(dim, ab + 8 * kk, dbs, idesc, 1u);
+          tc::mma_tf32_ta(dim, as + 8 * kk, dbb, idesc, 1u);
         }
         tc::commit(&empty[s]);
         last = it;
@@ -309,12 +317,15 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         for (int q = 0; q < 8; ++q) a[q] = ra[(8 * aq + q) * TM + am];
         const Split4 r0 = split4(a[0].x, a[1].x, a[2].x, a[3].x), r1 = split4(a[4].x, a[5].x, a[6].x, a[7].x);
         const Split4 m0 = split4(a[0].y, a[1].y, a[2].y, a[3].y), m1 = split4(a[4].y, a[5].y, a[6].y, a[7].y);
-        // row am of A_re = [Ar, Ai]: this warp's TMEM lanes are 32 (warp & 3) .. + 31
-        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + ACOL + (uint32_t)(s * 2 * KR);
-        tc::tmem_st8(ta + 8 * aq, r0.big, r1.big);
-        tc::tmem_st8(ta + TK + 8 * aq, m0.big, m1.big);
-        tc::tmem_st8(ta + KR + 8 * aq, r0.small, r1.small);
-        tc::tmem_st8(ta + KR + TK + 8 * aq, m0.small, m1.small);
+        // row am, [Ai | Ar | -Ai] per part: this warp's TMEM lanes are 32 (warp & 3) .. + 31
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + ACOL + (uint32_t)(s * 2 * APART);
+        const Split4 n0 = neg(m0), n1 = neg(m1);
+        tc::tmem_st8(ta + 8 * aq, m0.big, m1.big);
+        tc::tmem_st8(ta + TK + 8 * aq, r0.big, r1.big);
+        tc::tmem_st8(ta + 2 * TK + 8 * aq, n0.big, n1.big);
+        tc::tmem_st8(ta + APART + 8 * aq, m0.small, m1.small);
+        tc::tmem_st8(ta + APART + TK + 8 * aq, r0.small, r1.small);
+        tc::tmem_st8(ta + APART + 2 * TK + 8 * aq, n0.small, n1.small);
       }
       uint8_t* Bb = smem + s * STAGE_BYTES;
       uint8_t* Bs = Bb + B_BYTES;
@@ -336,12 +347,8 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
           b[3] = make_float2(v1.z, v1.w);
         }
         const int k4 = 8 * bq + 4 * hq;
-        const Split4 br = split4(b[0].x, b[1].x, b[2].x, b[3].x);
-        const Split4 bi = split4(b[0].y, b[1].y, b[2].y, b[3].y);
-        put(Bb, Bs, kmaj(bn, k4), br);              // row n:      Br
-        put(Bb, Bs, kmaj(bn, TK + k4), neg(bi));    //             -Bi
-        put(Bb, Bs, kmaj(TN + bn, k4), bi);         // row TN + n: Bi
-        put(Bb, Bs, kmaj(TN + bn, TK + k4), br);    //             Br
+        put(Bb, Bs, kmaj(bn, k4), split4(b[0].x, b[1].x, b[2].x, b[3].x));        // row n: Br
+        put(Bb, Bs, kmaj(bn, TK + k4), split4(b[0].y, b[1].y, b[2].y, b[3].y));   //        Bi
       }
       tc::tmem_wait_st();
       tc::fence_proxy_async();
