@@ -11,9 +11,10 @@
  * of 128 K), whose epilogue stores every image transposed, so the second pass transforms
  * the columns and the result comes back in row-major order.
  *
- * Supported: W in {32, 64, 128, 256}, 1 <= S and S W <= 4,194,240.  Device pointers,
- * 16-byte aligned, in and out may alias; the caller's workspace (256-byte aligned,
- * msp_dft2_tc_workspace_bytes) holds F and the intermediate.  Asynchronous on `stream`;
+ * Supported: W in {32, 64, 128, 256}, 1 <= S and S W <= 8,388,480 (65535 column tiles
+ * of 128).  Device pointers, 16-byte aligned, in and out may alias; the caller's
+ * workspace (256-byte aligned, msp_dft2_tc_workspace_bytes) holds F and the
+ * intermediate.  Asynchronous on `stream`;
  * a tensor-core wait that runs out raises the workspace flag (msp_check_workspace:
  * MSP_ETIMEOUT).
  */

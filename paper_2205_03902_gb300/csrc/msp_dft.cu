@@ -73,7 +73,7 @@ size_t msp_dft2_tc_workspace_bytes(int32_t W, int32_t S) {
 msp_status msp_dft2_tc(int32_t W, int32_t S, int32_t inverse, const float* in, float* out, void* ws, size_t ws_bytes,
                        void* stream) {
   set_last_error(MSP_OK, "");
-  if (!supported(W, S)) return fail(MSP_EUNSUPPORTED, "W must be 32, 64, 128 or 256 and 1 <= S, S W <= 4194240");
+  if (!supported(W, S)) return fail(MSP_EUNSUPPORTED, "W must be 32, 64, 128 or 256 and 1 <= S, S W <= 8388480");
   if (!in || !out || ((uintptr_t)in | (uintptr_t)out) % 16) return fail(MSP_EINVAL, "in and out must be non-NULL and 16-byte aligned");
   if (!ws || (uintptr_t)ws % 256) return fail(MSP_EINVAL, "workspace must be non-NULL and 256-byte aligned");
   const Layout l = layout(W, S, (char*)ws);

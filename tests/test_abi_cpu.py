@@ -125,7 +125,7 @@ def test_smd_calls_reject_bad_geometry_before_touching_the_device(lib):
 
 
 @pytest.mark.parametrize("W,S,ok", [(32, 1, True), (64, 37, True), (128, 4096, True), (256, 3, True),
-                                    (48, 4, False), (512, 1, False), (128, 0, False), (128, 40000, False)])
+                                    (48, 4, False), (512, 1, False), (128, 0, False), (128, 70000, False)])
 def test_dft_workspace_sizes_and_host_validation(lib, W, S, ok):
     n = lib.msp_dft2_tc_workspace_bytes(W, S)
     if ok:
