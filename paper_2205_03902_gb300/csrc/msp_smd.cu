@@ -281,16 +281,22 @@ __global__ void __launch_bounds__(threads_of(N)) farfield_kernel(float2* BC, int
   double obj = 0.0;
   for (int s = blockIdx.x; s < S; s += gridDim.x) {
     float2 v[2][fac2(N)];
+    float4 acc[fac2(N)];   // the partials in split order, every split's loads in flight together
+#pragma unroll
+    for (int j = 0; j < fac2(N); ++j)
+      acc[j] = *reinterpret_cast<const float4*>(BC + (size_t)s * n2 + owned(N, r0, c0, 0, j));
+    for (int z = 1; z < splits; ++z) {
+      const float2* Bz = BC + z * split_stride + (size_t)s * n2;
+#pragma unroll
+      for (int j = 0; j < fac2(N); ++j) {
+        const float4 q = *reinterpret_cast<const float4*>(Bz + owned(N, r0, c0, 0, j));
+        acc[j].x += q.x; acc[j].y += q.y; acc[j].z += q.z; acc[j].w += q.w;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < fac2(N); ++j) {
-      const size_t e = (size_t)s * n2 + owned(N, r0, c0, 0, j);
-      float4 acc = *reinterpret_cast<const float4*>(BC + e);
-      for (int z = 1; z < splits; ++z) {
-        const float4 q = *reinterpret_cast<const float4*>(BC + z * split_stride + e);
-        acc.x += q.x; acc.y += q.y; acc.z += q.z; acc.w += q.w;
-      }
-      v[0][j] = make_float2(acc.x, acc.y);
-      v[1][j] = make_float2(acc.z, acc.w);
+      v[0][j] = make_float2(acc[j].x, acc[j].y);
+      v[1][j] = make_float2(acc[j].z, acc[j].w);
     }
     dft2<N>(v, X, Y, tw, false, r0, c0);
     float o = 0.f;
@@ -371,7 +377,7 @@ __device__ __forceinline__ void impulse_forward(float2 (&v)[2][fac2(N)], int col
 #pragma unroll
       for (int j = 0; j < fac2(N); ++j) {
         const int e = owned(N, r0, c0, i, j);
-        if (STASH) stash[(m - 1) * n2 + e] = v[i][j];
+        if (STASH) stash[(m - 1) * n2 + (i * fac2(N) + j) * threads_of(N) + threadIdx.x] = v[i][j];
         v[i][j] = cmul(v[i][j], __ldg(&o[(size_t)m * n2 + e]));
       }
   }
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
   float2* X = reinterpret_cast<float2*>(smem4);
   float2* Y = X + N * ld_of(N);
   float2* Wt = Y + N * ld_of(N);
-  float2* stash = Wt + tw_elems(N);                                      // [M-1][N^2], thread-owned pixels
+  float2* stash = Wt + tw_elems(N);   // [M-1][pixel slot (i, j)][thread]: each thread reads back its own
   double* red = reinterpret_cast<double*>(stash + (M - 1) * N * N);
   float2* red2 = reinterpret_cast<float2*>(red);
   constexpr int n2 = N * N;
@@ -450,7 +456,7 @@ __global__ void __launch_bounds__(threads_of(N)) grad_kernel(const float2* __res
 #pragma unroll
         for (int j = 0; j < fac2(N); ++j) {
           const int e = owned(N, r0, c0, i, j);
-          const float2 g = cmulc(v[i][j], stash[(l - 1) * n2 + e]);
+          const float2 g = cmulc(v[i][j], stash[(l - 1) * n2 + (i * fac2(N) + j) * threads_of(N) + threadIdx.x]);
           acc[l - 1][i][j].x += g.x;
           acc[l - 1][i][j].y += g.y;
           v[i][j] = cmulc(v[i][j], __ldg(&o[(size_t)l * n2 + e]));
