@@ -50,18 +50,15 @@ def fft_flops(S, L, W):
     return S * (4 * L - 2) * 5.0 * n * math.log2(n)
 
 
-KERNEL_SOURCES = ["paper_2205_03902_gb300/csrc/msp_position.cu", "paper_2205_03902_gb300/csrc/msp_fft.cuh",
-                  "paper_2205_03902_gb300/csrc/msp_kernels.cuh"]
-
-
-def measured_traffic():
-    """DRAM bytes per launch of the fused kernel from the committed ncu capture, or None if
-    the kernel's sources changed since the counters were taken."""
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from its committed ncu capture (profiles/traffic.json:
+    per kernel the counters, the workload, the command and a hash of the kernel's sources),
+    or None if those sources changed since the counters were taken."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
         h = hashlib.sha1()
-        for f in KERNEL_SOURCES:
+        for f in rec["sources"]:
             h.update(open(os.path.join(ROOT, f), "rb").read())
         return rec["dram_bytes_per_launch"] if rec.get("source_sha1") == h.hexdigest() else None
     except Exception:
@@ -440,7 +437,8 @@ def run_smd(args, rank, world, local_rank):
                    "l2": "flushed between timed steps (256 MiB write outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / tf32_peak, "traffic": None,
+                     "frac": achieved / tf32_peak,
+                     "traffic": measured_traffic("cgemm_kernel") if cfg is synth.SMD_GAAS else None,
                      "kernel": "cgemm_kernel (tcgen05 kind::tf32, 3 tf32 products per FP32 product; A P and C P^H)",
                      "kernel_ms": gemm_ms,
                      "complex_fp32_equivalent_tflops": (gemm_flops / 2) / (gemm_ms * 1e-3) / 1e12,
@@ -699,7 +697,7 @@ def run_msp(args, rank, world, local_rank):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x clock
     fused_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
     achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
-    traffic = measured_traffic() if cfg is synth.C2 else None
+    traffic = measured_traffic("position_kernel") if cfg is synth.C2 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
