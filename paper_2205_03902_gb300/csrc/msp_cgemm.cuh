@@ -29,8 +29,8 @@ namespace msp {
 //
 // Warps 0..7 are producers.  They copy the raw complex K-tiles of A and B into shared
 // memory with cp.async, one tile ahead of the one they convert, so that no register waits
-// on a global load.  They split each tile and write A_re into tensor memory (row m in lane
-// m, its real K in consecutive columns; tcgen05.st) and B' in the canonical no-swizzle
+// on a global load.  They split each tile and write [Ai | Ar | -Ai] into tensor memory (row m
+// in lane m, its K in consecutive columns; tcgen05.st) and B' in the canonical no-swizzle
 // K-major layout into shared memory: a 2-stage ring (`full` mbarriers, one arrival per
 // producer thread).  A read from tensor memory costs no shared-memory bandwidth.  Warp 8
 // allocates TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's
