@@ -724,6 +724,33 @@ def run_msp(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_peaks(args):
+    """The FP32 FFMA rate and the tcgen05 kind::tf32 MMA rate per shape, from the stand-alone
+    micro-benchmarks in csrc/msp_peaks.cu: the figures the kernels' fractions are read against."""
+    if args.impl == "reference" or int(os.environ.get("RANK", 0)) != 0:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the pipe micro-benchmarks have no reference arm"}))
+        return
+    from paper_2205_03902_gb300 import build as B
+    import subprocess
+    exe = B.build_peaks()
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    if r.returncode != 0:
+        raise SystemExit("msp_peaks failed: " + r.stdout + r.stderr)
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    res.update({"metric": "compute pipe peaks", "unit": "TFLOP/s", "n_gpus": 1,
+                "config": {"workload": "micro-benchmarks (FFMA: 8 CTAs x 256 threads per SM, 8 chains each; "
+                                       "tf32 MMA: one CTA per SM, one thread issuing 768 MMAs)"},
+                "nominal_fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+                "derived_tf32_tflops": float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25})
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -731,12 +758,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="c2", choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3"],
+    ap.add_argument("--config", default="c2",
+                    choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3", "peaks"],
                     help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration; "
-                         "smd_gaas: Algorithm 2 on the Table 1 setting)")
+                         "smd_gaas: Algorithm 2 on the Table 1 setting; peaks: FFMA and tcgen05 tf32 "
+                         "MMA micro-benchmarks)")
     args = ap.parse_args()
     global CFG
     smd = args.config in synth.SMD_CONFIGS
+    if args.config == "peaks":
+        run_peaks(args)
+        return
     if args.config == "dft_c3":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the DFT study has no reference arm; see --config c3"}))

@@ -68,6 +68,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+PEAKS_SRC = os.path.join(CSRC, "msp_peaks.cu")
+PEAKS_EXE = os.path.join(OBJDIR, "msp_peaks")
+
+
+def build_peaks() -> str:
+    """Compile the stand-alone pipe micro-benchmarks (csrc/msp_peaks.cu, not part of libmsp)
+    if stale; returns the executable's path."""
+    deps = [PEAKS_SRC, os.path.join(CSRC, "msp_tc.cuh"), __file__]
+    if os.path.exists(PEAKS_EXE) and all(os.path.getmtime(d) <= os.path.getmtime(PEAKS_EXE) for d in deps):
+        return PEAKS_EXE
+    os.makedirs(OBJDIR, exist_ok=True)
+    cmd = [nvcc(), "-std=c++17", "-O3", ARCH, "-lineinfo", PEAKS_SRC, "-o", PEAKS_EXE]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+    return PEAKS_EXE
+
+
 if __name__ == "__main__":
     import sys
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
