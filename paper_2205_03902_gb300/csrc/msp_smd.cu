@@ -606,23 +606,13 @@ __global__ void probe_matrix_kernel(const float2* __restrict__ probe, const int2
   }
 }
 
-// h[ky][kx] = exp(-i pi dz lambda (qy^2 + qx^2)) / N^2, in double, rounded once.
-__global__ void propagator_kernel(float2* __restrict__ h, int N, double dzlam, double dq) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * N) return;
-  const int ky = e / N, kx = e % N;
-  const double qy = (ky < N / 2 ? ky : ky - N) * dq, qx = (kx < N / 2 ? kx : kx - N) * dq;
-  double s, c;
-  sincospi(-dzlam * (qy * qy + qx * qx), &s, &c);
-  const double inv = 1.0 / ((double)N * N);
-  h[e] = make_float2((float)(c * inv), (float)(s * inv));
-}
-
-// gk = G e_0, the real-space kernel of the propagator: with h = h1(ky) h1(kx) separable,
-// gk[y][x] = g1(y) g1(x), g1(y) = (1/N) sum_k h1(k) exp(2 pi i k y / N); in double, rounded once.
-// g1[y], one block of one warp per y (the FP64 work spread over N SMs): lanes take
-// k = lane, lane + 32, then a butterfly sum.
-__global__ void __launch_bounds__(32) kernel_row_kernel(double2* __restrict__ g1, int N, double dzlam, double dq) {
+// The propagator h[ky][kx] = exp(-i pi dz lambda (qy^2 + qx^2)) / N^2 = h1(ky) h1(kx) / N^2 and
+// its real-space kernel gk = G e_0, gk[y][x] = g1(y) g1(x), g1(y) = (1/N) sum_k h1(k)
+// exp(2 pi i k y / N), are outer products of one-dimensional factors: this kernel forms g1[y]
+// and h1[y] in double (one block of one warp per y, spreading the FP64 work over N SMs: lanes
+// take k = lane, lane + 32, then a butterfly sum), `kernel_column_kernel` the products.
+__global__ void __launch_bounds__(32) kernel_row_kernel(double2* __restrict__ g1, double2* __restrict__ h1, int N,
+                                                        double dzlam, double dq) {
   const int y = blockIdx.x, lane = threadIdx.x;
   double re = 0.0, im = 0.0;
   for (int k = lane; k < N; k += 32) {
@@ -637,14 +627,25 @@ __global__ void __launch_bounds__(32) kernel_row_kernel(double2* __restrict__ g1
     re += __shfl_xor_sync(0xffffffffu, re, off);
     im += __shfl_xor_sync(0xffffffffu, im, off);
   }
-  if (lane == 0) g1[y] = make_double2(re / N, im / N);
+  if (lane == 0) {
+    g1[y] = make_double2(re / N, im / N);
+    const double q = (y < N / 2 ? y : y - N) * dq;
+    double s, c;
+    sincospi(-dzlam * q * q, &s, &c);
+    h1[y] = make_double2(c, s);
+  }
 }
 
-__global__ void kernel_column_kernel(float2* __restrict__ gk, const double2* __restrict__ g1, int N) {
+// gk[y][x] = g1(y) g1(x) and h[ky][kx] = h1(ky) h1(kx) / N^2, in double, each rounded once.
+__global__ void kernel_column_kernel(float2* __restrict__ gk, float2* __restrict__ h, const double2* __restrict__ g1,
+                                     const double2* __restrict__ h1, int N) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= N * N) return;
   const double2 a = g1[e / N], b = g1[e % N];
   gk[e] = make_float2((float)(a.x * b.x - a.y * b.y), (float)(a.x * b.y + a.y * b.x));
+  const double2 u = h1[e / N], v = h1[e % N];
+  const double inv = 1.0 / ((double)N * N);
+  h[e] = make_float2((float)((u.x * v.x - u.y * v.y) * inv), (float)((u.x * v.y + u.y * v.x) * inv));
 }
 
 // Block partial sums of a float array over fixed chunks: FP32 within a thread (a few dozen
@@ -991,7 +992,7 @@ struct Layout {
   double* part2 = nullptr;   // kPartSlots
   float2* h = nullptr;
   float2* gk = nullptr;      // G e_0
-  double2* g1 = nullptr;     // its separable factor, N values
+  double2* g1 = nullptr;     // its separable factor, N values; the propagator's, N values from g1 + 64
   float2* P = nullptr;
   float2* BC = nullptr;      // splits1 * n2 * S
   float2* U = nullptr;       // splits2 * n2 * n2 (rank-S update partials)
@@ -1024,7 +1025,7 @@ static Layout layout(const msp_smd_geometry* g, const Dev& d, const PerN& pn, ch
   w.part2 = (double*)take(kPartSlots * sizeof(double));
   w.h = (float2*)take(n2 * sizeof(float2));
   w.gk = (float2*)take(n2 * sizeof(float2));
-  w.g1 = (double2*)take(64 * sizeof(double2));
+  w.g1 = (double2*)take(128 * sizeof(double2));
   w.P = (float2*)take(n2 * S * sizeof(float2));
   w.BC = (float2*)take((size_t)w.s1.splits * n2 * S * sizeof(float2));
   w.U = (float2*)take(w.s2.splits > 1 ? (size_t)w.s2.splits * n2 * n2 * sizeof(float2) : n2 * n2 * sizeof(float2));
@@ -1066,12 +1067,10 @@ static msp_status begin(const msp_smd_geometry* g, void* ws, size_t ws_bytes, vo
 
 static msp_status launch_propagator(const msp_smd_geometry* g, Call& c) {
   const int N = g->n;
-  propagator_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.h, N, g->dz_A * g->wavelength_A,
-                                                           1.0 / ((double)N * g->pixel_A));
+  kernel_row_kernel<<<N, 32, 0, c.st>>>(c.w.g1, c.w.g1 + 64, N, g->dz_A * g->wavelength_A,
+                                        1.0 / ((double)N * g->pixel_A));
   SMD_LAUNCHED(1);
-  kernel_row_kernel<<<N, 32, 0, c.st>>>(c.w.g1, N, g->dz_A * g->wavelength_A, 1.0 / ((double)N * g->pixel_A));
-  SMD_LAUNCHED(1);
-  kernel_column_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.gk, c.w.g1, N);
+  kernel_column_kernel<<<(N * N + 255) / 256, 256, 0, c.st>>>(c.w.gk, c.w.h, c.w.g1, c.w.g1 + 64, N);
   SMD_LAUNCHED(1);
   return MSP_OK;
 }
