@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   constexpr int TX = kGatherTX, TY = kGatherTY;
   constexpr int U = 16;
   __shared__ int2 spos[256];
-  __shared__ int sidx[256];
+  // per listed position, the element offsets of window pixel (0, 0) moved to the object
+  // origin: window value (dy, dx) of object pixel (py, px) sits at base + py W + px
+  __shared__ long long sbase0[256], sbase1[256];
   __shared__ int wcount[8];
   __shared__ float wmax[8];
   const int tid = threadIdx.x;
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
   const int px = tx0 + (tid % TX), py = ty0 + (tid / TX);
   const size_t WW = (size_t)W * W;
+  const long long pix = (long long)py * W + px;   // this thread's pixel, window-row stride
   float2 acc0 = make_float2(0.f, 0.f);
   float acc1 = 0.f;
   for (int base = 0; base < S; base += 256) {
@@ -108,8 +111,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
     }
     if (ov) {
       const int q = off + __popc(mask & ((1u << lane) - 1u));
+      const long long sq = base + tid, shift = (long long)ps.x * W + ps.y;
       spos[q] = ps;
-      sidx[q] = base + tid;
+      sbase0[q] = (sq * nl_src + l) * (long long)WW - shift;
+      sbase1[q] = sq * (long long)WW - shift;
     }
     __syncthreads();
     for (int q0 = 0; q0 < total; q0 += U) {
@@ -118,15 +123,18 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int q = q0 + u;
-        const bool live = q < total;
-        const int2 pq = live ? spos[q] : make_int2(-(1 << 29), -(1 << 29));
-        const int sq = live ? sidx[q] : 0;
-        const int dx = px - pq.y, dy = py - pq.x;
-        const bool in = ((unsigned)dx < (unsigned)W) && ((unsigned)dy < (unsigned)W);
-        const size_t o = ((size_t)sq * nl_src + l) * WW + (size_t)dy * W + dx;
-        if (CPLX) v0[u] = in ? reinterpret_cast<const float2*>(src0)[o] : make_float2(0.f, 0.f);
-        else v0[u] = make_float2(in ? src0[o] : 0.f, 0.f);
-        if (ILLUM) v1[u] = in ? src1[(size_t)sq * WW + (size_t)dy * W + dx] : 0.f;
+        const bool live = q < total;   // the list has `total` entries; nothing past it is read
+        int2 pq = make_int2(-(1 << 29), -(1 << 29));
+        long long o0 = 0, o1 = 0;
+        if (live) {
+          pq = spos[q];
+          o0 = sbase0[q] + pix;
+          if (ILLUM) o1 = sbase1[q] + pix;
+        }
+        const bool in = ((unsigned)(px - pq.y) < (unsigned)W) && ((unsigned)(py - pq.x) < (unsigned)W);
+        if (CPLX) v0[u] = in ? reinterpret_cast<const float2*>(src0)[o0] : make_float2(0.f, 0.f);
+        else v0[u] = make_float2(in ? src0[o0] : 0.f, 0.f);
+        if (ILLUM) v1[u] = in ? src1[o1] : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
