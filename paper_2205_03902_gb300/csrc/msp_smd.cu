@@ -589,20 +589,30 @@ __global__ void __launch_bounds__(threads_of(N)) setup_kernel(const float2* __re
 
 // P[:, s] = vec of the probe shifted cyclically by shifts[s] (Sec. 2.1).
 // Grid: x over the pixels k of a column, y over the shifts s (each thread takes every
-// gridDim.y-th shift).
+// gridDim.y-th shift).  The block first reduces its shifts modulo N into shared memory.
+constexpr int kProbeShifts = 128;   // shifts per block at most: S <= 128 gridDim.y
 __global__ void probe_matrix_kernel(const float2* __restrict__ probe, const int2* __restrict__ shifts, int N, int S,
                                     float2* __restrict__ P) {
+  __shared__ int2 sh[kProbeShifts];
+  const int mine = (S - (int)blockIdx.y + (int)gridDim.y - 1) / (int)gridDim.y;   // shifts of this block
+  for (int i = threadIdx.x; i < mine; i += blockDim.x) {
+    const int2 v = shifts[blockIdx.y + i * gridDim.y];
+    int ys = v.x % N, xs = v.y % N;
+    if (ys < 0) ys += N;
+    if (xs < 0) xs += N;
+    sh[i] = make_int2(ys, xs);
+  }
+  __syncthreads();
   const int n2 = N * N, k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n2) return;
   const int y = k / N, x = k - y * N;
 #pragma unroll 4
-  for (int s = blockIdx.y; s < S; s += gridDim.y) {
-    const int2 sh = shifts[s];
-    const int ys = ((sh.x % N) + N) % N, xs = ((sh.y % N) + N) % N;
-    int yy = y - ys, xx = x - xs;
+  for (int i = 0; i < mine; ++i) {
+    const int2 v = sh[i];
+    int yy = y - v.x, xx = x - v.y;
     if (yy < 0) yy += N;
     if (xx < 0) xx += N;
-    P[(size_t)s * n2 + k] = __ldg(&probe[yy * N + xx]);
+    P[(size_t)(blockIdx.y + i * gridDim.y) * n2 + k] = __ldg(&probe[yy * N + xx]);
   }
 }
 
@@ -1095,7 +1105,9 @@ static msp_status matrix_step_n(const msp_smd_geometry* g, Call& c, float2* A, c
   const size_t n2 = (size_t)N * N, S = g->n_pos;
   const Layout& w = c.w;
   SMD_CK(cudaMemsetAsync(w.err, 0, sizeof(int), c.st));   // the call's own error word
-  probe_matrix_kernel<<<dim3((unsigned)((n2 + 255) / 256), (unsigned)std::min<size_t>(S, 128)), 256, 0, c.st>>>(
+  // every block takes at most kProbeShifts shifts: gridDim.y >= S / kProbeShifts
+  const unsigned gy = (unsigned)std::min<size_t>(S, std::max<size_t>(128, (S + kProbeShifts - 1) / kProbeShifts));
+  probe_matrix_kernel<<<dim3((unsigned)((n2 + 255) / 256), gy), 256, 0, c.st>>>(
       probe, shifts, N, (int)S, w.P);
   SMD_LAUNCHED(1);
   const int nsum = std::min(kPartSlots, 4 * c.dev.sms);
