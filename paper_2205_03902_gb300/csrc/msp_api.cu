@@ -192,28 +192,6 @@ __global__ void __launch_bounds__(1024) later_slices_gain_kernel(const float2* _
   if (tid == 0) out[0] = prod;
 }
 
-// out = tau^2 * sum |p|^2, the squared zero-rule threshold (a threshold needs no more
-// than single-precision partial sums; the total is formed in double, in a fixed order).
-__global__ void __launch_bounds__(1024) zero_threshold_kernel(const float2* __restrict__ probe, int WW, double tau2,
-                                                              double* __restrict__ out) {
-  __shared__ float wsum[32];
-  const int tid = threadIdx.x;
-  float a = 0.f;
-  for (int i = tid; i < WW; i += 1024) {
-    const float2 v = probe[i];
-    a = fmaf(v.x, v.x, fmaf(v.y, v.y, a));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  if ((tid & 31) == 0) wsum[tid >> 5] = a;
-  __syncthreads();
-  if (tid == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 32; ++i) t += (double)wsum[i];
-    out[0] = tau2 * t;
-  }
-}
-
 // Single-block FP64 reduction in a fixed order.  op 0: sum, 1: max.
 __global__ void __launch_bounds__(1024) reduce_kernel(const double* __restrict__ in, int n, int op,
                                                       double* __restrict__ out, double* __restrict__ out2) {
@@ -276,8 +254,8 @@ __global__ void __launch_bounds__(1024) prepare_kernel(const float2* __restrict_
                                                        const float* __restrict__ V, float2* __restrict__ T, size_t n,
                                                        float sigma) {
   if (blockIdx.x == 0) {
-    // the threshold's arithmetic of zero_threshold_kernel: FP32 partials per thread and warp,
-    // the 32 warp sums in FP64 (FP64 throughput is low; a threshold needs no more)
+    // the squared zero-rule threshold tau^2 sum |p|^2: FP32 partials per thread and warp, the
+    // 32 warp sums in FP64 in a fixed order (FP64 throughput is low; a threshold needs no more)
     __shared__ float wsum[32];
     const int tid = threadIdx.x;
     float a = 0.f;
