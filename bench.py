@@ -50,16 +50,16 @@ def fft_flops(S, L, W):
     return S * (4 * L - 2) * 5.0 * n * math.log2(n)
 
 
-def measured_traffic(kernel: str):
+def measured_traffic(kernel: str, root: str = ROOT):
     """DRAM bytes per launch of `kernel` from its committed ncu capture (profiles/traffic.json:
     per kernel the counters, the workload, the command and a hash of the kernel's sources),
     or None if those sources changed since the counters were taken."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))[kernel]
         h = hashlib.sha1()
         for f in rec["sources"]:
-            h.update(open(os.path.join(ROOT, f), "rb").read())
+            h.update(open(os.path.join(root, f), "rb").read())
         return rec["dram_bytes_per_launch"] if rec.get("source_sha1") == h.hexdigest() else None
     except Exception:
         return None

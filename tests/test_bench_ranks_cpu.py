@@ -39,3 +39,20 @@ def test_replica_timing_is_max_over_ranks_and_throughput_sums_ranks():
     # 10 steps in 120 ms -> 12 ms per step, 2 replicas of 4096 units each
     assert out[0][1] == pytest.approx(2 * 4096 / 0.012)
     assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_roofline_traffic_follows_the_kernel_sources(tmp_path):
+    """`roofline.traffic` comes from a recorded ncu capture only while the kernel's sources
+    hash to the recorded value; any edit makes it null (the counters no longer apply)."""
+    import hashlib
+    import json
+    src = tmp_path / "k.cu"
+    src.write_text("__global__ void k() {}\n")
+    (tmp_path / "profiles").mkdir()
+    rec = {"k": {"dram_bytes_per_launch": 123.0, "sources": ["k.cu"],
+                 "source_sha1": hashlib.sha1(src.read_bytes()).hexdigest()}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.measured_traffic("k", root=str(tmp_path)) == 123.0
+    assert bench.measured_traffic("other", root=str(tmp_path)) is None
+    src.write_text("__global__ void k() { }\n")
+    assert bench.measured_traffic("k", root=str(tmp_path)) is None
