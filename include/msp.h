@@ -22,8 +22,14 @@
  *   - Fresnel propagator h = exp(-i pi dz lambda (qy^2 + qx^2)), Eq. (fresnel_element)
  *     with zero tilt, q_k = k / (W pixel) for k < W/2 and (k - W) / (W pixel) otherwise.
  *     The slices are separated by dz; no propagation follows the last slice.
- *   - Loss: L = sum_s sum_k (sqrt(I_meas) - |Psi|)^2 (Sec. 3.2, no factor 1/2), with
- *     Psi/|Psi| taken as 0 where Psi == 0.
+ *   - Loss: L = sum_s sum_k (sqrt(I_meas) - |Psi|)^2 (Sec. 3.2, no factor 1/2).  The
+ *     gradient's residual is R = Psi - sqrt(I_meas) Psi/|Psi|, with the fraction Psi/|Psi|
+ *     taken as 0 (so R = Psi) where the far-field value counts as zero (Sec. 3.2 sets the
+ *     fraction to 0 where Qz = 0): where |Psi_k| <= 1e-5 ||p||_2, ||p||_2 being the probe's
+ *     L2 norm (by Parseval the RMS far-field amplitude of a pattern of pure-phase slices).
+ *     The threshold resolves "Psi = 0" above FP32 round-off and far below physical
+ *     amplitudes; a literal Psi == 0 test would let round-off choose the residual's phase
+ *     wherever the exact far field vanishes (outside the probe aperture at V = 0).
  *   - Complex arrays are interleaved float pairs (re, im), row-major.
  *
  * Memory and ownership
@@ -63,7 +69,10 @@ typedef enum {
   MSP_ENOMEM = 2,        /* reserved: the library never allocates */
   MSP_ECUDA = 3,         /* a CUDA launch or runtime call failed */
   MSP_EUNSUPPORTED = 4,  /* valid but not implemented here (window size, parametrisation) */
-  MSP_ETIMEOUT = 5       /* a bounded device-side wait ran out (msp_check_workspace) */
+  MSP_ETIMEOUT = 5,      /* a bounded device-side wait ran out (msp_check_workspace) */
+  MSP_EDEVICE = 6        /* a tensor-core kernel could not confirm that its own MMAs had finished
+                            before it released tensor memory: the device is no longer trusted
+                            (msp_check_workspace; every later call on that device returns this) */
 } msp_status;
 
 /* Slice parametrisation: real potentials (X_m = exp(i sigma V_m)) or complex
@@ -150,11 +159,18 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V,
  *   - potentials only (MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED);
  *   - window_error (device int32, may be NULL) is set to 0, or to 1 if a window lay
  *     outside the object (that position's pattern is then zero);
- *   - the first call on a device looks up the array's device address (with that
- *     device current) and caches it; make that first call before any stream capture;
+ *   - every call looks the array's device address up (cudaGetSymbolAddress, with the
+ *     calling device current), so the address stays right after a device reset and in
+ *     a caller's own driver-API context;
+ *   - the array is part of the library's device code, which CUDA loads on a device when
+ *     it is first used there (lazy module loading): the FIRST call on each device loads
+ *     it, which reserves the array and may synchronise that device.  Make one warm-up
+ *     call on each device before any loop that must not allocate and before any stream
+ *     capture; later calls allocate nothing;
  *   - every call uses the same array: calls that may overlap on the GPU (other
  *     streams, other host threads) race and must be serialised by the caller.
- * Nothing is allocated or freed, by this library or on its behalf. */
+ * Apart from that one-time load, nothing is allocated or freed, by this library or on
+ * its behalf. */
 msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const float* V,
                                const int32_t* pos, float* I_out, int32_t* window_error,
                                void* stream);
@@ -162,7 +178,12 @@ msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const 
 /* Synchronises `stream`, then reports (and clears) the workspace flag raised by the
  * most recent compute call on `ws` (every call that can raise it clears it when it
  * starts): MSP_OK; MSP_EINVAL when a scan window lay outside the object; MSP_ETIMEOUT
- * when a bounded wait for the tensor core ran out (msp_smd_matrix_step). */
+ * when a bounded wait for the tensor core's pipeline ran out (msp_smd_matrix_step,
+ * msp_dft2_tc: the call's results are invalid, the device stays usable); MSP_EDEVICE when,
+ * after such a timeout, the kernel's bounded wait for its own issued MMAs also ran out, so
+ * tensor memory may have been released under running MMAs.  MSP_EDEVICE marks the current
+ * device as untrusted for the rest of the process: every later compute call on it returns
+ * MSP_EDEVICE (end the process or reset the device). */
 msp_status msp_check_workspace(void* ws, void* stream);
 
 /* Failure-detection hook: the number of polls after which a wait of the tensor-core

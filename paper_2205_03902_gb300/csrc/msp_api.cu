@@ -425,6 +425,26 @@ void count_launches(int n) { counted(n); }
 static std::atomic<int> g_wait_limit{1 << 20};
 int tc_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
+// Devices on which a tensor-core kernel reported that its drain wait ran out (workspace
+// flag 3): tensor memory may have been released under running MMAs, so no later result
+// from that device is trusted for the rest of the process.
+static std::atomic<bool> g_untrusted[64];
+
+static int current_device() {
+  int dev = -1;
+  return (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) ? dev : -1;
+}
+
+// MSP_EDEVICE if the current device has been marked untrusted; every compute entry point
+// calls this before it launches anything.
+msp_status refuse_untrusted_device() {
+  const int dev = current_device();
+  if (dev >= 0 && g_untrusted[dev].load())
+    return fail(MSP_EDEVICE, "this device reported a tensor-core drain timeout earlier in the process; "
+                             "its results are no longer trusted (end the process or reset the device)");
+  return MSP_OK;
+}
+
 #define MSP_CK(call)                                                                      \
   do {                                                                                    \
     cudaError_t e_ = (call);                                                              \
@@ -522,6 +542,8 @@ struct Call {
 
 static msp_status begin(const msp_geometry* g, void* ws, size_t ws_bytes, void* stream, Call* c) {
   msp_status s = check_geometry(g);
+  if (s != MSP_OK) return s;
+  s = refuse_untrusted_device();
   if (s != MSP_OK) return s;
   if (!device_info(&c->dev)) return fail(MSP_ECUDA, "no current CUDA device");
   c->gcap = grid_cap(c->dev, g->win);
@@ -861,10 +883,16 @@ msp_status msp_check_workspace(void* ws, void* stream) {
   MSP_CK(cudaMemcpy(&flag, ws, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     MSP_CK(cudaMemset(ws, 0, sizeof(int)));
+    if (flag == 3) {
+      const int dev = current_device();
+      if (dev >= 0) g_untrusted[dev].store(true);
+      return fail(MSP_EDEVICE, "a tensor-core wait timed out and the kernel could not confirm that its own MMAs "
+                               "had finished before it released tensor memory; the device is no longer trusted");
+    }
     if (flag == 2) return fail(MSP_ETIMEOUT, "a wait for the tensor core timed out; the call's results are not valid");
     return fail(MSP_EINVAL, "a scan window lies outside the object (position skipped)");
   }
-  return MSP_OK;
+  return refuse_untrusted_device();
 }
 
 const char* msp_status_string(msp_status s) {
@@ -875,6 +903,7 @@ const char* msp_status_string(msp_status s) {
     case MSP_ECUDA: return "MSP_ECUDA";
     case MSP_EUNSUPPORTED: return "MSP_EUNSUPPORTED";
     case MSP_ETIMEOUT: return "MSP_ETIMEOUT";
+    case MSP_EDEVICE: return "MSP_EDEVICE";
   }
   return "MSP_UNKNOWN";
 }

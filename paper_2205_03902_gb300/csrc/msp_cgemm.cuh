@@ -36,7 +36,9 @@ namespace msp {
 // allocates TMEM and one of its threads issues the MMAs; a tcgen05.commit to the stage's
 // `empty` mbarrier hands the stage back once the MMAs have read it.  Every wait is bounded
 // (by `wait_limit` polls): on timeout the CTA raises *err = 2 and stops; the MMA thread
-// still waits, bounded, for the MMAs it issued before the TMEM is freed.
+// still waits, bounded, for the MMAs it issued before the TMEM is freed.  If that drain wait
+// runs out too, the CTA raises *err = 3 instead: tensor memory may then be released while
+// MMAs still write it, and the host treats the device as untrusted.
 namespace gemm {
 constexpr int TM = 128, TN = 128, TK = 16;                  // complex tile and K-tile
 constexpr int KR = 2 * TK;                                  // real K per tile
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
   uint64_t* dfree = empty + STAGES;   // the producers have read the accumulator out
   uint32_t* tslot = reinterpret_cast<uint32_t*>(dfree + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+  volatile int* drain_fail = reinterpret_cast<volatile int*>(tslot + 2);   // the MMA thread's drain ran out
   const int t = threadIdx.x, warp = t >> 5;
   const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;
   const int kb = blockIdx.z * k_chunk;
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     tc::mbar_init(dfree, NPROD);
     tc::fence_mbar_init();
     *abort_flag = 0;
+    *drain_fail = 0;
   }
   if (warp == 8) tc::tmem_alloc(tslot, TMEM_COLS);
   tc::fence_before();
@@ -243,7 +247,10 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
         last = it;
       }
       // every MMA issued must be done before tensor memory is freed, aborted or not
-      if (last >= 0 && !drain_wait(&empty[last % STAGES], (last / STAGES) & 1)) *abort_flag = 1;
+      if (last >= 0 && !drain_wait(&empty[last % STAGES], (last / STAGES) & 1)) {
+        *drain_fail = 1;
+        *abort_flag = 1;
+      }
     }
   } else {
     float re[CPT], im[CPT];
@@ -397,7 +404,8 @@ __global__ void __launch_bounds__(gemm::NTHREADS, 1) cgemm_kernel(int M, int N, 
     tc::fence_after();
     tc::tmem_dealloc(tmem, TMEM_COLS);
   }
-  if (t == 0 && *abort_flag) atomicExch(err, 2);
+  // the most severe outcome wins across CTAs: 3 (drain ran out) over 2 (pipeline wait ran out)
+  if (t == 0 && *abort_flag) atomicMax(err, *drain_fail ? 3 : 2);
 }
 
 }  // namespace msp

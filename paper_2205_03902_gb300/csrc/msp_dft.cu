@@ -13,6 +13,7 @@
 namespace msp {
 
 msp_status set_last_error(msp_status s, const std::string& m);
+msp_status refuse_untrusted_device();
 void count_launches(int n);
 int tc_wait_limit();
 msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& launch);
@@ -74,6 +75,10 @@ msp_status msp_dft2_tc(int32_t W, int32_t S, int32_t inverse, const float* in, f
                        void* stream) {
   set_last_error(MSP_OK, "");
   if (!supported(W, S)) return fail(MSP_EUNSUPPORTED, "W must be 32, 64, 128 or 256 and 1 <= S, S W <= 8388480");
+  {
+    const msp_status u = refuse_untrusted_device();
+    if (u != MSP_OK) return u;
+  }
   if (!in || !out || ((uintptr_t)in | (uintptr_t)out) % 16) return fail(MSP_EINVAL, "in and out must be non-NULL and 16-byte aligned");
   if (!ws || (uintptr_t)ws % 256) return fail(MSP_EINVAL, "workspace must be non-NULL and 256-byte aligned");
   const Layout l = layout(W, S, (char*)ws);

@@ -8,16 +8,19 @@
 // cannot hand the other entry points a workspace either.  This file gives them
 // the fused forward kernel with its scratch (the slice transmissions, the
 // propagator factor and an error word) in one file-scope device array of fixed
-// size, reserved when the library is loaded and held by every GPU that loads it
-// until the process exits.
+// size.  The array belongs to this library's device code: it is reserved on a
+// device when that code is loaded there (under CUDA's lazy module loading, by the
+// first call made on that device) and held until the process exits.
 //
 // Host code must not pass `g_noalloc_scratch` itself to a kernel: in host code
-// that name is a host-side stand-in, not a device address.  The device address
-// is looked up with cudaGetSymbolAddress once per device, by the first call made
-// while that device is current, and cached.
+// that name is a host-side stand-in, not a device address.  Every call looks the
+// device address up with cudaGetSymbolAddress, with the calling device current.
+// The lookup allocates nothing once the module is loaded; doing it on every call
+// (rather than caching an address per device index) keeps the address right after
+// a cudaDeviceReset, which reloads the module, and in a caller's own driver-API
+// context, where the same device holds a different copy of the array.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "msp.h"
@@ -38,27 +41,17 @@ constexpr size_t kNoallocMaxCells = (kNoallocBytes - kNoallocHeader) / sizeof(fl
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 msp_status set_last_error(msp_status s, const std::string& m);   // shown by msp_last_error_message()
-
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[64] = {};
+msp_status refuse_untrusted_device();                            // MSP_EDEVICE once a drain wait ran out
 
 static msp_status noalloc_fail(msp_status s, const std::string& m) { return set_last_error(s, m); }
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current context, looked up on every call.
 static msp_status noalloc_scratch(unsigned char** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return noalloc_fail(MSP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= 64) return noalloc_fail(MSP_EUNSUPPORTED, "device index beyond 63");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || !ptr)
-      return noalloc_fail(MSP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_noalloc_addr[dev] = ptr;
-  }
-  *out = (unsigned char*)g_noalloc_addr[dev];
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || !ptr)
+    return noalloc_fail(MSP_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = (unsigned char*)ptr;
   return MSP_OK;
 }
 
@@ -70,6 +63,8 @@ extern "C" msp_status msp_forward_noalloc(const msp_geometry* g, const float* pr
                                           const int32_t* pos, float* I_out, int32_t* window_error,
                                           void* stream) {
   msp_status s = msp_validate_geometry(g);   // also clears this thread's error message
+  if (s != MSP_OK) return s;
+  s = refuse_untrusted_device();
   if (s != MSP_OK) return s;
   if (g->param != MSP_PARAM_POTENTIAL)
     return noalloc_fail(MSP_EUNSUPPORTED, "msp_forward_noalloc takes potentials only; use msp_forward");

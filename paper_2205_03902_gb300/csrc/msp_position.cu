@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
     const int y0 = ps.x, x0 = ps.y;
     const bool ok = (y0 >= 0) && (x0 >= 0) && (y0 <= p.Ny - W) && (x0 <= p.Nx - W);
     if (!ok) {
-      if (tid == 0) atomicOr(p.err, 1);
+      if (tid == 0) atomicMax(p.err, 1);
       // outputs of a skipped position are zero
       if (MODE == MODE_FORWARD) {
         for (size_t i = tid; i < WW; i += G::NT) p.I_out[s * WW + i] = 0.f;

@@ -89,7 +89,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
     const int y0 = ps.x, x0 = ps.y;
     const bool ok = (y0 >= 0) && (x0 >= 0) && (y0 <= p.Ny - W) && (x0 <= p.Nx - W);
     if (!ok) {   // the same decision on every CTA of the cluster
-      if (tid == 0 && rank == 0) atomicOr(p.err, 1);
+      if (tid == 0 && rank == 0) atomicMax(p.err, 1);
       const size_t r0 = (size_t)rank * RW * W, r1 = r0 + (size_t)RW * W;
       if (MODE == MODE_FORWARD) {
         for (size_t i = r0 + tid; i < r1; i += NT) p.I_out[s * WW + i] = 0.f;

@@ -43,6 +43,7 @@
 namespace msp {
 
 msp_status set_last_error(msp_status s, const std::string& m);   // shown by msp_last_error_message()
+msp_status refuse_untrusted_device();                            // MSP_EDEVICE once a drain wait ran out
 void count_launches(int n);
 int tc_wait_limit();
 msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& launch);
@@ -1064,6 +1065,7 @@ static msp_status need(const void* p, const char* name) {
 
 static msp_status begin(const msp_smd_geometry* g, void* ws, size_t ws_bytes, void* stream, Call* c) {
   SMD_TRY(check(g));
+  SMD_TRY(refuse_untrusted_device());
   SMD_TRY(device(&c->dev, &c->pn, g->n));
   const size_t need_b = layout(g, c->dev, c->pn, nullptr).bytes;
   if (!ws) return fail(MSP_EINVAL, "workspace is NULL");

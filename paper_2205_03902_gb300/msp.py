@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmsp.so")
 
-MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EUNSUPPORTED, MSP_ETIMEOUT = range(6)
+MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EUNSUPPORTED, MSP_ETIMEOUT, MSP_EDEVICE = range(7)
 MSP_PARAM_POTENTIAL, MSP_PARAM_TRANSMISSION = 0, 1
 
 

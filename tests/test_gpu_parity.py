@@ -8,9 +8,10 @@ conditioning kappa (see `oracle.msp_oracle.residual_conditioning`: ~||Psi|| / ||
 where a small model amplitude meets a large measured one and the residual is set by
 the model's phase).  The FP32 forward applies 2L - 1 rounded 2-D FFTs, so its error is
 taken as e = 2 (2L - 1) 2^-24 per unit of the RMS far-field amplitude, and the bar is
-    max(1e-5, (e kappa + flip) c)
-with c the cancellation of the sum over positions (probe gradient only) and flip the
-bound on zero-rule decisions that round-off may turn (0 on noisy data).
+    min(max(1e-5, (e kappa + flip) c), cap)
+with c the cancellation of the sum over positions (probe gradient only), flip the
+bound on zero-rule decisions that round-off may turn (0 on noisy data), and a fixed
+cap (1e-4 for dV and the loss, 2e-3 for dprobe) that no state may exceed.
   * strong-misfit states (kappa ~ 1): the bar is 1e-5 on every output;
   * realistic states (the workloads' own starting points, noiseless or nearly fitted
     data, the full benchmark workload): the derived bar.
@@ -57,11 +58,19 @@ def fwd_err(n_slices):
     return 2 * (2 * n_slices - 1) * U32
 
 
+# Fixed ceilings on the FP32 path's derived bars: whatever a state's conditioning, the fast
+# path must stay below these (the precise-forward mode is held to TOL on the same states).
+CAP_GRAD = 1e-4       # dV (and the transmission-mode gradient)
+CAP_PROBE_GRAD = 2e-3  # dprobe: the sum over positions cancels, amplifying the per-position error
+CAP_LOSS = 1e-4
+
+
 def derived_tol(gd, probe, pos, I, V, probe_grad=False):
     e = fwd_err(gd["n_slices"])
     band = 2 * e * float(np.linalg.norm(probe))
     kappa, canc, flip = O.residual_conditioning(gd, probe, pos, I, V=V, band=band)
-    return max(TOL, (e * kappa + flip) * (canc if probe_grad else 1.0))
+    bar = max(TOL, (e * kappa + flip) * (canc if probe_grad else 1.0))
+    return min(bar, CAP_PROBE_GRAD if probe_grad else CAP_GRAD)
 
 
 def loss_tol(gd, probe, n_pos, loss_ref):
@@ -70,7 +79,7 @@ def loss_tol(gd, probe, n_pos, loss_ref):
     if loss_ref <= 0:
         return TOL
     kappa = np.sqrt(n_pos * gd["win"] ** 2 * float(np.sum(np.abs(probe) ** 2)) / loss_ref)
-    return max(TOL, 2 * fwd_err(gd["n_slices"]) * kappa)
+    return min(max(TOL, 2 * fwd_err(gd["n_slices"]) * kappa), CAP_LOSS)
 
 
 class Case:

@@ -416,6 +416,55 @@ def test_layerwise_estimation_lowers_the_loss_on_a_small_workload():
     assert err1 < err0
 
 
+def test_layerwise_estimation_is_gauss_seidel_over_ascending_slices():
+    """Algorithm 1 (Sec. 3.3): within a sweep the slices are taken in ascending order and the
+    prefix S_l of slice l is formed from the slices already updated in this sweep.  Two sweeps
+    must equal six explicitly chained single-slice steps; a Jacobi sweep (every slice stepped
+    from the sweep's starting slices) and a descending sweep give different potentials, so
+    either mistake fails here."""
+    g, probe, pos, I, V0 = make_problem(21, L=3)
+    V_alg, hist = O.layerwise_estimation(g, probe, pos, I, V0, sweeps=2)
+    Vc, losses = np.array(V0, copy=True), []
+    for _ in range(2):
+        for layer in range(3):
+            Vc, loss, _ = O.layer_step(g, probe, pos, I, layer, V=Vc)
+            losses.append(loss)
+    assert np.array_equal(V_alg, Vc)
+    assert hist == losses
+    # Jacobi order
+    Vj = np.array(V0, copy=True)
+    for _ in range(2):
+        nxt = Vj.copy()
+        for layer in range(3):
+            nxt[layer] = O.layer_step(g, probe, pos, I, layer, V=Vj)[0][layer]
+        Vj = nxt
+    # descending order
+    Vd = np.array(V0, copy=True)
+    for _ in range(2):
+        for layer in (2, 1, 0):
+            Vd, _, _ = O.layer_step(g, probe, pos, I, layer, V=Vd)
+    for other in (Vj, Vd):
+        assert np.linalg.norm(other - V_alg) > 1e-3 * np.linalg.norm(V_alg - V0)
+
+
+def test_relative_reconstruction_error_closed_form():
+    """Eq. (error_metric_object): the mean over slices of ||O_m - O^_m||_F / ||O_m||_F.  An estimate
+    that scales slice m by a_m has error |a_m - 1| on that slice; with a = (1.1, 0.7, 1 + 0.2i) the
+    metric is exactly (0.1 + 0.3 + 0.2) / 3 = 0.2.  Normalising by the estimate, summing instead of
+    averaging, or averaging squares instead of norms gives 0.239, 0.6 or 0.216."""
+    X = cplx((3, 9, 7), 33)
+    a = np.array([1.1, 0.7, 1 + 0.2j])
+    est = a[:, None, None] * X
+    assert O.relative_reconstruction_error(X, est) == pytest.approx(0.2, rel=1e-12)
+    assert O.relative_reconstruction_error(X, X) == 0.0
+    # the error of each slice is relative to that slice: rescaling one true slice and its
+    # estimate together leaves the metric unchanged
+    X2, est2 = X.copy(), est.copy()
+    X2[1] *= 1e3
+    est2[1] *= 1e3
+    assert O.relative_reconstruction_error(X2, est2) == pytest.approx(0.2, rel=1e-12)
+
+
 @pytest.mark.parametrize("layer", [0, 2])
 def test_potential_step_is_the_tangent_projection_of_the_transmission_step(layer):
     """Potential mode moves V so that exp(i sigma V) follows the transmission-mode amplitude-flow

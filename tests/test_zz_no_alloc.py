@@ -58,6 +58,38 @@ def test_noalloc_forward_matches_msp_forward_on_two_calls(cfg, sub):
         assert werr.item() == 0
 
 
+def test_noalloc_forward_w256_cluster_path_on_two_calls():
+    """W = 256 runs each position on a four-CTA cluster; its forward mode must not touch the
+    exit-wave stash or the loss buffers, which the no-allocation entry point does not have.
+    Two slices of 320 x 320 (204,800 cells, inside the fixed scratch) on a 3 x 3 scan."""
+    __graft_entry__.build()
+    from paper_2205_03902_gb300 import msp
+    lib = msp.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    cfg = synth.C4
+    obj, L = 320, 2
+    pos = np.array([(y, x) for y in (0, 32, 64) for x in (0, 32, 64)], dtype=np.int32)
+    gd = dict(synth.geometry(cfg, n_pos=len(pos)), n_slices=L, obj_ny=obj, obj_nx=obj)
+    g = msp.geometry(**gd)
+    probe = torch.from_numpy(synth.probe(cfg).astype(np.complex64)).to(dev)
+    V_true = synth.potential_slices(cfg)[:L, :obj, :obj]
+    dpos = torch.from_numpy(pos).to(dev)
+    werr = torch.full((1,), 7, dtype=torch.int32, device=dev)
+    for scale in (1.0, 0.3):
+        V = torch.from_numpy(np.ascontiguousarray(scale * V_true).astype(np.float32)).to(dev)
+        ref = msp.forward(g, probe, V, dpos)
+        out = torch.full_like(ref, float("nan"))
+        st = lib.msp_forward_noalloc(ctypes.byref(g), _ptr(probe), _ptr(V), _ptr(dpos), _ptr(out), _ptr(werr),
+                                     stream)
+        assert st == msp.MSP_OK, lib.msp_last_error_message()
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all()
+        assert _rel(out, ref) <= TOL
+        assert werr.item() == 0
+
+
 def test_noalloc_forward_limits_and_window_flag():
     __graft_entry__.build()
     from paper_2205_03902_gb300 import msp
