@@ -146,6 +146,36 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V,
                           int32_t normalize, double* loss_before, double* mu_out,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* The plain method: Algorithm 1 (Layer-wise Estimation, Sec. 3.3) with optional probe
+ * estimation (Sec. 3.5), run entirely on `stream` without host synchronisation.
+ *   for t in [T]:  for l = 0 .. L-1 (ascending; each slice's prefix uses the slices already
+ *                  updated in this sweep, Gauss-Seidel):  K steps of msp_layer_step on l
+ *                  then P steps of msp_probe_step
+ * The paper estimates the probe after the object (Sec. 3.5); P > 0 alternates the two,
+ * which an initial probe with a defocus error needs; K = 0 runs probe steps only, so
+ * "object, then probe" is two calls. */
+typedef struct {
+  int32_t sweeps;            /* T >= 0: iterations of Algorithm 1                         */
+  int32_t steps_per_layer;   /* K >= 0: gradient steps per slice per sweep                */
+  int32_t probe_steps;       /* P >= 0: probe steps after each sweep (0: probe known)     */
+  int32_t normalize_probe;   /* != 0: rescale the probe after each probe step (msp_probe_step) */
+  double layer_step;         /* mu of the slice steps; <= 0: the spectral step (msp_layer_step) */
+  double probe_step;         /* mu of the probe steps; <= 0: 1 / (S W^2) (msp_probe_step)      */
+} msp_plan;
+
+/* Entries of the loss history of msp_reconstruct: T (L K + P) + 1 (0 if g or plan is invalid). */
+size_t msp_reconstruct_history_length(const msp_geometry* g, const msp_plan* plan);
+
+/* Runs `plan` from the caller's probe and slices, both updated in place (the probe only when
+ * P > 0).  loss_history (device double [msp_reconstruct_history_length], may be NULL) receives
+ * the loss before every step, in the order the steps run, and last the loss after the final
+ * step.  pos, I_meas and the workspace are as for msp_layer_step (its workspace size covers
+ * this call).  Argument errors return before anything is launched; a launch failure returns
+ * MSP_ECUDA with the steps issued so far left queued on the stream. */
+msp_status msp_reconstruct(const msp_geometry* g, const msp_plan* plan, float* probe, float* V,
+                           const int32_t* pos, const float* I_meas, double* loss_history,
+                           void* ws, size_t ws_bytes, void* stream);
+
 /* msp_forward for callers that cannot allocate device memory.  The paper has no
  * counterpart; it exists because some callers cannot call cudaMalloc (a host
  * application that owns all device memory through its own pool, or a loop that

@@ -318,6 +318,30 @@ def layerwise_estimation(geom: dict, probe, pos, i_meas, V0, sweeps: int, steps_
     return V, history
 
 
+def plain_method(geom: dict, probe, pos, i_meas, V0, sweeps: int, steps_per_layer: int = 1, probe_steps: int = 0,
+                 normalize=False, layer_mu=None, probe_mu=None):
+    """Algorithm 1 (Sec. 3.3) with probe estimation (Sec. 3.5), potential mode.  Each sweep takes
+    every slice in ascending order for `steps_per_layer` gradient steps (Gauss-Seidel), then the
+    probe for `probe_steps` amplitude-flow steps with the slices just estimated.  The paper
+    estimates the probe after the object; alternating the two per sweep is what a probe guess
+    with a defocus error needs, and steps_per_layer = 0 leaves probe steps only.
+    Returns (V, probe, history): history holds the loss before every step, in the order the steps
+    run, and last the loss after the final step."""
+    V = np.array(V0, dtype=np.float64, copy=True)
+    p = np.asarray(probe, dtype=np.complex128).copy()
+    history = []
+    for _ in range(sweeps):
+        for layer in range(V.shape[0]):
+            for _ in range(steps_per_layer):
+                V, loss, _ = layer_step(geom, p, pos, i_meas, layer, V=V, step=layer_mu)
+                history.append(loss)
+        for _ in range(probe_steps):
+            p, loss, _ = probe_step(geom, p, pos, i_meas, V=V, step=probe_mu, normalize=normalize)
+            history.append(loss)
+    history.append(loss_grad(geom, p, pos, i_meas, V=V, want_probe=False)["loss"])
+    return V, p, history
+
+
 def residual_conditioning(geom: dict, probe, pos, i_meas, V=None, T=None, band=0.0):
     """How strongly a state amplifies rounding in the forward model into its gradients.
 

@@ -847,6 +847,53 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, c
   return MSP_OK;
 }
 
+static msp_status check_plan(const msp_geometry* g, const msp_plan* plan) {
+  MSP_TRY(check_geometry(g));
+  if (!plan) return fail(MSP_EINVAL, "plan is NULL");
+  if (plan->sweeps < 0 || plan->steps_per_layer < 0 || plan->probe_steps < 0)
+    return fail(MSP_EINVAL, "sweeps, steps_per_layer and probe_steps must be >= 0");
+  if (!std::isfinite(plan->layer_step) || !std::isfinite(plan->probe_step))
+    return fail(MSP_EINVAL, "step sizes must be finite");
+  const double steps = (double)plan->sweeps * ((double)g->n_slices * plan->steps_per_layer + plan->probe_steps);
+  if (steps > 1.0e9) return fail(MSP_EINVAL, "plan has more than 1e9 steps");
+  return MSP_OK;
+}
+
+size_t msp_reconstruct_history_length(const msp_geometry* g, const msp_plan* plan) {
+  if (check_plan(g, plan) != MSP_OK) return 0;
+  return (size_t)plan->sweeps * ((size_t)g->n_slices * plan->steps_per_layer + plan->probe_steps) + 1;
+}
+
+msp_status msp_reconstruct(const msp_geometry* g, const msp_plan* plan, float* probe, float* V, const int32_t* pos,
+                           const float* I_meas, double* loss_history, void* ws, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  MSP_TRY(check_plan(g, plan));
+  if (loss_history && misaligned(loss_history, 8)) return fail(MSP_EINVAL, "loss_history must be 8-byte aligned");
+  {
+    // every argument the steps take is checked once here, before the first launch
+    Call c;
+    MSP_TRY(begin(g, ws, ws_bytes, stream, &c));
+    MSP_TRY(need_ptr(probe, "probe"));
+    MSP_TRY(need_ptr(V, "V"));
+    if (g->n_pos > 0) {
+      MSP_TRY(need_ptr(pos, "pos"));
+      MSP_TRY(need_ptr(I_meas, "I_meas"));
+    }
+  }
+  size_t k = 0;
+  auto slot = [&]() { return loss_history ? loss_history + k++ : nullptr; };
+  for (int t = 0; t < plan->sweeps; ++t) {
+    for (int l = 0; l < g->n_slices; ++l)
+      for (int i = 0; i < plan->steps_per_layer; ++i)
+        MSP_TRY(msp_layer_step(g, probe, V, pos, I_meas, l, plan->layer_step, slot(), nullptr, ws, ws_bytes, stream));
+    for (int i = 0; i < plan->probe_steps; ++i)
+      MSP_TRY(msp_probe_step(g, (float*)probe, V, pos, I_meas, plan->probe_step, plan->normalize_probe, slot(),
+                             nullptr, ws, ws_bytes, stream));
+  }
+  if (loss_history) MSP_TRY(msp_loss_grad(g, probe, V, pos, I_meas, slot(), nullptr, nullptr, ws, ws_bytes, stream));
+  return MSP_OK;
+}
+
 msp_status msp_set_wait_limit(int32_t polls) {
   g_err.clear();
   g_wait_limit.store(polls >= 1 ? polls : (1 << 20), std::memory_order_relaxed);

@@ -64,6 +64,23 @@ class SmdGeometry(ctypes.Structure):
     ]
 
 
+class Plan(ctypes.Structure):
+    """msp_plan (include/msp.h): Algorithm 1 (Sec. 3.3) with optional probe steps (Sec. 3.5)."""
+    _fields_ = [
+        ("sweeps", ctypes.c_int32),
+        ("steps_per_layer", ctypes.c_int32),
+        ("probe_steps", ctypes.c_int32),
+        ("normalize_probe", ctypes.c_int32),
+        ("layer_step", ctypes.c_double),
+        ("probe_step", ctypes.c_double),
+    ]
+
+
+def plan(sweeps, steps_per_layer=1, probe_steps=0, normalize_probe=False, layer_step=0.0, probe_step=0.0) -> Plan:
+    return Plan(int(sweeps), int(steps_per_layer), int(probe_steps), 1 if normalize_probe else 0,
+                float(layer_step), float(probe_step))
+
+
 def smd_geometry(n, n_slices, n_pos, wavelength_A, dz_A, pixel_A, **_ignored) -> SmdGeometry:
     return SmdGeometry(int(n), int(n_slices), int(n_pos), float(wavelength_A), float(dz_A), float(pixel_A))
 
@@ -81,6 +98,8 @@ _SIGS = {
                        ctypes.c_int),
     "msp_probe_step": ([_G, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P],
                        ctypes.c_int),
+    "msp_reconstruct_history_length": ([_G, ctypes.POINTER(Plan)], ctypes.c_size_t),
+    "msp_reconstruct": ([_G, ctypes.POINTER(Plan), _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "msp_check_workspace": ([_P, _P], ctypes.c_int),
     "msp_forward_noalloc": ([_G, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "msp_profile_enable": ([ctypes.c_int32], ctypes.c_int),
@@ -261,6 +280,25 @@ def probe_step(g: Geometry, probe, V, pos, I_meas, step: float = 0.0, normalize:
                                 1 if normalize else 0, _ptr(loss_before), _ptr(mu), ws.ptr(), ws.nbytes,
                                 _stream(stream)), "msp_probe_step")
     return loss_before, mu
+
+
+def reconstruct(g: Geometry, pl: Plan, probe, V, pos, I_meas, ws=None, stream=None, history=None):
+    """The plain method (msp_reconstruct): `pl.sweeps` iterations of Algorithm 1 with optional probe
+    steps; probe and V are updated in place.  Returns the loss history (float64, on the device):
+    the loss before every step in order, then the loss after the last step."""
+    device = _arrays(g, probe, V, pos, I_meas)
+    n = int(lib().msp_reconstruct_history_length(ctypes.byref(g), ctypes.byref(pl)))
+    if n == 0:
+        _check(lib().msp_validate_geometry(ctypes.byref(g)), "msp_reconstruct")
+        raise MspError(MSP_EINVAL, "msp_reconstruct", "invalid plan")
+    if history is None:
+        history = torch.empty(n, dtype=torch.float64, device=device)
+    elif history.numel() < n or history.dtype != torch.float64 or history.device != device:
+        raise ValueError(f"history must be a float64 tensor of at least {n} entries on {device}")
+    ws = _ws(g, ws, device)
+    _check(lib().msp_reconstruct(ctypes.byref(g), ctypes.byref(pl), _ptr(probe), _ptr(V), _ptr(pos), _ptr(I_meas),
+                                 _ptr(history), ws.ptr(), ws.nbytes, _stream(stream)), "msp_reconstruct")
+    return history[:n]
 
 
 def check_workspace(ws: Workspace, stream=None) -> None:

@@ -73,7 +73,8 @@ def test_geometry_validation(lib, kw, status):
 def test_null_geometry_and_status_strings(lib):
     assert lib.msp_validate_geometry(None) == msp.MSP_EINVAL
     assert b"NULL" in lib.msp_last_error_message()
-    for s, name in enumerate(["MSP_OK", "MSP_EINVAL", "MSP_ENOMEM", "MSP_ECUDA", "MSP_EUNSUPPORTED", "MSP_ETIMEOUT"]):
+    for s, name in enumerate(["MSP_OK", "MSP_EINVAL", "MSP_ENOMEM", "MSP_ECUDA", "MSP_EUNSUPPORTED", "MSP_ETIMEOUT",
+                              "MSP_EDEVICE"]):
         assert msp.status_string(s) == name
     assert msp.status_string(99) == "MSP_UNKNOWN"
 
@@ -134,6 +135,24 @@ def test_dft_workspace_sizes_and_host_validation(lib, W, S, ok):
     else:
         assert n == 0
         assert lib.msp_dft2_tc(W, S, 0, None, None, None, 0, None) == msp.MSP_EUNSUPPORTED
+
+
+def test_reconstruct_history_length_and_plan_validation(lib):
+    g = geom()
+    pl = msp.plan(50, steps_per_layer=1, probe_steps=1)
+    assert lib.msp_reconstruct_history_length(ctypes.byref(g), ctypes.byref(pl)) == 50 * (4 + 1) + 1
+    pl = msp.plan(3, steps_per_layer=2)
+    assert lib.msp_reconstruct_history_length(ctypes.byref(g), ctypes.byref(pl)) == 3 * 8 + 1
+    pl = msp.plan(0)
+    assert lib.msp_reconstruct_history_length(ctypes.byref(g), ctypes.byref(pl)) == 1
+    for bad in (msp.plan(-1), msp.plan(2, steps_per_layer=-1), msp.plan(2, probe_steps=-3),
+                msp.plan(2, layer_step=float("nan"))):
+        assert lib.msp_reconstruct_history_length(ctypes.byref(g), ctypes.byref(bad)) == 0
+        st = lib.msp_reconstruct(ctypes.byref(g), ctypes.byref(bad), None, None, None, None, None, None, 0, None)
+        assert st == msp.MSP_EINVAL
+    assert lib.msp_reconstruct_history_length(ctypes.byref(g), None) == 0
+    assert lib.msp_reconstruct(ctypes.byref(g), None, None, None, None, None, None, None, 0, None) == msp.MSP_EINVAL
+    assert b"plan" in lib.msp_last_error_message()
 
 
 def test_wait_limit_hook_needs_no_device(lib):

@@ -447,6 +447,38 @@ def test_layerwise_estimation_is_gauss_seidel_over_ascending_slices():
         assert np.linalg.norm(other - V_alg) > 1e-3 * np.linalg.norm(V_alg - V0)
 
 
+def test_plain_method_orders_slice_sweeps_and_probe_steps():
+    """The plain method runs, per sweep, Algorithm 1's ascending Gauss-Seidel slice steps and then the
+    probe steps of Sec. 3.5 with the slices just estimated; its history is the loss before each step
+    and the loss after the last.  Without probe steps it is Algorithm 1 itself.  Swapping the probe
+    steps before the slice steps, or leaving the history's final loss out, fails here."""
+    g, probe, pos, I, V0 = make_problem(23, L=2)
+    p0 = probe * np.exp(0.2j) * 1.1
+    V, p, hist = O.plain_method(g, p0, pos, I, V0, sweeps=2, probe_steps=1)
+    Vc, pc, ref = np.array(V0, copy=True), p0.copy(), []
+    for _ in range(2):
+        for layer in range(2):
+            Vc, loss, _ = O.layer_step(g, pc, pos, I, layer, V=Vc)
+            ref.append(loss)
+        pc, loss, _ = O.probe_step(g, pc, pos, I, V=Vc)
+        ref.append(loss)
+    ref.append(O.loss_grad(g, pc, pos, I, V=Vc, want_probe=False)["loss"])
+    assert np.array_equal(V, Vc) and np.array_equal(p, pc)
+    assert hist == ref
+    # probe steps first in each sweep give a different trajectory
+    Vs, ps = np.array(V0, copy=True), p0.copy()
+    for _ in range(2):
+        ps, _, _ = O.probe_step(g, ps, pos, I, V=Vs)
+        for layer in range(2):
+            Vs, _, _ = O.layer_step(g, ps, pos, I, layer, V=Vs)
+    assert np.linalg.norm(ps - p) > 1e-6 * np.linalg.norm(p)
+    # no probe steps: Algorithm 1
+    V1, p1, h1 = O.plain_method(g, p0, pos, I, V0, sweeps=2)
+    Va, ha = O.layerwise_estimation(g, p0, pos, I, V0, sweeps=2)
+    assert np.array_equal(V1, Va) and np.array_equal(p1, p0) and h1[:-1] == ha
+    assert h1[-1] == O.loss_grad(g, p0, pos, I, V=Va, want_probe=False)["loss"] < ha[0]
+
+
 def test_relative_reconstruction_error_closed_form():
     """Eq. (error_metric_object): the mean over slices of ||O_m - O^_m||_F / ||O_m||_F.  An estimate
     that scales slice m by a_m has error |a_m - 1| on that slice; with a = (1.1, 0.7, 1 + 0.2i) the

@@ -202,15 +202,22 @@ def probe(cfg: Workload, defocus_A: float | None = None, norm2: float | None = N
     return p
 
 
-def poisson_counts(intensity: np.ndarray, dose: float | None, seed: int) -> np.ndarray:
-    """Counting noise: each pattern is scaled to `dose` expected counts, then Poisson-sampled."""
+def poisson_counts(intensity: np.ndarray, dose: float | None, seed: int, index=None) -> np.ndarray:
+    """Counting noise: each pattern is scaled to `dose` expected counts, then Poisson-sampled.
+
+    Pattern k draws from its own stream, seeded by (seed, its scan index); `index` gives the
+    scan indices of the patterns passed (default 0, 1, ...), so the noise of a sample of
+    positions equals that of the same positions in the full scan."""
     if dose is None:
         return intensity.copy()
-    rng = np.random.default_rng([seed, 23])
+    index = np.arange(intensity.shape[0]) if index is None else np.asarray(index)
     tot = intensity.reshape(intensity.shape[0], -1).sum(axis=1)
     scale = np.where(tot > 0, dose / np.maximum(tot, 1e-300), 0.0)
-    lam = intensity * scale[:, None, None]
-    return rng.poisson(lam).astype(np.float64)
+    out = np.empty(intensity.shape, dtype=np.float64)
+    for k in range(intensity.shape[0]):
+        rng = np.random.default_rng([seed, 23, int(index[k])])
+        out[k] = rng.poisson(intensity[k] * scale[k])
+    return out
 
 
 def random_complex(shape, seed: int) -> np.ndarray:
