@@ -79,6 +79,16 @@ typedef enum {
  * transmissions o_m (the paper's parametrisation). */
 enum { MSP_PARAM_POTENTIAL = 0, MSP_PARAM_TRANSMISSION = 1 };
 
+/* Arithmetic of the forward model and the residual.
+ *   MSP_PRECISION_FP32: everything in FP32 in the fused per-position kernel (the fast path).
+ *   MSP_PRECISION_FP64_FORWARD: the forward model (transmit, Fresnel propagation, far field,
+ *     Sec. 2.1) and the residual R = Psi - sqrt(I) Psi/|Psi| and loss (Sec. 3.2) in FP64, R
+ *     and the stored exit waves rounded to FP32 once, the adjoint in FP32.  Near a fit the
+ *     gradient is a small difference of far-field amplitudes, so the FP32 forward's rounding
+ *     is amplified by ||Psi|| / ||R||; this mode removes that amplification.  Slower (GB300's
+ *     FP64 rate is 1/64 of its FP32 rate) and with a larger workspace. */
+enum { MSP_PRECISION_FP32 = 0, MSP_PRECISION_FP64_FORWARD = 1 };
+
 /* Statement of the problem (Sec. 2.1).  Supported windows: W = 64, 128 or 256 (W = 256 runs
  * each position on a four-CTA thread-block cluster). */
 typedef struct {
@@ -92,6 +102,7 @@ typedef struct {
   double sigma;         /* interaction constant, rad / (V angstrom)               */
   double dz_A;          /* slice separation = Fresnel distance Delta (Eq. fresnel_element) */
   double pixel_A;       /* real-space pixel size in angstrom                       */
+  int32_t precision;    /* MSP_PRECISION_FP32 or MSP_PRECISION_FP64_FORWARD         */
 } msp_geometry;
 
 /* Checks a geometry on the host.  MSP_OK, MSP_EINVAL or MSP_EUNSUPPORTED. */
@@ -186,7 +197,8 @@ msp_status msp_reconstruct(const msp_geometry* g, const msp_plan* plan, float* p
  *     word) is one 16 MiB file-scope device array that every GPU loading the library
  *     holds until the process exits; L * Ny * Nx may not exceed 2,096,640 (returns
  *     MSP_EUNSUPPORTED, with the reason in msp_last_error_message(), otherwise);
- *   - potentials only (MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED);
+ *   - potentials only (MSP_PARAM_TRANSMISSION returns MSP_EUNSUPPORTED) and the FP32
+ *     forward only (other precisions return MSP_EUNSUPPORTED);
  *   - window_error (device int32, may be NULL) is set to 0, or to 1 if a window lay
  *     outside the object (that position's pattern is then zero);
  *   - every call looks the array's device address up (cudaGetSymbolAddress, with the

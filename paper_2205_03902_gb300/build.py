@@ -16,7 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libmsp.so")
-SOURCES = ["msp_position.cu", "msp_position_cluster.cu", "msp_api.cu", "msp_noalloc.cu", "msp_smd.cu", "msp_dft.cu"]
+SOURCES = ["msp_position.cu", "msp_position_cluster.cu", "msp_api.cu", "msp_noalloc.cu", "msp_smd.cu", "msp_dft.cu",
+           "msp_precise.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -28,6 +28,10 @@ namespace msp {
 cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int grid, cudaStream_t st);
 int position_slots(int win);
 
+// the precise-forward mode (msp_precise.cu)
+size_t precise_extra_bytes(int W, int L, int Ny, int Nx, int S);
+cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in, cudaStream_t st, long long* launches);
+
 // ---------------------------------------------------------------------------
 // element-wise kernels
 // ---------------------------------------------------------------------------
@@ -488,6 +492,8 @@ static msp_status check_geometry(const msp_geometry* g) {
   if (!(std::isfinite(g->pixel_A) && g->pixel_A > 0)) return fail(MSP_EINVAL, "pixel size must be > 0");
   if (!(std::isfinite(g->dz_A) && g->dz_A >= 0)) return fail(MSP_EINVAL, "slice thickness must be >= 0");
   if (!std::isfinite(g->sigma)) return fail(MSP_EINVAL, "sigma must be finite");
+  if (g->precision != MSP_PRECISION_FP32 && g->precision != MSP_PRECISION_FP64_FORWARD)
+    return fail(MSP_EINVAL, "precision must be MSP_PRECISION_FP32 or MSP_PRECISION_FP64_FORWARD");
   const double cells = (double)g->n_slices * g->obj_ny * g->obj_nx;
   if (cells > 4.0e9) return fail(MSP_EUNSUPPORTED, "object too large");
   if ((size_t)((g->obj_nx + kGatherTX - 1) / kGatherTX) * ((g->obj_ny + kGatherTY - 1) / kGatherTY) > (size_t)kRedSlots)
@@ -502,7 +508,10 @@ static int grid_cap(const DevInfo& d, int win) {
 }
 
 // Loss partials per position: one per CTA that holds part of the wave.
-static int loss_slots(int win) { return win == 256 ? 4 : 1; }
+static int loss_slots(const msp_geometry* g) {
+  return (g->win == 256 && g->precision == MSP_PRECISION_FP32) ? 4 : 1;
+}
+static bool precise(const msp_geometry* g) { return g->precision == MSP_PRECISION_FP64_FORWARD; }
 
 // Carve the workspace; with base == nullptr only the size is computed.
 static Workspace layout(const msp_geometry* g, int gcap, char* base) {
@@ -523,9 +532,10 @@ static Workspace layout(const msp_geometry* g, int gcap, char* base) {
   w.willum = base ? w.wgrad + cw * S * WW : nullptr;
   w.dprobe_part = (float2*)take((size_t)gcap * WW * sizeof(float2));
   w.dprobe_sum = (float2*)take(WW * sizeof(float2));
-  w.loss_part = (double*)take((S > 0 ? S : 1) * loss_slots((int)W) * sizeof(double));
+  w.loss_part = (double*)take((S > 0 ? S : 1) * loss_slots(g) * sizeof(double));
   w.map0 = (float*)take(2 * plane * sizeof(float));   // complex in transmission mode
   w.map1 = (float*)take(plane * sizeof(float));
+  w.precise = precise(g) ? (char*)take(precise_extra_bytes((int)W, (int)L, g->obj_ny, g->obj_nx, (int)S)) : nullptr;
   w.bytes = off;
   return w;
 }
@@ -537,6 +547,8 @@ struct Call {
   Workspace ws;
   int gcap = 0;
   int grid = 0;
+  int parts = 0;               // per-CTA probe-gradient partials the fused pass leaves
+  const float* V = nullptr;    // the caller's slices (potentials, or complex in transmission mode)
   cudaStream_t st = nullptr;
 };
 
@@ -554,6 +566,7 @@ static msp_status begin(const msp_geometry* g, void* ws, size_t ws_bytes, void* 
     return fail(MSP_EINVAL, "workspace too small: " + std::to_string(ws_bytes) + " < " + std::to_string(need));
   c->ws = layout(g, c->gcap, (char*)ws);
   c->grid = g->n_pos < c->gcap ? g->n_pos : c->gcap;
+  c->parts = precise(g) ? 1 : c->grid;
   c->st = (cudaStream_t)stream;
   return MSP_OK;
 }
@@ -585,6 +598,7 @@ static msp_status prepare(const msp_geometry* g, const float* probe, const float
 
 static PosParams base_params(const msp_geometry* g, const float* probe, const float* V, const int32_t* pos,
                              Call& c) {
+  c.V = V;
   PosParams p{};
   p.probe = (const float2*)probe;
   p.cplx = g->param == MSP_PARAM_TRANSMISSION;
@@ -639,6 +653,20 @@ msp_status profiled_launch(cudaStream_t st, const std::function<cudaError_t()>& 
 
 static msp_status run_position(const msp_geometry* g, int mode, const PosParams& p, Call& c) {
   if (g->n_pos == 0) return MSP_OK;
+  if (precise(g)) {
+    PreciseIn in{};
+    in.V = p.cplx ? nullptr : c.V;
+    in.X = p.cplx ? (const float2*)c.V : nullptr;
+    in.sigma = g->sigma;
+    in.dzlam = g->dz_A * g->wavelength_A;
+    in.dq = 1.0 / ((double)g->win * g->pixel_A);
+    in.extra = c.ws.precise;
+    in.sms = c.dev.sms;
+    long long n = 0;
+    const msp_status s = profiled_launch(c.st, [&] { return run_precise(mode, p, g->win, in, c.st, &n); });
+    if (n > 1) counted((int)(n - 1));   // profiled_launch counted one
+    return s;
+  }
   return profiled_launch(c.st, [&] { return launch_position_kernel(g->win, mode, p, c.grid, c.st); });
 }
 
@@ -648,7 +676,7 @@ static msp_status reduce_loss(const msp_geometry* g, Call& c, double* extra) {
     if (extra) MSP_CK(cudaMemsetAsync(extra, 0, sizeof(double), c.st));
     return MSP_OK;
   }
-  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.loss_part, g->n_pos * loss_slots(g->win), 0, c.ws.scal, extra);
+  reduce_kernel<<<1, 1024, 0, c.st>>>(c.ws.loss_part, g->n_pos * loss_slots(g), 0, c.ws.scal, extra);
   MSP_CK(cudaGetLastError());
   counted();
   return MSP_OK;
@@ -729,7 +757,7 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   counted();
   }
   if (dprobe) {
-    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.grid, (int)WW,
+    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
                                                                    (float2*)dprobe);
     MSP_CK(cudaGetLastError());
   counted();
@@ -785,7 +813,7 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   }
   // potential mode: mu = 1 / (2 sigma^2 W^2 max illum); transmission: 1 / (W^2 max illum prod max|o_m|^2)
   const double c_w2 = (p.cplx ? 1.0 : 2.0 * g->sigma * g->sigma) * (double)W * (double)W;
-  layer_finish_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nblk, c.ws.loss_part, g->n_pos * loss_slots(W), step, c_w2,
+  layer_finish_kernel<<<1, 1024, 0, c.st>>>(c.ws.red, nblk, c.ws.loss_part, g->n_pos * loss_slots(g), step, c_w2,
                                             p.cplx, c.ws.scal, mu_out, loss_before);
   MSP_CK(cudaGetLastError());
   counted();
@@ -825,7 +853,7 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, c
     p.I_meas = I_meas;
     p.want_dprobe = 1;
     MSP_TRY(run_position(g, MODE_PROBE, p, c));
-    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.grid, (int)WW,
+    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
                                                                    c.ws.dprobe_sum);
     MSP_CK(cudaGetLastError());
   counted();

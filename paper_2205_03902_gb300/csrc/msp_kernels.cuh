@@ -46,7 +46,18 @@ struct Workspace {
   double* loss_part;       // [S]
   float* map0;             // [Ny][Nx] layer gradient map
   float* map1;             // [Ny][Nx] illumination map
+  char* precise;           // the precise-forward mode's buffers (NULL in the FP32 mode)
   size_t bytes;
+};
+
+// Inputs of the precise-forward mode beyond the fused kernel's parameters.
+struct PreciseIn {
+  const float* V;        // FP32 potentials (potential mode) or NULL
+  const float2* X;       // the caller's complex slices (transmission mode) or NULL
+  double sigma;          // interaction constant
+  double dzlam, dq;      // dz lambda and the reciprocal pixel 1 / (W pixel) of the propagator
+  char* extra;           // the precise mode's workspace segment
+  int sms;               // SMs of the device (grid sizes of the element-wise kernels)
 };
 
 constexpr int kRedSlots = 8192;

@@ -66,6 +66,8 @@ extern "C" msp_status msp_forward_noalloc(const msp_geometry* g, const float* pr
   if (s != MSP_OK) return s;
   s = refuse_untrusted_device();
   if (s != MSP_OK) return s;
+  if (g->precision != MSP_PRECISION_FP32)
+    return noalloc_fail(MSP_EUNSUPPORTED, "msp_forward_noalloc runs the FP32 forward only; use msp_forward");
   if (g->param != MSP_PARAM_POTENTIAL)
     return noalloc_fail(MSP_EUNSUPPORTED, "msp_forward_noalloc takes potentials only; use msp_forward");
   const size_t cells = (size_t)g->n_slices * g->obj_ny * g->obj_nx;

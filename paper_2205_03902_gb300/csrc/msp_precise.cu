@@ -1,0 +1,430 @@
+// msp_precise.cu -- the precise-forward mode (MSP_PRECISION_FP64_FORWARD).
+//
+// The gradients of Sec. 3.2 are linear in the far-field residual R = Psi - sqrt(I) Psi/|Psi|.
+// Near a fit (the states a reconstruction visits), ||R|| is a small fraction of ||Psi||, so
+// the forward model's rounding, an absolute error of a few units in the last place of Psi,
+// becomes a relative error of R amplified by ||Psi|| / ||R|| (hundreds at the workloads'
+// starting points).  That amplification happens in the forward model alone: the adjoint
+// recursion chi_{m-1} = G^H (conj(X_m) o chi_m) (Sec. 3.3) is linear in R, so its own
+// rounding stays relative to ||R||.  This mode therefore runs the forward model (every
+// transmit, Fresnel propagation and the far-field transform of Sec. 2.1) in FP64, forms R
+// and the loss in FP64, rounds R and the stored exit waves to FP32 once, and runs the
+// adjoint in FP32.  Rounding the far field alone to higher precision does not help: the
+// error is already in the exit wave of the last slice.
+//
+// Layout: positions are taken in batches of B, sized so that one batch's FP64 waves
+// (B W^2 x 16 bytes) stay resident in L2 across the passes over them.  Every operator is
+// its own batched kernel over [B][W][W]:
+//   lines_fft_kernel   W-point DFTs of every row or every column of every wave of the batch
+//                      (radix-2, in shared memory; unnormalised, either direction)
+//   start / transmit   E_1 = P o X_1, E_m = psi_m o X_m, keeping E_m (or psi_m) for the adjoint
+//   propagator         x h(ky, kx) / W^2 (the separable factor h1 of Eq. fresnel_element)
+//   residual           loss, R, intensities
+//   adjoint step       window gradients, conj(X_m) o chi_m, the probe-gradient terms
+// The window gradients land in the same per-position buffers as the fused kernel's, so the
+// overlap-add, the reductions and the updates downstream are shared with the fast path.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "msp.h"
+#include "msp_kernels.cuh"
+
+namespace msp {
+namespace precise {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename C> struct Real;
+template <> struct Real<float2> { using type = float; };
+template <> struct Real<double2> { using type = double; };
+
+template <typename C>
+__device__ __forceinline__ C mk(typename Real<C>::type a, typename Real<C>::type b) {
+  C c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <typename C>
+__device__ __forceinline__ C add(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C>
+__device__ __forceinline__ C sub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C>
+__device__ __forceinline__ C mul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename C>   // a * conj(b)
+__device__ __forceinline__ C mulc(C a, C b) { return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
+
+__device__ __forceinline__ double2 widen(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ float2 narrow(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+__device__ __forceinline__ bool window_ok(int2 ps, int Ny, int Nx, int W) {
+  return ps.x >= 0 && ps.y >= 0 && ps.x <= Ny - W && ps.y <= Nx - W;
+}
+
+// ---------------------------------------------------------------------------
+// batched line DFTs
+// ---------------------------------------------------------------------------
+constexpr int kLines = 8;        // lines per CTA
+constexpr int kFftThreads = 256;
+
+template <int W> struct Log2;
+template <> struct Log2<64> { static constexpr int v = 6; };
+template <> struct Log2<128> { static constexpr int v = 7; };
+template <> struct Log2<256> { static constexpr int v = 8; };
+
+// y_k = sum_n x_n exp(-+2 pi i k n / W) (unnormalised; INV: the + sign) of kLines lines of one
+// wave: rows (ROWS) or columns.  The lines are read in bit-reversed order into shared memory,
+// transformed by log2(W) radix-2 decimation-in-time stages and written back in natural order.
+// Twiddles exp(-+2 pi i k / W), k < W/2, are evaluated in double and, for float2, rounded once.
+// Grid: (W / kLines, batch).
+template <typename C, int W, bool ROWS>
+__global__ void __launch_bounds__(kFftThreads) lines_fft_kernel(C* __restrict__ data, int inverse) {
+  using R = typename Real<C>::type;
+  __shared__ C buf[kLines][W];
+  __shared__ C tw[W / 2];
+  const int tid = threadIdx.x;
+  const int line0 = blockIdx.x * kLines;
+  C* img = data + (size_t)blockIdx.y * W * W;
+  for (int k = tid; k < W / 2; k += kFftThreads) {
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)W, &sn, &cs);
+    tw[k] = mk<C>((R)cs, (R)(inverse ? sn : -sn));
+  }
+  for (int i = tid; i < kLines * W; i += kFftThreads) {
+    // rows: consecutive i run along a row; columns: consecutive i run across the kLines columns
+    const int line = ROWS ? i / W : i % kLines;
+    const int k = ROWS ? i % W : i / kLines;
+    const size_t e = ROWS ? (size_t)(line0 + line) * W + k : (size_t)k * W + line0 + line;
+    buf[line][__brev((unsigned)k) >> (32 - Log2<W>::v)] = img[e];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int half = 1; half < W; half <<= 1) {
+    const int stride = W / (2 * half);   // twiddle index step of this stage
+    for (int b = tid; b < kLines * (W / 2); b += kFftThreads) {
+      const int line = b / (W / 2), j = b % (W / 2);
+      const int q = j % half;
+      const int p0 = (j / half) * 2 * half + q;
+      const C u = buf[line][p0];
+      const C v = mul(buf[line][p0 + half], tw[q * stride]);
+      buf[line][p0] = add(u, v);
+      buf[line][p0 + half] = sub(u, v);
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < kLines * W; i += kFftThreads) {
+    const int line = ROWS ? i / W : i % kLines;
+    const int k = ROWS ? i % W : i / kLines;
+    const size_t e = ROWS ? (size_t)(line0 + line) * W + k : (size_t)k * W + line0 + line;
+    img[e] = buf[line][k];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels over a batch [nb][W][W]
+// ---------------------------------------------------------------------------
+
+// FP64 slice transmissions: exp(i sigma V) from the FP32 potentials, or the caller's complex
+// slices widened.
+__global__ void table64_kernel(const float* __restrict__ V, const float2* __restrict__ X, double2* __restrict__ T,
+                               size_t n, double sigma) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (X) {
+      T[i] = widen(X[i]);
+    } else {
+      double sn, cs;
+      sincos(sigma * (double)V[i], &sn, &cs);
+      T[i] = make_double2(cs, sn);
+    }
+  }
+}
+
+// h1(k) = exp(-i pi dz lambda q_k^2) / W in double (the propagator factor of the fast path
+// before its rounding to single).
+__global__ void h1_64_kernel(double2* __restrict__ h1, int W, double dzlam, double dq) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= W) return;
+  const double q = (double)(k < W / 2 ? k : k - W) * dq;
+  double t = dzlam * q * q;
+  t = t - 2.0 * floor(t * 0.5);
+  double sn, cs;
+  sincospi(t, &sn, &cs);
+  h1[k] = make_double2(cs / W, -sn / W);
+}
+
+struct Batch {
+  const int2* pos;     // positions of this batch (pos + b0)
+  int nb, W, Ny, Nx, L;
+  size_t plane;
+};
+
+// Slice `l` (0: the probe itself is the incident wave) : E = psi o X_l, stashed for the adjoint
+// (the incident psi in transmission mode), in FP32.  A window outside the object gives zeros.
+__global__ void transmit_kernel(Batch bt, int l, const float2* __restrict__ probe, const double2* __restrict__ T,
+                                double2* __restrict__ wave, float2* __restrict__ stash, int stash_l0, int keep,
+                                int cplx) {
+  const int W = bt.W;
+  const size_t WW = (size_t)W * W, n = (size_t)bt.nb * WW;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / WW);
+    const int r = (int)((i % WW) / W), c = (int)(i % W);
+    const int2 ps = bt.pos[b];
+    double2 e = make_double2(0.0, 0.0), psi = e;
+    if (window_ok(ps, bt.Ny, bt.Nx, W)) {
+      psi = l == 0 ? widen(probe[i % WW]) : wave[i];
+      e = mul(psi, T[(size_t)l * bt.plane + (size_t)(ps.x + r) * bt.Nx + ps.y + c]);
+    }
+    wave[i] = e;
+    if (keep) stash[((size_t)b * bt.L + (l - stash_l0)) * WW + (i % WW)] = narrow(cplx ? psi : e);
+  }
+}
+
+// x h1(ky) h1(kx) (CONJ: the conjugate, for G^H) on the spectrum of every wave.
+template <typename C, typename H>
+__global__ void propagator_kernel(Batch bt, const H* __restrict__ h1, C* __restrict__ data, int conj) {
+  const int W = bt.W;
+  const size_t WW = (size_t)W * W, n = (size_t)bt.nb * WW;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int ky = (int)((i % WW) / W), kx = (int)(i % W);
+    C h = mul(mk<C>(h1[ky].x, h1[ky].y), mk<C>(h1[kx].x, h1[kx].y));
+    if (conj) h.y = -h.y;
+    data[i] = mul(data[i], h);
+  }
+}
+
+// Far field Psi (FP64) -> the loss of each position, R = Psi - sqrt(I) Psi / |Psi| (the fraction 0
+// where |Psi|^2 <= thr2) rounded to FP32, or the intensities |Psi|^2.  One CTA per position.
+__global__ void __launch_bounds__(256) residual_kernel(Batch bt, const double2* __restrict__ psi,
+                                                       const float* __restrict__ I_meas, const double* __restrict__ zthr2,
+                                                       float2* __restrict__ R, double* __restrict__ loss_part,
+                                                       float* __restrict__ I_out) {
+  __shared__ double red[8];
+  const int W = bt.W;
+  const size_t WW = (size_t)W * W;
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const bool ok = window_ok(bt.pos[b], bt.Ny, bt.Nx, W);
+  const double thr2 = I_out ? 0.0 : zthr2[0];
+  double acc = 0.0;
+  for (size_t k = tid; k < WW; k += 256) {
+    const double2 v = psi[(size_t)b * WW + k];
+    const double a2 = v.x * v.x + v.y * v.y;
+    if (I_out) {
+      I_out[(size_t)b * WW + k] = (float)a2;
+      continue;
+    }
+    const double a = sqrt(a2), rt = sqrt((double)I_meas[(size_t)b * WW + k]);
+    const double d = rt - a;
+    acc += d * d;
+    const double f = (a2 > thr2) ? 1.0 - rt / a : 1.0;
+    R[(size_t)b * WW + k] = make_float2((float)(v.x * f), (float)(v.y * f));
+  }
+  if (I_out) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    loss_part[b] = ok ? s : 0.0;   // a skipped position contributes nothing (as in the fused kernel)
+  }
+}
+
+// Adjoint at slice l on chi = dL/dconj(E_l) (FP32): the window gradient of slice l
+//   potential mode 2 sigma Im(conj(E_l) chi)  -> wgrad (float), transmission mode conj(psi_l) chi (float2),
+// the illumination |psi_in,l|^2 of a layer step, then chi <- conj(X_l) o chi (if go_on), and at
+// l = 0 the probe-gradient term conj(X_1) o chi_1 of each position.
+struct AdjOut {
+  float* wgrad;        // this slice's window gradients of position s at wgrad + wstride * s (or NULL)
+  size_t wstride;      // floats between consecutive positions' windows
+  float* willum;       // [S][W][W] (layer step) or NULL
+  float2* contrib;     // [nb][W][W] probe-gradient terms (l = 0) or NULL
+  int s0;              // scan index of the batch's first position
+};
+__global__ void adjoint_kernel(Batch bt, int l, float2* __restrict__ chi, const float2* __restrict__ stash_l,
+                               const float2* __restrict__ X, AdjOut o, int go_on, int cplx, float two_sigma) {
+  const int W = bt.W;
+  const size_t WW = (size_t)W * W, n = (size_t)bt.nb * WW;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / WW);
+    const size_t k = i % WW;
+    const int r = (int)(k / W), c = (int)(k % W);
+    const int2 ps = bt.pos[b];
+    const bool ok = window_ok(ps, bt.Ny, bt.Nx, W);
+    float2 v = chi[i];
+    if (!ok) v = make_float2(0.f, 0.f);
+    const size_t s = (size_t)(o.s0 + b);
+    if (o.wgrad || o.willum) {
+      const float2 e = stash_l[(size_t)b * bt.L * WW + k];   // stash_l points at slice l of position 0
+      if (o.wgrad) {
+        if (cplx) reinterpret_cast<float2*>(o.wgrad)[(o.wstride / 2) * s + k] = mulc(v, e);
+        else o.wgrad[o.wstride * s + k] = two_sigma * (e.x * v.y - e.y * v.x);
+      }
+      if (o.willum) o.willum[s * WW + k] = e.x * e.x + e.y * e.y;
+    }
+    if (go_on) {
+      const float2 t = ok ? X[(size_t)l * bt.plane + (size_t)(ps.x + r) * bt.Nx + ps.y + c] : make_float2(0.f, 0.f);
+      v = mulc(v, t);
+      if (l == 0) {
+        if (o.contrib) o.contrib[i] = v;
+      } else {
+        chi[i] = v;
+      }
+    }
+  }
+}
+
+// dp64[k] += sum_{b < nb} contrib[b][k], b ascending (FP64, fixed order).
+__global__ void dprobe_accumulate_kernel(const float2* __restrict__ contrib, int nb, int WW, double2* __restrict__ dp64,
+                                         int first) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= WW) return;
+  double2 a = first ? make_double2(0.0, 0.0) : dp64[k];
+  for (int b = 0; b < nb; ++b) {
+    const float2 v = contrib[(size_t)b * WW + k];
+    a.x += v.x;
+    a.y += v.y;
+  }
+  dp64[k] = a;
+}
+
+__global__ void dprobe_finish_kernel(const double2* __restrict__ dp64, int WW, float2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < WW) out[k] = narrow(dp64[k]);
+}
+
+__global__ void flag_windows_kernel(const int2* __restrict__ pos, int S, int Ny, int Nx, int W, int* err) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x)
+    if (!window_ok(pos[s], Ny, Nx, W)) atomicMax(err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+template <typename C, int W>
+static void fft2(C* data, int nb, bool inverse, cudaStream_t st) {
+  const dim3 grid(W / kLines, nb);
+  lines_fft_kernel<C, W, true><<<grid, kFftThreads, 0, st>>>(data, inverse ? 1 : 0);
+  lines_fft_kernel<C, W, false><<<grid, kFftThreads, 0, st>>>(data, inverse ? 1 : 0);
+}
+
+template <typename C>
+static void fft2_w(int W, C* data, int nb, bool inverse, cudaStream_t st) {
+  if (W == 64) fft2<C, 64>(data, nb, inverse, st);
+  else if (W == 128) fft2<C, 128>(data, nb, inverse, st);
+  else fft2<C, 256>(data, nb, inverse, st);
+}
+
+static int elem_blocks(size_t n, int sms) {
+  const size_t b = (n + 255) / 256, cap = (size_t)sms * 8;
+  return (int)(b < cap ? (b ? b : 1) : cap);
+}
+
+}  // namespace precise
+
+// Positions per batch of the precise mode: one batch's FP64 waves take 64 MiB.
+int precise_batch(int W, int S) {
+  const int b = (int)((size_t(64) << 20) / ((size_t)W * W * sizeof(double2)));
+  return S < b ? (S > 0 ? S : 1) : b;
+}
+
+// Workspace of the precise mode beyond the fast path's (every segment 256-byte aligned).
+size_t precise_extra_bytes(int W, int L, int Ny, int Nx, int S) {
+  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t WW = (size_t)W * W, B = (size_t)precise_batch(W, S);
+  return a((size_t)L * Ny * Nx * sizeof(double2)) + a(W * sizeof(double2)) + a(B * WW * sizeof(double2)) +
+         a(B * WW * sizeof(float2)) + a(B * L * WW * sizeof(float2)) + a(B * WW * sizeof(float2)) +
+         a(WW * sizeof(double2));
+}
+
+// The forward model in FP64 and the FP32 adjoint of `mode` over all positions, writing what the
+// fused kernel writes: I_out (forward), loss_part, the window gradients and illumination, and
+// the probe gradient into dprobe_part[0] (one partial).  Returns the number of kernels launched.
+cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in, cudaStream_t st, long long* launches) {
+  using namespace precise;
+  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int L = p.L, S = p.S;
+  const size_t WW = (size_t)W * W, plane = (size_t)p.Ny * p.Nx;
+  const int B = precise_batch(W, S);
+  char* q = in.extra;
+  double2* T64 = (double2*)q;  q += a((size_t)L * plane * sizeof(double2));
+  double2* h1d = (double2*)q;  q += a(W * sizeof(double2));
+  double2* wave = (double2*)q; q += a((size_t)B * WW * sizeof(double2));
+  float2* chi = (float2*)q;    q += a((size_t)B * WW * sizeof(float2));
+  float2* stash = (float2*)q;  q += a((size_t)B * L * WW * sizeof(float2));
+  float2* contrib = (float2*)q; q += a((size_t)B * WW * sizeof(float2));
+  double2* dp64 = (double2*)q;
+  long long n_launch = 0;
+
+  table64_kernel<<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X, T64,
+                                                                          (size_t)L * plane, in.sigma);
+  h1_64_kernel<<<(W + 255) / 256, 256, 0, st>>>(h1d, W, in.dzlam, in.dq);
+  flag_windows_kernel<<<(S + 255) / 256, 256, 0, st>>>(p.pos, S, p.Ny, p.Nx, W, p.err);
+  n_launch += 3;
+
+  const bool fwd = mode == MODE_FORWARD;
+  const int lowest = mode == MODE_LAYER ? p.layer : 0;
+  const bool want_dprobe = mode != MODE_LAYER && !fwd && p.want_dprobe;
+  const int CW = p.cplx ? 2 : 1;
+  for (int b0 = 0; b0 < S; b0 += B) {
+    const int nb = S - b0 < B ? S - b0 : B;
+    Batch bt{p.pos + b0, nb, W, p.Ny, p.Nx, L, plane};
+    const int eb = elem_blocks((size_t)nb * WW, in.sms);
+    // forward, FP64: slice 0, then (propagate, transmit) for every later slice
+    for (int l = 0; l < L; ++l) {
+      if (l > 0) {
+        fft2_w<double2>(W, wave, nb, false, st);
+        propagator_kernel<double2, double2><<<eb, 256, 0, st>>>(bt, h1d, wave, 0);
+        fft2_w<double2>(W, wave, nb, true, st);
+        n_launch += 5;
+      }
+      const int keep = !fwd && l >= lowest;
+      transmit_kernel<<<eb, 256, 0, st>>>(bt, l, p.probe, T64, wave, stash, 0, keep, p.cplx);
+      ++n_launch;
+    }
+    fft2_w<double2>(W, wave, nb, false, st);   // far field Psi = F(E_L)
+    residual_kernel<<<nb, 256, 0, st>>>(bt, wave, fwd ? nullptr : p.I_meas + (size_t)b0 * WW, p.zthr2, chi,
+                                        fwd ? nullptr : p.loss_part + b0, fwd ? p.I_out + (size_t)b0 * WW : nullptr);
+    n_launch += 3;
+    if (fwd) continue;
+    // adjoint, FP32: chi_L = F^H R, then down the slices
+    fft2_w<float2>(W, chi, nb, true, st);
+    n_launch += 2;
+    for (int l = L - 1; l >= lowest; --l) {
+      const bool grad_here = mode == MODE_LOSS_GRAD || (mode == MODE_LAYER && l == p.layer);
+      const bool go_on = (l > lowest) || (l == 0 && want_dprobe);
+      AdjOut o{};
+      o.s0 = b0;
+      if (grad_here) {
+        o.wgrad = mode == MODE_LOSS_GRAD ? p.wgrad + (size_t)CW * l * WW : p.wgrad;
+        o.wstride = (size_t)CW * WW * (mode == MODE_LOSS_GRAD ? L : 1);
+        if (mode == MODE_LAYER) o.willum = p.willum;
+      }
+      if (l == 0 && want_dprobe) o.contrib = contrib;
+      adjoint_kernel<<<eb, 256, 0, st>>>(bt, l, chi, stash + (size_t)l * WW, p.T, o, go_on ? 1 : 0, p.cplx,
+                                         p.two_sigma);
+      ++n_launch;
+      if (!go_on || l == 0) break;
+      fft2_w<float2>(W, chi, nb, false, st);
+      propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, chi, 1);
+      fft2_w<float2>(W, chi, nb, true, st);
+      n_launch += 5;
+    }
+    if (want_dprobe) {
+      dprobe_accumulate_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(contrib, nb, (int)WW, dp64, b0 == 0);
+      ++n_launch;
+    }
+  }
+  if (want_dprobe) {
+    dprobe_finish_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(dp64, (int)WW, p.dprobe_part);
+    ++n_launch;
+  }
+  *launches = n_launch;
+  return cudaGetLastError();
+}
+
+}  // namespace msp

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmsp.so")
 
 MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EUNSUPPORTED, MSP_ETIMEOUT, MSP_EDEVICE = range(7)
 MSP_PARAM_POTENTIAL, MSP_PARAM_TRANSMISSION = 0, 1
+MSP_PRECISION_FP32, MSP_PRECISION_FP64_FORWARD = 0, 1
 
 
 class MspError(RuntimeError):
@@ -40,6 +41,7 @@ class Geometry(ctypes.Structure):
         ("sigma", ctypes.c_double),
         ("dz_A", ctypes.c_double),
         ("pixel_A", ctypes.c_double),
+        ("precision", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -47,9 +49,9 @@ class Geometry(ctypes.Structure):
 
 
 def geometry(n_slices, obj_ny, obj_nx, win, n_pos, wavelength_A, sigma, dz_A, pixel_A,
-             param=MSP_PARAM_POTENTIAL, **_ignored) -> Geometry:
+             param=MSP_PARAM_POTENTIAL, precision=MSP_PRECISION_FP32, **_ignored) -> Geometry:
     return Geometry(int(n_slices), int(obj_ny), int(obj_nx), int(win), int(n_pos), int(param),
-                    float(wavelength_A), float(sigma), float(dz_A), float(pixel_A))
+                    float(wavelength_A), float(sigma), float(dz_A), float(pixel_A), int(precision))
 
 
 class SmdGeometry(ctypes.Structure):
