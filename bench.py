@@ -1,16 +1,21 @@
-"""Benchmark: fwd+adjoint pattern*slices per second of the layer-wise multislice step.
+"""Benchmark: fwd+adjoint patterns*slices per second of the multislice loss and gradient.
 
-One step is one gradient step of Algorithm 1 (Sec. 3.3) on slice 0 of the
-W = 128, L = 4, S = 1024 workload: transmission, window gather, the multislice
-forward through all four slices, far-field loss and residual, the adjoint back
-through every slice, the atomic-free overlap-add of the slice gradient and of
-the illumination map, the FP64 step-size reduction and the update of V_0.
-value = S * L / (time per step).
+One step is one msp_loss_grad call on the W = 128, L = 4, S = 1024 workload (c2) at the
+reconstruction's starting point (V = 0, the probe guess with a 20 angstrom defocus error,
+Poisson-noisy patterns): the transmissions (Sec. 2.1), the window gather, the multislice forward
+through all four slices, the far-field loss and residual (Sec. 3.2), the adjoint back through
+every slice, the atomic-free overlap-add of every slice's potential gradient and the probe
+gradient sum.  value = S * L / (time per step).  The same run also times, on the same GPU:
+  * the layer step of Algorithm 1 (msp_layer_step: the same pass, one slice's gradient and step);
+  * the plain method to its final loss (msp_reconstruct): c1, 50 sweeps from V = 0 with the known
+    probe; c2, sweeps of the four slice steps and one probe step from the probe guess, in the FP32
+    mode and in the precise-forward mode (time to the final loss, and the final losses);
+  * the full 4096-position, 8-slice workload (c3), and the precise mode's cost per pass.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference] [--config c2|smd_gaas]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference] [--config c2|...]
 
---impl reference times the FP64 CPU oracle on the host cores (a bounded sample
-of the same workload); it is a reported baseline, not the target.
+--impl reference times the FP64 CPU oracle on all the host's cores (a bounded sample of the
+same workload and state per step); it is a reported baseline, not the target.
 
 --config smd_gaas times the paper's second method instead: one iteration of
 Algorithm 2 (Sec. 3.4: one matrix step of Eq. Opt_Prob_Matrix, the proximal step
@@ -40,7 +45,6 @@ from workloads import synth  # noqa: E402
 METRIC = "fwd+adjoint patterns·slices/s"
 UNIT = "pattern·slices/s"
 CFG = synth.C2
-LAYER = 0
 
 
 def fft_flops(S, L, W):
@@ -142,11 +146,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(msp, torch, dev, cfg):
-    """Seeded synthetic specimen, probe guess, raster and Poisson-noisy intensities."""
+def make_inputs(msp, torch, dev, cfg, precision=0):
+    """Seeded synthetic specimen, probe guess, raster and Poisson-noisy intensities (the library's
+    FP32 forward model of the true specimen, then per-position seeded counting noise)."""
     pos = synth.scan_positions(cfg)
     gd = synth.geometry(cfg, n_pos=len(pos))
-    g = msp.geometry(**gd)
+    g = msp.geometry(**gd, precision=precision)
     V_true = synth.potential_slices(cfg).astype(np.float32)
     p_true = synth.probe(cfg).astype(np.complex64)
     p_guess = synth.probe(cfg, defocus_A=cfg.defocus_guess_A or cfg.defocus_A).astype(np.complex64)
@@ -157,53 +162,108 @@ def make_inputs(msp, torch, dev, cfg):
     return g, gd, pos, d_pos, ws, V_true, p_guess, I_meas
 
 
-def cpu_baseline(cfg, budget_s=12.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload's positions."""
+def _oracle_chunk(job):
+    """One worker's share of the CPU baseline: the oracle's loss and gradients over its positions
+    (a process of a spawn pool; one numpy thread per process)."""
+    gd, probe, pos, I, L, obj = job
     from oracle import msp_oracle as O
-    pos = synth.scan_positions(cfg)
+    t0 = time.perf_counter()
+    O.loss_grad(dict(gd, n_pos=len(pos)), probe, pos, I, V=np.zeros((L, obj, obj)))
+    return time.perf_counter() - t0
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def cpu_oracle_rate(cfg, pos, I, probe, budget_s, cores):
+    """pattern*slices/s of the FP64 oracle's loss and gradients (the CPU form of one msp_loss_grad
+    pass) at the reconstruction's starting point, on `cores` processes of a spawn pool (1: this
+    process), on as many positions as fit `budget_s`.  Returns (rate, positions, seconds)."""
     gd = synth.geometry(cfg)
-    V = np.zeros((cfg.n_slices, cfg.obj, cfg.obj))
-    probe = synth.probe(cfg, defocus_A=cfg.defocus_guess_A or cfg.defocus_A)
-    I_fake = np.abs(np.fft.fft2(probe)) ** 2
-    n = 4
-    t_used = 0.0
-    done = 0
-    cpu0 = time.process_time()
-    while True:
-        sub = pos[done:done + n]
-        I = np.broadcast_to(I_fake, (len(sub),) + I_fake.shape)
+    from oracle import msp_oracle as O
+    if cores <= 1:
+        done, t_used, n = 0, 0.0, 2
+        while done < len(pos) and t_used < budget_s:
+            sub = slice(done, min(len(pos), done + n))
+            t0 = time.perf_counter()
+            O.loss_grad(dict(gd, n_pos=sub.stop - sub.start), probe, pos[sub], I[sub],
+                        V=np.zeros((cfg.n_slices, cfg.obj, cfg.obj)))
+            t_used += time.perf_counter() - t0
+            done = sub.stop
+            n = min(2 * n, 64)
+        return done * cfg.n_slices / t_used, done, t_used
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    # positions per worker from a single-position probe of the per-position cost
+    t0 = time.perf_counter()
+    O.loss_grad(dict(gd, n_pos=1), probe, pos[:1], I[:1], V=np.zeros((cfg.n_slices, cfg.obj, cfg.obj)))
+    per = max(time.perf_counter() - t0, 1e-3)
+    k = max(1, min(len(pos) // cores if len(pos) >= cores else 1, int(budget_s / per)))
+    n = min(len(pos), k * cores)
+    jobs = [(gd, probe, pos[i::cores][:k], I[i::cores][:k], cfg.n_slices, cfg.obj) for i in range(cores)]
+    jobs = [j for j in jobs if len(j[2])]
+    with ctx.Pool(len(jobs), initializer=_single_thread_env) as pool:
+        pool.map(_oracle_chunk, jobs[:1])          # start-up (imports) outside the timing
         t0 = time.perf_counter()
-        O.layer_step(dict(gd, n_pos=len(sub)), probe, sub, I, LAYER, V=V)
-        t_used += time.perf_counter() - t0
-        done += len(sub)
-        if t_used > budget_s or done >= len(pos):
-            break
-        n = min(len(pos) - done, max(4, int(n * 2)))
-    cores = max(1, round((time.process_time() - cpu0) / max(t_used, 1e-9)))
-    return {"value": done * cfg.n_slices / t_used, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {len(pos)} scan positions of {cfg.name}, FP64 numpy oracle layer step "
-                      f"(slice {LAYER}), {t_used:.1f} s; cores = process CPU time / wall time"}
+        pool.map(_oracle_chunk, jobs)
+        dt = time.perf_counter() - t0
+    return n * cfg.n_slices / dt, n, dt
+
+
+def cpu_baseline(cfg, pos, I, probe, budget_s=10.0):
+    """The FP64 oracle, as it stands, on the host: one thread, and all host cores (a spawn pool over
+    positions), each on a bounded sample of the workload's positions at the GPU arm's state."""
+    nproc = os.cpu_count() or 1
+    r1, n1, t1 = cpu_oracle_rate(cfg, pos, I, probe, budget_s, 1)
+    ra, na, ta = cpu_oracle_rate(cfg, pos, I, probe, budget_s, nproc)
+    return {"value": ra, "unit": UNIT, "cores": nproc, "kind": "oracle", "nproc": nproc,
+            "sample": f"FP64 numpy oracle loss and gradients (all slices, probe) at V = 0 with the probe guess and "
+                      f"the GPU arm's measured patterns: {na} of {len(pos)} positions of {cfg.name} on {nproc} "
+                      f"processes ({ta:.1f} s); single thread: {n1} positions ({t1:.1f} s)",
+            "single_thread": {"value": r1, "unit": UNIT, "cores": 1, "positions": n1, "seconds": t1},
+            "all_cores": {"value": ra, "unit": UNIT, "cores": nproc, "positions": na, "seconds": ta}}
+
+
+def reference_state(cfg, idx):
+    """The measured patterns of scan positions `idx` of the workload, made on the host by the oracle
+    (the GPU arm makes the same patterns with the library's forward model), with the same
+    per-position counting noise, and the probe guess."""
+    from oracle import msp_oracle as O
+    pos = synth.scan_positions(cfg)[idx]
+    gd = synth.geometry(cfg, n_pos=len(pos))
+    I = O.forward(gd, synth.probe(cfg).astype(np.complex64), pos, V=synth.potential_slices(cfg).astype(np.float32))
+    I = synth.poisson_counts(I, cfg.dose, cfg.seed, index=idx).astype(np.float32)
+    probe = synth.probe(cfg, defocus_A=cfg.defocus_guess_A or cfg.defocus_A).astype(np.complex64)
+    return pos, I, probe
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    cfg = CFG
+    nproc = os.cpu_count() or 1
+    # a sample of positions spread over the scan, patterns made once (outside the steps)
+    idx = np.linspace(0, cfg.n_pos - 1, min(cfg.n_pos, 32 * nproc)).astype(int)
+    pos, I, probe = reference_state(cfg, idx)
     per_step = []
-    base = None
+    budget = max(0.5, 120.0 / max(1, args.steps + args.warmup))
     for i in range(args.warmup + args.steps):
-        # the whole run stays near 90 s: each step times a bounded sample of positions
-        r = cpu_baseline(CFG, budget_s=max(0.05, 90.0 / max(1, args.steps + args.warmup)))
+        r, n, dt = cpu_oracle_rate(cfg, pos, I, probe, budget, nproc)
         if i >= args.warmup:
-            per_step.append(r["value"])
-            base = r
+            per_step.append(r)
     value = float(np.median(per_step))
+    base = {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": f"per step, up to {n} of {cfg.n_pos} positions of {cfg.name} (spread over the scan) on {nproc} "
+                      f"processes: FP64 numpy oracle loss and gradients at V = 0 with the probe guess"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": CFG.n_pos * CFG.n_slices / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": cfg.n_pos * cfg.n_slices / value * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": CFG.name, "call": "oracle.layer_step(slice 0)",
-                       "parallelism": f"cpu, {base['cores']} cores busy"},
-            "cpu_baseline": dict(base, value=value),
+            "config": {"workload": cfg.name, "call": "oracle.loss_grad (all slices and the probe)",
+                       "parallelism": f"cpu, {nproc} processes"},
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -575,6 +635,45 @@ def run_dft(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def time_events(fn, n, stream, flush=None):
+    """Mean ms of fn() over n calls, CUDA events on `stream`, L2 flushed before each (outside)."""
+    import torch
+    ms = 0.0
+    for i in range(n):
+        if flush is not None:
+            flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    return ms / n
+
+
+def plain_method_run(msp, torch, dev, cfg, sweeps, probe_steps, precision, stream):
+    """Time to the plain method's final loss: msp_reconstruct from V = 0 and the workload's probe
+    guess (the true probe when it is known), CUDA events around the whole call."""
+    g, gd, pos, d_pos, ws, V_true, p_guess, I_meas = make_inputs(msp, torch, dev, cfg, precision)
+    I = torch.from_numpy(I_meas).to(dev)
+    plan = msp.plan(sweeps, probe_steps=probe_steps)
+    out = {}
+    for rep in range(2):                       # the first run warms up
+        V = torch.zeros((cfg.n_slices, cfg.obj, cfg.obj), dtype=torch.float32, device=dev)
+        p = torch.from_numpy(p_guess).to(dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        h = msp.reconstruct(g, plan, p, V, d_pos, I, ws=ws)
+        b.record(stream)
+        b.synchronize()
+        out = {"ms": a.elapsed_time(b), "sweeps": sweeps, "probe_steps_per_sweep": probe_steps,
+               "passes": int(sweeps * (cfg.n_slices + probe_steps) + 1),
+               "loss_first": float(h[0].item()), "loss_final": float(h[-1].item())}
+    out["precision"] = "fp64_forward" if precision else "fp32"
+    return out
+
+
 def run_msp(args, rank, world, local_rank):
     import torch
     from paper_2205_03902_gb300 import msp
@@ -596,17 +695,17 @@ def run_msp(args, rank, world, local_rank):
     V = torch.zeros((L, cfg.obj, cfg.obj), dtype=torch.float32, device=dev)   # Alg. 1 starts from V = 0
     I_meas = torch.from_numpy(I_meas_h).to(dev)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
-    mu = torch.empty(1, dtype=torch.float64, device=dev)
+    dV = torch.empty_like(V)
+    dprobe = torch.empty_like(probe)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
     stream = torch.cuda.current_stream()
 
     def step():
-        msp.layer_step(g, probe, V, d_pos, I_meas, LAYER, ws=ws, loss_before=loss, mu=mu)
+        msp.loss_grad(g, probe, V, d_pos, I_meas, ws=ws, loss=loss, dV=dV, dprobe=dprobe)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    loss_first = float(loss.item())
 
     msp.profile_read(reset=True)
     msp.profile_enable(True)
@@ -624,32 +723,33 @@ def run_msp(args, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = sampler.stop()
     prof = msp.profile_read(reset=True)
     msp.profile_enable(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(float(sum(step_ms)), dist, dev)
     ms_per_step = total_ms / args.steps
     value = job_throughput(world, S * L, ms_per_step)
+    loss_step = float(loss.item())
 
     # ---- end to end through the public API with host buffers (pinned), copies timed ----
-    # Every step copies its inputs from pinned host memory and reads its result (the
-    # updated slice and the FP64 loss / step size) back.  As a caller would, the copy of
+    # Every step copies its inputs (patterns, potentials, probe, positions) from pinned host
+    # memory and reads its results (dV, dprobe, loss) back.  As a caller would, the copy of
     # step k+1's inputs runs on a copy stream while step k computes (two input sets).
     h_I = torch.from_numpy(I_meas_h).pin_memory()
     h_V = torch.zeros((L, cfg.obj, cfg.obj), dtype=torch.float32).pin_memory()
     h_p = torch.from_numpy(p_guess).pin_memory()
     h_pos = torch.from_numpy(pos).pin_memory()
-    h_out = [torch.empty((cfg.obj, cfg.obj), dtype=torch.float32).pin_memory() for _ in range(2)]
-    h_scal = [torch.empty(2, dtype=torch.float64).pin_memory() for _ in range(2)]
+    h_dV = [torch.empty_like(h_V).pin_memory() for _ in range(2)]
+    h_dp = [torch.empty_like(h_p).pin_memory() for _ in range(2)]
+    h_loss = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
     sets = [dict(I=torch.empty_like(I_meas), V=torch.empty_like(V), p=torch.empty_like(probe),
-                 pos=torch.empty_like(d_pos), scal=torch.empty(2, dtype=torch.float64, device=dev))
-            for _ in range(2)]
+                 pos=torch.empty_like(d_pos), loss=torch.empty(1, dtype=torch.float64, device=dev),
+                 dV=torch.empty_like(V), dp=torch.empty_like(probe)) for _ in range(2)]
     copy_stream = torch.cuda.Stream(dev)
     ev_copy = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
     h2d = h_I.numel() * 4 + h_V.numel() * 4 + h_p.numel() * 8 + h_pos.numel() * 4
-    d2h = h_out[0].numel() * 4 + h_scal[0].numel() * 8
+    d2h = h_dV[0].numel() * 4 + h_dp[0].numel() * 8 + 8
 
     def issue_copy(k):
         b = sets[k % 2]
@@ -665,10 +765,10 @@ def run_msp(args, rank, world, local_rank):
     def issue_step(k):
         b = sets[k % 2]
         stream.wait_event(ev_copy[k % 2])
-        msp.layer_step(g, b["p"], b["V"], b["pos"], b["I"], LAYER, ws=ws, loss_before=b["scal"][0:1],
-                       mu=b["scal"][1:2])
-        h_out[k % 2].copy_(b["V"][LAYER], non_blocking=True)
-        h_scal[k % 2].copy_(b["scal"], non_blocking=True)
+        msp.loss_grad(g, b["p"], b["V"], b["pos"], b["I"], ws=ws, loss=b["loss"], dV=b["dV"], dprobe=b["dp"])
+        h_dV[k % 2].copy_(b["dV"], non_blocking=True)
+        h_dp[k % 2].copy_(b["dp"], non_blocking=True)
+        h_loss[k % 2].copy_(b["loss"], non_blocking=True)
         ev_done[k % 2].record(stream)
 
     e_steps = max(3, min(args.steps, 50))
@@ -683,13 +783,66 @@ def run_msp(args, rank, world, local_rank):
         issue_step(k)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e_steps
-    assert np.isfinite(h_scal[e_steps % 2].numpy()).all()
+    assert np.isfinite(h_loss[e_steps % 2].numpy()).all()
     e2e_value = job_throughput(world, S * L, 1e3 * max_over_ranks(e2e_s, dist, dev))
 
     if rank != 0:
+        sampler.stop()
         if dist:
             dist.destroy_process_group()
         return
+
+    # ---- further measurements of this run (rank 0), clocks still sampled ----
+    extra = {}
+    if not args.quick:
+        # the layer step of Algorithm 1 on the same state
+        Vl = torch.zeros_like(V)
+        lb, mu = torch.empty(1, dtype=torch.float64, device=dev), torch.empty(1, dtype=torch.float64, device=dev)
+        msp.profile_read(reset=True)
+        msp.profile_enable(True)
+        lms = time_events(lambda: msp.layer_step(g, probe, Vl, d_pos, I_meas, 0, ws=ws, loss_before=lb, mu=mu),
+                          10, stream, flush)
+        pl = msp.profile_read(reset=True)
+        msp.profile_enable(False)
+        extra["layer_step"] = {"call": "msp_layer_step(layer=0, auto step)", "ms": lms,
+                               "value": S * L / (lms * 1e-3), "unit": UNIT,
+                               "fused_kernel_ms": pl["fused_ms"] / max(1, pl["fused_launches"])}
+        # the precise-forward mode's cost per pass on the same state
+        gp = msp.geometry(**gd, precision=msp.MSP_PRECISION_FP64_FORWARD)
+        wsp = msp.make_workspace(gp, dev)
+        pms = time_events(lambda: msp.loss_grad(gp, probe, V, d_pos, I_meas, ws=wsp), 3, stream, flush)
+        extra["precise_forward"] = {"call": "msp_loss_grad, MSP_PRECISION_FP64_FORWARD", "ms": pms,
+                                    "value": S * L / (pms * 1e-3), "unit": UNIT, "cost_vs_fp32": pms / ms_per_step}
+        del wsp
+        # the plain method to its final loss
+        extra["plain_method"] = {
+            "c1_known_probe": plain_method_run(msp, torch, dev, synth.C1, 50, 0, 0, stream),
+            "c2_probe_estimation_fp32": plain_method_run(msp, torch, dev, cfg, 20, 1, 0, stream),
+            "c2_probe_estimation_precise": plain_method_run(msp, torch, dev, cfg, 20, 1, 1, stream),
+        }
+        a, b = (extra["plain_method"]["c2_probe_estimation_fp32"], extra["plain_method"]["c2_probe_estimation_precise"])
+        extra["plain_method"]["c2_fp32_vs_precise"] = {
+            "final_loss_rel_diff": abs(a["loss_final"] - b["loss_final"]) / b["loss_final"],
+            "time_ratio_precise_over_fp32": b["ms"] / a["ms"]}
+        # the full 8-slice, 4096-position workload
+        c3 = synth.C3
+        g3, gd3, pos3, d_pos3, ws3, _, p3g, I3 = make_inputs(msp, torch, dev, c3)
+        p3 = torch.from_numpy(p3g).to(dev)
+        V3 = torch.zeros((c3.n_slices, c3.obj, c3.obj), dtype=torch.float32, device=dev)
+        I3d = torch.from_numpy(I3).to(dev)
+        msp.loss_grad(g3, p3, V3, d_pos3, I3d, ws=ws3)
+        msp.profile_read(reset=True)
+        msp.profile_enable(True)
+        c3ms = time_events(lambda: msp.loss_grad(g3, p3, V3, d_pos3, I3d, ws=ws3), 5, stream, flush)
+        p3p = msp.profile_read(reset=True)
+        msp.profile_enable(False)
+        k3 = p3p["fused_ms"] / max(1, p3p["fused_launches"])
+        extra["c3_full"] = {"workload": c3.name, "call": "msp_loss_grad", "ms": c3ms,
+                            "value": c3.n_pos * c3.n_slices / (c3ms * 1e-3), "unit": UNIT, "fused_kernel_ms": k3,
+                            "fused_kernel_tflops": fft_flops(c3.n_pos, c3.n_slices, c3.win) / (k3 * 1e-3) / 1e12}
+        del ws3
+    clocks = sampler.stop()
+    clocks["window"] = "the timed steps and the measurements of this run that follow them"
 
     peaks = read_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -697,28 +850,30 @@ def run_msp(args, rank, world, local_rank):
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x clock
     fused_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
     achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
-    traffic = measured_traffic("position_kernel") if cfg is synth.C2 else None
+    kname = "position_kernel<128, LOSS_GRAD>" if W == 128 else ("position_cluster_kernel<LOSS_GRAD>" if W == 256
+                                                                 else f"position_kernel<{W}, LOSS_GRAD>")
+    traffic = measured_traffic("position_kernel_loss_grad") if cfg is synth.C2 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": cfg.name, "call": f"msp_layer_step(layer={LAYER}, auto step)",
+        "config": {"workload": cfg.name, "call": "msp_loss_grad (loss, dV of every slice, dprobe)",
                    "positions": S, "slices": L, "window": W, "object": [cfg.obj, cfg.obj],
+                   "state": "V = 0, probe guess (20 A defocus error), Poisson-noisy patterns",
                    "l2": "flushed between timed steps (256 MiB write outside the step events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
-                     "kernel": ("position_cluster_kernel<LAYER> (fused fwd+adjoint, 4-CTA cluster)" if W == 256
-                   else f"position_kernel<{W}, LAYER> (fused fwd+adjoint)"),
-                     "kernel_ms": fused_ms,
+                     "kernel": kname + " (fused fwd+adjoint)", "kernel_ms": fused_ms,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["all_launches"]),
         "clocks": clocks,
-        "loss_first_timed_step": loss_first,
+        "loss_timed_step": loss_step,
     }
+    line.update(extra)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg)
+        line["cpu_baseline"] = cpu_baseline(cfg, pos, I_meas_h, p_guess)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -758,6 +913,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="the timed loss/gradient steps and e2e only")
     ap.add_argument("--config", default="c2",
                     choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3", "peaks"],
                     help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration; "

@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
           if (ILLUM) o1 = sbase1[q] + pix;
         }
         const bool in = ((unsigned)(px - pq.y) < (unsigned)W) && ((unsigned)(py - pq.x) < (unsigned)W);
-        if (CPLX) v0[u] = in ? reinterpret_cast<const float2*>(src0)[o0] : make_float2(0.f, 0.f);
-        else v0[u] = make_float2(in ? src0[o0] : 0.f, 0.f);
-        if (ILLUM) v1[u] = in ? src1[o1] : 0.f;
+        if (CPLX) v0[u] = in ? __ldcs(reinterpret_cast<const float2*>(src0) + o0) : make_float2(0.f, 0.f);
+        else v0[u] = make_float2(in ? __ldcs(src0 + o0) : 0.f, 0.f);
+        if (ILLUM) v1[u] = in ? __ldcs(src1 + o1) : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -233,17 +233,45 @@ __global__ void __launch_bounds__(256) sum_blocks_kernel(const float* __restrict
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// dprobe[i] = sum_b part[b][i] in CTA order (FP64 accumulation).
-__global__ void dprobe_reduce_kernel(const float2* __restrict__ part, int G, int WW, float2* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= WW) return;
+// dprobe[i] = sum_b part[b][i] (FP64 accumulation, fixed order).  A block of 256 threads owns 32
+// consecutive probe values: warp g sums the partials b = g, g + 8, g + 16, ... (lane = value, so
+// every load is 256 contiguous bytes), four loads in flight per thread, and the eight warp sums
+// are added in warp order.  512 blocks for W = 128 keep every SM loading.
+constexpr int kDprobeVals = 32;
+__global__ void __launch_bounds__(256) dprobe_reduce_kernel(const float2* __restrict__ part, int G, int WW,
+                                                            float2* __restrict__ out) {
+  __shared__ double2 acc_w[8][kDprobeVals];
+  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int i = blockIdx.x * kDprobeVals + lane;
   double re = 0.0, im = 0.0;
-  for (int b = 0; b < G; ++b) {
-    const float2 v = part[(size_t)b * WW + i];
-    re += v.x;
-    im += v.y;
+  if (i < WW) {
+    int b = g;
+    for (; b + 24 < G; b += 32) {
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldcs(part + (size_t)(b + 8 * u) * WW + i);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        re += v[u].x;
+        im += v[u].y;
+      }
+    }
+    for (; b < G; b += 8) {
+      const float2 v = __ldcs(part + (size_t)b * WW + i);
+      re += v.x;
+      im += v.y;
+    }
   }
-  out[i] = make_float2((float)re, (float)im);
+  acc_w[g][lane] = make_double2(re, im);
+  __syncthreads();
+  if (g == 0 && i < WW) {
+    double2 t = acc_w[0][lane];
+    for (int w = 1; w < 8; ++w) {
+      t.x += acc_w[w][lane].x;
+      t.y += acc_w[w][lane].y;
+    }
+    out[i] = make_float2((float)t.x, (float)t.y);
+  }
 }
 
 // Step size of a layer step: mu = step, or 1 / (c W^2 max illumination) with c = 2 sigma^2
@@ -757,7 +785,7 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   counted();
   }
   if (dprobe) {
-    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
+    dprobe_reduce_kernel<<<(int)((WW + kDprobeVals - 1) / kDprobeVals), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
                                                                    (float2*)dprobe);
     MSP_CK(cudaGetLastError());
   counted();
@@ -853,7 +881,7 @@ msp_status msp_probe_step(const msp_geometry* g, float* probe, const float* V, c
     p.I_meas = I_meas;
     p.want_dprobe = 1;
     MSP_TRY(run_position(g, MODE_PROBE, p, c));
-    dprobe_reduce_kernel<<<(int)((WW + 255) / 256), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
+    dprobe_reduce_kernel<<<(int)((WW + kDprobeVals - 1) / kDprobeVals), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
                                                                    c.ws.dprobe_sum);
     MSP_CK(cudaGetLastError());
   counted();

@@ -26,7 +26,10 @@
 // The only per-slice global traffic is the transmission window (read), the exit
 // wave of each slice (written to this CTA's stash slot on the way forward, read
 // back on the way down; the slots are reused position after position so they
-// stay L2-resident) and the per-position window gradient.
+// stay L2-resident) and the per-position window gradient.  The data each position
+// touches once (measured pattern, window gradients, illumination) is loaded and
+// stored with the evict-first (streaming) cache hint, so that it does not push the
+// stash slots out of L2.
 #include "msp_fft.cuh"
 #include "msp_kernels.cuh"
 
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           if (MODE != MODE_FORWARD) {
             const float* ip = p.I_meas + s * WW + c;
 #pragma unroll
-            for (int m = 0; m < N1; ++m) im[m] = ip[(j + 8 * m) * W];   // in flight during the transform
+            for (int m = 0; m < N1; ++m) im[m] = __ldcs(ip + (j + 8 * m) * W);   // read once: evict first; in flight during the transform
           }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = sm[ca(m)];
@@ -308,15 +311,15 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
             // dL/dconj(o_l) on the window: conj(psi_in,l) o chi_l
             float2* wg2 = reinterpret_cast<float2*>(wg) + r * W + j;
 #pragma unroll
-            for (int m = 0; m < N1; ++m) wg2[8 * m] = cmulc(v[m], e[m]);
+            for (int m = 0; m < N1; ++m) __stcs(wg2 + 8 * m, cmulc(v[m], e[m]));
           } else {
             // dL/dV_l on the window: 2 sigma Im(conj(E_l) chi_l)
 #pragma unroll
-            for (int m = 0; m < N1; ++m) wg[r * W + j + 8 * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
+            for (int m = 0; m < N1; ++m) __stcs(wg + r * W + j + 8 * m, p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x));
           }
           if (MODE == MODE_LAYER) {   // |psi_in,l|^2 (= |E_l|^2 for unimodular slices)
 #pragma unroll
-            for (int m = 0; m < N1; ++m) p.willum[s * WW + r * W + j + 8 * m] = fmaf(e[m].x, e[m].x, e[m].y * e[m].y);
+            for (int m = 0; m < N1; ++m) __stcs(p.willum + s * WW + r * W + j + 8 * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));
           }
         }
         if (go_on) {

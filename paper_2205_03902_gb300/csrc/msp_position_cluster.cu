@@ -193,7 +193,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
           if (MODE != MODE_FORWARD) {
             const float* ip = p.I_meas + s * WW + c;
 #pragma unroll
-            for (int m = 0; m < N1; ++m) im[m] = ip[(size_t)(j + T * m) * W];
+            for (int m = 0; m < N1; ++m) im[m] = __ldcs(ip + (size_t)(j + T * m) * W);   // read once: evict first
           }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = rows[m >> 2][cix(c, m)];
@@ -259,16 +259,16 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
           if (CPLX) {
             float2* wg2 = reinterpret_cast<float2*>(wg) + (size_t)gr * W + j;
 #pragma unroll
-            for (int m = 0; m < N1; ++m) wg2[T * m] = cmulc(v[m], e[m]);
+            for (int m = 0; m < N1; ++m) __stcs(wg2 + T * m, cmulc(v[m], e[m]));
           } else {
 #pragma unroll
             for (int m = 0; m < N1; ++m)
-              wg[(size_t)gr * W + j + T * m] = p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x);
+              __stcs(wg + (size_t)gr * W + j + T * m, p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x));
           }
           if (MODE == MODE_LAYER) {
 #pragma unroll
             for (int m = 0; m < N1; ++m)
-              p.willum[s * WW + (size_t)gr * W + j + T * m] = fmaf(e[m].x, e[m].x, e[m].y * e[m].y);
+              __stcs(p.willum + s * WW + (size_t)gr * W + j + T * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));
           }
         }
         if (go_on) {
