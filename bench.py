@@ -670,7 +670,7 @@ def plain_method_run(msp, torch, dev, cfg, sweeps, probe_steps, precision, strea
         out = {"ms": a.elapsed_time(b), "sweeps": sweeps, "probe_steps_per_sweep": probe_steps,
                "passes": int(sweeps * (cfg.n_slices + probe_steps) + 1),
                "loss_first": float(h[0].item()), "loss_final": float(h[-1].item())}
-    out["precision"] = "fp64_forward" if precision else "fp32"
+    out["precision"] = {0: "fp32", 1: "fp64_forward", 2: "split_bf16_dft"}[precision]
     return out
 
 
@@ -814,16 +814,35 @@ def run_msp(args, rank, world, local_rank):
         extra["precise_forward"] = {"call": "msp_loss_grad, MSP_PRECISION_FP64_FORWARD", "ms": pms,
                                     "value": S * L / (pms * 1e-3), "unit": UNIT, "cost_vs_fp32": pms / ms_per_step}
         del wsp
+        # the split-BF16 precision form (tensor-core DFT passes) on the same state
+        gb = msp.geometry(**gd, precision=msp.MSP_PRECISION_BF16X3_DFT)
+        wsb = msp.make_workspace(gb, dev)
+        msp.loss_grad(gb, probe, V, d_pos, I_meas, ws=wsb)
+        msp.profile_read(reset=True)
+        msp.profile_enable(True)
+        bms = time_events(lambda: msp.loss_grad(gb, probe, V, d_pos, I_meas, ws=wsb), 5, stream, flush)
+        msp.profile_enable(False)
+        extra["split_bf16_dft"] = {"call": "msp_loss_grad, MSP_PRECISION_BF16X3_DFT", "ms": bms,
+                                   "value": S * L / (bms * 1e-3), "unit": UNIT, "cost_vs_fp32": bms / ms_per_step}
+        del wsb
         # the plain method to its final loss
-        extra["plain_method"] = {
+        pm = {
             "c1_known_probe": plain_method_run(msp, torch, dev, synth.C1, 50, 0, 0, stream),
             "c2_probe_estimation_fp32": plain_method_run(msp, torch, dev, cfg, 20, 1, 0, stream),
             "c2_probe_estimation_precise": plain_method_run(msp, torch, dev, cfg, 20, 1, 1, stream),
+            "c2_probe_estimation_split_bf16": plain_method_run(msp, torch, dev, cfg, 20, 1, 2, stream),
+            "c3_probe_estimation_fp32": plain_method_run(msp, torch, dev, synth.C3, 5, 1, 0, stream),
+            "c3_probe_estimation_split_bf16": plain_method_run(msp, torch, dev, synth.C3, 5, 1, 2, stream),
         }
-        a, b = (extra["plain_method"]["c2_probe_estimation_fp32"], extra["plain_method"]["c2_probe_estimation_precise"])
-        extra["plain_method"]["c2_fp32_vs_precise"] = {
-            "final_loss_rel_diff": abs(a["loss_final"] - b["loss_final"]) / b["loss_final"],
-            "time_ratio_precise_over_fp32": b["ms"] / a["ms"]}
+
+        def versus(a, b):   # form b against the FP32 form a: final loss and time
+            return {"final_loss_rel_diff": abs(pm[a]["loss_final"] - pm[b]["loss_final"]) / pm[a]["loss_final"],
+                    "time_ratio_over_fp32": pm[b]["ms"] / pm[a]["ms"]}
+
+        pm["c2_precise_vs_fp32"] = versus("c2_probe_estimation_fp32", "c2_probe_estimation_precise")
+        pm["c2_split_bf16_vs_fp32"] = versus("c2_probe_estimation_fp32", "c2_probe_estimation_split_bf16")
+        pm["c3_split_bf16_vs_fp32"] = versus("c3_probe_estimation_fp32", "c3_probe_estimation_split_bf16")
+        extra["plain_method"] = pm
         # the full 8-slice, 4096-position workload
         c3 = synth.C3
         g3, gd3, pos3, d_pos3, ws3, _, p3g, I3 = make_inputs(msp, torch, dev, c3)
@@ -841,6 +860,13 @@ def run_msp(args, rank, world, local_rank):
                             "value": c3.n_pos * c3.n_slices / (c3ms * 1e-3), "unit": UNIT, "fused_kernel_ms": k3,
                             "fused_kernel_tflops": fft_flops(c3.n_pos, c3.n_slices, c3.win) / (k3 * 1e-3) / 1e12}
         del ws3
+        g3b = msp.geometry(**gd3, precision=msp.MSP_PRECISION_BF16X3_DFT)
+        ws3b = msp.make_workspace(g3b, dev)
+        msp.loss_grad(g3b, p3, V3, d_pos3, I3d, ws=ws3b)
+        c3b = time_events(lambda: msp.loss_grad(g3b, p3, V3, d_pos3, I3d, ws=ws3b), 3, stream, flush)
+        extra["c3_full"]["split_bf16_dft"] = {"ms": c3b, "value": c3.n_pos * c3.n_slices / (c3b * 1e-3),
+                                              "cost_vs_fp32": c3b / c3ms}
+        del ws3b
     clocks = sampler.stop()
     clocks["window"] = "the timed steps and the measurements of this run that follow them"
 

@@ -79,15 +79,21 @@ typedef enum {
  * transmissions o_m (the paper's parametrisation). */
 enum { MSP_PARAM_POTENTIAL = 0, MSP_PARAM_TRANSMISSION = 1 };
 
-/* Arithmetic of the forward model and the residual.
+/* Arithmetic of the forward model, the residual and the adjoint.
  *   MSP_PRECISION_FP32: everything in FP32 in the fused per-position kernel (the fast path).
  *   MSP_PRECISION_FP64_FORWARD: the forward model (transmit, Fresnel propagation, far field,
  *     Sec. 2.1) and the residual R = Psi - sqrt(I) Psi/|Psi| and loss (Sec. 3.2) in FP64, R
  *     and the stored exit waves rounded to FP32 once, the adjoint in FP32.  Near a fit the
  *     gradient is a small difference of far-field amplitudes, so the FP32 forward's rounding
  *     is amplified by ||Psi|| / ||R||; this mode removes that amplification.  Slower (GB300's
- *     FP64 rate is 1/64 of its FP32 rate) and with a larger workspace. */
-enum { MSP_PRECISION_FP32 = 0, MSP_PRECISION_FP64_FORWARD = 1 };
+ *     FP64 rate is 1/64 of its FP32 rate) and with a larger workspace.
+ *   MSP_PRECISION_BF16X3_DFT: the split-BF16 precision form.  Every 2-D Fourier transform of
+ *     the forward model and of the adjoint is two passes of the W-point DFT as a matrix
+ *     product on the tensor cores (the matrix-product form of the propagation that Sec. 6
+ *     suggests), operands split into bf16 pairs x = hi + lo and multiplied as
+ *     hi*hi + hi*lo + lo*hi with FP32 accumulation; waves in FP32, loss and probe-gradient
+ *     sums in FP64.  About 2^-16 relative error per product. */
+enum { MSP_PRECISION_FP32 = 0, MSP_PRECISION_FP64_FORWARD = 1, MSP_PRECISION_BF16X3_DFT = 2 };
 
 /* Statement of the problem (Sec. 2.1).  Supported windows: W = 64, 128 or 256 (W = 256 runs
  * each position on a four-CTA thread-block cluster). */
@@ -102,7 +108,7 @@ typedef struct {
   double sigma;         /* interaction constant, rad / (V angstrom)               */
   double dz_A;          /* slice separation = Fresnel distance Delta (Eq. fresnel_element) */
   double pixel_A;       /* real-space pixel size in angstrom                       */
-  int32_t precision;    /* MSP_PRECISION_FP32 or MSP_PRECISION_FP64_FORWARD         */
+  int32_t precision;    /* MSP_PRECISION_FP32, _FP64_FORWARD or _BF16X3_DFT         */
 } msp_geometry;
 
 /* Checks a geometry on the host.  MSP_OK, MSP_EINVAL or MSP_EUNSUPPORTED. */

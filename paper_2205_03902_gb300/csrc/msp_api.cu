@@ -29,7 +29,7 @@ cudaError_t launch_position_kernel(int win, int mode, const PosParams& p, int gr
 int position_slots(int win);
 
 // the precise-forward mode (msp_precise.cu)
-size_t precise_extra_bytes(int W, int L, int Ny, int Nx, int S);
+size_t precise_extra_bytes(int precision, int W, int L, int Ny, int Nx, int S);
 cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in, cudaStream_t st, long long* launches);
 
 // ---------------------------------------------------------------------------
@@ -520,8 +520,9 @@ static msp_status check_geometry(const msp_geometry* g) {
   if (!(std::isfinite(g->pixel_A) && g->pixel_A > 0)) return fail(MSP_EINVAL, "pixel size must be > 0");
   if (!(std::isfinite(g->dz_A) && g->dz_A >= 0)) return fail(MSP_EINVAL, "slice thickness must be >= 0");
   if (!std::isfinite(g->sigma)) return fail(MSP_EINVAL, "sigma must be finite");
-  if (g->precision != MSP_PRECISION_FP32 && g->precision != MSP_PRECISION_FP64_FORWARD)
-    return fail(MSP_EINVAL, "precision must be MSP_PRECISION_FP32 or MSP_PRECISION_FP64_FORWARD");
+  if (g->precision != MSP_PRECISION_FP32 && g->precision != MSP_PRECISION_FP64_FORWARD &&
+      g->precision != MSP_PRECISION_BF16X3_DFT)
+    return fail(MSP_EINVAL, "precision must be MSP_PRECISION_FP32, _FP64_FORWARD or _BF16X3_DFT");
   const double cells = (double)g->n_slices * g->obj_ny * g->obj_nx;
   if (cells > 4.0e9) return fail(MSP_EUNSUPPORTED, "object too large");
   if ((size_t)((g->obj_nx + kGatherTX - 1) / kGatherTX) * ((g->obj_ny + kGatherTY - 1) / kGatherTY) > (size_t)kRedSlots)
@@ -539,7 +540,8 @@ static int grid_cap(const DevInfo& d, int win) {
 static int loss_slots(const msp_geometry* g) {
   return (g->win == 256 && g->precision == MSP_PRECISION_FP32) ? 4 : 1;
 }
-static bool precise(const msp_geometry* g) { return g->precision == MSP_PRECISION_FP64_FORWARD; }
+// The FP64-forward and split-BF16 modes run the batched path (msp_precise.cu).
+static bool precise(const msp_geometry* g) { return g->precision != MSP_PRECISION_FP32; }
 
 // Carve the workspace; with base == nullptr only the size is computed.
 static Workspace layout(const msp_geometry* g, int gcap, char* base) {
@@ -563,7 +565,8 @@ static Workspace layout(const msp_geometry* g, int gcap, char* base) {
   w.loss_part = (double*)take((S > 0 ? S : 1) * loss_slots(g) * sizeof(double));
   w.map0 = (float*)take(2 * plane * sizeof(float));   // complex in transmission mode
   w.map1 = (float*)take(plane * sizeof(float));
-  w.precise = precise(g) ? (char*)take(precise_extra_bytes((int)W, (int)L, g->obj_ny, g->obj_nx, (int)S)) : nullptr;
+  w.precise = precise(g) ? (char*)take(precise_extra_bytes(g->precision, (int)W, (int)L, g->obj_ny, g->obj_nx, (int)S))
+                         : nullptr;
   w.bytes = off;
   return w;
 }
@@ -690,6 +693,8 @@ static msp_status run_position(const msp_geometry* g, int mode, const PosParams&
     in.dq = 1.0 / ((double)g->win * g->pixel_A);
     in.extra = c.ws.precise;
     in.sms = c.dev.sms;
+    in.precision = g->precision;
+    in.wait_limit = tc_wait_limit();
     long long n = 0;
     const msp_status s = profiled_launch(c.st, [&] { return run_precise(mode, p, g->win, in, c.st, &n); });
     if (n > 1) counted((int)(n - 1));   // profiled_launch counted one

@@ -50,14 +50,16 @@ struct Workspace {
   size_t bytes;
 };
 
-// Inputs of the precise-forward mode beyond the fused kernel's parameters.
+// Inputs of the batched modes (FP64 forward, split-BF16 DFT) beyond the fused kernel's parameters.
 struct PreciseIn {
   const float* V;        // FP32 potentials (potential mode) or NULL
   const float2* X;       // the caller's complex slices (transmission mode) or NULL
   double sigma;          // interaction constant
   double dzlam, dq;      // dz lambda and the reciprocal pixel 1 / (W pixel) of the propagator
-  char* extra;           // the precise mode's workspace segment
+  char* extra;           // the batched modes' workspace segment
   int sms;               // SMs of the device (grid sizes of the element-wise kernels)
+  int precision;         // MSP_PRECISION_FP64_FORWARD or MSP_PRECISION_BF16X3_DFT
+  int wait_limit;        // poll bound of the tensor-core waits
 };
 
 constexpr int kRedSlots = 8192;

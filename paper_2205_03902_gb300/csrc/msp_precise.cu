@@ -23,6 +23,11 @@
 //   adjoint step       window gradients, conj(X_m) o chi_m, the probe-gradient terms
 // The window gradients land in the same per-position buffers as the fused kernel's, so the
 // overlap-add, the reductions and the updates downstream are shared with the fast path.
+//
+// The same batched structure runs the split-BF16 precision form (MSP_PRECISION_BF16X3_DFT):
+// every 2-D transform of the forward and of the adjoint is two tensor-core passes of the W-point
+// DFT as a matrix product with 3-term split-BF16 operands (msp_tcdft.cu), the waves are FP32,
+// and the loss and the probe-gradient sum accumulate in FP64.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,6 +64,11 @@ __device__ __forceinline__ C mulc(C a, C b) { return mk<C>(a.x * b.x + a.y * b.y
 
 __device__ __forceinline__ double2 widen(float2 a) { return make_double2((double)a.x, (double)a.y); }
 __device__ __forceinline__ float2 narrow(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 widen(double2 a) { return a; }
+__device__ __forceinline__ float2 narrow(float2 a) { return a; }
+template <typename C> __device__ __forceinline__ C from_f2(float2 a);
+template <> __device__ __forceinline__ float2 from_f2<float2>(float2 a) { return a; }
+template <> __device__ __forceinline__ double2 from_f2<double2>(float2 a) { return widen(a); }
 
 __device__ __forceinline__ bool window_ok(int2 ps, int Ny, int Nx, int W) {
   return ps.x >= 0 && ps.y >= 0 && ps.x <= Ny - W && ps.y <= Nx - W;
@@ -163,18 +173,18 @@ struct Batch {
 
 // Slice `l` (0: the probe itself is the incident wave) : E = psi o X_l, stashed for the adjoint
 // (the incident psi in transmission mode), in FP32.  A window outside the object gives zeros.
-__global__ void transmit_kernel(Batch bt, int l, const float2* __restrict__ probe, const double2* __restrict__ T,
-                                double2* __restrict__ wave, float2* __restrict__ stash, int stash_l0, int keep,
-                                int cplx) {
+template <typename C>
+__global__ void transmit_kernel(Batch bt, int l, const float2* __restrict__ probe, const C* __restrict__ T,
+                                C* __restrict__ wave, float2* __restrict__ stash, int stash_l0, int keep, int cplx) {
   const int W = bt.W;
   const size_t WW = (size_t)W * W, n = (size_t)bt.nb * WW;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int b = (int)(i / WW);
     const int r = (int)((i % WW) / W), c = (int)(i % W);
     const int2 ps = bt.pos[b];
-    double2 e = make_double2(0.0, 0.0), psi = e;
+    C e = mk<C>(0, 0), psi = e;
     if (window_ok(ps, bt.Ny, bt.Nx, W)) {
-      psi = l == 0 ? widen(probe[i % WW]) : wave[i];
+      psi = l == 0 ? from_f2<C>(probe[i % WW]) : wave[i];
       e = mul(psi, T[(size_t)l * bt.plane + (size_t)(ps.x + r) * bt.Nx + ps.y + c]);
     }
     wave[i] = e;
@@ -197,7 +207,8 @@ __global__ void propagator_kernel(Batch bt, const H* __restrict__ h1, C* __restr
 
 // Far field Psi (FP64) -> the loss of each position, R = Psi - sqrt(I) Psi / |Psi| (the fraction 0
 // where |Psi|^2 <= thr2) rounded to FP32, or the intensities |Psi|^2.  One CTA per position.
-__global__ void __launch_bounds__(256) residual_kernel(Batch bt, const double2* __restrict__ psi,
+template <typename C>
+__global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __restrict__ psi,
                                                        const float* __restrict__ I_meas, const double* __restrict__ zthr2,
                                                        float2* __restrict__ R, double* __restrict__ loss_part,
                                                        float* __restrict__ I_out) {
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const double2* 
   const double thr2 = I_out ? 0.0 : zthr2[0];
   double acc = 0.0;
   for (size_t k = tid; k < WW; k += 256) {
-    const double2 v = psi[(size_t)b * WW + k];
+    const double2 v = widen(psi[(size_t)b * WW + k]);
     const double a2 = v.x * v.x + v.y * v.y;
     if (I_out) {
       I_out[(size_t)b * WW + k] = (float)a2;
@@ -326,45 +337,114 @@ static int elem_blocks(size_t n, int sms) {
 
 }  // namespace precise
 
-// Positions per batch of the precise mode: one batch's FP64 waves take 64 MiB.
+cudaError_t tcdft_prepare(int W, int inverse, void* mat, cudaStream_t st);
+cudaError_t tcdft_pass(int W, const float2* in, float2* out, int nb, const void* mat, int* err, int wait_limit,
+                       cudaStream_t st);
+size_t tcdft_matrix_bytes(int W);
+
+// Positions per batch of the batched modes: one batch's FP64 waves take 64 MiB (the split-BF16
+// mode uses the same batches of FP32 waves and a second buffer of the same size).
 int precise_batch(int W, int S) {
   const int b = (int)((size_t(64) << 20) / ((size_t)W * W * sizeof(double2)));
   return S < b ? (S > 0 ? S : 1) : b;
 }
 
-// Workspace of the precise mode beyond the fast path's (every segment 256-byte aligned).
-size_t precise_extra_bytes(int W, int L, int Ny, int Nx, int S) {
+namespace {
+struct Segs {
+  double2* T64 = nullptr;     // FP64 transmissions (FP64-forward mode)
+  double2* h1d = nullptr;     // FP64 propagator factor (FP64-forward mode)
+  void* wave = nullptr;       // [B][W][W] forward waves: double2 (FP64 forward) or float2 (split BF16)
+  float2* tmp = nullptr;      // [B][W][W] second buffer of the tensor-core passes (split BF16)
+  float2* chi = nullptr;      // [B][W][W] adjoint waves
+  float2* stash = nullptr;    // [B][L][W][W] exit (or incident) waves kept for the adjoint
+  float2* contrib = nullptr;  // [B][W][W] probe-gradient terms of the batch
+  double2* dp64 = nullptr;    // [W][W] probe-gradient sum
+  void* mat_f = nullptr;      // split-BF16 DFT matrices, forward and inverse (split BF16)
+  void* mat_i = nullptr;
+  size_t bytes = 0;
+};
+
+Segs carve(int precision, int W, int L, int Ny, int Nx, int S, char* base) {
   auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  Segs g;
+  size_t off = 0;
+  auto take = [&](size_t b) { char* q = base ? base + off : nullptr; off += a(b); return (void*)q; };
   const size_t WW = (size_t)W * W, B = (size_t)precise_batch(W, S);
-  return a((size_t)L * Ny * Nx * sizeof(double2)) + a(W * sizeof(double2)) + a(B * WW * sizeof(double2)) +
-         a(B * WW * sizeof(float2)) + a(B * L * WW * sizeof(float2)) + a(B * WW * sizeof(float2)) +
-         a(WW * sizeof(double2));
+  const bool tc = precision == MSP_PRECISION_BF16X3_DFT;
+  if (!tc) {
+    g.T64 = (double2*)take((size_t)L * Ny * Nx * sizeof(double2));
+    g.h1d = (double2*)take(W * sizeof(double2));
+  }
+  g.wave = take(B * WW * (tc ? sizeof(float2) : sizeof(double2)));
+  if (tc) g.tmp = (float2*)take(B * WW * sizeof(float2));
+  g.chi = (float2*)take(B * WW * sizeof(float2));
+  g.stash = (float2*)take(B * L * WW * sizeof(float2));
+  g.contrib = (float2*)take(B * WW * sizeof(float2));
+  g.dp64 = (double2*)take(WW * sizeof(double2));
+  if (tc) {
+    g.mat_f = take(tcdft_matrix_bytes(W));
+    g.mat_i = take(tcdft_matrix_bytes(W));
+  }
+  g.bytes = off;
+  return g;
+}
+}  // namespace
+
+// Workspace of the batched modes beyond the fast path's (every segment 256-byte aligned).
+size_t precise_extra_bytes(int precision, int W, int L, int Ny, int Nx, int S) {
+  return carve(precision, W, L, Ny, Nx, S, nullptr).bytes;
 }
 
-// The forward model in FP64 and the FP32 adjoint of `mode` over all positions, writing what the
+// The forward model and the adjoint of `mode` over all positions in batches, writing what the
 // fused kernel writes: I_out (forward), loss_part, the window gradients and illumination, and
-// the probe gradient into dprobe_part[0] (one partial).  Returns the number of kernels launched.
+// the probe gradient into dprobe_part[0] (one partial).  FP64-forward mode: FP64 forward with the
+// radix-2 FFT, FP32 adjoint.  Split-BF16 mode: every 2-D transform as two tensor-core passes,
+// FP32 waves.  Reports the number of kernels launched.
 cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in, cudaStream_t st, long long* launches) {
   using namespace precise;
-  auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int L = p.L, S = p.S;
   const size_t WW = (size_t)W * W, plane = (size_t)p.Ny * p.Nx;
   const int B = precise_batch(W, S);
-  char* q = in.extra;
-  double2* T64 = (double2*)q;  q += a((size_t)L * plane * sizeof(double2));
-  double2* h1d = (double2*)q;  q += a(W * sizeof(double2));
-  double2* wave = (double2*)q; q += a((size_t)B * WW * sizeof(double2));
-  float2* chi = (float2*)q;    q += a((size_t)B * WW * sizeof(float2));
-  float2* stash = (float2*)q;  q += a((size_t)B * L * WW * sizeof(float2));
-  float2* contrib = (float2*)q; q += a((size_t)B * WW * sizeof(float2));
-  double2* dp64 = (double2*)q;
+  const bool tc = in.precision == MSP_PRECISION_BF16X3_DFT;
+  const Segs g = carve(in.precision, W, L, p.Ny, p.Nx, S, in.extra);
   long long n_launch = 0;
+  cudaError_t err = cudaSuccess;
 
-  table64_kernel<<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X, T64,
-                                                                          (size_t)L * plane, in.sigma);
-  h1_64_kernel<<<(W + 255) / 256, 256, 0, st>>>(h1d, W, in.dzlam, in.dq);
+  if (tc) {
+    if ((err = tcdft_prepare(W, 0, g.mat_f, st)) != cudaSuccess) return err;
+    if ((err = tcdft_prepare(W, 1, g.mat_i, st)) != cudaSuccess) return err;
+    n_launch += 2;
+  } else {
+    table64_kernel<<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X, g.T64,
+                                                                            (size_t)L * plane, in.sigma);
+    h1_64_kernel<<<(W + 255) / 256, 256, 0, st>>>(g.h1d, W, in.dzlam, in.dq);
+    n_launch += 2;
+  }
   flag_windows_kernel<<<(S + 255) / 256, 256, 0, st>>>(p.pos, S, p.Ny, p.Nx, W, p.err);
-  n_launch += 3;
+  ++n_launch;
+
+  // 2-D transforms: unnormalised, forward or inverse
+  auto keep_first = [&](cudaError_t e) {
+    if (err == cudaSuccess) err = e;
+  };
+  auto fwd2 = [&](int nb, bool inverse) {   // the forward model's waves
+    if (tc) {
+      keep_first(tcdft_pass(W, (float2*)g.wave, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+      keep_first(tcdft_pass(W, g.tmp, (float2*)g.wave, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+    } else {
+      fft2_w<double2>(W, (double2*)g.wave, nb, inverse, st);
+    }
+    n_launch += 2;
+  };
+  auto adj2 = [&](int nb, bool inverse) {   // the adjoint's waves
+    if (tc) {
+      keep_first(tcdft_pass(W, g.chi, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+      keep_first(tcdft_pass(W, g.tmp, g.chi, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+    } else {
+      fft2_w<float2>(W, g.chi, nb, inverse, st);
+    }
+    n_launch += 2;
+  };
 
   const bool fwd = mode == MODE_FORWARD;
   const int lowest = mode == MODE_LAYER ? p.layer : 0;
@@ -374,26 +454,30 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     const int nb = S - b0 < B ? S - b0 : B;
     Batch bt{p.pos + b0, nb, W, p.Ny, p.Nx, L, plane};
     const int eb = elem_blocks((size_t)nb * WW, in.sms);
-    // forward, FP64: slice 0, then (propagate, transmit) for every later slice
+    // forward: slice 0, then (propagate, transmit) for every later slice
     for (int l = 0; l < L; ++l) {
-      if (l > 0) {
-        fft2_w<double2>(W, wave, nb, false, st);
-        propagator_kernel<double2, double2><<<eb, 256, 0, st>>>(bt, h1d, wave, 0);
-        fft2_w<double2>(W, wave, nb, true, st);
-        n_launch += 5;
-      }
       const int keep = !fwd && l >= lowest;
-      transmit_kernel<<<eb, 256, 0, st>>>(bt, l, p.probe, T64, wave, stash, 0, keep, p.cplx);
+      if (l > 0) {
+        fwd2(nb, false);
+        if (tc) propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, (float2*)g.wave, 0);
+        else propagator_kernel<double2, double2><<<eb, 256, 0, st>>>(bt, g.h1d, (double2*)g.wave, 0);
+        fwd2(nb, true);
+        ++n_launch;
+      }
+      if (tc) transmit_kernel<float2><<<eb, 256, 0, st>>>(bt, l, p.probe, p.T, (float2*)g.wave, g.stash, 0, keep, p.cplx);
+      else transmit_kernel<double2><<<eb, 256, 0, st>>>(bt, l, p.probe, g.T64, (double2*)g.wave, g.stash, 0, keep, p.cplx);
       ++n_launch;
     }
-    fft2_w<double2>(W, wave, nb, false, st);   // far field Psi = F(E_L)
-    residual_kernel<<<nb, 256, 0, st>>>(bt, wave, fwd ? nullptr : p.I_meas + (size_t)b0 * WW, p.zthr2, chi,
-                                        fwd ? nullptr : p.loss_part + b0, fwd ? p.I_out + (size_t)b0 * WW : nullptr);
-    n_launch += 3;
+    fwd2(nb, false);   // far field Psi = F(E_L)
+    const float* Im = fwd ? nullptr : p.I_meas + (size_t)b0 * WW;
+    double* lp = fwd ? nullptr : p.loss_part + b0;
+    float* Io = fwd ? p.I_out + (size_t)b0 * WW : nullptr;
+    if (tc) residual_kernel<float2><<<nb, 256, 0, st>>>(bt, (const float2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
+    else residual_kernel<double2><<<nb, 256, 0, st>>>(bt, (const double2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
+    ++n_launch;
     if (fwd) continue;
-    // adjoint, FP32: chi_L = F^H R, then down the slices
-    fft2_w<float2>(W, chi, nb, true, st);
-    n_launch += 2;
+    // adjoint: chi_L = F^H R, then down the slices
+    adj2(nb, true);
     for (int l = L - 1; l >= lowest; --l) {
       const bool grad_here = mode == MODE_LOSS_GRAD || (mode == MODE_LAYER && l == p.layer);
       const bool go_on = (l > lowest) || (l == 0 && want_dprobe);
@@ -404,27 +488,28 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
         o.wstride = (size_t)CW * WW * (mode == MODE_LOSS_GRAD ? L : 1);
         if (mode == MODE_LAYER) o.willum = p.willum;
       }
-      if (l == 0 && want_dprobe) o.contrib = contrib;
-      adjoint_kernel<<<eb, 256, 0, st>>>(bt, l, chi, stash + (size_t)l * WW, p.T, o, go_on ? 1 : 0, p.cplx,
+      if (l == 0 && want_dprobe) o.contrib = g.contrib;
+      adjoint_kernel<<<eb, 256, 0, st>>>(bt, l, g.chi, g.stash + (size_t)l * WW, p.T, o, go_on ? 1 : 0, p.cplx,
                                          p.two_sigma);
       ++n_launch;
       if (!go_on || l == 0) break;
-      fft2_w<float2>(W, chi, nb, false, st);
-      propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, chi, 1);
-      fft2_w<float2>(W, chi, nb, true, st);
-      n_launch += 5;
+      adj2(nb, false);
+      propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, g.chi, 1);
+      adj2(nb, true);
+      ++n_launch;
     }
     if (want_dprobe) {
-      dprobe_accumulate_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(contrib, nb, (int)WW, dp64, b0 == 0);
+      dprobe_accumulate_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(g.contrib, nb, (int)WW, g.dp64, b0 == 0);
       ++n_launch;
     }
   }
   if (want_dprobe) {
-    dprobe_finish_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(dp64, (int)WW, p.dprobe_part);
+    dprobe_finish_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(g.dp64, (int)WW, p.dprobe_part);
     ++n_launch;
   }
   *launches = n_launch;
-  return cudaGetLastError();
+  const cudaError_t last = cudaGetLastError();
+  return err != cudaSuccess ? err : last;
 }
 
 }  // namespace msp

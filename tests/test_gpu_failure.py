@@ -66,3 +66,36 @@ def test_a_wait_that_runs_out_is_reported_and_the_device_stays_usable(msp):
     y = msp.dft2_tc(x).cpu().numpy()
     ref = np.stack([O.dft2(v) for v in x.cpu().numpy().astype(np.complex128)])
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_split_bf16_dft_wait_that_runs_out_is_reported(msp):
+    """The split-BF16 DFT passes wait for their own MMAs with the same bound: cut to one poll, a
+    pass gives up, the call's workspace flag reads MSP_ETIMEOUT, and the same process then runs the
+    mode correctly (its forward intensities against the oracle at the mode's bar)."""
+    cfg = synth.C1
+    pos = synth.scan_positions(cfg, sub=(2, 2))
+    gd = synth.geometry(cfg, n_pos=len(pos))
+    g = msp.geometry(**gd, precision=msp.MSP_PRECISION_BF16X3_DFT)
+    probe = synth.probe(cfg).astype(np.complex64)
+    V = synth.potential_slices(cfg).astype(np.float32)
+    dp, dV, dpos = (torch.from_numpy(probe).cuda(), torch.from_numpy(V).cuda(), torch.from_numpy(pos).cuda())
+    ws = msp.make_workspace(g)
+    timed_out = False
+    try:
+        msp.set_wait_limit(1)
+        for _ in range(3):
+            msp.forward(g, dp, dV, dpos, ws=ws)
+            try:
+                msp.check_workspace(ws)
+            except msp.MspError as e:
+                assert e.status == msp.MSP_ETIMEOUT
+                timed_out = True
+                break
+    finally:
+        msp.set_wait_limit(0)
+    assert timed_out
+    I = msp.forward(g, dp, dV, dpos, ws=ws).cpu().numpy()
+    msp.check_workspace(ws)
+    ref = O.forward(gd, probe.astype(np.complex128), pos, V=V.astype(np.float64))
+    bar = 2 * 2 * (2 * cfg.n_slices - 1) * 2.0 ** -16
+    assert np.linalg.norm(I - ref) / np.linalg.norm(ref) <= bar

@@ -307,6 +307,43 @@ def test_precise_mode_edge_cases(msp, c1):
         assert torch.equal(x, y)
 
 
+# --------------------------------------------------------------------------- split-BF16 precision form
+# Every 2-D transform of the forward model and the adjoint as two tensor-core DFT passes with
+# 3-term split-BF16 operands.  Each pass keeps 16 mantissa bits of every operand (x = hi + lo):
+# about 2^-16 relative error per pass, so the forward's 2 (2L - 1) passes give
+# e = 2 (2L - 1) 2^-16; the intensities carry 2e, and the gradients inherit e amplified by the
+# state's conditioning exactly as the FP32 path's do (no cap: this form is the reduced-precision
+# one, and its errors are a stated result).
+
+def bf16_bars(c):
+    e = 2 * (2 * c.gd["n_slices"] - 1) * 2.0 ** -16
+    kappa, canc, flip = O.residual_conditioning(c.gd, c.probe, c.pos, c.I, V=c.V, band=2 * e * float(np.linalg.norm(c.probe)))
+    S, W2 = len(c.pos), c.gd["win"] ** 2
+    return dict(I=2 * e, grad=max(TOL, e * kappa + flip), probe_grad=max(TOL, (e * kappa + flip) * canc), e=e)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2_ragged", "c3_sub", "c4_sub", "c2_strong", "c3_strong"])
+def test_bf16x3_mode_per_result_errors(msp, which, request):
+    c = request.getfixturevalue(which)
+    g = msp.geometry(**c.gd, precision=msp.MSP_PRECISION_BF16X3_DFT)
+    _, p, V, pos, I = c.dev(msp)
+    Ig = msp.forward(g, p, V, pos).cpu().numpy()
+    Iref = O.forward(c.gd, c.probe, c.pos, V=c.V)
+    loss, dV, dprobe = msp.loss_grad(g, p, V, pos, I)
+    ref = O.loss_grad(c.gd, c.probe, c.pos, c.I, V=c.V)
+    errs = dict(I=rel(Ig, Iref), loss=abs(loss.item() - ref["loss"]) / ref["loss"],
+                dV=rel(dV.cpu().numpy(), ref["dV"]), dprobe=rel(dprobe.cpu().numpy(), ref["dprobe"]))
+    bars = bf16_bars(c)
+    kappa = np.sqrt(len(c.pos) * c.gd["win"] ** 2 * float(np.sum(np.abs(c.probe) ** 2)) / ref["loss"])
+    lbar = max(TOL, 2 * bars["e"] * kappa)
+    print("bf16x3", which, {k: f"{v:.2e}" for k, v in errs.items()},
+          "bars", {k: f"{v:.2e}" for k, v in dict(I=bars["I"], loss=lbar, dV=bars["grad"], dprobe=bars["probe_grad"]).items()})
+    assert errs["I"] <= bars["I"]
+    assert errs["loss"] <= lbar
+    assert errs["dV"] <= bars["grad"]
+    assert errs["dprobe"] <= bars["probe_grad"]
+
+
 def test_gradients_are_bit_reproducible(msp, c2_ragged):
     g, p, V, pos, I = c2_ragged.dev(msp)
     ws = msp.make_workspace(g)
