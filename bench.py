@@ -85,6 +85,12 @@ def job_throughput(world: int, units_per_rank: float, ms_per_step: float) -> flo
     return world * units_per_rank / (ms_per_step * 1e-3)
 
 
+# The tcgen05 kind::tf32 pipe rate measured by this repository's micro-benchmark
+# (bench.py --config peaks: M = 128, N = 256, K = 8 MMAs back to back on every SM of a GB300):
+# the denominator of the tf32 contractions' roofline fractions.
+TF32_MEASURED_TFLOPS = 1073.0
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -485,8 +491,7 @@ def run_smd(args, rank, world, local_rank):
     # the contraction runs on the tensor cores as a real tf32 product with operands split into
     # (big, small) pairs: 3 tf32 products of 8 flops per complex multiply-add, 24 N^4 S per launch
     tc_flops = 3 * gemm_flops / 2
-    bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    tf32_peak = bf16 * 1.1 / 2.25
+    tf32_peak = TF32_MEASURED_TFLOPS
     achieved = tc_flops / (gemm_ms * 1e-3) / 1e12
     line = {
         "metric": SMD_METRIC, "value": value, "unit": SMD_UNIT, "n_gpus": world, "steps": args.steps,
@@ -502,7 +507,7 @@ def run_smd(args, rank, world, local_rank):
                      "kernel": "cgemm_kernel (tcgen05 kind::tf32, 3 tf32 products per FP32 product; A P and C P^H)",
                      "kernel_ms": gemm_ms,
                      "complex_fp32_equivalent_tflops": (gemm_flops / 2) / (gemm_ms * 1e-3) / 1e12,
-                     "peak_source": f"measured bf16 burst {bf16:.1f} TFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"},
+                     "peak_source": "measured tcgen05 kind::tf32 pipe rate (bench.py --config peaks, N = 256)"},
         "step_tflops": (gemm_flops + dft_flops) / (ms_per_step * 1e-3) / 1e12,
         "e2e": {"value": e2e_value, "unit": SMD_UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["all_launches"]),
@@ -566,9 +571,7 @@ def run_dft(args, rank, world, local_rank):
     value = S / (ms * 1e-3)
     pass_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
     tc_flops = 24.0 * S * W ** 3                      # one pass: 24 M N K with M = K = W, N = S W
-    peaks = read_peaks()
-    bf16 = float(peaks.get("bf16_tflops", 1900.0))
-    tf32_peak = bf16 * 1.1 / 2.25
+    tf32_peak = TF32_MEASURED_TFLOPS
     # end to end: host -> device, transform, device -> host (pinned buffers)
     x_pin = torch.from_numpy(x_h).pin_memory()
     y_pin = torch.empty_like(x_pin).pin_memory()
@@ -609,7 +612,7 @@ def run_dft(args, rank, world, local_rank):
                      "unit": "TFLOP/s", "frac": tc_flops / (pass_ms * 1e-3) / 1e12 / tf32_peak, "traffic": None,
                      "kernel": "cgemm_kernel<false, true> (one DFT pass, tcgen05 kind::tf32, split operands)",
                      "kernel_ms": pass_ms,
-                     "peak_source": f"measured bf16 burst {bf16:.1f} TFLOP/s x nominal tf32/bf16 ratio 1.1/2.25"},
+                     "peak_source": "measured tcgen05 kind::tf32 pipe rate (bench.py --config peaks, N = 256)"},
         "smem_fft_comparison": {"fused_kernel": "position_kernel<128, LAYER> on the c3 layer step",
                                 "fused_kernel_ms": fused_ms, "fft_transforms_per_s": fft_rate,
                                 "tensor_dft_over_smem_fft": value / fft_rate},
