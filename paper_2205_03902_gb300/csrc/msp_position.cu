@@ -32,6 +32,7 @@
 // stash slots out of L2.
 #include "msp_fft.cuh"
 #include "msp_kernels.cuh"
+#include "msp_tc.cuh"
 
 // Twiddles of the line transforms from shared memory (0) or registers (1).
 #ifndef MSP_TWIDDLE_REGISTERS
@@ -43,6 +44,47 @@
 #endif
 
 namespace msp {
+
+// Exit-wave stash in tensor memory (W = 128, one CTA per SM).  The fused kernel issues no MMAs,
+// so the SM's 256 KB of tensor memory is free: each thread keeps the values it stashes for two
+// slices in its own TMEM lane (warp w: lanes 32 (w % 4) .., columns 128 (w / 4) .. + 127; a
+// slice takes 2 row iterations x 16 complex values = 64 columns).  Those slices neither pass
+// through the L1 data pipe nor compete for L2 with the streaming window gradients; the others
+// use the CTA's global stash slot.  Loss and gradients: the last two slices (the first ones
+// the adjoint reads back); layer step: the one stashed slice.
+#ifndef MSP_TMEM_STASH
+#define MSP_TMEM_STASH 1
+#endif
+struct TmemStash {
+  uint32_t base;   // this thread's lane and its warp's first column
+  // 16 complex values of row iteration `it` of stash slot `slot` (0 or 1)
+  __device__ __forceinline__ uint32_t addr(int slot, int it) const { return base + (uint32_t)(64 * slot + 32 * it); }
+  __device__ __forceinline__ void store(int slot, int it, const float2 (&v)[16]) const {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(addr(slot, it)),
+        "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y),
+        "f"(v[4].x), "f"(v[4].y), "f"(v[5].x), "f"(v[5].y), "f"(v[6].x), "f"(v[6].y), "f"(v[7].x), "f"(v[7].y),
+        "f"(v[8].x), "f"(v[8].y), "f"(v[9].x), "f"(v[9].y), "f"(v[10].x), "f"(v[10].y), "f"(v[11].x), "f"(v[11].y),
+        "f"(v[12].x), "f"(v[12].y), "f"(v[13].x), "f"(v[13].y), "f"(v[14].x), "f"(v[14].y), "f"(v[15].x),
+        "f"(v[15].y)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  __device__ __forceinline__ void load(int slot, int it, float2 (&v)[16]) const {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x), "=f"(v[2].y), "=f"(v[3].x),
+          "=f"(v[3].y), "=f"(v[4].x), "=f"(v[4].y), "=f"(v[5].x), "=f"(v[5].y), "=f"(v[6].x), "=f"(v[6].y),
+          "=f"(v[7].x), "=f"(v[7].y), "=f"(v[8].x), "=f"(v[8].y), "=f"(v[9].x), "=f"(v[9].y), "=f"(v[10].x),
+          "=f"(v[10].y), "=f"(v[11].x), "=f"(v[11].y), "=f"(v[12].x), "=f"(v[12].y), "=f"(v[13].x), "=f"(v[13].y),
+          "=f"(v[14].x), "=f"(v[14].y), "=f"(v[15].x), "=f"(v[15].y)
+        : "r"(addr(slot, it))
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  }
+};
 
 #if MSP_TRANSPOSED_EXCHANGE
 #define LINE_FFT line_fft_t
@@ -127,6 +169,23 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   const bool need_stash = (MODE == MODE_LOSS_GRAD) || (MODE == MODE_LAYER);
   const int lowest = (MODE == MODE_LAYER) ? p.layer : 0;
   bool first_dprobe = true;
+  // TMEM stash (W = 128 only): slot of slice l, or -1 for the global stash
+  constexpr bool kTmem = MSP_TMEM_STASH && W == 128 && (MODE == MODE_LOSS_GRAD || MODE == MODE_LAYER);
+  __shared__ uint32_t s_tmem;
+  TmemStash ts{0};
+  if constexpr (kTmem) {
+    if (tid < 32) tc::tmem_alloc(&s_tmem, 512);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const int warp = tid >> 5;
+    ts.base = s_tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(128 * (warp >> 2));
+  }
+  auto tslot = [&](int l) -> int {
+    if constexpr (!kTmem) return -1;
+    if (MODE == MODE_LAYER) return 0;
+    return l >= L - 2 ? l - (L - 2 > 0 ? L - 2 : 0) : -1;
+  };
 
   for (int s = blockIdx.x; s < p.S; s += gridDim.x) {
     const int2 ps = p.pos[s];
@@ -160,15 +219,26 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
       const float2* T0 = p.T + win0 + (size_t)r * p.Nx;
 #pragma unroll
       for (int m = 0; m < N1; ++m) v[m] = p.probe[r * W + j + 8 * m];
-      if (CPLX && need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+      const bool keep0 = need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0);
+      if (CPLX && keep0) {
+        if constexpr (kTmem) {
+          if (tslot(0) >= 0) ts.store(tslot(0), it, v);   // incident wave
+        }
+        if (tslot(0) < 0) {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // incident wave
+          for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // incident wave
+        }
       }
 #pragma unroll
       for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], T0[j + 8 * m]);
-      if (!CPLX && need_stash && (MODE == MODE_LOSS_GRAD || p.layer == 0)) {
+      if (!CPLX && keep0) {
+        if constexpr (kTmem) {
+          if (tslot(0) >= 0) ts.store(tslot(0), it, v);   // exit wave
+        }
+        if (tslot(0) < 0) {
 #pragma unroll
-        for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // exit wave
+          for (int m = 0; m < N1; ++m) stash[r * W + j + 8 * m] = v[m];   // exit wave
+        }
       }
       LINE_FFT<W, false>(v, tw, xb, j);
 #pragma unroll
@@ -213,14 +283,24 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
           for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
           LINE_FFT<W, true>(v, tw, xb, j);
           if (CPLX && keep) {
+            if constexpr (kTmem) {
+              if (tslot(l + 1) >= 0) ts.store(tslot(l + 1), it, v);   // incident wave
+            }
+            if (tslot(l + 1) < 0) {
 #pragma unroll
-            for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // incident wave
+              for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // incident wave
+            }
           }
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], t[m]);
           if (!CPLX && keep) {
+            if constexpr (kTmem) {
+              if (tslot(l + 1) >= 0) ts.store(tslot(l + 1), it, v);   // exit wave
+            }
+            if (tslot(l + 1) < 0) {
 #pragma unroll
-            for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // exit wave
+              for (int m = 0; m < N1; ++m) st[r * W + j + 8 * m] = v[m];   // exit wave
+            }
           }
           LINE_FFT<W, false>(v, tw, xb, j);
 #pragma unroll
@@ -300,8 +380,13 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         const RowIdx<W> ra(r, j);
         float2 e[N1], v[N1];
         if (grad_here) {
+          if constexpr (kTmem) {
+            if (tslot(l) >= 0) ts.load(tslot(l), it, e);
+          }
+          if (tslot(l) < 0) {
 #pragma unroll
-          for (int m = 0; m < N1; ++m) e[m] = st[r * W + j + 8 * m];   // in flight during the transform
+            for (int m = 0; m < N1; ++m) e[m] = st[r * W + j + 8 * m];   // in flight during the transform
+          }
         }
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
@@ -370,6 +455,14 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
   if ((MODE == MODE_LOSS_GRAD || MODE == MODE_PROBE) && p.want_dprobe && first_dprobe) {
     float2* dp = p.dprobe_part + (size_t)blockIdx.x * WW;
     for (size_t i = tid; i < WW; i += G::NT) dp[i] = make_float2(0.f, 0.f);
+  }
+  if constexpr (kTmem) {
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) {
+      tc::fence_after();
+      tc::tmem_dealloc(s_tmem, 512);
+    }
   }
 }
 
