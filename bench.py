@@ -673,7 +673,7 @@ def plain_method_run(msp, torch, dev, cfg, sweeps, probe_steps, precision, strea
         out = {"ms": a.elapsed_time(b), "sweeps": sweeps, "probe_steps_per_sweep": probe_steps,
                "passes": int(sweeps * (cfg.n_slices + probe_steps) + 1),
                "loss_first": float(h[0].item()), "loss_final": float(h[-1].item())}
-    out["precision"] = {0: "fp32", 1: "fp64_forward", 2: "split_bf16_dft"}[precision]
+    out["precision"] = {0: "fp32", 1: "fp64_forward", 2: "split_bf16_dft", 3: "double_float_forward"}[precision]
     return out
 
 
@@ -817,6 +817,14 @@ def run_msp(args, rank, world, local_rank):
         extra["precise_forward"] = {"call": "msp_loss_grad, MSP_PRECISION_FP64_FORWARD", "ms": pms,
                                     "value": S * L / (pms * 1e-3), "unit": UNIT, "cost_vs_fp32": pms / ms_per_step}
         del wsp
+        gd_ = msp.geometry(**gd, precision=msp.MSP_PRECISION_DF_FORWARD)
+        wsd = msp.make_workspace(gd_, dev)
+        msp.loss_grad(gd_, probe, V, d_pos, I_meas, ws=wsd)
+        dms = time_events(lambda: msp.loss_grad(gd_, probe, V, d_pos, I_meas, ws=wsd), 5, stream, flush)
+        extra["precise_forward_double_float"] = {"call": "msp_loss_grad, MSP_PRECISION_DF_FORWARD", "ms": dms,
+                                                 "value": S * L / (dms * 1e-3), "unit": UNIT,
+                                                 "cost_vs_fp32": dms / ms_per_step}
+        del wsd
         # the split-BF16 precision form (tensor-core DFT passes) on the same state
         gb = msp.geometry(**gd, precision=msp.MSP_PRECISION_BF16X3_DFT)
         wsb = msp.make_workspace(gb, dev)
@@ -833,6 +841,7 @@ def run_msp(args, rank, world, local_rank):
             "c1_known_probe": plain_method_run(msp, torch, dev, synth.C1, 50, 0, 0, stream),
             "c2_probe_estimation_fp32": plain_method_run(msp, torch, dev, cfg, 20, 1, 0, stream),
             "c2_probe_estimation_precise": plain_method_run(msp, torch, dev, cfg, 20, 1, 1, stream),
+            "c2_probe_estimation_double_float": plain_method_run(msp, torch, dev, cfg, 20, 1, 3, stream),
             "c2_probe_estimation_split_bf16": plain_method_run(msp, torch, dev, cfg, 20, 1, 2, stream),
             "c3_probe_estimation_fp32": plain_method_run(msp, torch, dev, synth.C3, 5, 1, 0, stream),
             "c3_probe_estimation_split_bf16": plain_method_run(msp, torch, dev, synth.C3, 5, 1, 2, stream),
@@ -843,6 +852,7 @@ def run_msp(args, rank, world, local_rank):
                     "time_ratio_over_fp32": pm[b]["ms"] / pm[a]["ms"]}
 
         pm["c2_precise_vs_fp32"] = versus("c2_probe_estimation_fp32", "c2_probe_estimation_precise")
+        pm["c2_double_float_vs_fp32"] = versus("c2_probe_estimation_fp32", "c2_probe_estimation_double_float")
         pm["c2_split_bf16_vs_fp32"] = versus("c2_probe_estimation_fp32", "c2_probe_estimation_split_bf16")
         pm["c3_split_bf16_vs_fp32"] = versus("c3_probe_estimation_fp32", "c3_probe_estimation_split_bf16")
         extra["plain_method"] = pm

@@ -92,8 +92,17 @@ enum { MSP_PARAM_POTENTIAL = 0, MSP_PARAM_TRANSMISSION = 1 };
  *     product on the tensor cores (the matrix-product form of the propagation that Sec. 6
  *     suggests), operands split into bf16 pairs x = hi + lo and multiplied as
  *     hi*hi + hi*lo + lo*hi with FP32 accumulation; waves in FP32, loss and probe-gradient
- *     sums in FP64.  About 2^-16 relative error per product. */
-enum { MSP_PRECISION_FP32 = 0, MSP_PRECISION_FP64_FORWARD = 1, MSP_PRECISION_BF16X3_DFT = 2 };
+ *     sums in FP64.  About 2^-16 relative error per product.
+ *   MSP_PRECISION_DF_FORWARD: MSP_PRECISION_FP64_FORWARD with the forward model in
+ *     double-float arithmetic (each value an unevaluated sum of two FP32 numbers, about 48
+ *     significand bits, operated on by error-free sums and fused-multiply-add products) on the
+ *     FP32 pipe instead of the FP64 pipe: the same residual accuracy at a fraction of the cost. */
+enum {
+  MSP_PRECISION_FP32 = 0,
+  MSP_PRECISION_FP64_FORWARD = 1,
+  MSP_PRECISION_BF16X3_DFT = 2,
+  MSP_PRECISION_DF_FORWARD = 3
+};
 
 /* Statement of the problem (Sec. 2.1).  Supported windows: W = 64, 128 or 256 (W = 256 runs
  * each position on a four-CTA thread-block cluster). */
@@ -108,7 +117,7 @@ typedef struct {
   double sigma;         /* interaction constant, rad / (V angstrom)               */
   double dz_A;          /* slice separation = Fresnel distance Delta (Eq. fresnel_element) */
   double pixel_A;       /* real-space pixel size in angstrom                       */
-  int32_t precision;    /* MSP_PRECISION_FP32, _FP64_FORWARD or _BF16X3_DFT         */
+  int32_t precision;    /* MSP_PRECISION_FP32, _FP64_FORWARD, _BF16X3_DFT, _DF_FORWARD */
 } msp_geometry;
 
 /* Checks a geometry on the host.  MSP_OK, MSP_EINVAL or MSP_EUNSUPPORTED. */

@@ -520,9 +520,8 @@ static msp_status check_geometry(const msp_geometry* g) {
   if (!(std::isfinite(g->pixel_A) && g->pixel_A > 0)) return fail(MSP_EINVAL, "pixel size must be > 0");
   if (!(std::isfinite(g->dz_A) && g->dz_A >= 0)) return fail(MSP_EINVAL, "slice thickness must be >= 0");
   if (!std::isfinite(g->sigma)) return fail(MSP_EINVAL, "sigma must be finite");
-  if (g->precision != MSP_PRECISION_FP32 && g->precision != MSP_PRECISION_FP64_FORWARD &&
-      g->precision != MSP_PRECISION_BF16X3_DFT)
-    return fail(MSP_EINVAL, "precision must be MSP_PRECISION_FP32, _FP64_FORWARD or _BF16X3_DFT");
+  if (g->precision < MSP_PRECISION_FP32 || g->precision > MSP_PRECISION_DF_FORWARD)
+    return fail(MSP_EINVAL, "precision must be MSP_PRECISION_FP32, _FP64_FORWARD, _BF16X3_DFT or _DF_FORWARD");
   const double cells = (double)g->n_slices * g->obj_ny * g->obj_nx;
   if (cells > 4.0e9) return fail(MSP_EUNSUPPORTED, "object too large");
   if ((size_t)((g->obj_nx + kGatherTX - 1) / kGatherTX) * ((g->obj_ny + kGatherTY - 1) / kGatherTY) > (size_t)kRedSlots)

@@ -69,6 +69,62 @@ __device__ __forceinline__ float2 narrow(float2 a) { return a; }
 template <typename C> __device__ __forceinline__ C from_f2(float2 a);
 template <> __device__ __forceinline__ float2 from_f2<float2>(float2 a) { return a; }
 template <> __device__ __forceinline__ double2 from_f2<double2>(float2 a) { return widen(a); }
+template <typename C> __device__ __forceinline__ C from_d(double re, double im);
+template <> __device__ __forceinline__ float2 from_d<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+template <> __device__ __forceinline__ double2 from_d<double2>(double re, double im) { return make_double2(re, im); }
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic: a value is an unevaluated sum h + l of two FP32 numbers with
+// |l| <= ulp(h) / 2 (about 48 significand bits), operated on with the error-free
+// transformations of Knuth (two-sum) and of the fused multiply-add (two-product).  Additions
+// use the short form, whose error is bounded relative to the operands' magnitudes, as the
+// error of an FP64 addition is; that is the bound an FFT's error analysis uses.  Every
+// operation runs on the FP32 pipe.
+// ---------------------------------------------------------------------------
+struct dff {
+  float h, l;
+};
+struct dfc {   // complex: re, im
+  dff re, im;
+};
+__device__ __forceinline__ dff two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dff fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dff df_add(dff x, dff y) {
+  const dff s = two_sum(x.h, y.h);
+  return fast_two_sum(s.h, s.l + (x.l + y.l));
+}
+__device__ __forceinline__ dff df_neg(dff x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dff df_mul(dff x, dff y) {
+  const float p = x.h * y.h;
+  float e = fmaf(x.h, y.h, -p);
+  e = fmaf(x.h, y.l, e);
+  e = fmaf(x.l, y.h, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dff df_from(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_to(dff x) { return (double)x.h + (double)x.l; }
+
+__device__ __forceinline__ dfc add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc sub(dfc a, dfc b) { return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
+__device__ __forceinline__ dfc mul(dfc a, dfc b) {
+  return {df_add(df_mul(a.re, b.re), df_neg(df_mul(a.im, b.im))), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ dfc mulc(dfc a, dfc b) {   // a * conj(b)
+  return {df_add(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.im, b.re), df_neg(df_mul(a.re, b.im)))};
+}
+__device__ __forceinline__ double2 widen(dfc a) { return make_double2(df_to(a.re), df_to(a.im)); }
+__device__ __forceinline__ float2 narrow(dfc a) { return make_float2((float)df_to(a.re), (float)df_to(a.im)); }
+template <> __device__ __forceinline__ dfc from_f2<dfc>(float2 a) { return {{a.x, 0.f}, {a.y, 0.f}}; }
+template <> __device__ __forceinline__ dfc from_d<dfc>(double re, double im) { return {df_from(re), df_from(im)}; }
 
 __device__ __forceinline__ bool window_ok(int2 ps, int Ny, int Nx, int W) {
   return ps.x >= 0 && ps.y >= 0 && ps.x <= Ny - W && ps.y <= Nx - W;
@@ -92,7 +148,6 @@ template <> struct Log2<256> { static constexpr int v = 8; };
 // Grid: (W / kLines, batch).
 template <typename C, int W, bool ROWS>
 __global__ void __launch_bounds__(kFftThreads) lines_fft_kernel(C* __restrict__ data, int inverse) {
-  using R = typename Real<C>::type;
   __shared__ C buf[kLines][W];
   __shared__ C tw[W / 2];
   const int tid = threadIdx.x;
@@ -101,7 +156,7 @@ __global__ void __launch_bounds__(kFftThreads) lines_fft_kernel(C* __restrict__ 
   for (int k = tid; k < W / 2; k += kFftThreads) {
     double sn, cs;
     sincospi(2.0 * (double)k / (double)W, &sn, &cs);
-    tw[k] = mk<C>((R)cs, (R)(inverse ? sn : -sn));
+    tw[k] = from_d<C>(cs, inverse ? sn : -sn);
   }
   for (int i = tid; i < kLines * W; i += kFftThreads) {
     // rows: consecutive i run along a row; columns: consecutive i run across the kLines columns
@@ -139,22 +194,24 @@ __global__ void __launch_bounds__(kFftThreads) lines_fft_kernel(C* __restrict__ 
 
 // FP64 slice transmissions: exp(i sigma V) from the FP32 potentials, or the caller's complex
 // slices widened.
-__global__ void table64_kernel(const float* __restrict__ V, const float2* __restrict__ X, double2* __restrict__ T,
-                               size_t n, double sigma) {
+template <typename C>
+__global__ void table64_kernel(const float* __restrict__ V, const float2* __restrict__ X, C* __restrict__ T, size_t n,
+                               double sigma) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     if (X) {
-      T[i] = widen(X[i]);
+      T[i] = from_f2<C>(X[i]);
     } else {
       double sn, cs;
       sincos(sigma * (double)V[i], &sn, &cs);
-      T[i] = make_double2(cs, sn);
+      T[i] = from_d<C>(cs, sn);
     }
   }
 }
 
 // h1(k) = exp(-i pi dz lambda q_k^2) / W in double (the propagator factor of the fast path
 // before its rounding to single).
-__global__ void h1_64_kernel(double2* __restrict__ h1, int W, double dzlam, double dq) {
+template <typename C>
+__global__ void h1_64_kernel(C* __restrict__ h1, int W, double dzlam, double dq) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= W) return;
   const double q = (double)(k < W / 2 ? k : k - W) * dq;
@@ -162,7 +219,7 @@ __global__ void h1_64_kernel(double2* __restrict__ h1, int W, double dzlam, doub
   t = t - 2.0 * floor(t * 0.5);
   double sn, cs;
   sincospi(t, &sn, &cs);
-  h1[k] = make_double2(cs / W, -sn / W);
+  h1[k] = from_d<C>(cs / W, -sn / W);
 }
 
 struct Batch {
@@ -182,7 +239,7 @@ __global__ void transmit_kernel(Batch bt, int l, const float2* __restrict__ prob
     const int b = (int)(i / WW);
     const int r = (int)((i % WW) / W), c = (int)(i % W);
     const int2 ps = bt.pos[b];
-    C e = mk<C>(0, 0), psi = e;
+    C e = from_d<C>(0.0, 0.0), psi = e;
     if (window_ok(ps, bt.Ny, bt.Nx, W)) {
       psi = l == 0 ? from_f2<C>(probe[i % WW]) : wave[i];
       e = mul(psi, T[(size_t)l * bt.plane + (size_t)(ps.x + r) * bt.Nx + ps.y + c]);
@@ -199,9 +256,8 @@ __global__ void propagator_kernel(Batch bt, const H* __restrict__ h1, C* __restr
   const size_t WW = (size_t)W * W, n = (size_t)bt.nb * WW;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const int ky = (int)((i % WW) / W), kx = (int)(i % W);
-    C h = mul(mk<C>(h1[ky].x, h1[ky].y), mk<C>(h1[kx].x, h1[kx].y));
-    if (conj) h.y = -h.y;
-    data[i] = mul(data[i], h);
+    const C h = mul(h1[ky], h1[kx]);
+    data[i] = conj ? mulc(data[i], h) : mul(data[i], h);
   }
 }
 
@@ -351,9 +407,9 @@ int precise_batch(int W, int S) {
 
 namespace {
 struct Segs {
-  double2* T64 = nullptr;     // FP64 transmissions (FP64-forward mode)
-  double2* h1d = nullptr;     // FP64 propagator factor (FP64-forward mode)
-  void* wave = nullptr;       // [B][W][W] forward waves: double2 (FP64 forward) or float2 (split BF16)
+  double2* T64 = nullptr;     // transmissions of the FP64 / double-float forward
+  double2* h1d = nullptr;     // propagator factor of the FP64 / double-float forward
+  void* wave = nullptr;       // [B][W][W] forward waves: double2, double-float or float2 (split BF16)
   float2* tmp = nullptr;      // [B][W][W] second buffer of the tensor-core passes (split BF16)
   float2* chi = nullptr;      // [B][W][W] adjoint waves
   float2* stash = nullptr;    // [B][L][W][W] exit (or incident) waves kept for the adjoint
@@ -371,7 +427,8 @@ Segs carve(int precision, int W, int L, int Ny, int Nx, int S, char* base) {
   auto take = [&](size_t b) { char* q = base ? base + off : nullptr; off += a(b); return (void*)q; };
   const size_t WW = (size_t)W * W, B = (size_t)precise_batch(W, S);
   const bool tc = precision == MSP_PRECISION_BF16X3_DFT;
-  if (!tc) {
+  static_assert(sizeof(precise::dfc) == sizeof(double2), "double-float and FP64 complex share the segments");
+  if (!tc) {   // FP64 or double-float (both 16 bytes per complex value)
     g.T64 = (double2*)take((size_t)L * Ny * Nx * sizeof(double2));
     g.h1d = (double2*)take(W * sizeof(double2));
   }
@@ -398,7 +455,7 @@ size_t precise_extra_bytes(int precision, int W, int L, int Ny, int Nx, int S) {
 // The forward model and the adjoint of `mode` over all positions in batches, writing what the
 // fused kernel writes: I_out (forward), loss_part, the window gradients and illumination, and
 // the probe gradient into dprobe_part[0] (one partial).  FP64-forward mode: FP64 forward with the
-// radix-2 FFT, FP32 adjoint.  Split-BF16 mode: every 2-D transform as two tensor-core passes,
+// radix-2 FFT, FP32 adjoint.  Double-float mode: the same with the forward in double-float.  Split-BF16 mode: every 2-D transform as two tensor-core passes,
 // FP32 waves.  Reports the number of kernels launched.
 cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in, cudaStream_t st, long long* launches) {
   using namespace precise;
@@ -406,6 +463,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
   const size_t WW = (size_t)W * W, plane = (size_t)p.Ny * p.Nx;
   const int B = precise_batch(W, S);
   const bool tc = in.precision == MSP_PRECISION_BF16X3_DFT;
+  const bool df = in.precision == MSP_PRECISION_DF_FORWARD;
   const Segs g = carve(in.precision, W, L, p.Ny, p.Nx, S, in.extra);
   long long n_launch = 0;
   cudaError_t err = cudaSuccess;
@@ -414,10 +472,16 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     if ((err = tcdft_prepare(W, 0, g.mat_f, st)) != cudaSuccess) return err;
     if ((err = tcdft_prepare(W, 1, g.mat_i, st)) != cudaSuccess) return err;
     n_launch += 2;
+  } else if (df) {
+    table64_kernel<dfc><<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X,
+                                                                                 (dfc*)g.T64, (size_t)L * plane,
+                                                                                 in.sigma);
+    h1_64_kernel<dfc><<<(W + 255) / 256, 256, 0, st>>>((dfc*)g.h1d, W, in.dzlam, in.dq);
+    n_launch += 2;
   } else {
-    table64_kernel<<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X, g.T64,
-                                                                            (size_t)L * plane, in.sigma);
-    h1_64_kernel<<<(W + 255) / 256, 256, 0, st>>>(g.h1d, W, in.dzlam, in.dq);
+    table64_kernel<double2><<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X,
+                                                                                     g.T64, (size_t)L * plane, in.sigma);
+    h1_64_kernel<double2><<<(W + 255) / 256, 256, 0, st>>>(g.h1d, W, in.dzlam, in.dq);
     n_launch += 2;
   }
   flag_windows_kernel<<<(S + 255) / 256, 256, 0, st>>>(p.pos, S, p.Ny, p.Nx, W, p.err);
@@ -431,6 +495,8 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     if (tc) {
       keep_first(tcdft_pass(W, (float2*)g.wave, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
       keep_first(tcdft_pass(W, g.tmp, (float2*)g.wave, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+    } else if (df) {
+      fft2_w<dfc>(W, (dfc*)g.wave, nb, inverse, st);
     } else {
       fft2_w<double2>(W, (double2*)g.wave, nb, inverse, st);
     }
@@ -460,11 +526,14 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
       if (l > 0) {
         fwd2(nb, false);
         if (tc) propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, (float2*)g.wave, 0);
+        else if (df) propagator_kernel<dfc, dfc><<<eb, 256, 0, st>>>(bt, (const dfc*)g.h1d, (dfc*)g.wave, 0);
         else propagator_kernel<double2, double2><<<eb, 256, 0, st>>>(bt, g.h1d, (double2*)g.wave, 0);
         fwd2(nb, true);
         ++n_launch;
       }
       if (tc) transmit_kernel<float2><<<eb, 256, 0, st>>>(bt, l, p.probe, p.T, (float2*)g.wave, g.stash, 0, keep, p.cplx);
+      else if (df)
+        transmit_kernel<dfc><<<eb, 256, 0, st>>>(bt, l, p.probe, (const dfc*)g.T64, (dfc*)g.wave, g.stash, 0, keep, p.cplx);
       else transmit_kernel<double2><<<eb, 256, 0, st>>>(bt, l, p.probe, g.T64, (double2*)g.wave, g.stash, 0, keep, p.cplx);
       ++n_launch;
     }
@@ -473,6 +542,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     double* lp = fwd ? nullptr : p.loss_part + b0;
     float* Io = fwd ? p.I_out + (size_t)b0 * WW : nullptr;
     if (tc) residual_kernel<float2><<<nb, 256, 0, st>>>(bt, (const float2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
+    else if (df) residual_kernel<dfc><<<nb, 256, 0, st>>>(bt, (const dfc*)g.wave, Im, p.zthr2, g.chi, lp, Io);
     else residual_kernel<double2><<<nb, 256, 0, st>>>(bt, (const double2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
     ++n_launch;
     if (fwd) continue;

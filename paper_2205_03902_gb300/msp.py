@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmsp.so")
 
 MSP_OK, MSP_EINVAL, MSP_ENOMEM, MSP_ECUDA, MSP_EUNSUPPORTED, MSP_ETIMEOUT, MSP_EDEVICE = range(7)
 MSP_PARAM_POTENTIAL, MSP_PARAM_TRANSMISSION = 0, 1
-MSP_PRECISION_FP32, MSP_PRECISION_FP64_FORWARD, MSP_PRECISION_BF16X3_DFT = 0, 1, 2
+MSP_PRECISION_FP32, MSP_PRECISION_FP64_FORWARD, MSP_PRECISION_BF16X3_DFT, MSP_PRECISION_DF_FORWARD = 0, 1, 2, 3
 
 
 class MspError(RuntimeError):

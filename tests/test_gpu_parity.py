@@ -112,7 +112,11 @@ class Case:
         return TOL if self.strong else loss_tol(self.gd, self.probe, len(self.pos), loss_ref)
 
     def dev(self, msp, precise=False):
-        g = msp.geometry(**self.gd, precision=msp.MSP_PRECISION_FP64_FORWARD if precise else msp.MSP_PRECISION_FP32)
+        """precise: False (FP32), True or "fp64" (FP64 forward), "df" (double-float forward)."""
+        prec = msp.MSP_PRECISION_FP32
+        if precise:
+            prec = msp.MSP_PRECISION_DF_FORWARD if precise == "df" else msp.MSP_PRECISION_FP64_FORWARD
+        g = msp.geometry(**self.gd, precision=prec)
         return g, to_dev(self.probe, np.complex64), to_dev(self.V, np.float32), to_dev(self.pos, np.int32), \
             to_dev(self.I, np.float32)
 
@@ -211,31 +215,35 @@ def test_loss_and_gradients(msp, which, request):
         assert rel(dV.cpu().numpy()[l], ref["dV"][l]) <= c.tol()
 
 
-# --------------------------------------------------------------------------- precise-forward mode
-# The forward model and the residual in FP64, the adjoint in FP32: every output is held to
-# TOL = 1e-5 on every state, realistic ones included.
+# --------------------------------------------------------------------------- precise-forward modes
+# The forward model and the residual in FP64 (or double-float), the adjoint in FP32: every output
+# is held to TOL = 1e-5 on every state, realistic ones included.
+PRECISE = ["fp64", "df"]
 
+
+@pytest.mark.parametrize("mode", PRECISE)
 @pytest.mark.parametrize("which", ALL)
-def test_precise_mode_intensities_loss_and_gradients(msp, which, request):
+def test_precise_mode_intensities_loss_and_gradients(msp, which, mode, request):
     c = request.getfixturevalue(which)
-    g, p, V, pos, I = c.dev(msp, precise=True)
+    g, p, V, pos, I = c.dev(msp, precise=mode)
     Ig = msp.forward(g, p, V, pos).cpu().numpy()
     assert rel(Ig, O.forward(c.gd, c.probe, c.pos, V=c.V)) <= TOL
     loss, dV, dprobe = msp.loss_grad(g, p, V, pos, I)
     ref = O.loss_grad(c.gd, c.probe, c.pos, c.I, V=c.V)
     errs = dict(loss=abs(loss.item() - ref["loss"]) / ref["loss"], dV=rel(dV.cpu().numpy(), ref["dV"]),
                 dprobe=rel(dprobe.cpu().numpy(), ref["dprobe"]))
-    print("precise", which, errs)
+    print("precise", mode, which, errs)
     assert max(errs.values()) <= TOL, errs
     for l in range(c.gd["n_slices"]):
         assert rel(dV.cpu().numpy()[l], ref["dV"][l]) <= TOL
 
 
+@pytest.mark.parametrize("mode", PRECISE)
 @pytest.mark.parametrize("which,layer", [("c1", 1), ("c2_ragged", 0), ("c2_ragged", 3), ("c3_sub", 5), ("c4_sub", 11),
                                          ("c4_strong", 2)])
-def test_precise_mode_layer_step(msp, which, layer, request):
+def test_precise_mode_layer_step(msp, which, layer, mode, request):
     c = request.getfixturevalue(which)
-    g, p, V, pos, I = c.dev(msp, precise=True)
+    g, p, V, pos, I = c.dev(msp, precise=mode)
     loss, mu = msp.layer_step(g, p, V, pos, I, layer)
     Vn, loss_ref, mu_ref = O.layer_step(c.gd, c.probe, c.pos, c.I, layer, V=c.V)
     assert abs(loss.item() - loss_ref) / loss_ref <= TOL
@@ -248,12 +256,13 @@ def test_precise_mode_layer_step(msp, which, layer, request):
     assert np.array_equal(Vg[others], c.V[others].astype(np.float32))
 
 
+@pytest.mark.parametrize("mode", PRECISE)
 @pytest.mark.parametrize("which", ["c1", "c2_ragged", "c3_sub", "c4_sub"])
-def test_precise_mode_probe_step(msp, which, request):
+def test_precise_mode_probe_step(msp, which, mode, request):
     """The probe update -mu dL/dconj(p) at TOL, plus the FP32 rounding of the stored probe: an update
     much smaller than the probe keeps only the bits of the sum, 2^-24 ||p_new|| at most."""
     c = request.getfixturevalue(which)
-    g, p, V, pos, I = c.dev(msp, precise=True)
+    g, p, V, pos, I = c.dev(msp, precise=mode)
     loss, mu = msp.probe_step(g, p, V, pos, I)
     pn, loss_ref, mu_ref = O.probe_step(c.gd, c.probe, c.pos, c.I, V=c.V)
     assert abs(loss.item() - loss_ref) / loss_ref <= TOL
@@ -264,12 +273,13 @@ def test_precise_mode_probe_step(msp, which, request):
     assert err <= bar
 
 
-def test_precise_mode_transmission_slices(msp, c2_ragged):
+@pytest.mark.parametrize("mode", PRECISE)
+def test_precise_mode_transmission_slices(msp, c2_ragged, mode):
     """The paper's complex slices on a realistic state: intensities, loss and Wirtinger gradients at TOL."""
     c = c2_ragged
     T = transmission_case(c)
     gd = dict(c.gd, param=msp.MSP_PARAM_TRANSMISSION)
-    g = msp.geometry(**gd, precision=msp.MSP_PRECISION_FP64_FORWARD)
+    g = msp.geometry(**gd, precision=msp.MSP_PRECISION_DF_FORWARD if mode == "df" else msp.MSP_PRECISION_FP64_FORWARD)
     p, X, pos, I = to_dev(c.probe, np.complex64), to_dev(T, np.complex64), to_dev(c.pos, np.int32), to_dev(c.I, np.float32)
     assert rel(msp.forward(g, p, X, pos).cpu().numpy(), O.forward(c.gd, c.probe, c.pos, T=T)) <= TOL
     loss, dX, dprobe = msp.loss_grad(g, p, X, pos, I)
@@ -282,12 +292,13 @@ def test_precise_mode_transmission_slices(msp, c2_ragged):
     assert rel(X.cpu().numpy()[1] - T[1], Xl[1] - T[1]) <= TOL
 
 
-def test_precise_mode_edge_cases(msp, c1):
+@pytest.mark.parametrize("mode", PRECISE)
+def test_precise_mode_edge_cases(msp, c1, mode):
     """Empty scan, a window outside the object (skipped and flagged, as in the FP32 mode), the zero
     probe (zero rule everywhere) and bit-reproducible repeats."""
-    g, p, V, pos, I = c1.dev(msp, precise=True)
+    g, p, V, pos, I = c1.dev(msp, precise=mode)
     empty = Case(synth.C1, pos=np.zeros((0, 2), dtype=np.int32))
-    ge, pe, Ve, pse, Ie = empty.dev(msp, precise=True)
+    ge, pe, Ve, pse, Ie = empty.dev(msp, precise=mode)
     loss, dV, dprobe = msp.loss_grad(ge, pe, Ve, pse, Ie)
     assert loss.item() == 0.0 and torch.count_nonzero(dV) == 0 and torch.count_nonzero(dprobe) == 0
     loss, dV, dprobe = msp.loss_grad(g, torch.zeros_like(p), V, pos, I)

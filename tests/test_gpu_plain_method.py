@@ -130,7 +130,7 @@ def check_path(tag, h, o, V, b, n, loss_bars, amp=1.0, p=None, bp=None):
         assert rel(p, pr) <= bp * n, msg
 
 
-PRECISIONS = ["fp32", "precise"]
+PRECISIONS = ["fp32", "precise", "df"]
 
 
 @pytest.mark.parametrize("mode", PRECISIONS)
@@ -150,14 +150,15 @@ def test_c1_fifty_sweeps_from_zero_with_known_probe(msp, mode):
     assert o["hist"][-1] < 0.05 * o["hist"][0]          # the method converges on noiseless data
     amp, d = amplification(o, oracle_path(gd, probe, pos, I, V0, sweeps, bars=False, round32=False), n)
     print(f"c1 50 sweeps: oracle paths with and without FP32 storage differ by {d:.3e}")
-    prec = msp.MSP_PRECISION_FP64_FORWARD if mode == "precise" else msp.MSP_PRECISION_FP32
+    prec = {"fp32": msp.MSP_PRECISION_FP32, "precise": msp.MSP_PRECISION_FP64_FORWARD,
+            "df": msp.MSP_PRECISION_DF_FORWARD}[mode]
     g = msp.geometry(**gd, precision=prec)
     V = to_dev(V0, np.float32)
     h = msp.reconstruct(g, msp.plan(sweeps), to_dev(probe, np.complex64), V, to_dev(pos, np.int32),
                         to_dev(I, np.float32)).cpu().numpy()
     assert len(h) == len(o["hist"]) == n + 1
-    if mode == "precise":
-        check_path("c1 50 sweeps precise", h, o, V.cpu().numpy(), TOL, n, TOL, amp)
+    if mode != "fp32":
+        check_path(f"c1 50 sweeps {mode}", h, o, V.cpu().numpy(), TOL, n, TOL, amp)
     else:
         check_path("c1 50 sweeps fp32", h, o, V.cpu().numpy(), o["b"], n, o["lbar"], amp)
 
@@ -178,15 +179,16 @@ def test_c2_sub_scan_with_probe_estimation(msp, mode):
     n = sweeps * (cfg.n_slices + 1)
     o = oracle_path(gd, probe, pos, I, V0, sweeps, probe_steps=1, bars=mode == "fp32")
     amp, d = amplification(o, oracle_path(gd, probe, pos, I, V0, sweeps, probe_steps=1, bars=False, round32=False), n)
-    prec = msp.MSP_PRECISION_FP64_FORWARD if mode == "precise" else msp.MSP_PRECISION_FP32
+    prec = {"fp32": msp.MSP_PRECISION_FP32, "precise": msp.MSP_PRECISION_FP64_FORWARD,
+            "df": msp.MSP_PRECISION_DF_FORWARD}[mode]
     g = msp.geometry(**gd, precision=prec)
     V = to_dev(V0, np.float32)
     p = to_dev(probe, np.complex64)
     h = msp.reconstruct(g, msp.plan(sweeps, probe_steps=1), p, V, to_dev(pos, np.int32),
                         to_dev(I, np.float32)).cpu().numpy()
     assert len(h) == len(o["hist"]) == n + 1
-    if mode == "precise":
-        check_path("c2 4x4 probe estimation precise", h, o, V.cpu().numpy(), TOL, n, TOL, amp,
+    if mode != "fp32":
+        check_path(f"c2 4x4 probe estimation {mode}", h, o, V.cpu().numpy(), TOL, n, TOL, amp,
                    p=p.cpu().numpy(), bp=TOL)
     else:
         check_path("c2 4x4 probe estimation fp32", h, o, V.cpu().numpy(), o["b"], n, o["lbar"], amp,
