@@ -677,6 +677,103 @@ def plain_method_run(msp, torch, dev, cfg, sweeps, probe_steps, precision, strea
     return out
 
 
+def net_macs_per_pixel(L):
+    """Multiply-adds per pixel of the proposal network's forward pass (true channel counts)."""
+    ch = [2 * L, 64, 64, 64, 64, 64, L]
+    return sum(9 * ch[i] * ch[i + 1] for i in range(6))
+
+
+def learned_proposal_run(msp, torch, dev, stream, peaks, n_train=4, sweeps=16, train_steps=300, every=2):
+    """The learned-proposal form on the eight-slice workload: a corpus from plain-method
+    trajectories of `n_train` seeded specimens, Adam training, the network's kernel rates, and the
+    wall time to the plain method's final loss on a held-out specimen, learned (acceptance loop)
+    against plain (msp_reconstruct)."""
+    from paper_2205_03902_gb300 import learned
+    cfg5 = synth.C5
+    L, N = cfg5.n_slices, cfg5.obj
+    zeros = lambda: torch.zeros((L, N, N), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    corpus = learned.Corpus()
+    for k in range(n_train):
+        c = synth.c5_specimen(100 + k)
+        g, gd, pos, d_pos, ws, _, p, I = make_inputs(msp, torch, dev, c)
+        probe, I = torch.from_numpy(p).to(dev), torch.from_numpy(I).to(dev)
+        states, _ = learned.plain_trajectory(g, probe, zeros(), d_pos, I, sweeps, ws=ws)
+        learned.add_trajectory(corpus, g, probe, d_pos, I, states, every=every, ws=ws)
+        del ws
+    torch.cuda.synchronize()
+    corpus_s = time.perf_counter() - t0
+    sv, sg, sd = learned.input_scales(corpus)
+    s = msp.net_shape(L, N, N, sv, sg, sd)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    a, b = ev()
+    a.record(stream)
+    params, tl = learned.train(s, corpus, train_steps, lr=1e-3, seed=0)
+    b.record(stream)
+    b.synchronize()
+    train_ms = a.elapsed_time(b)
+    # kernel rates of the network
+    nws = msp.net_make_workspace(s, dev)
+    out = torch.empty_like(corpus.V[0])
+    msp.net_forward(s, params, corpus.V[0], corpus.G[0], out=out, ws=nws)
+    msp.profile_read(reset=True)
+    fms = time_events(lambda: msp.net_forward(s, params, corpus.V[0], corpus.G[0], out=out, ws=nws), 10, stream)
+    pc, m_, v_ = params.clone(), torch.zeros_like(params), torch.zeros_like(params)
+    tms = time_events(lambda: msp.net_train_step(s, pc, m_, v_, 1, 1e-3, corpus.V[0], corpus.G[0], corpus.T[0],
+                                                 ws=nws), 10, stream)
+    P_px = N * N
+    fwd_flop = 2.0 * P_px * net_macs_per_pixel(L)
+    ch = [2 * L, 64, 64, 64, 64, 64, L]
+    dgrad_flop = 2.0 * P_px * sum(9 * ch[i] * ch[i + 1] for i in range(1, 6))
+    train_flop = 2 * fwd_flop + dgrad_flop          # forward, weight gradients, data gradients
+    bf16_peak = float(peaks.get("bf16_tflops", 0.0)) or None
+    # held-out specimen: plain to its final loss, then the learned loop to the same loss
+    c = synth.c5_specimen(200)
+    g, gd, pos, d_pos, ws, _, p, I = make_inputs(msp, torch, dev, c)
+    probe, I = torch.from_numpy(p).to(dev), torch.from_numpy(I).to(dev)
+    lws = msp.learned_make_workspace(g, s, dev)
+    msp.reconstruct(g, msp.plan(1), probe, zeros(), d_pos, I, ws=ws)                 # warm-up
+    msp.learned_propose(g, s, params, probe, zeros(), d_pos, I, ws=ws, learn_ws=lws)
+    V = zeros()
+    torch.cuda.synchronize()
+    a, b = ev()
+    a.record(stream)
+    h = msp.reconstruct(g, msp.plan(sweeps), probe, V, d_pos, I, ws=ws)
+    b.record(stream)
+    b.synchronize()
+    plain_ms, target = a.elapsed_time(b), float(h[-1].item())
+    V = zeros()
+    torch.cuda.synchronize()
+    a, b = ev()
+    a.record(stream)
+    hist = learned.reconstruct_learned(g, s, params, probe, V, d_pos, I, 2 * sweeps, target_loss=target, ws=ws,
+                                       learn_ws=lws)
+    b.record(stream)
+    b.synchronize()
+    learned_ms = a.elapsed_time(b)
+    reached = hist[-1][2] <= target
+    acc = [x[1] for x in hist]
+    return {
+        "workload": cfg5.name, "specimens": {"train": [100 + k for k in range(n_train)], "held_out": 200},
+        "corpus": {"samples": len(corpus), "trajectory_sweeps": sweeps, "state_every": every,
+                   "build_s": corpus_s, "note": "target = V_K - V_k along each plain trajectory"},
+        "scales": {"s_V": sv, "s_G": sg, "s_D": sd},
+        "training": {"steps": train_steps, "ms": train_ms, "loss_first10": float(np.mean(tl[:10])),
+                     "loss_last10": float(np.mean(tl[-10:]))},
+        "net_forward": {"ms": fms, "tflops": fwd_flop / (fms * 1e-3) / 1e12,
+                        "frac_of_bf16_peak": (fwd_flop / (fms * 1e-3) / 1e12) / bf16_peak if bf16_peak else None,
+                        "flop": fwd_flop},
+        "net_train_step": {"ms": tms, "tflops": train_flop / (tms * 1e-3) / 1e12,
+                           "frac_of_bf16_peak": (train_flop / (tms * 1e-3) / 1e12) / bf16_peak if bf16_peak else None,
+                           "flop": train_flop},
+        "time_to_plain_final_loss": {"target_loss": target, "plain_ms": plain_ms, "plain_sweeps": sweeps,
+                                     "learned_ms": learned_ms if reached else None, "learned_reached": bool(reached),
+                                     "learned_iterations": len(hist), "accepted": int(sum(acc)),
+                                     "learned_final_loss": hist[-1][2],
+                                     "speedup": plain_ms / learned_ms if reached else None},
+    }
+
+
 def run_msp(args, rank, world, local_rank):
     import torch
     from paper_2205_03902_gb300 import msp
@@ -880,6 +977,7 @@ def run_msp(args, rank, world, local_rank):
         extra["c3_full"]["split_bf16_dft"] = {"ms": c3b, "value": c3.n_pos * c3.n_slices / (c3b * 1e-3),
                                               "cost_vs_fp32": c3b / c3ms}
         del ws3b
+        extra["learned_proposal"] = learned_proposal_run(msp, torch, dev, stream, read_peaks())
     clocks = sampler.stop()
     clocks["window"] = "the timed steps and the measurements of this run that follow them"
 

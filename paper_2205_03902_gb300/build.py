@@ -17,7 +17,7 @@ OBJDIR = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libmsp.so")
 SOURCES = ["msp_position.cu", "msp_position_cluster.cu", "msp_api.cu", "msp_noalloc.cu", "msp_smd.cu", "msp_dft.cu",
-           "msp_precise.cu", "msp_tcdft.cu"]
+           "msp_precise.cu", "msp_tcdft.cu", "msp_learn.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

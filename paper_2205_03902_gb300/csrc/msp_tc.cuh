@@ -45,6 +45,29 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, ui
       "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Instruction descriptor of kind::f16 with bf16 operands: D in f32, A and B bf16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (TMEM) = A B^T (+ D when acc != 0), kind::f16 (bf16 operands from shared memory), one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Byte offset of 16-bit element (r, k) of an R x 64 operand block in the canonical no-swizzle
+// K-major layout: core matrices of 8 rows x 8 elements (16 bytes a row), 128 bytes apart along K
+// (the descriptor's LBO) and 1024 bytes apart along the rows (its SBO).
+__host__ __device__ constexpr uint32_t kmaj16(int r, int k) {
+  return (uint32_t)((k >> 3) * 128 + (r >> 3) * 1024 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// Bounded wait on an mbarrier phase; false when `limit` polls ran out.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, int limit);
+
 // The mbarrier receives one arrival once every tcgen05 operation this thread issued so far is done.
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -109,6 +132,14 @@ __device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint4& v) {
                : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i) {
+    if (mbar_test(bar, parity)) return true;
+    if (i > 64) __nanosleep(32);
+  }
+  return false;
+}
 
 
 }  // namespace tc

@@ -34,6 +34,11 @@
 namespace msp {
 namespace tcdft {
 
+using tc::kmaj16;
+using tc::idesc_bf16;
+using tc::mma_bf16;
+using tc::wait_phase;
+
 constexpr int kM = 128;        // lines per CTA
 constexpr int kKC = 64;        // real K per chunk (32 complex inputs)
 constexpr int kThreads = 256;
@@ -45,24 +50,6 @@ __host__ __device__ constexpr int n_chunks(int W) { return 2 * W / kKC; }
 // bf16 elements of one (tile, chunk, part) block of B': NT rows x kKC
 __host__ __device__ constexpr size_t block_elems(int W) { return (size_t)n_tile(W) * kKC; }
 
-// Byte offset of element (r, k) of an R x kKC bf16 operand block in the canonical K-major layout:
-// core matrices of 8 rows x 8 elements (16 bytes a row), 128 bytes apart along K (LBO), and
-// (kKC / 8) x 128 = 1024 bytes apart along the rows (SBO).
-__host__ __device__ constexpr uint32_t kmaj16(int r, int k) {
-  return (uint32_t)((k >> 3) * 128 + (r >> 3) * 1024 + (r & 7) * 16 + (k & 7) * 2);
-}
-
-// kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
 
 // B' of the W-point DFT (sign -1: forward, +1: inverse) as split bf16, laid out block by block:
 // block (tile t, chunk c, part p) at ((t * n_chunks + c) * 2 + p) * block_elems, each block in
@@ -96,14 +83,6 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Bounded wait on an mbarrier phase (thread-local); false when `limit` polls ran out.
-__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, int limit) {
-  for (int i = 0; i < limit; ++i) {
-    if (tc::mbar_test(bar, parity)) return true;
-    if (i > 64) __nanosleep(32);
-  }
-  return false;
-}
 
 // One pass: out[b][n][r] = sum_m in[b][r][m] w^(m n) for every wave b < nb (see the file comment).
 // `in` and `out` must not overlap.  err: 2 = a wait for the tensor core ran out (results invalid),

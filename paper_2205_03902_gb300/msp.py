@@ -87,6 +87,22 @@ def smd_geometry(n, n_slices, n_pos, wavelength_A, dz_A, pixel_A, **_ignored) ->
     return SmdGeometry(int(n), int(n_slices), int(n_pos), float(wavelength_A), float(dz_A), float(pixel_A))
 
 
+class NetShape(ctypes.Structure):
+    """msp_net_shape of include/msp_learn.h."""
+    _fields_ = [
+        ("n_slices", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("scale_v", ctypes.c_double),
+        ("scale_g", ctypes.c_double),
+        ("scale_d", ctypes.c_double),
+    ]
+
+
+def net_shape(n_slices, height, width, scale_v=1.0, scale_g=1.0, scale_d=1.0) -> NetShape:
+    return NetShape(int(n_slices), int(height), int(width), float(scale_v), float(scale_g), float(scale_d))
+
+
 _lib = None
 _P = ctypes.c_void_p
 _G = ctypes.POINTER(Geometry)
@@ -116,6 +132,20 @@ _SIGS = {
     "msp_smd_final_slices": ([_GS, _P, _P, _P, _P], ctypes.c_int),
     "msp_dft2_tc_workspace_bytes": ([ctypes.c_int32, ctypes.c_int32], ctypes.c_size_t),
     "msp_dft2_tc": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_net_validate": ([ctypes.POINTER(NetShape)], ctypes.c_int),
+    "msp_net_param_count": ([ctypes.POINTER(NetShape)], ctypes.c_size_t),
+    "msp_net_workspace_bytes": ([ctypes.POINTER(NetShape)], ctypes.c_size_t),
+    "msp_net_init": ([ctypes.POINTER(NetShape), _P, ctypes.c_uint64, _P], ctypes.c_int),
+    "msp_net_forward": ([ctypes.POINTER(NetShape), _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_net_loss_grad": ([ctypes.POINTER(NetShape), _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_net_train_step": ([ctypes.POINTER(NetShape), _P, _P, _P, ctypes.c_int32, ctypes.c_double, _P, _P, _P, _P, _P,
+                            ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_learned_workspace_bytes": ([_G, ctypes.POINTER(NetShape)], ctypes.c_size_t),
+    "msp_learned_propose": ([_G, ctypes.POINTER(NetShape), _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P,
+                             ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_conv3x3_test": ([ctypes.c_int32] * 4 + [_P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_conv3x3_wgrad_test": ([ctypes.c_int32] * 4 + [_P, _P, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "msp_conv3x3_test_workspace_bytes": ([ctypes.c_int32] * 4, ctypes.c_size_t),
     "msp_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "msp_last_error_message": ([], ctypes.c_char_p),
 }
@@ -503,3 +533,165 @@ class MultisliceLoss(torch.autograd.Function):
 def multislice_loss(geom: Geometry, V, probe, pos, I_meas, ws=None):
     """Differentiable loss L(V, probe) (float64 scalar tensor); see MultisliceLoss."""
     return MultisliceLoss.apply(V, probe, geom, pos, I_meas, _ws(geom, ws, V.device))
+
+
+# ---------------------------------------------------------------------------------------------
+# learned proposal (include/msp_learn.h)
+# ---------------------------------------------------------------------------------------------
+def net_validate(s: NetShape) -> int:
+    return lib().msp_net_validate(ctypes.byref(s))
+
+
+def net_param_count(s: NetShape) -> int:
+    n = lib().msp_net_param_count(ctypes.byref(s))
+    if n == 0:
+        _check(net_validate(s), "msp_net_param_count")
+    return int(n)
+
+
+def _aligned_buffer(n: int, device) -> Workspace:
+    buf = torch.empty(n + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return Workspace(buf[off:off + n])
+
+
+def net_make_workspace(s: NetShape, device=None) -> Workspace:
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n = lib().msp_net_workspace_bytes(ctypes.byref(s))
+    if n == 0:
+        _check(net_validate(s), "msp_net_workspace_bytes")
+    return _aligned_buffer(int(n), device)
+
+
+def _net_ws(s, ws, device):
+    if ws is None:
+        return net_make_workspace(s, device)
+    if ws.nbytes < lib().msp_net_workspace_bytes(ctypes.byref(s)):
+        raise ValueError("workspace too small for this network shape")
+    return ws
+
+
+def net_init(s: NetShape, seed: int, device=None, stream=None) -> torch.Tensor:
+    """The network's initial FP32 parameters (msp_net_init)."""
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    params = torch.empty(net_param_count(s), dtype=torch.float32, device=device)
+    _check(lib().msp_net_init(ctypes.byref(s), _ptr(params), ctypes.c_uint64(seed), _stream(stream)), "msp_net_init")
+    return params
+
+
+def _net_planes(s: NetShape, params, V, G, target=None):
+    device = V.device
+    _need(params, "params", torch.float32, (net_param_count(s),), device)
+    shp = (s.n_slices, s.height, s.width)
+    _need(V, "V", torch.float32, shp, device)
+    _need(G, "G", torch.float32, shp, device)
+    if target is not None:
+        _need(target, "target", torch.float32, shp, device)
+    return device
+
+
+def net_forward(s: NetShape, params, V, G, out=None, ws=None, stream=None):
+    """Proposal dV_prop [L][H][W] = s_D net(s_V V, s_G G) (msp_net_forward)."""
+    device = _net_planes(s, params, V, G)
+    if out is None:
+        out = torch.empty_like(V)
+    _need(out, "dV_prop", torch.float32, tuple(V.shape), device)
+    ws = _net_ws(s, ws, device)
+    _check(lib().msp_net_forward(ctypes.byref(s), _ptr(params), _ptr(V), _ptr(G), _ptr(out), ws.ptr(), ws.nbytes,
+                                 _stream(stream)), "msp_net_forward")
+    return out
+
+
+def net_loss_grad(s: NetShape, params, V, G, target, ws=None, stream=None):
+    """(loss (device float64 scalar), gradient (FP32, parameter layout)) (msp_net_loss_grad)."""
+    device = _net_planes(s, params, V, G, target)
+    ws = _net_ws(s, ws, device)
+    grad = torch.empty_like(params)
+    loss = torch.empty((), dtype=torch.float64, device=device)
+    _check(lib().msp_net_loss_grad(ctypes.byref(s), _ptr(params), _ptr(V), _ptr(G), _ptr(target), _ptr(grad),
+                                   _ptr(loss), ws.ptr(), ws.nbytes, _stream(stream)), "msp_net_loss_grad")
+    return loss, grad
+
+
+def net_train_step(s: NetShape, params, adam_m, adam_v, step: int, lr: float, V, G, target, loss=None, ws=None,
+                   stream=None):
+    """One Adam step in place on params / adam_m / adam_v (msp_net_train_step); returns the loss
+    before the step (device float64 scalar)."""
+    device = _net_planes(s, params, V, G, target)
+    _need(adam_m, "adam_m", torch.float32, tuple(params.shape), device)
+    _need(adam_v, "adam_v", torch.float32, tuple(params.shape), device)
+    ws = _net_ws(s, ws, device)
+    if loss is None:
+        loss = torch.empty((), dtype=torch.float64, device=device)
+    _check(lib().msp_net_train_step(ctypes.byref(s), _ptr(params), _ptr(adam_m), _ptr(adam_v), int(step), float(lr),
+                                    _ptr(V), _ptr(G), _ptr(target), _ptr(loss), ws.ptr(), ws.nbytes,
+                                    _stream(stream)), "msp_net_train_step")
+    return loss
+
+
+def learned_make_workspace(g: Geometry, s: NetShape, device=None) -> Workspace:
+    device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    n = lib().msp_learned_workspace_bytes(ctypes.byref(g), ctypes.byref(s))
+    if n == 0:
+        _check(net_validate(s), "msp_learned_workspace_bytes")
+        _check(validate_geometry(g), "msp_learned_workspace_bytes")
+        raise MspError(MSP_EINVAL, "msp_learned_workspace_bytes", "network shape and geometry disagree")
+    return _aligned_buffer(int(n), device)
+
+
+def learned_propose(g: Geometry, s: NetShape, params, probe, V, pos, I_meas, accepted=None, loss=None, ws=None,
+                    learn_ws=None, stream=None):
+    """One proposal under the acceptance rule (msp_learned_propose): V becomes V + net(V, dL/dV)
+    if that lowers the loss, in place.  Returns (accepted (device int32), loss (device float64
+    [2]: before, at the candidate))."""
+    device = _arrays(g, probe, V, pos, I_meas)
+    _need(params, "params", torch.float32, (net_param_count(s),), device)
+    ws = _ws(g, ws, device)
+    if learn_ws is None:
+        learn_ws = learned_make_workspace(g, s, device)
+    if accepted is None:
+        accepted = torch.zeros((), dtype=torch.int32, device=device)
+    if loss is None:
+        loss = torch.empty(2, dtype=torch.float64, device=device)
+    _check(lib().msp_learned_propose(ctypes.byref(g), ctypes.byref(s), _ptr(params), _ptr(probe), _ptr(V), _ptr(pos),
+                                     _ptr(I_meas), _ptr(accepted), _ptr(loss), ws.ptr(), ws.nbytes, learn_ws.ptr(),
+                                     learn_ws.nbytes, _stream(stream)), "msp_learned_propose")
+    return accepted, loss
+
+
+def _conv_ws(H, W, cin, cout, device):
+    n = lib().msp_conv3x3_test_workspace_bytes(H, W, cin, cout)
+    if n == 0:
+        raise MspError(MSP_EUNSUPPORTED, "msp_conv3x3_test", "c_in, c_out in {16, 64}, width a multiple of 128")
+    return _aligned_buffer(int(n), device)
+
+
+def conv3x3_test(x_bf16, w, bias=None, stream=None):
+    """Pre-activation conv(x) + bias (FP32 [H][W][c_out]) of one BF16 NHWC image (msp_conv3x3_test)."""
+    H, W, cin = x_bf16.shape
+    cout = w.shape[0]
+    device = x_bf16.device
+    _need(x_bf16, "in", torch.bfloat16, (H, W, cin), device)
+    _need(w, "w", torch.float32, (cout, 9, cin), device)
+    if bias is not None:
+        _need(bias, "bias", torch.float32, (cout,), device)
+    out = torch.empty((H, W, cout), dtype=torch.float32, device=device)
+    ws = _conv_ws(H, W, cin, cout, device)
+    _check(lib().msp_conv3x3_test(H, W, cin, cout, _ptr(x_bf16), _ptr(w), _ptr(bias), _ptr(out), ws.ptr(), ws.nbytes,
+                                  _stream(stream)), "msp_conv3x3_test")
+    return out, ws
+
+
+def conv3x3_wgrad_test(x_bf16, g_bf16, stream=None):
+    """(dW [c_out][9][c_in], db [c_out]) of a 3 x 3 convolution (msp_conv3x3_wgrad_test)."""
+    H, W, cin = x_bf16.shape
+    cout = g_bf16.shape[2]
+    device = x_bf16.device
+    _need(x_bf16, "in", torch.bfloat16, (H, W, cin), device)
+    _need(g_bf16, "grad_pre", torch.bfloat16, (H, W, cout), device)
+    dW = torch.empty((cout, 9, cin), dtype=torch.float32, device=device)
+    db = torch.empty((cout,), dtype=torch.float32, device=device)
+    ws = _conv_ws(H, W, cin, cout, device)
+    _check(lib().msp_conv3x3_wgrad_test(H, W, cin, cout, _ptr(x_bf16), _ptr(g_bf16), _ptr(dW), _ptr(db), ws.ptr(),
+                                        ws.nbytes, _stream(stream)), "msp_conv3x3_wgrad_test")
+    return dW, db, ws

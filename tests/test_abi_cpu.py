@@ -158,3 +158,46 @@ def test_reconstruct_history_length_and_plan_validation(lib):
 def test_wait_limit_hook_needs_no_device(lib):
     assert lib.msp_set_wait_limit(5) == msp.MSP_OK
     assert lib.msp_set_wait_limit(0) == msp.MSP_OK
+
+
+# ---- learned proposal (include/msp_learn.h) ----------------------------------------------------
+@pytest.mark.parametrize("kw,status", [
+    ({}, msp.MSP_OK),
+    (dict(n_slices=8, height=1, width=128), msp.MSP_OK),
+    (dict(n_slices=0), msp.MSP_EUNSUPPORTED),
+    (dict(n_slices=9), msp.MSP_EUNSUPPORTED),
+    (dict(width=200), msp.MSP_EUNSUPPORTED),
+    (dict(width=0), msp.MSP_EUNSUPPORTED),
+    (dict(height=0), msp.MSP_EUNSUPPORTED),
+    (dict(height=70000), msp.MSP_EUNSUPPORTED),
+    (dict(scale_v=0.0), msp.MSP_EINVAL),
+    (dict(scale_d=float("nan")), msp.MSP_EINVAL),
+])
+def test_net_shape_validation(lib, kw, status):
+    base = dict(n_slices=4, height=384, width=384, scale_v=1.0, scale_g=1.0, scale_d=1.0)
+    base.update(kw)
+    assert msp.net_validate(msp.net_shape(**base)) == status
+
+
+def test_net_parameter_count_matches_the_layer_list(lib):
+    from oracle import proposal_oracle as P
+    for L in (1, 2, 4, 8):
+        assert msp.net_param_count(msp.net_shape(L, 128, 128)) == P.param_count(L)
+    assert lib.msp_net_param_count(None) == 0
+    assert lib.msp_net_workspace_bytes(ctypes.byref(msp.net_shape(4, 128, 100))) == 0
+    assert lib.msp_net_workspace_bytes(ctypes.byref(msp.net_shape(4, 384, 384))) > 0
+
+
+def test_net_calls_reject_bad_arguments_before_any_launch(lib):
+    s = msp.net_shape(4, 128, 128)
+    n = lib.msp_net_workspace_bytes(ctypes.byref(s))
+    assert lib.msp_net_forward(ctypes.byref(s), None, None, None, None, None, n, None) != msp.MSP_OK
+    bad = msp.net_shape(4, 128, 120)
+    assert lib.msp_net_forward(ctypes.byref(bad), None, None, None, None, None, 0, None) == msp.MSP_EUNSUPPORTED
+    assert lib.msp_net_train_step(ctypes.byref(bad), None, None, None, 1, 1e-3, None, None, None, None, None, 0,
+                                  None) == msp.MSP_EUNSUPPORTED
+    for args in [(4, 128, 16, 64), (4, 130, 16, 64), (4, 128, 32, 64), (0, 128, 16, 16), (4, 128, 64, 8)]:
+        want = 0 if args[1] % 128 or args[2] not in (16, 64) or args[3] not in (16, 64) or args[0] < 1 else 1
+        got = lib.msp_conv3x3_test_workspace_bytes(*args)
+        assert (got > 0) == bool(want), args
+    assert lib.msp_conv3x3_test(4, 130, 16, 64, None, None, None, None, None, 0, None) == msp.MSP_EUNSUPPORTED

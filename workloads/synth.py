@@ -64,7 +64,23 @@ C3 = Workload("c3_L8_obj384_W128_S4096", 8, 384, 0.15, 2.0, 30, 128, (64, 64), 4
               lattice_A=3.9, species_vnm=(1.0, 2.5), vacancy=0.3, rotate=True, dose=1e5, seed=2)
 C4 = Workload("c4_L16_obj640_W256_S2304", 16, 640, 0.1, 1.0, 30, 256, (48, 48), 8, 30.0, 100.0, None,
               lattice_A=3.9, species_vnm=None, seed=3)
-CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c4": C4}
+# The learned-proposal workload: the c2 scan geometry with eight slices; every specimen of its
+# corpus draws its own lattice constant (3-5 A), rotation, one to three species, vacancy fraction
+# (0-40 %) and dose (1e5-1e7 electrons per pattern): `c5_specimen(seed)`.
+C5 = Workload("c5_L8_obj384_W128_S1024", 8, 384, 0.15, 2.0, 30, 128, (32, 32), 8, 30.0, 100.0, None,
+              lattice_A=3.9, species_vnm=(1.0, 2.5), vacancy=0.3, rotate=True, dose=1e6, seed=6)
+CONFIGS = {"c1": C1, "c2": C2, "c3": C3, "c4": C4, "c5": C5}
+
+
+def c5_specimen(seed: int, base: Workload = C5) -> Workload:
+    """One seeded specimen of the learned-proposal corpus (see C5)."""
+    rng = np.random.default_rng([seed, 55])
+    n_species = int(rng.integers(1, 4))
+    return dataclasses.replace(
+        base, lattice_A=float(rng.uniform(3.0, 5.0)),
+        species_vnm=tuple(float(a) for a in rng.uniform(0.5, 3.0, size=n_species)),
+        vacancy=float(rng.uniform(0.0, 0.4)), rotate=True, dose=float(10.0 ** rng.uniform(5.0, 7.0)),
+        seed=int(seed))
 
 # Algorithm 2 on the paper's own setting (Table 1, GaAs): a 2 x 2 supercell of the
 # 5.6533 A cubic cell on a 40 x 40 grid, every one of the 40 x 40 cyclic probe shifts,
