@@ -244,11 +244,13 @@ msp_status msp_forward_noalloc(const msp_geometry* g, const float* probe, const 
 msp_status msp_check_workspace(void* ws, void* stream);
 
 /* Failure-detection hook: the number of polls after which a wait of the tensor-core
- * kernels (msp_smd_matrix_step, msp_dft2_tc) for their own pipeline gives up, for every
- * later call of this process.  The default (polls < 1 restores it) is 2^20 polls, well
- * under a second; a tiny bound makes the waits run out on purpose, which the kernels
- * report through the workspace flag (msp_check_workspace: MSP_ETIMEOUT) after freeing
- * their tensor memory, leaving the device usable. */
+ * kernels (msp_smd_matrix_step, msp_dft2_tc, the split-BF16 mode, the convolutions of
+ * msp_learn.h) for their own pipeline gives up, for every later call of this process.
+ * polls = 0 restores the default, 2^20 polls, well under a second; polls < 0 makes every
+ * such wait give up without polling.  A tiny or negative bound makes the waits run out on
+ * purpose, which the kernels report through the workspace flag (msp_check_workspace:
+ * MSP_ETIMEOUT) after waiting (with their own fixed bound) for the MMAs they issued and
+ * freeing their tensor memory, leaving the device usable. */
 msp_status msp_set_wait_limit(int32_t polls);
 
 /* Profiling hooks, off by default.  While enabled, every launch of the dominant

@@ -956,7 +956,7 @@ msp_status msp_reconstruct(const msp_geometry* g, const msp_plan* plan, float* p
 
 msp_status msp_set_wait_limit(int32_t polls) {
   g_err.clear();
-  g_wait_limit.store(polls >= 1 ? polls : (1 << 20), std::memory_order_relaxed);
+  g_wait_limit.store(polls >= 1 ? polls : polls == 0 ? (1 << 20) : 0, std::memory_order_relaxed);
   return MSP_OK;
 }
 

@@ -4,20 +4,23 @@
 //
 // Every convolution is an implicit GEMM on tcgen05 (kind::f16, bf16 operands, FP32 accumulator
 // in tensor memory):
-//   forward / data gradient:  D[pixel][c_out] = sum_k A[pixel][k] B[c_out][k], k = 9-tap x c_in,
-//     A gathered per K chunk of 64 from the NHWC activations (8 channels of one tap are 16
-//     contiguous bytes), zero outside the image; B the packed weights.  One CTA per 128 pixels
-//     of an image row.  The data gradient is the forward convolution of the gradient with the
-//     weights mirrored in the taps and transposed in the channels.
-//   weight gradient:  D[c_out][(tap, c_in)] = sum_p dPre[c_out][p] in[c_in][p + tap], K = the
-//     pixels of one image row per CTA, operands from the channel-major (CHW) copies every
-//     layer also writes; the per-row partial sums are added in a fixed order.
-// Operands are staged through shared memory in the canonical no-swizzle K-major layout
-// (core matrices of 8 rows x 16 bytes); one thread issues the MMAs and commits them to an
-// mbarrier whose bounded wait records a timeout in the error word.
+//   forward / data gradient:  D[pixel][c_out] = sum over taps and c_in of in[pixel + tap][c_in]
+//     w[c_out][tap][c_in], 128 pixels of an image row per accumulator; persistent CTAs stage each
+//     input row once (NHWC, 8 channels of a pixel are 16 contiguous bytes, zero outside the
+//     image) and read all nine taps from it; the weights stay resident.  The data gradient is
+//     the forward convolution of the gradient with the weights mirrored in the taps and
+//     transposed in the channels.
+//   weight gradient:  D_tap[c_in][c_out] = sum_p in[p + tap][c_in] dPre[p][c_out], K = the pixels
+//     of a CTA's rows, both operands MN-major from the same staged NHWC rows; the bias gradient
+//     is one more row of it (a constant group of ones); the per-CTA partial sums are added in a
+//     fixed order.
+// Operands are staged through shared memory in the canonical no-swizzle layouts (core matrices
+// of 8 rows x 16 bytes, loaded with cp.async); one thread issues the MMAs and commits them to
+// mbarriers whose bounded waits record a timeout in the error word.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <string>
@@ -39,7 +42,6 @@ using bf16 = __nv_bfloat16;
 constexpr int kLayers = 6;
 constexpr int kHid = 64;
 constexpr int kPix = 128;      // pixels per CTA (M)
-constexpr int kKC = 64;        // K per chunk
 constexpr int kThreads = 256;
 constexpr int kDrainLimit = 1 << 20;
 
@@ -50,101 +52,112 @@ __device__ __forceinline__ float gelu_grad(float x) {
   return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
-__host__ __device__ constexpr int kchunks(int cin) { return (9 * cin + kKC - 1) / kKC; }
 
 // ---------------------------------------------------------------------------
 // forward / data-gradient convolution
 // ---------------------------------------------------------------------------
-// in  [H][Wd][CIN] bf16; B packed: kchunks(CIN) blocks of COUT x 64 bf16 (canonical layout).
-// pre (FP32 [H][Wd][COUT], may be NULL) receives D + bias (bias[c] for c < nbias, else 0).  EPI_GELU: out = gelu(pre) in bf16,
-// NHWC and CHW.  EPI_GELU_GRAD: out = D * gelu'(aux) (aux FP32 [H][Wd][COUT]), NHWC and CHW.
+// A persistent CTA owns a strip of 128 output columns and a run of output rows.  It stages
+// every input row it needs once in shared memory (130 pixels with the halo, zero outside the
+// image) and keeps all nine taps of the weights resident; the nine taps of an output row then
+// read the staged rows through matrix descriptors whose start is offset by the tap (dx pixels
+// = dx x 16 bytes: pixels are consecutive 16-byte rows of the K-major core matrices, the 8-channel
+// groups are kRows x 16 bytes apart).  The accumulator is double-buffered in tensor memory: the
+// MMAs of row k run while the epilogue of row k - 1 drains the other buffer and row k + 3 is
+// fetched with cp.async.
+constexpr int kRows = 137;   // staged pixels per channel group (130 used); 137 x 16 B staggers the banks
+constexpr int kSlots = 4;    // staged input rows in flight
+
+// packed weights of conv2_kernel: [9 taps][CIN / 8 channel groups][COUT rows][8 channels]
+__host__ __device__ constexpr size_t packed_off(int t, int n, int k, int CIN, int COUT) {
+  return (size_t)t * COUT * CIN + (size_t)(k >> 3) * COUT * 8 + (size_t)n * 8 + (k & 7);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int CIN, int COUT>
+struct Conv {
+  static constexpr int G = CIN / 8;                                  // channel groups
+  static constexpr uint32_t SLOT = (uint32_t)G * kRows * 16;         // bytes of one staged row
+  static constexpr uint32_t WB = 9u * COUT * CIN * 2;                // bytes of the weights
+  static constexpr uint32_t TC = COUT < 32 ? 32 : COUT;              // TMEM columns per accumulator
+  static constexpr size_t SMEM = 1024 + (size_t)WB + (size_t)kSlots * SLOT + 64;
+};
+
+// in  [H][Wd][CIN] bf16 (NHWC); Bp packed as packed_off.  Output rows [y0, y1) of column strip
+// blockIdx.x, with y0 = blockIdx.y * rows_per_cta.
+// pre (FP32 [H][Wd][COUT], may be NULL) receives D + bias (bias[c] for c < nbias, else 0).
+// EPI_GELU: out = gelu(D + bias) in bf16 (NHWC).
+// EPI_GELU_GRAD: out = D * gelu'(aux) (aux FP32 [H][Wd][COUT]) in bf16 (NHWC).
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(kThreads, 1) conv_kernel(const bf16* __restrict__ in, const bf16* __restrict__ Bp,
                                                            const float* __restrict__ bias, const float* __restrict__ aux,
                                                            float* __restrict__ pre, bf16* __restrict__ out,
-                                                           bf16* __restrict__ out_chw, int nbias, int H, int Wd,
-                                                           int* err, int wait_limit) {
-  constexpr int NC = kchunks(CIN);
-  constexpr uint32_t A_BYTES = kPix * kKC * 2, B_BYTES = COUT * kKC * 2;
-  constexpr uint32_t TCOLS = COUT < 32 ? 32 : COUT;
+                                                           int nbias, int H, int Wd,
+                                                           int rows_per_cta, int* err, int wait_limit) {
+  using C = Conv<CIN, COUT>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sa = smem;
-  uint8_t* sb = sa + A_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sb + B_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint8_t* sw = smem;                 // weights
+  uint8_t* srow = sw + C::WB;         // staged rows
+  uint64_t* bar = reinterpret_cast<uint64_t*>(srow + kSlots * C::SLOT);   // [2] accumulator commits
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   volatile int* flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int y = blockIdx.y, x0 = blockIdx.x * kPix;
+  const int x0 = blockIdx.x * kPix;
+  const int y0 = blockIdx.y * rows_per_cta;
+  const int n = min(rows_per_cta, H - y0);   // output rows of this CTA
+  if (n <= 0) return;
+
+  // stage input row y0 - 1 + i into its slot (zero outside the image)
+  auto stage = [&](int i) {
+    const int yy = y0 - 1 + i;
+    const uint32_t base = tc::smem_u32(srow + (i % kSlots) * C::SLOT);
+    for (int q = tid; q < 130 * C::G; q += kThreads) {
+      const int r = q / C::G, j = q % C::G;
+      const int xx = x0 - 1 + r;
+      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+      const bf16* src = ok ? in + ((size_t)yy * Wd + xx) * CIN + 8 * j : in;
+      cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
+    }
+    cp_async_commit();
+  };
+
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
     tc::fence_mbar_init();
     *flag = 0;
   }
-  if (warp == 0) tc::tmem_alloc(tslot, TCOLS);
+  // weights (once) and the first three input rows
+  for (int i = tid; i < (int)(C::WB / 16); i += kThreads)
+    cp_async16(tc::smem_u32(sw) + 16u * i, reinterpret_cast<const uint4*>(Bp) + i, true);
+  cp_async_commit();
+  for (int i = 0; i < 3 && i < n + 2; ++i) stage(i);
+  if (warp == 0) tc::tmem_alloc(tslot, 2 * C::TC);
+  cp_async_wait_all();
+  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
   constexpr uint32_t idesc = tc::idesc_bf16(kPix, COUT);
-  int issued = -1;
-#pragma unroll 1
-  for (int c = 0; c < NC; ++c) {
-    if (c > 0) {
-      if (tid == 0 && !tc::wait_phase(bar, (uint32_t)((c - 1) & 1), wait_limit)) *flag = 2;
-      __syncthreads();
-      if (*flag) break;
-    }
-    // A: 128 pixels x 64 K, 16-byte pieces (8 channels of one tap)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      // 1024 pieces; eight consecutive threads take eight rows of one core matrix (no bank conflict)
-      const int piece = tid + kThreads * i;
-      const int r = (piece & 7) | ((piece >> 6) << 3), q = (piece >> 3) & 7;
-      const int k0 = c * kKC + 8 * q;
-      const int t = k0 / CIN, ci = k0 % CIN;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (t < 9) {
-        const int yy = y + t / 3 - 1, xx = x0 + r + t % 3 - 1;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < Wd)
-          v = *reinterpret_cast<const uint4*>(in + ((size_t)yy * Wd + xx) * CIN + ci);
-      }
-      *reinterpret_cast<uint4*>(sa + tc::kmaj16(r, 8 * q)) = v;
-    }
-    // B: the packed chunk
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(Bp + (size_t)c * COUT * kKC);
-      for (int i = tid; i < (int)(B_BYTES / 16); i += kThreads) reinterpret_cast<uint4*>(sb)[i] = src[i];
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t a = tc::smem_u32(sa), b = tc::smem_u32(sb);
-#pragma unroll
-      for (int s = 0; s < kKC / 16; ++s)
-        tc::mma_bf16(tmem, tc::smem_desc(a + s * 256, 128, 1024), tc::smem_desc(b + s * 256, 128, 1024), idesc,
-                     (c > 0 || s > 0) ? 1u : 0u);
-      tc::commit(bar);
-    }
-    issued = c;
-  }
-  if (!*flag && issued == NC - 1) {
-    if (tid == 0 && !tc::wait_phase(bar, (uint32_t)((NC - 1) & 1), wait_limit)) *flag = 2;
-  }
-  __syncthreads();
-  tc::fence_after();
-  if (!*flag && warp < 4) {
-    const int r = 32 * warp + lane;
-    const int x = x0 + r;
-    const bool ok = x < Wd;
+  const uint32_t a0 = tc::smem_u32(srow), b0 = tc::smem_u32(sw);
+  int issued = -1, confirmed = -1;   // MMA rows issued and known complete (thread 0's view)
+
+  auto epilogue = [&](int k) {   // output row y0 + k from accumulator k & 1 (warps 0..3)
+    if (warp >= 4) return;
+    const int y = y0 + k, r = 32 * warp + lane, x = x0 + r;
     const size_t p = (size_t)y * Wd + x;
+    const uint32_t acc = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(k & 1) * C::TC;
 #pragma unroll 1
     for (int j0 = 0; j0 < COUT; j0 += 16) {
       uint32_t d[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)j0, d);
+      tc::tmem_ld16(acc + (uint32_t)j0, d);
       tc::tmem_wait_ld();
-      if (!ok) continue;
       float v[16];
 #pragma unroll
       for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[u]) + (j0 + u < nbias ? bias[j0 + u] : 0.f);
@@ -154,250 +167,324 @@ __global__ void __launch_bounds__(kThreads, 1) conv_kernel(const bf16* __restric
         for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
       }
       if (EPI != EPI_NONE) {
+        float g[16];
+        if (EPI == EPI_GELU_GRAD) {
+          const float4* ap = reinterpret_cast<const float4*>(aux + p * COUT + j0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 a = ap[u];
+            g[4 * u] = a.x, g[4 * u + 1] = a.y, g[4 * u + 2] = a.z, g[4 * u + 3] = a.w;
+          }
+        }
         __align__(16) bf16 o[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-          const float a = EPI == EPI_GELU ? gelu(v[u]) : v[u] * gelu_grad(aux[p * COUT + j0 + u]);
+          const float a = EPI == EPI_GELU ? gelu(v[u]) : v[u] * gelu_grad(g[u]);
           o[u] = __float2bfloat16_rn(a);
-          out_chw[(size_t)(j0 + u) * H * Wd + p] = o[u];
         }
         uint4* dst = reinterpret_cast<uint4*>(out + p * COUT + j0);
         dst[0] = reinterpret_cast<const uint4*>(o)[0];
         dst[1] = reinterpret_cast<const uint4*>(o)[1];
       }
     }
+  };
+
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    // MMAs of output row k: rows k, k + 1, k + 2 are staged; accumulator k & 1 is free
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t dcol = tmem + (uint32_t)(k & 1) * C::TC;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int dy = t / 3, dx = t % 3;   // staged row k + dy, pixel offset dx
+        const uint32_t a = a0 + (uint32_t)((k + dy) % kSlots) * C::SLOT + (uint32_t)dx * 16u;
+        const uint32_t b = b0 + (uint32_t)t * (COUT * CIN * 2);
+#pragma unroll
+        for (int s = 0; s < CIN / 16; ++s)
+          tc::mma_bf16(dcol, tc::smem_desc(a + (uint32_t)(2 * s) * (kRows * 16), kRows * 16, 128),
+                       tc::smem_desc(b + (uint32_t)(2 * s) * (COUT * 16), COUT * 16, 128), idesc,
+                       (t > 0 || s > 0) ? 1u : 0u);
+      }
+      tc::commit(&bar[k & 1]);
+      issued = k;
+    }
+    if (k >= 1) {   // wait for row k - 1: its accumulator and staged row k - 1 become free
+      if (tid == 0) {
+        if (tc::wait_phase(&bar[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), wait_limit)) confirmed = k - 1;
+        else *flag = 2;
+      }
+      __syncthreads();
+      if (*flag) break;
+      tc::fence_after();
+    }
+    if (k + 3 < n + 2) stage(k + 3);   // into the slot of row k - 1
+    if (k >= 1) epilogue(k - 1);
+    cp_async_wait_all();
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
   }
-  if (tid == 0 && *flag && issued >= 0 && !tc::wait_phase(bar, (uint32_t)(issued & 1), kDrainLimit)) *flag = 3;
+  if (!*flag) {
+    if (tid == 0) {
+      if (tc::wait_phase(&bar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), wait_limit)) confirmed = n - 1;
+      else *flag = 2;
+    }
+    __syncthreads();
+    tc::fence_after();
+    if (!*flag) epilogue(n - 1);
+  }
+  cp_async_wait_all();
+  if (tid == 0 && *flag) {   // drain the MMAs still in flight before the tensor memory is released
+    for (int k = confirmed + 1; k <= issued; ++k)
+      if (!tc::wait_phase(&bar[k & 1], (uint32_t)((k >> 1) & 1), kDrainLimit)) *flag = 3;
+  }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tmem, TCOLS);
+    tc::tmem_dealloc(tmem, 2 * C::TC);
   }
   if (tid == 0 && *flag) atomicMax(err, *flag);
 }
 
 template <int CIN, int COUT>
 constexpr size_t conv_smem() {
-  return 1024 + (size_t)kPix * kKC * 2 + (size_t)COUT * kKC * 2 + 64;
+  return Conv<CIN, COUT>::SMEM;
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient: D[c_out][n = tap CIN + c_in] over the pixels of one image row
+// weight and bias gradients
 // ---------------------------------------------------------------------------
-// g_chw [COUT][H Wd], in_chw [CIN][H Wd] (bf16).  Partial sums [H][COUT][9 CIN] (FP32): row y of
-// the image contributes its pixels.  N tile NT = 9 CIN / n_tiles, rows of A beyond COUT are zero.
-template <int CIN, int COUT>
-struct WG {
-  static constexpr int N = 9 * CIN;
-  static constexpr int NTILES = N <= 256 ? 1 : 3;
-  static constexpr int NT = N / NTILES;   // 144 (CIN = 16) or 192 (CIN = 64)
-};
+// D_t[ci][co] = sum_p in[p + off(t)][ci] g[p][co] over the pixels of a CTA's strip and rows, on
+// the tensor core with M = 128 rows of c_in (the first CIN real) and N = COUT, K = 16 pixels per
+// MMA.  Both operands come from staged NHWC rows exactly as in the convolution: for one pixel the
+// channels are 16 contiguous bytes, so they are MN-major operands (channel groups kRows x 16 bytes
+// apart, 8-pixel groups 128 bytes apart) and a tap's pixel shift is again a start offset.  Row
+// CIN of the input operand reads a constant group of ones, which turns the centre tap's row CIN
+// into the bias gradient sum_p g[p][co].  Each CTA accumulates all its rows in tensor memory
+// (five or four taps x COUT columns: the taps are split over two CTA groups) and writes one
+// partial sum; the partials are then added in a fixed order.
+constexpr int kMaxSpatial = 512;   // spatial CTAs of one weight-gradient launch at most
+// MN-major operands without swizzle: the descriptor's LBO is the stride between 8-row K groups and
+// its SBO the stride between 8-element MN groups (the reverse of the K-major roles).
+constexpr uint32_t kMnStrideLbo = 0;
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restrict__ g_chw, const bf16* __restrict__ in_chw,
-                                                            float* __restrict__ part, int H, int Wd, int* err,
+struct WGrad {
+  static constexpr int G = CIN / 8, GO = COUT / 8;
+  static constexpr uint32_t GRP = kRows * 16;              // bytes of one channel group of a staged row
+  static constexpr uint32_t ISLOT = (G + 1) * GRP;         // an input row and a group of ones
+  static constexpr uint32_t GSLOT = GO * GRP;              // a gradient row
+  static constexpr uint32_t PAD = (16 - G - 1) * GRP;      // the M = 128 operand spans 16 groups
+  static constexpr int TAPS = 5;                           // taps [0, 5) or [5, 9) per CTA
+  static constexpr uint32_t TC = TAPS * COUT <= 128 ? 128 : (TAPS * COUT <= 256 ? 256 : 512);
+  static constexpr size_t SMEM = 1024 + (size_t)kSlots * ISLOT + PAD + 2 * (size_t)GSLOT + 64;
+};
+
+// g [H][Wd][COUT], in [H][Wd][CIN] (bf16 NHWC).  CTA (strip blockIdx.x, rows blockIdx.y,
+// taps blockIdx.z) writes part[sp][t][co][ci] for its taps (sp = blockIdx.y * gridDim.x +
+// blockIdx.x) and, for the centre tap's group, bpart[sp][co].
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restrict__ g, const bf16* __restrict__ in,
+                                                            float* __restrict__ part, float* __restrict__ bpart,
+                                                            int H, int Wd, int rows_per_cta, int* err,
                                                             int wait_limit) {
-  constexpr int NT = WG<CIN, COUT>::NT, N = WG<CIN, COUT>::N;
-  constexpr uint32_t A_BYTES = kPix * kKC * 2, B_BYTES = NT * kKC * 2;
-  constexpr uint32_t TCOLS = 256;
+  using C = WGrad<CIN, COUT>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sa = smem;
-  uint8_t* sb = sa + A_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sb + B_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  uint8_t* sin = smem;
+  uint8_t* sg = sin + kSlots * C::ISLOT + C::PAD;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sg + 2 * C::GSLOT);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   volatile int* flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int y = blockIdx.x, tile = blockIdx.y;
-  const size_t P = (size_t)H * Wd;
+  const int x0 = blockIdx.x * kPix, y0 = blockIdx.y * rows_per_cta;
+  const int t0 = blockIdx.z * C::TAPS, nt = blockIdx.z == 0 ? C::TAPS : 9 - C::TAPS;
+  const int sp = blockIdx.y * gridDim.x + blockIdx.x;
+  const int n = min(rows_per_cta, H - y0);
+  if (n <= 0) return;
+
+  auto stage = [&](const bf16* src_img, int C_, uint8_t* dst_base, int yy) {   // 130 pixels, halo, zeros outside
+    const int GG = C_ / 8;
+    const uint32_t base = tc::smem_u32(dst_base);
+    for (int q = tid; q < 130 * GG; q += kThreads) {
+      const int r = q / GG, j = q % GG;
+      const int xx = x0 - 1 + r;
+      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+      const bf16* src = ok ? src_img + ((size_t)yy * Wd + xx) * C_ + 8 * j : src_img;
+      cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
+    }
+    cp_async_commit();
+  };
+  auto stage_in = [&](int i) { stage(in, CIN, sin + (i % kSlots) * C::ISLOT, y0 - 1 + i); };
+  auto stage_g = [&](int k) { stage(g, COUT, sg + (k & 1) * C::GSLOT, y0 + k); };
+
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
+    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[1], 1);
     tc::fence_mbar_init();
     *flag = 0;
   }
-  // rows of A beyond COUT stay zero for the whole kernel
-  for (int i = tid; i < (int)(A_BYTES / 16); i += kThreads) reinterpret_cast<uint4*>(sa)[i] = make_uint4(0u, 0u, 0u, 0u);
-  if (warp == 0) tc::tmem_alloc(tslot, TCOLS);
+  {   // the group of ones after every input slot; the padding after the last slot is zero
+    const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);   // bf16 1.0 x 8
+    for (int i = tid; i < kSlots * kRows; i += kThreads)
+      *reinterpret_cast<uint4*>(sin + (i / kRows) * C::ISLOT + C::G * C::GRP + (i % kRows) * 16) = ones;
+    for (int i = tid; i < (int)(C::PAD / 16); i += kThreads)
+      reinterpret_cast<uint4*>(sin + kSlots * C::ISLOT)[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int i = 0; i < 3; ++i) stage_in(i);
+  stage_g(0);
+  if (warp == 0) tc::tmem_alloc(tslot, C::TC);
+  cp_async_wait_all();
+  tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::idesc_bf16(kPix, NT);
-  const int NC = Wd / kKC;
-  int issued = -1;
+  constexpr uint32_t idesc = tc::idesc_bf16(kPix, COUT) | (1u << 15) | (1u << 16);   // A and B MN-major
+  constexpr uint32_t LBO = kMnStrideLbo ? C::GRP : 128u, SBO = kMnStrideLbo ? 128u : C::GRP;
+  const uint32_t a0 = tc::smem_u32(sin), b0 = tc::smem_u32(sg);
+  int issued = -1, confirmed = -1;
+
 #pragma unroll 1
-  for (int c = 0; c < NC; ++c) {
-    if (c > 0) {
-      if (tid == 0 && !tc::wait_phase(bar, (uint32_t)((c - 1) & 1), wait_limit)) *flag = 2;
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {   // input rows k .. k + 2 and gradient row k are staged
+      tc::fence_after();
+      const uint32_t b = b0 + (uint32_t)(k & 1) * C::GSLOT + 16u;   // gradient pixel r at staged index r + 1
+#pragma unroll 1
+      for (int tl = 0; tl < nt; ++tl) {
+        const int t = t0 + tl, dy = t / 3, dx = t % 3;
+        const uint32_t a = a0 + (uint32_t)((k + dy) % kSlots) * C::ISLOT + (uint32_t)dx * 16u;
+#pragma unroll
+        for (int s = 0; s < kPix / 16; ++s)
+          tc::mma_bf16(tmem + (uint32_t)(tl * COUT), tc::smem_desc(a + (uint32_t)s * 256u, LBO, SBO),
+                       tc::smem_desc(b + (uint32_t)s * 256u, LBO, SBO), idesc, (k > 0 || s > 0) ? 1u : 0u);
+      }
+      tc::commit(&bar[k & 1]);
+      issued = k;
+    }
+    if (k >= 1) {   // the MMAs of row k - 1 are done: its input slot and gradient slot are free
+      if (tid == 0) {
+        if (tc::wait_phase(&bar[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), wait_limit)) confirmed = k - 1;
+        else *flag = 2;
+      }
       __syncthreads();
       if (*flag) break;
     }
-    const int p0 = c * kKC;   // column of the image row
-    // A: rows c_out < COUT, 64 pixels: 8 pieces of 16 bytes each
-    for (int piece = tid; piece < COUT * 8; piece += kThreads) {
-      const int r = piece >> 3, q = piece & 7;
-      const uint4 v = *reinterpret_cast<const uint4*>(g_chw + (size_t)r * P + (size_t)y * Wd + p0 + 8 * q);
-      *reinterpret_cast<uint4*>(sa + tc::kmaj16(r, 8 * q)) = v;
+    if (k + 3 < n + 2) stage_in(k + 3);
+    if (k + 1 < n) stage_g(k + 1);
+    cp_async_wait_all();
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+  }
+  if (!*flag) {
+    if (tid == 0) {
+      if (tc::wait_phase(&bar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), wait_limit)) confirmed = n - 1;
+      else *flag = 2;
     }
-    // B: rows n = tap CIN + c_in of this tile, 64 pixels shifted by the tap (zero outside)
-    for (int piece = tid; piece < NT * 8; piece += kThreads) {
-      const int rr = piece >> 3, q = piece & 7;
-      const int n = tile * NT + rr;
-      const int t = n / CIN, ci = n % CIN;
-      const int yy = y + t / 3 - 1, dx = t % 3 - 1;
-      __align__(16) bf16 v[8];
-      const int xs = p0 + 8 * q + dx;
-      if (yy < 0 || yy >= H) {
+    __syncthreads();
+    tc::fence_after();
+  }
+  if (!*flag && warp < 4) {   // lane = row of D: c_in (< CIN) or the bias row (CIN)
+    const int row = 32 * warp + lane;
+    const bool active = __any_sync(0xffffffffu, row <= CIN);
+    if (active) {
+#pragma unroll 1
+      for (int tl = 0; tl < nt; ++tl) {
+        const int t = t0 + tl;
+#pragma unroll 1
+        for (int j0 = 0; j0 < COUT; j0 += 16) {
+          uint32_t d[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(tl * COUT + j0), d);
+          tc::tmem_wait_ld();
+          if (row < CIN) {
+            float* dst = part + (((size_t)sp * 9 + t) * COUT + j0) * CIN + row;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn(0.f);
-      } else if (dx == 0) {
-        *reinterpret_cast<uint4*>(v) = *reinterpret_cast<const uint4*>(in_chw + (size_t)ci * P + (size_t)yy * Wd + xs);
-      } else {
-        const bf16* row = in_chw + (size_t)ci * P + (size_t)yy * Wd;
+            for (int u = 0; u < 16; ++u) dst[(size_t)u * CIN] = __uint_as_float(d[u]);
+          } else if (row == CIN && t == 4) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int xx = xs + e;
-          v[e] = (xx >= 0 && xx < Wd) ? row[xx] : __float2bfloat16_rn(0.f);
+            for (int u = 0; u < 16; ++u) bpart[(size_t)sp * COUT + j0 + u] = __uint_as_float(d[u]);
+          }
         }
       }
-      *reinterpret_cast<uint4*>(sb + tc::kmaj16(rr, 8 * q)) = *reinterpret_cast<const uint4*>(v);
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t a = tc::smem_u32(sa), b = tc::smem_u32(sb);
-#pragma unroll
-      for (int s = 0; s < kKC / 16; ++s)
-        tc::mma_bf16(tmem, tc::smem_desc(a + s * 256, 128, 1024), tc::smem_desc(b + s * 256, 128, 1024), idesc,
-                     (c > 0 || s > 0) ? 1u : 0u);
-      tc::commit(bar);
-    }
-    issued = c;
-  }
-  if (!*flag && issued == NC - 1) {
-    if (tid == 0 && !tc::wait_phase(bar, (uint32_t)((NC - 1) & 1), wait_limit)) *flag = 2;
-  }
-  __syncthreads();
-  tc::fence_after();
-  if (!*flag && warp < 4 && 32 * warp < COUT) {
-    const int co = 32 * warp + lane;
-#pragma unroll 1
-    for (int j0 = 0; j0 < NT; j0 += 16) {
-      uint32_t d[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)j0, d);
-      tc::tmem_wait_ld();
-      if (co < COUT) {
-        float* dst = part + ((size_t)y * COUT + co) * N + tile * NT + j0;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) dst[u] = __uint_as_float(d[u]);
-      }
     }
   }
-  if (tid == 0 && *flag && issued >= 0 && !tc::wait_phase(bar, (uint32_t)(issued & 1), kDrainLimit)) *flag = 3;
+  cp_async_wait_all();
+  if (tid == 0 && *flag) {
+    for (int k = confirmed + 1; k <= issued; ++k)
+      if (!tc::wait_phase(&bar[k & 1], (uint32_t)((k >> 1) & 1), kDrainLimit)) *flag = 3;
+  }
   tc::fence_before();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after();
-    tc::tmem_dealloc(tmem, TCOLS);
+    tc::tmem_dealloc(tmem, C::TC);
   }
   if (tid == 0 && *flag) atomicMax(err, *flag);
 }
 
-// At least 90 KB so that no more than two CTAs (2 x 256 TMEM columns) share an SM.
-template <int CIN>
-constexpr size_t wgrad_smem() {
-  return 1024 + (size_t)kPix * kKC * 2 + (size_t)WG<CIN, 16>::NT * kKC * 2 + 64 > 90 * 1024
-             ? 1024 + (size_t)kPix * kKC * 2 + (size_t)WG<CIN, 16>::NT * kKC * 2 + 64
-             : 90 * 1024;
-}
-
-// dW[co][n] (n = tap CIN + c_in, valid c_in < cin_true) = sum over image rows of part, in row order;
-// written to the parameter layout [co][9][cin_true] of rows co < cout_true.
-__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int H, int COUT, int CIN, int cout_true,
-                                    int cin_true, float* __restrict__ dW) {
-  const int N = 9 * CIN;
+// dW[co][t][ci] (co < cout_true, ci < cin_true, the parameter layout) = sum over the nsp spatial
+// partials in order; db[co] likewise.
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ bpart, int nsp, int COUT,
+                                    int CIN, int cout_true, int cin_true, float* __restrict__ dW,
+                                    float* __restrict__ db) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= cout_true * N) return;
-  const int co = idx / N, n = idx % N;
-  const int t = n / CIN, ci = n % CIN;
-  if (ci >= cin_true) return;
-  float s = 0.f;
-  for (int y = 0; y < H; ++y) s += part[((size_t)y * COUT + co) * N + n];
-  dW[((size_t)co * 9 + t) * cin_true + ci] = s;
-}
-
-// db[co] = sum over pixels of g[p][co] (NHWC bf16, COUT channels), per-block partials in a fixed
-// order: block b sums rows of pixels b, b + gridDim.x, ... into part[b][co]; then row order.
-__global__ void bias_grad_part_kernel(const bf16* __restrict__ g, size_t P, int COUT, float* __restrict__ part) {
-  __shared__ float acc[256];
-  const int co = threadIdx.x % COUT, lanes = blockDim.x / COUT, li = threadIdx.x / COUT;
-  float s = 0.f;
-  for (size_t p = (size_t)blockIdx.x * lanes + li; p < P; p += (size_t)gridDim.x * lanes)
-    s += __bfloat162float(g[p * COUT + co]);
-  acc[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x < COUT) {
-    float t = 0.f;
-    for (int i = 0; i < lanes; ++i) t += acc[i * COUT + threadIdx.x];
-    part[(size_t)blockIdx.x * COUT + threadIdx.x] = t;
+  const int nw = 9 * COUT * CIN;
+  if (idx < nw) {
+    const int t = idx / (COUT * CIN), co = (idx / CIN) % COUT, ci = idx % CIN;
+    if (co >= cout_true || ci >= cin_true) return;
+    float s = 0.f;
+    for (int i = 0; i < nsp; ++i) s += part[(size_t)i * nw + idx];
+    dW[((size_t)co * 9 + t) * cin_true + ci] = s;
+  } else if (idx < nw + cout_true) {
+    const int co = idx - nw;
+    float s = 0.f;
+    for (int i = 0; i < nsp; ++i) s += bpart[(size_t)i * COUT + co];
+    db[co] = s;
   }
-}
-__global__ void bias_grad_sum_kernel(const float* __restrict__ part, int nb, int COUT, int cout_true, float* __restrict__ db) {
-  const int co = threadIdx.x;
-  if (co >= cout_true) return;
-  float s = 0.f;
-  for (int b = 0; b < nb; ++b) s += part[(size_t)b * COUT + co];
-  db[co] = s;
 }
 
 // ---------------------------------------------------------------------------
 // packing, input, output, loss, Adam, initialisation
 // ---------------------------------------------------------------------------
 
-// B operand of the forward convolution from w [cout_true][9][cin_true] FP32: chunk c, row co
-// (< COUT), k = tap CIN + ci; zero for padded channels and taps >= 9.
+// B operand of the forward convolution from w [cout_true][9][cin_true] FP32: tap t, row co (< COUT),
+// channel ci (< CIN), at packed_off; zero for padded channels.
 __global__ void pack_fwd_kernel(const float* __restrict__ w, int cin_true, int cout_true, int CIN, int COUT,
                                 bf16* __restrict__ Bp) {
-  const int NC = (9 * CIN + kKC - 1) / kKC;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= NC * COUT * kKC) return;
-  const int c = idx / (COUT * kKC), rem = idx % (COUT * kKC);
-  const int co = rem / kKC, kk = rem % kKC;
-  const int k = c * kKC + kk, t = k / CIN, ci = k % CIN;
+  if (idx >= 9 * COUT * CIN) return;
+  const int t = idx / (COUT * CIN), co = (idx / CIN) % COUT, ci = idx % CIN;
   float v = 0.f;
-  if (t < 9 && ci < cin_true && co < cout_true) v = w[((size_t)co * 9 + t) * cin_true + ci];
-  Bp[(size_t)c * COUT * kKC + tc::kmaj16(co, kk) / 2] = __float2bfloat16_rn(v);
+  if (ci < cin_true && co < cout_true) v = w[((size_t)co * 9 + t) * cin_true + ci];
+  Bp[packed_off(t, co, ci, CIN, COUT)] = __float2bfloat16_rn(v);
 }
 
-// B operand of the data-gradient convolution: rows ci (< CIN of the layer), k = tap' COUT + co,
-// value w[co][8 - tap'][ci] (taps mirrored, channels transposed).
+// B operand of the data-gradient convolution (a forward convolution from COUT channels to CIN):
+// tap t', row ci (< CIN), channel co (< COUT): w[co][8 - t'][ci] (taps mirrored, channels
+// transposed).
 __global__ void pack_dgrad_kernel(const float* __restrict__ w, int cin_true, int cout_true, int CIN, int COUT,
                                   bf16* __restrict__ Bp) {
-  const int NC = (9 * COUT + kKC - 1) / kKC;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= NC * CIN * kKC) return;
-  const int c = idx / (CIN * kKC), rem = idx % (CIN * kKC);
-  const int ci = rem / kKC, kk = rem % kKC;
-  const int k = c * kKC + kk, t = k / COUT, co = k % COUT;
+  if (idx >= 9 * COUT * CIN) return;
+  const int t = idx / (COUT * CIN), ci = (idx / COUT) % CIN, co = idx % COUT;
   float v = 0.f;
-  if (t < 9 && ci < cin_true && co < cout_true) v = w[((size_t)co * 9 + (8 - t)) * cin_true + ci];
-  Bp[(size_t)c * CIN * kKC + tc::kmaj16(ci, kk) / 2] = __float2bfloat16_rn(v);
+  if (ci < cin_true && co < cout_true) v = w[((size_t)co * 9 + (8 - t)) * cin_true + ci];
+  Bp[packed_off(t, ci, co, COUT, CIN)] = __float2bfloat16_rn(v);
 }
 
-// Network input: x[p][c] = s_V V_c (c < L), s_G G_{c-L} (L <= c < 2L), 0 up to 16; NHWC and CHW.
+// Network input: x[p][c] = s_V V_c (c < L), s_G G_{c-L} (L <= c < 2L), 0 up to 16 (NHWC).
 __global__ void input_kernel(const float* __restrict__ V, const float* __restrict__ G, int L, size_t P, float sv,
-                             float sg, bf16* __restrict__ x, bf16* __restrict__ x_chw) {
+                             float sg, bf16* __restrict__ x) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 16; i += (size_t)gridDim.x * blockDim.x) {
     const size_t p = i / 16;
     const int c = (int)(i % 16);
     float v = 0.f;
     if (c < L) v = sv * V[(size_t)c * P + p];
     else if (c < 2 * L) v = sg * G[(size_t)(c - L) * P + p];
-    const bf16 b = __float2bfloat16_rn(v);
-    x[i] = b;
-    x_chw[(size_t)c * P + p] = b;
+    x[i] = __float2bfloat16_rn(v);
   }
 }
 
@@ -410,9 +497,9 @@ __global__ void output_kernel(const float* __restrict__ pre, int L, size_t P, fl
 }
 
 // Mean squared error against target / s_D and its gradient with respect to the last layer's
-// pre-activation (bf16, NHWC and CHW, padded channels 0); per-block loss partials (FP64).
+// pre-activation (bf16 NHWC, padded channels 0); per-block loss partials (FP64).
 __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ pre, const float* __restrict__ target, int L,
-                                                   size_t P, float inv_sd, bf16* __restrict__ g, bf16* __restrict__ g_chw,
+                                                   size_t P, float inv_sd, bf16* __restrict__ g,
                                                    double* __restrict__ part) {
   __shared__ double red[8];
   const double inv_n = 1.0 / ((double)P * L);
@@ -426,9 +513,7 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ pre
       acc += (double)d * d;
       gv = (float)(2.0 * inv_n) * d;
     }
-    const bf16 b = __float2bfloat16_rn(gv);
-    g[i] = b;
-    g_chw[(size_t)c * P + p] = b;
+    g[i] = __float2bfloat16_rn(gv);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -441,18 +526,16 @@ __global__ void __launch_bounds__(256) loss_kernel(const float* __restrict__ pre
   }
 }
 
-__global__ void loss_sum_kernel(const double* __restrict__ part, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    out[0] = s;
+// out = sum of the 512 loss partials: a fixed-order tree over one block of 512 threads.
+__global__ void __launch_bounds__(512) loss_sum_kernel(const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double s[512];
+  s[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int h = 256; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
   }
-}
-
-// NHWC -> CHW copy of a bf16 image (the weight-gradient test hook).
-__global__ void to_chw_kernel(const bf16* __restrict__ in, size_t P, int C, bf16* __restrict__ out) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * C; i += (size_t)gridDim.x * blockDim.x)
-    out[(i % C) * P + i / C] = in[i];
+  if (threadIdx.x == 0) out[0] = s[0];
 }
 
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
@@ -532,23 +615,20 @@ Net make_net(int L) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-size_t packed_fwd_elems(const Layer& l) { return (size_t)kchunks(l.cin) * l.cout * kKC; }
-size_t packed_dgrad_elems(const Layer& l) { return (size_t)kchunks(l.cout) * l.cin * kKC; }
+size_t packed_fwd_elems(const Layer& l) { return (size_t)9 * l.cin * l.cout; }
+size_t packed_dgrad_elems(const Layer& l) { return (size_t)9 * l.cin * l.cout; }
 
 struct Ws {
   int* err;
   double* loss_part;            // [512]
   bf16* x;                      // [P][16] input, NHWC
-  bf16* x_chw;                  // [16][P]
   bf16* act[kLayers - 1];       // [P][64] outputs of the hidden layers (gelu), NHWC
-  bf16* act_chw[kLayers - 1];   // [64][P]
   float* pre[kLayers];          // [P][cout] pre-activations (FP32)
   bf16* g[2];                   // [P][64] gradients of a pre-activation, NHWC (ping-pong)
-  bf16* g_chw[2];               // [64][P]
   bf16* Bf[kLayers];            // packed forward weights
   bf16* Bd[kLayers];            // packed data-gradient weights
-  float* part;                  // [H][64][576] weight-gradient partials
-  float* bpart;                 // [512][64] bias-gradient partials
+  float* part;                  // [kMaxSpatial][9][64][64] weight-gradient partials
+  float* bpart;                 // [kMaxSpatial][64] bias-gradient partials
   float* grad;                  // [n_params]
   size_t bytes;
 };
@@ -561,22 +641,15 @@ Ws carve(const Net& n, int H, int Wd, char* base) {
   w.err = (int*)take(sizeof(int));
   w.loss_part = (double*)take(512 * sizeof(double));
   w.x = (bf16*)take(P * 16 * 2);
-  w.x_chw = (bf16*)take(P * 16 * 2);
-  for (int i = 0; i < kLayers - 1; ++i) {
-    w.act[i] = (bf16*)take(P * kHid * 2);
-    w.act_chw[i] = (bf16*)take(P * kHid * 2);
-  }
+  for (int i = 0; i < kLayers - 1; ++i) w.act[i] = (bf16*)take(P * kHid * 2);
   for (int i = 0; i < kLayers; ++i) w.pre[i] = (float*)take(P * n.layer[i].cout * 4);
-  for (int i = 0; i < 2; ++i) {
-    w.g[i] = (bf16*)take(P * kHid * 2);
-    w.g_chw[i] = (bf16*)take(P * kHid * 2);
-  }
+  for (int i = 0; i < 2; ++i) w.g[i] = (bf16*)take(P * kHid * 2);
   for (int i = 0; i < kLayers; ++i) {
     w.Bf[i] = (bf16*)take(packed_fwd_elems(n.layer[i]) * 2);
     w.Bd[i] = (bf16*)take(packed_dgrad_elems(n.layer[i]) * 2);
   }
-  w.part = (float*)take((size_t)H * kHid * 9 * kHid * 4);
-  w.bpart = (float*)take(512 * kHid * 4);
+  w.part = (float*)take((size_t)kMaxSpatial * 9 * kHid * kHid * 4);
+  w.bpart = (float*)take((size_t)kMaxSpatial * kHid * 4);
   w.grad = (float*)take(n.n_params * 4);
   w.bytes = off;
   return w;
@@ -586,26 +659,37 @@ msp_status fail(msp_status s, const std::string& m) { return set_last_error(s, m
 
 template <int CIN, int COUT, int EPI>
 cudaError_t launch_conv(const bf16* in, const bf16* Bp, const float* bias, const float* aux, float* pre, bf16* out,
-                        bf16* out_chw, int nbias, int H, int Wd, int* err, cudaStream_t st) {
-  static bool attr[64] = {};
+                        int nbias, int H, int Wd, int* err, cudaStream_t st) {
+  static int resident[64] = {};   // co-resident CTAs per SM (shared memory, threads, tensor memory)
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && !attr[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, EPI>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem<CIN, COUT>());
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!resident[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)conv_smem<CIN, COUT>());
     if (e != cudaSuccess) return e;
-    attr[dev] = true;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_kernel<CIN, COUT, EPI>, kThreads,
+                                                      conv_smem<CIN, COUT>());
+    if (e != cudaSuccess) return e;
+    resident[dev] = std::max(1, std::min(occ, (int)(512 / (2 * Conv<CIN, COUT>::TC))));
   }
-  conv_kernel<CIN, COUT, EPI><<<dim3((unsigned)(Wd / kPix), (unsigned)H), kThreads, conv_smem<CIN, COUT>(), st>>>(
-      in, Bp, bias, aux, pre, out, out_chw, nbias, H, Wd, err, tc_wait_limit());
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int strips = Wd / kPix;
+  const int want = std::max(1, sms * resident[dev] / strips);   // CTAs along the rows
+  const int rows = (H + std::min(want, H) - 1) / std::min(want, H);
+  const int ny = (H + rows - 1) / rows;
+  conv_kernel<CIN, COUT, EPI><<<dim3((unsigned)strips, (unsigned)ny), kThreads, conv_smem<CIN, COUT>(), st>>>(
+      in, Bp, bias, aux, pre, out, nbias, H, Wd, rows, err, tc_wait_limit());
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t conv(int cin, int cout, int epi, const bf16* in, const bf16* Bp, const float* bias, const float* aux,
-                 float* pre, bf16* out, bf16* out_chw, int nbias, int H, int Wd, int* err, cudaStream_t st) {
+                 float* pre, bf16* out, int nbias, int H, int Wd, int* err, cudaStream_t st) {
 #define MSP_CONV(CI, CO, E) \
-  if (cin == CI && cout == CO && epi == E) return launch_conv<CI, CO, E>(in, Bp, bias, aux, pre, out, out_chw, nbias, H, Wd, err, st);
+  if (cin == CI && cout == CO && epi == E) return launch_conv<CI, CO, E>(in, Bp, bias, aux, pre, out, nbias, H, Wd, err, st);
   MSP_CONV(16, 64, EPI_GELU)
   MSP_CONV(64, 64, EPI_GELU)
   MSP_CONV(64, 16, EPI_NONE)
@@ -618,29 +702,51 @@ cudaError_t conv(int cin, int cout, int epi, const bf16* in, const bf16* Bp, con
   return cudaErrorInvalidValue;
 }
 
+// Weight and bias gradients of one convolution into the parameter layout (dW [cout_true][9]
+// [cin_true], db [cout_true]): the partial-sum kernel over (strips x row runs x 2 tap groups), then
+// the fixed-order reduction.
 template <int CIN, int COUT>
-cudaError_t launch_wgrad(const bf16* g_chw, const bf16* in_chw, float* part, int H, int Wd, int* err, cudaStream_t st) {
-  static bool attr[64] = {};
+cudaError_t launch_wgrad(const bf16* g, const bf16* in, float* part, float* bpart, int cout_true, int cin_true,
+                         float* dW, float* db, int H, int Wd, int* err, cudaStream_t st) {
+  using C = WGrad<CIN, COUT>;
+  static int resident[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 64 && !attr[dev]) {
-    const cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)wgrad_smem<CIN>());
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!resident[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::SMEM);
     if (e != cudaSuccess) return e;
-    attr[dev] = true;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wgrad_kernel<CIN, COUT>, kThreads, C::SMEM);
+    if (e != cudaSuccess) return e;
+    resident[dev] = std::max(1, std::min(occ, (int)(512 / C::TC)));
   }
-  wgrad_kernel<CIN, COUT><<<dim3((unsigned)H, (unsigned)WG<CIN, COUT>::NTILES), kThreads, wgrad_smem<CIN>(), st>>>(
-      g_chw, in_chw, part, H, Wd, err, tc_wait_limit());
-  count_launches(1);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int strips = Wd / kPix;
+  int want = std::max(1, std::min(sms * resident[dev] / 2, kMaxSpatial) / strips);
+  want = std::min(want, H);
+  const int rows = (H + want - 1) / want;
+  const int ny = (H + rows - 1) / rows;
+  wgrad_kernel<CIN, COUT><<<dim3((unsigned)strips, (unsigned)ny, 2u), kThreads, C::SMEM, st>>>(
+      g, in, part, bpart, H, Wd, rows, err, tc_wait_limit());
+  const int nred = 9 * COUT * CIN + cout_true;
+  wgrad_reduce_kernel<<<(nred + 255) / 256, 256, 0, st>>>(part, bpart, strips * ny, COUT, CIN, cout_true, cin_true,
+                                                          dW, db);
+  count_launches(2);
   return cudaGetLastError();
 }
 
-cudaError_t wgrad(int cin, int cout, const bf16* g_chw, const bf16* in_chw, float* part, int H, int Wd, int* err,
-                  cudaStream_t st) {
-  if (cin == 16 && cout == 64) return launch_wgrad<16, 64>(g_chw, in_chw, part, H, Wd, err, st);
-  if (cin == 64 && cout == 64) return launch_wgrad<64, 64>(g_chw, in_chw, part, H, Wd, err, st);
-  if (cin == 64 && cout == 16) return launch_wgrad<64, 16>(g_chw, in_chw, part, H, Wd, err, st);
-  if (cin == 16 && cout == 16) return launch_wgrad<16, 16>(g_chw, in_chw, part, H, Wd, err, st);
+cudaError_t wgrad(int cin, int cout, const bf16* g, const bf16* in, float* part, float* bpart, int cout_true,
+                  int cin_true, float* dW, float* db, int H, int Wd, int* err, cudaStream_t st) {
+#define MSP_WGRAD(CI, CO) \
+  if (cin == CI && cout == CO) return launch_wgrad<CI, CO>(g, in, part, bpart, cout_true, cin_true, dW, db, H, Wd, err, st);
+  MSP_WGRAD(16, 64)
+  MSP_WGRAD(64, 64)
+  MSP_WGRAD(64, 16)
+  MSP_WGRAD(16, 16)
+#undef MSP_WGRAD
   return cudaErrorInvalidValue;
 }
 
@@ -662,15 +768,17 @@ cudaError_t pack_all(const Net& n, const float* params, const Ws& w, bool dgrad,
   return cudaGetLastError();
 }
 
-// Forward through the six layers from the packed input; keeps every pre-activation.
-cudaError_t forward(const Net& n, const float* params, const Ws& w, int H, int Wd, cudaStream_t st) {
+// Forward through the six layers from the packed input.  For training (`train`) every layer also
+// keeps its FP32 pre-activation (the backward pass reads it); the proposal alone needs only the
+// last layer's.
+cudaError_t forward(const Net& n, const float* params, const Ws& w, int H, int Wd, bool train, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < kLayers && e == cudaSuccess; ++i) {
     const Layer& l = n.layer[i];
     const bf16* in = i == 0 ? w.x : w.act[i - 1];
     const bool last = i == kLayers - 1;
-    e = conv(l.cin, l.cout, last ? EPI_NONE : EPI_GELU, in, w.Bf[i], params + l.b_off, nullptr, w.pre[i],
-             last ? nullptr : w.act[i], last ? nullptr : w.act_chw[i], l.cout_true, H, Wd, w.err, st);
+    e = conv(l.cin, l.cout, last ? EPI_NONE : EPI_GELU, in, w.Bf[i], params + l.b_off, nullptr,
+             (last || train) ? w.pre[i] : nullptr, last ? nullptr : w.act[i], l.cout_true, H, Wd, w.err, st);
   }
   return e;
 }
@@ -758,9 +866,9 @@ msp_status msp_net_forward(const msp_net_shape* s, const float* params, const fl
   const size_t P = (size_t)H * Wd;
   LEARN_CK(cudaMemsetAsync(w.err, 0, sizeof(int), cs));
   LEARN_CK(pack_all(n, params, w, false, cs));
-  input_kernel<<<grid1d(P * 16), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x, w.x_chw);
+  input_kernel<<<grid1d(P * 16), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x);
   count_launches(1);
-  LEARN_CK(forward(n, params, w, H, Wd, cs));
+  LEARN_CK(forward(n, params, w, H, Wd, false, cs));
   output_kernel<<<grid1d(P * L), 256, 0, cs>>>(w.pre[kLayers - 1], L, P, (float)s->scale_d, dV_prop);
   count_launches(1);
   LEARN_CK(cudaGetLastError());
@@ -777,32 +885,27 @@ static msp_status net_loss_grad(const msp_net_shape* s, const Net& n, const Ws& 
   const size_t P = (size_t)H * Wd;
   LEARN_CK(cudaMemsetAsync(w.err, 0, sizeof(int), cs));
   LEARN_CK(pack_all(n, params, w, true, cs));
-  input_kernel<<<grid1d(P * 16), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x, w.x_chw);
+  input_kernel<<<grid1d(P * 16), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x);
   count_launches(1);
-  LEARN_CK(forward(n, params, w, H, Wd, cs));
+  LEARN_CK(forward(n, params, w, H, Wd, true, cs));
   const int lb = 512;
-  loss_kernel<<<lb, 256, 0, cs>>>(w.pre[kLayers - 1], target, L, P, (float)(1.0 / s->scale_d), w.g[0], w.g_chw[0],
+  loss_kernel<<<lb, 256, 0, cs>>>(w.pre[kLayers - 1], target, L, P, (float)(1.0 / s->scale_d), w.g[0],
                                   w.loss_part);
   count_launches(1);
   if (loss_out) {
-    loss_sum_kernel<<<1, 32, 0, cs>>>(w.loss_part, lb, loss_out);
+    loss_sum_kernel<<<1, lb, 0, cs>>>(w.loss_part, loss_out);
     count_launches(1);
   }
   // backward, last layer first: g[cur] holds the gradient of layer i's pre-activation
   int cur = 0;
   for (int i = kLayers - 1; i >= 0; --i) {
     const Layer& l = n.layer[i];
-    const bf16* in_chw = i == 0 ? w.x_chw : w.act_chw[i - 1];
-    LEARN_CK(wgrad(l.cin, l.cout, w.g_chw[cur], in_chw, w.part, H, Wd, w.err, cs));
-    const int nred = l.cout_true * 9 * l.cin;
-    wgrad_reduce_kernel<<<(nred + 255) / 256, 256, 0, cs>>>(w.part, H, l.cout, l.cin, l.cout_true, l.cin_true,
-                                                            grad + l.w_off);
-    bias_grad_part_kernel<<<lb, 256, 0, cs>>>(w.g[cur], P, l.cout, w.bpart);
-    bias_grad_sum_kernel<<<1, 64, 0, cs>>>(w.bpart, lb, l.cout, l.cout_true, grad + l.b_off);
-    count_launches(3);
+    const bf16* in = i == 0 ? w.x : w.act[i - 1];
+    LEARN_CK(wgrad(l.cin, l.cout, w.g[cur], in, w.part, w.bpart, l.cout_true, l.cin_true, grad + l.w_off,
+                   grad + l.b_off, H, Wd, w.err, cs));
     if (i > 0) {   // gradient of the previous layer's pre-activation: conv with mirrored weights x gelu'
       LEARN_CK(conv(l.cout, l.cin, EPI_GELU_GRAD, w.g[cur], w.Bd[i], nullptr, w.pre[i - 1], nullptr, w.g[1 - cur],
-                    w.g_chw[1 - cur], 0, H, Wd, w.err, cs));
+                    0, H, Wd, w.err, cs));
       cur = 1 - cur;
     }
   }
@@ -904,9 +1007,8 @@ size_t msp_conv3x3_test_workspace_bytes(int32_t height, int32_t width, int32_t c
   if (height < 1 || height > 65535 || width < kPix || width % kPix || (c_in != 16 && c_in != 64) ||
       (c_out != 16 && c_out != 64))
     return 0;
-  const size_t P = (size_t)height * width;
-  return align256(sizeof(int)) + align256((size_t)kchunks(c_in) * c_out * kKC * 2) +
-         align256((size_t)height * c_out * 9 * c_in * 4) + align256(512 * 64 * 4) + align256(2 * P * 64 * 2);
+  return align256(sizeof(int)) + align256((size_t)9 * c_in * c_out * 2) +
+         align256((size_t)kMaxSpatial * 9 * c_out * c_in * 4) + align256((size_t)kMaxSpatial * 64 * 4);
 }
 
 msp_status msp_conv3x3_test(int32_t height, int32_t width, int32_t c_in, int32_t c_out, const void* in_bf16,
@@ -921,10 +1023,10 @@ msp_status msp_conv3x3_test(int32_t height, int32_t width, int32_t c_in, int32_t
   int* err = (int*)b;
   bf16* Bp = (bf16*)(b + align256(sizeof(int)));
   LEARN_CK(cudaMemsetAsync(err, 0, sizeof(int), cs));
-  const size_t ne = (size_t)kchunks(c_in) * c_out * kKC;
+  const size_t ne = (size_t)9 * c_in * c_out;
   pack_fwd_kernel<<<grid1d(ne), 256, 0, cs>>>(w, c_in, c_out, c_in, c_out, Bp);
   count_launches(1);
-  LEARN_CK(conv(c_in, c_out, EPI_NONE, (const bf16*)in_bf16, Bp, bias, nullptr, pre_out, nullptr, nullptr,
+  LEARN_CK(conv(c_in, c_out, EPI_NONE, (const bf16*)in_bf16, Bp, bias, nullptr, pre_out, nullptr,
                 bias ? c_out : 0, height, width, err, cs));
   return MSP_OK;
 }
@@ -938,31 +1040,15 @@ msp_status msp_conv3x3_wgrad_test(int32_t height, int32_t width, int32_t c_in, i
   if (!ws || ((uintptr_t)ws) % 256 || ws_bytes < need) return fail(MSP_EINVAL, "workspace");
   if (!in_bf16 || !grad_pre_bf16 || !dW || !db) return fail(MSP_EINVAL, "in, grad_pre, dW and db must be non-NULL");
   cudaStream_t cs = (cudaStream_t)stream;
-  const size_t P = (size_t)height * width;
   char* b = (char*)ws;
   int* err = (int*)b;
-  size_t off = align256(sizeof(int)) + align256((size_t)kchunks(c_in) * c_out * kKC * 2);
+  size_t off = align256(sizeof(int)) + align256((size_t)9 * c_in * c_out * 2);
   float* part = (float*)(b + off);
-  off += align256((size_t)height * c_out * 9 * c_in * 4);
+  off += align256((size_t)kMaxSpatial * 9 * c_out * c_in * 4);
   float* bpart = (float*)(b + off);
-  off += align256(512 * 64 * 4);
-  bf16* in_chw = (bf16*)(b + off);
-  bf16* g_chw = in_chw + P * 64;
   LEARN_CK(cudaMemsetAsync(err, 0, sizeof(int), cs));
-  // channel-major copies of the NHWC operands
-  {
-    const bf16* src = (const bf16*)in_bf16;
-    const bf16* gs = (const bf16*)grad_pre_bf16;
-    const size_t n1 = P * c_in, n2 = P * c_out;
-    to_chw_kernel<<<grid1d(n1), 256, 0, cs>>>(src, P, c_in, in_chw);
-    to_chw_kernel<<<grid1d(n2), 256, 0, cs>>>(gs, P, c_out, g_chw);
-    count_launches(2);
-  }
-  LEARN_CK(wgrad(c_in, c_out, g_chw, in_chw, part, height, width, err, cs));
-  wgrad_reduce_kernel<<<(c_out * 9 * c_in + 255) / 256, 256, 0, cs>>>(part, height, c_out, c_in, c_out, c_in, dW);
-  bias_grad_part_kernel<<<512, 256, 0, cs>>>((const bf16*)grad_pre_bf16, P, c_out, bpart);
-  bias_grad_sum_kernel<<<1, 64, 0, cs>>>(bpart, 512, c_out, c_out, db);
-  count_launches(3);
+  LEARN_CK(wgrad(c_in, c_out, (const bf16*)grad_pre_bf16, (const bf16*)in_bf16, part, bpart, c_out, c_in, dW, db,
+                 height, width, err, cs));
   LEARN_CK(cudaGetLastError());
   return MSP_OK;
 }

@@ -339,7 +339,8 @@ def check_workspace(ws: Workspace, stream=None) -> None:
 
 
 def set_wait_limit(polls: int = 0) -> None:
-    """Poll bound of the tensor-core kernels' waits (0: the default); a test hook for failure detection."""
+    """Poll bound of the tensor-core kernels' waits (0: the default, < 0: no poll at all); a test hook
+    for failure detection."""
     _check(lib().msp_set_wait_limit(int(polls)), "msp_set_wait_limit")
 
 

@@ -210,10 +210,12 @@ def test_training_reduces_the_loss_on_a_fixed_batch(msp):
 
 
 def test_conv_wait_that_runs_out_is_reported(msp):
-    """With the wait bound cut to one poll, a convolution's wait for its MMAs gives up once several
-    CTAs share each SM's tensor core (1024 CTAs here); the call's workspace then reads MSP_ETIMEOUT
-    and the same process runs the network correctly afterwards."""
-    L, H, W = 2, 256, 512
+    """With no poll allowed (msp_set_wait_limit(-1)) every convolution's first wait for its MMAs
+    gives up: the kernel stops, waits for the MMAs it issued and frees its tensor memory; the
+    call's workspace reads MSP_ETIMEOUT and the same process runs the network correctly
+    afterwards.  (With a bound of one poll the waits succeed: each CTA waits for the MMAs of a row
+    only after staging the next input row.)"""
+    L, H, W = 2, 64, 256
     V, G, T = _problem(L, H, W, seed=5)
     s = _shape(msp, L, H, W)
     d = lambda a: torch.from_numpy(a).cuda()
@@ -221,7 +223,7 @@ def test_conv_wait_that_runs_out_is_reported(msp):
     ws = msp.net_make_workspace(s)
     timed_out = False
     try:
-        msp.set_wait_limit(1)
+        msp.set_wait_limit(-1)
         for _ in range(3):
             msp.net_forward(s, p, d(V), d(G), ws=ws)
             try:
