@@ -62,10 +62,13 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // read the staged rows through matrix descriptors whose start is offset by the tap (dx pixels
 // = dx x 16 bytes: pixels are consecutive 16-byte rows of the K-major core matrices, the 8-channel
 // groups are kRows x 16 bytes apart).  The accumulator is double-buffered in tensor memory: the
-// MMAs of row k run while the epilogue of row k - 1 drains the other buffer and row k + 3 is
-// fetched with cp.async.
+// MMAs of row k run while all eight warps drain the other buffer (the epilogue of row k - 1)
+// and rows k + 3 and k + 4 are fetched with cp.async.
 constexpr int kRows = 137;   // staged pixels per channel group (130 used); 137 x 16 B staggers the banks
-constexpr int kSlots = 4;    // staged input rows in flight
+constexpr int kCSlots = 5;   // staged input rows of the weight-gradient kernel: three in use, two in flight
+constexpr int kFSlots = 5;   // staged input rows of the convolution: three in use, two in flight
+constexpr int kFLag = kFSlots - 3;
+constexpr int kGSlots = 3;   // staged gradient rows of the weight-gradient kernel: one in use, two in flight
 
 // packed weights of conv2_kernel: [9 taps][CIN / 8 channel groups][COUT rows][8 channels]
 __host__ __device__ constexpr size_t packed_off(int t, int n, int k, int CIN, int COUT) {
@@ -75,8 +78,18 @@ __host__ __device__ constexpr size_t packed_off(int t, int n, int k, int CIN, in
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
+// Programmatic dependent launch: wait for the preceding kernel of the stream to complete (its
+// writes visible), and allow the next one to be scheduled.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// all but the most recent group of this thread's copies have landed
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+// all but the N most recent groups have landed
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int CIN, int COUT>
 struct Conv {
@@ -84,27 +97,44 @@ struct Conv {
   static constexpr uint32_t SLOT = (uint32_t)G * kRows * 16;         // bytes of one staged row
   static constexpr uint32_t WB = 9u * COUT * CIN * 2;                // bytes of the weights
   static constexpr uint32_t TC = COUT < 32 ? 32 : COUT;              // TMEM columns per accumulator
-  static constexpr size_t SMEM = 1024 + (size_t)WB + (size_t)kSlots * SLOT + 64;
+  static constexpr size_t SMEM = 1024 + (size_t)WB + (size_t)kFSlots * SLOT + 2 * 8 * kFSlots + 4 * 8 + 16;
 };
 
-// in  [H][Wd][CIN] bf16 (NHWC); Bp packed as packed_off.  Output rows [y0, y1) of column strip
-// blockIdx.x, with y0 = blockIdx.y * rows_per_cta.
+// in  [H][Wd][CIN] bf16 (NHWC); Bp packed as packed_off.  Output rows [y0, y0 + rows_per_cta)
+// of column strip blockIdx.x, with y0 = blockIdx.y * rows_per_cta.
 // pre (FP32 [H][Wd][COUT], may be NULL) receives D + bias (bias[c] for c < nbias, else 0).
 // EPI_GELU: out = gelu(D + bias) in bf16 (NHWC).
 // EPI_GELU_GRAD: out = D * gelu'(aux) (aux FP32 [H][Wd][COUT]) in bf16 (NHWC).
+//
+// Warp roles, synchronised by mbarriers only:
+//   warp 8 (producer): stages input row i into slot i % kFSlots once the MMAs of output row
+//     i - kFSlots released it (empty[slot]), then waits for its own copies, fences them to the
+//     async proxy and arrives on full[slot];
+//   warp 9, one thread (MMA): for output row k waits for staged row k + 2 (full) and for the
+//     epilogue to have drained accumulator k & 1 (acc_empty), issues the 9 x CIN / 16 MMAs,
+//     commits to acc_full[k & 1] and to empty[k % kFSlots] (row k has no later reader);
+//   warps 0..7 (epilogue): wait for acc_full, read the accumulator, write the outputs, arrive on
+//     acc_empty.
+// Every wait is bounded: the first that runs out raises the flag, the other roles see it and
+// stop, and the MMA thread waits for its last commit before the tensor memory is released.
+constexpr int kConvThreads = 320;
+
 template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(kThreads, 1) conv_kernel(const bf16* __restrict__ in, const bf16* __restrict__ Bp,
-                                                           const float* __restrict__ bias, const float* __restrict__ aux,
-                                                           float* __restrict__ pre, bf16* __restrict__ out,
-                                                           int nbias, int H, int Wd,
-                                                           int rows_per_cta, int* err, int wait_limit) {
+__global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __restrict__ in, const bf16* __restrict__ Bp,
+                                                               const float* __restrict__ bias,
+                                                               const float* __restrict__ aux, float* __restrict__ pre,
+                                                               bf16* __restrict__ out, int nbias, int H, int Wd,
+                                                               int rows_per_cta, int* err, int wait_limit) {
   using C = Conv<CIN, COUT>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sw = smem;                 // weights
   uint8_t* srow = sw + C::WB;         // staged rows
-  uint64_t* bar = reinterpret_cast<uint64_t*>(srow + kSlots * C::SLOT);   // [2] accumulator commits
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(srow + kFSlots * C::SLOT);
+  uint64_t* empty = full + kFSlots;
+  uint64_t* acc_full = empty + kFSlots;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * kPix;
@@ -112,31 +142,22 @@ __global__ void __launch_bounds__(kThreads, 1) conv_kernel(const bf16* __restric
   const int n = min(rows_per_cta, H - y0);   // output rows of this CTA
   if (n <= 0) return;
 
-  // stage input row y0 - 1 + i into its slot (zero outside the image)
-  auto stage = [&](int i) {
-    const int yy = y0 - 1 + i;
-    const uint32_t base = tc::smem_u32(srow + (i % kSlots) * C::SLOT);
-    for (int q = tid; q < 130 * C::G; q += kThreads) {
-      const int r = q / C::G, j = q % C::G;
-      const int xx = x0 - 1 + r;
-      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-      const bf16* src = ok ? in + ((size_t)yy * Wd + xx) * CIN + 8 * j : in;
-      cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
-    }
-    cp_async_commit();
-  };
-
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int i = 0; i < kFSlots; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&empty[i], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&acc_full[b], 1);
+      tc::mbar_init(&acc_empty[b], 8);
+    }
     tc::fence_mbar_init();
     *flag = 0;
   }
-  // weights (once) and the first three input rows
-  for (int i = tid; i < (int)(C::WB / 16); i += kThreads)
+  // the weights, once, by all threads
+  for (int i = tid; i < (int)(C::WB / 16); i += kConvThreads)
     cp_async16(tc::smem_u32(sw) + 16u * i, reinterpret_cast<const uint4*>(Bp) + i, true);
   cp_async_commit();
-  for (int i = 0; i < 3 && i < n + 2; ++i) stage(i);
   if (warp == 0) tc::tmem_alloc(tslot, 2 * C::TC);
   cp_async_wait_all();
   tc::fence_proxy_async();
@@ -144,100 +165,134 @@ __global__ void __launch_bounds__(kThreads, 1) conv_kernel(const bf16* __restric
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::idesc_bf16(kPix, COUT);
-  const uint32_t a0 = tc::smem_u32(srow), b0 = tc::smem_u32(sw);
-  int issued = -1, confirmed = -1;   // MMA rows issued and known complete (thread 0's view)
 
-  auto epilogue = [&](int k) {   // output row y0 + k from accumulator k & 1 (warps 0..3)
-    if (warp >= 4) return;
-    const int y = y0 + k, r = 32 * warp + lane, x = x0 + r;
-    const size_t p = (size_t)y * Wd + x;
-    const uint32_t acc = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(k & 1) * C::TC;
-#pragma unroll 1
-    for (int j0 = 0; j0 < COUT; j0 += 16) {
-      uint32_t d[16];
-      tc::tmem_ld16(acc + (uint32_t)j0, d);
-      tc::tmem_wait_ld();
-      float v[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[u]) + (j0 + u < nbias ? bias[j0 + u] : 0.f);
-      if (pre) {
-        float4* dst = reinterpret_cast<float4*>(pre + p * COUT + j0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-      }
-      if (EPI != EPI_NONE) {
-        float g[16];
-        if (EPI == EPI_GELU_GRAD) {
-          const float4* ap = reinterpret_cast<const float4*>(aux + p * COUT + j0);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4 a = ap[u];
-            g[4 * u] = a.x, g[4 * u + 1] = a.y, g[4 * u + 2] = a.z, g[4 * u + 3] = a.w;
-          }
-        }
-        __align__(16) bf16 o[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-          const float a = EPI == EPI_GELU ? gelu(v[u]) : v[u] * gelu_grad(g[u]);
-          o[u] = __float2bfloat16_rn(a);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(out + p * COUT + j0);
-        dst[0] = reinterpret_cast<const uint4*>(o)[0];
-        dst[1] = reinterpret_cast<const uint4*>(o)[1];
-      }
-    }
-  };
-
-#pragma unroll 1
-  for (int k = 0; k < n; ++k) {
-    // MMAs of output row k: rows k, k + 1, k + 2 are staged; accumulator k & 1 is free
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t dcol = tmem + (uint32_t)(k & 1) * C::TC;
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int dy = t / 3, dx = t % 3;   // staged row k + dy, pixel offset dx
-        const uint32_t a = a0 + (uint32_t)((k + dy) % kSlots) * C::SLOT + (uint32_t)dx * 16u;
-        const uint32_t b = b0 + (uint32_t)t * (COUT * CIN * 2);
-#pragma unroll
-        for (int s = 0; s < CIN / 16; ++s)
-          tc::mma_bf16(dcol, tc::smem_desc(a + (uint32_t)(2 * s) * (kRows * 16), kRows * 16, 128),
-                       tc::smem_desc(b + (uint32_t)(2 * s) * (COUT * 16), COUT * 16, 128), idesc,
-                       (t > 0 || s > 0) ? 1u : 0u);
-      }
-      tc::commit(&bar[k & 1]);
-      issued = k;
-    }
-    if (k >= 1) {   // wait for row k - 1: its accumulator and staged row k - 1 become free
-      if (tid == 0) {
-        if (tc::wait_phase(&bar[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), wait_limit)) confirmed = k - 1;
-        else *flag = 2;
-      }
-      __syncthreads();
+  if (warp == 8) {
+    // ---- producer: staged rows 0 .. n + 1 (input rows y0 - 1 .. y0 + n) ----
+    // The prologue above (barriers, tensor memory, weights packed by an earlier kernel) may
+    // overlap the preceding kernel; the input it wrote is read only after it has completed.
+    grid_dependency_wait();
+    if (lane == 0) grid_dependents_launch();
+    int i = 0;
+    for (; i < n + 2; ++i) {
+      const int slot = i % kFSlots;
+      if (i >= kFSlots && !tc::wait_phase(&empty[slot], (uint32_t)((i / kFSlots - 1) & 1), wait_limit)) *flag = 2;
+      __syncwarp();
       if (*flag) break;
-      tc::fence_after();
+      const int yy = y0 - 1 + i;
+      const uint32_t base = tc::smem_u32(srow + slot * C::SLOT);
+      for (int q = lane; q < 130 * C::G; q += 32) {
+        const int r = q / C::G, j = q % C::G;
+        const int xx = x0 - 1 + r;
+        const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+        const bf16* src = ok ? in + ((size_t)yy * Wd + xx) * CIN + 8 * j : in;
+        cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
+      }
+      cp_async_commit();
+      if (i >= kFLag) {   // row i - kFLag has landed: hand it to the MMA thread
+        cp_async_wait_group<kFLag>();
+        tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&full[(i - kFLag) % kFSlots]);
+      }
     }
-    if (k + 3 < n + 2) stage(k + 3);   // into the slot of row k - 1
-    if (k >= 1) epilogue(k - 1);
     cp_async_wait_all();
     tc::fence_proxy_async();
-    tc::fence_before();
-    __syncthreads();
-  }
-  if (!*flag) {
-    if (tid == 0) {
-      if (tc::wait_phase(&bar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), wait_limit)) confirmed = n - 1;
-      else *flag = 2;
+    __syncwarp();
+    if (lane == 0 && !*flag)
+      for (int r = max(0, i - kFLag); r < i; ++r) tc::mbar_arrive(&full[r % kFSlots]);
+  } else if (warp == 9) {
+    // ---- MMA issuer ----
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc::idesc_bf16(kPix, COUT);
+      const uint32_t a0 = tc::smem_u32(srow), b0 = tc::smem_u32(sw);
+      int issued = -1;
+      for (int k = 0; k < n && !*flag; ++k) {
+        bool ok = true;
+        for (int i = (k == 0 ? 0 : k + 2); i <= k + 2 && ok; ++i)
+          ok = tc::wait_phase(&full[i % kFSlots], (uint32_t)((i / kFSlots) & 1), wait_limit);
+        if (ok && k >= 2) ok = tc::wait_phase(&acc_empty[k & 1], (uint32_t)(((k - 2) >> 1) & 1), wait_limit);
+        if (!ok) {
+          *flag = 2;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t dcol = tmem + (uint32_t)(k & 1) * C::TC;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const int dy = t / 3, dx = t % 3;   // staged row k + dy, pixel offset dx
+          const uint32_t a = a0 + (uint32_t)((k + dy) % kFSlots) * C::SLOT + (uint32_t)dx * 16u;
+          const uint32_t b = b0 + (uint32_t)t * (COUT * CIN * 2);
+#pragma unroll
+          for (int s = 0; s < CIN / 16; ++s)
+            tc::mma_bf16(dcol, tc::smem_desc(a + (uint32_t)(2 * s) * (kRows * 16), kRows * 16, 128),
+                         tc::smem_desc(b + (uint32_t)(2 * s) * (COUT * 16), COUT * 16, 128), idesc,
+                         (t > 0 || s > 0) ? 1u : 0u);
+        }
+        tc::commit(&acc_full[k & 1]);
+        tc::commit(&empty[k % kFSlots]);
+        issued = k;
+      }
+      // Before the CTA exits, every commit has arrived: the latest one on each staging slot (rows
+      // issued - 4 .. issued, which the producer may never have waited for) and, after an
+      // abort, on both accumulators.  Each is the last completion of its barrier, so the
+      // parity names it without ambiguity.
+      for (int k = max(0, issued - (kFSlots - 1)); k <= issued; ++k)
+        if (!tc::wait_phase(&empty[k % kFSlots], (uint32_t)((k / kFSlots) & 1), kDrainLimit)) *flag = 3;
+      if (*flag)
+        for (int k = max(0, issued - 1); k <= issued; ++k)
+          if (!tc::wait_phase(&acc_full[k & 1], (uint32_t)((k >> 1) & 1), kDrainLimit)) *flag = 3;
     }
-    __syncthreads();
-    tc::fence_after();
-    if (!*flag) epilogue(n - 1);
-  }
-  cp_async_wait_all();
-  if (tid == 0 && *flag) {   // drain the MMAs still in flight before the tensor memory is released
-    for (int k = confirmed + 1; k <= issued; ++k)
-      if (!tc::wait_phase(&bar[k & 1], (uint32_t)((k >> 1) & 1), kDrainLimit)) *flag = 3;
+  } else {
+    // ---- epilogue: warps w and w + 4 read TMEM lanes 32 (w % 4) .., the lower and the upper
+    // half of the channels (warps 0..3 all of them if COUT = 16) ----
+    constexpr int HALF = COUT >= 32 ? COUT / 2 : COUT;
+    const bool active = !(COUT < 32 && warp >= 4);
+    const int q = warp & 3, c0 = (warp >> 2) * HALF;
+    for (int k = 0; k < n; ++k) {
+      if (lane == 0 && !tc::wait_phase(&acc_full[k & 1], (uint32_t)((k >> 1) & 1), wait_limit)) *flag = 2;
+      __syncwarp();
+      if (*flag) break;
+      tc::fence_after();
+      if (active) {
+        const int y = y0 + k, r = 32 * q + lane, x = x0 + r;
+        const size_t p = (size_t)y * Wd + x;
+        const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(k & 1) * C::TC;
+#pragma unroll 1
+        for (int j0 = c0; j0 < c0 + HALF; j0 += 16) {
+          uint32_t d[16];
+          tc::tmem_ld16(acc + (uint32_t)j0, d);
+          tc::tmem_wait_ld();
+          float v[16];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[u]) + (j0 + u < nbias ? bias[j0 + u] : 0.f);
+          if (pre) {
+            float4* dst = reinterpret_cast<float4*>(pre + p * COUT + j0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+          }
+          if (EPI != EPI_NONE) {
+            float g[16];
+            if (EPI == EPI_GELU_GRAD) {
+              const float4* ap = reinterpret_cast<const float4*>(aux + p * COUT + j0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float4 a = ap[u];
+                g[4 * u] = a.x, g[4 * u + 1] = a.y, g[4 * u + 2] = a.z, g[4 * u + 3] = a.w;
+              }
+            }
+            __align__(16) bf16 o[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16_rn(EPI == EPI_GELU ? gelu(v[u]) : v[u] * gelu_grad(g[u]));
+            uint4* dst = reinterpret_cast<uint4*>(out + p * COUT + j0);
+            dst[0] = reinterpret_cast<const uint4*>(o)[0];
+            dst[1] = reinterpret_cast<const uint4*>(o)[1];
+          }
+        }
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acc_empty[k & 1]);
+    }
   }
   tc::fence_before();
   __syncthreads();
@@ -279,7 +334,7 @@ struct WGrad {
   static constexpr uint32_t PAD = (16 - G - 1) * GRP;      // the M = 128 operand spans 16 groups
   static constexpr int TAPS = 5;                           // taps [0, 5) or [5, 9) per CTA
   static constexpr uint32_t TC = TAPS * COUT <= 128 ? 128 : (TAPS * COUT <= 256 ? 256 : 512);
-  static constexpr size_t SMEM = 1024 + (size_t)kSlots * ISLOT + PAD + 2 * (size_t)GSLOT + 64;
+  static constexpr size_t SMEM = 1024 + (size_t)kCSlots * ISLOT + PAD + kGSlots * (size_t)GSLOT + 64;
 };
 
 // g [H][Wd][COUT], in [H][Wd][CIN] (bf16 NHWC).  CTA (strip blockIdx.x, rows blockIdx.y,
@@ -294,8 +349,8 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sin = smem;
-  uint8_t* sg = sin + kSlots * C::ISLOT + C::PAD;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sg + 2 * C::GSLOT);
+  uint8_t* sg = sin + kCSlots * C::ISLOT + C::PAD;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sg + kGSlots * C::GSLOT);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   volatile int* flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -315,10 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
       const bf16* src = ok ? src_img + ((size_t)yy * Wd + xx) * C_ + 8 * j : src_img;
       cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
     }
-    cp_async_commit();
   };
-  auto stage_in = [&](int i) { stage(in, CIN, sin + (i % kSlots) * C::ISLOT, y0 - 1 + i); };
-  auto stage_g = [&](int k) { stage(g, COUT, sg + (k & 1) * C::GSLOT, y0 + k); };
+  auto stage_in = [&](int i) { stage(in, CIN, sin + (i % kCSlots) * C::ISLOT, y0 - 1 + i); };
+  auto stage_g = [&](int k) { stage(g, COUT, sg + (k % kGSlots) * C::GSLOT, y0 + k); };
 
   if (tid == 0) {
     tc::mbar_init(&bar[0], 1);
@@ -328,15 +382,21 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
   }
   {   // the group of ones after every input slot; the padding after the last slot is zero
     const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);   // bf16 1.0 x 8
-    for (int i = tid; i < kSlots * kRows; i += kThreads)
+    for (int i = tid; i < kCSlots * kRows; i += kThreads)
       *reinterpret_cast<uint4*>(sin + (i / kRows) * C::ISLOT + C::G * C::GRP + (i % kRows) * 16) = ones;
     for (int i = tid; i < (int)(C::PAD / 16); i += kThreads)
-      reinterpret_cast<uint4*>(sin + kSlots * C::ISLOT)[i] = make_uint4(0u, 0u, 0u, 0u);
+      reinterpret_cast<uint4*>(sin + kCSlots * C::ISLOT)[i] = make_uint4(0u, 0u, 0u, 0u);
   }
+  if (warp == 0) tc::tmem_alloc(tslot, C::TC);
+  grid_dependency_wait();   // the gradient rows come from the preceding kernel
+  if (tid == 0) grid_dependents_launch();
   for (int i = 0; i < 3; ++i) stage_in(i);
   stage_g(0);
-  if (warp == 0) tc::tmem_alloc(tslot, C::TC);
+  cp_async_commit();
   cp_async_wait_all();
+  if (3 < n + 2) stage_in(3);   // the next rows in flight: one group per row step
+  if (1 < n) stage_g(1);
+  cp_async_commit();
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
@@ -349,13 +409,13 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
 
 #pragma unroll 1
   for (int k = 0; k < n; ++k) {
-    if (tid == 0) {   // input rows k .. k + 2 and gradient row k are staged
+    if (tid == 0) {   // input rows k .. k + 2 and gradient row k are staged (the next ones in flight)
       tc::fence_after();
-      const uint32_t b = b0 + (uint32_t)(k & 1) * C::GSLOT + 16u;   // gradient pixel r at staged index r + 1
+      const uint32_t b = b0 + (uint32_t)(k % kGSlots) * C::GSLOT + 16u;   // gradient pixel r at staged index r + 1
 #pragma unroll 1
       for (int tl = 0; tl < nt; ++tl) {
         const int t = t0 + tl, dy = t / 3, dx = t % 3;
-        const uint32_t a = a0 + (uint32_t)((k + dy) % kSlots) * C::ISLOT + (uint32_t)dx * 16u;
+        const uint32_t a = a0 + (uint32_t)((k + dy) % kCSlots) * C::ISLOT + (uint32_t)dx * 16u;
 #pragma unroll
         for (int s = 0; s < kPix / 16; ++s)
           tc::mma_bf16(tmem + (uint32_t)(tl * COUT), tc::smem_desc(a + (uint32_t)s * 256u, LBO, SBO),
@@ -372,9 +432,10 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
       __syncthreads();
       if (*flag) break;
     }
-    if (k + 3 < n + 2) stage_in(k + 3);
-    if (k + 1 < n) stage_g(k + 1);
-    cp_async_wait_all();
+    if (k + 4 < n + 2) stage_in(k + 4);   // into the slots of row k - 1
+    if (k + 2 < n) stage_g(k + 2);
+    cp_async_commit();
+    cp_async_wait_prior();                 // input row k + 3 and gradient row k + 1 have landed
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
@@ -475,16 +536,22 @@ __global__ void pack_dgrad_kernel(const float* __restrict__ w, int cin_true, int
   Bp[packed_off(t, ci, co, COUT, CIN)] = __float2bfloat16_rn(v);
 }
 
-// Network input: x[p][c] = s_V V_c (c < L), s_G G_{c-L} (L <= c < 2L), 0 up to 16 (NHWC).
+// Network input: x[p][c] = s_V V_c (c < L), s_G G_{c-L} (L <= c < 2L), 0 up to 16 (NHWC); one
+// thread per pixel (the planes are read coalesced, the 16 channels written as 32 bytes).
 __global__ void input_kernel(const float* __restrict__ V, const float* __restrict__ G, int L, size_t P, float sv,
                              float sg, bf16* __restrict__ x) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P * 16; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = i / 16;
-    const int c = (int)(i % 16);
-    float v = 0.f;
-    if (c < L) v = sv * V[(size_t)c * P + p];
-    else if (c < 2 * L) v = sg * G[(size_t)(c - L) * P + p];
-    x[i] = __float2bfloat16_rn(v);
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      float a = 0.f;
+      if (c < L) a = sv * V[(size_t)c * P + p];
+      else if (c < 2 * L) a = sg * G[(size_t)(c - L) * P + p];
+      v[c] = __float2bfloat16_rn(a);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(x + p * 16);
+    dst[0] = reinterpret_cast<const uint4*>(v)[0];
+    dst[1] = reinterpret_cast<const uint4*>(v)[1];
   }
 }
 
@@ -669,7 +736,7 @@ cudaError_t launch_conv(const bf16* in, const bf16* Bp, const float* bias, const
                                          (int)conv_smem<CIN, COUT>());
     if (e != cudaSuccess) return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_kernel<CIN, COUT, EPI>, kThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, conv_kernel<CIN, COUT, EPI>, kConvThreads,
                                                       conv_smem<CIN, COUT>());
     if (e != cudaSuccess) return e;
     resident[dev] = std::max(1, std::min(occ, (int)(512 / (2 * Conv<CIN, COUT>::TC))));
@@ -680,10 +747,20 @@ cudaError_t launch_conv(const bf16* in, const bf16* Bp, const float* bias, const
   const int want = std::max(1, sms * resident[dev] / strips);   // CTAs along the rows
   const int rows = (H + std::min(want, H) - 1) / std::min(want, H);
   const int ny = (H + rows - 1) / rows;
-  conv_kernel<CIN, COUT, EPI><<<dim3((unsigned)strips, (unsigned)ny), kThreads, conv_smem<CIN, COUT>(), st>>>(
-      in, Bp, bias, aux, pre, out, nbias, H, Wd, rows, err, tc_wait_limit());
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3((unsigned)strips, (unsigned)ny);
+  cfg.blockDim = dim3(kConvThreads);
+  cfg.dynamicSmemBytes = conv_smem<CIN, COUT>();
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, conv_kernel<CIN, COUT, EPI>, in, Bp, bias, aux, pre, out, nbias, H, Wd,
+                                           rows, err, tc_wait_limit());
   count_launches(1);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t conv(int cin, int cout, int epi, const bf16* in, const bf16* Bp, const float* bias, const float* aux,
@@ -729,8 +806,19 @@ cudaError_t launch_wgrad(const bf16* g, const bf16* in, float* part, float* bpar
   want = std::min(want, H);
   const int rows = (H + want - 1) / want;
   const int ny = (H + rows - 1) / rows;
-  wgrad_kernel<CIN, COUT><<<dim3((unsigned)strips, (unsigned)ny, 2u), kThreads, C::SMEM, st>>>(
-      g, in, part, bpart, H, Wd, rows, err, tc_wait_limit());
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.gridDim = dim3((unsigned)strips, (unsigned)ny, 2u);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, wgrad_kernel<CIN, COUT>, g, in, part, bpart, H, Wd, rows, err,
+                                     tc_wait_limit());
+  if (e != cudaSuccess) return e;
   const int nred = 9 * COUT * CIN + cout_true;
   wgrad_reduce_kernel<<<(nred + 255) / 256, 256, 0, st>>>(part, bpart, strips * ny, COUT, CIN, cout_true, cin_true,
                                                           dW, db);
@@ -753,18 +841,48 @@ cudaError_t wgrad(int cin, int cout, const bf16* g, const bf16* in, float* part,
 int grid1d(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
 
 // Packs every layer's forward (and, for training, data-gradient) operand from the FP32 weights.
+// Packs every layer's forward (and, for training, data-gradient) operand from the FP32 weights,
+// in one launch: blockIdx.y is the layer, blockIdx.z the operand.
+struct PackJob {
+  const float* w[kLayers];
+  bf16* Bf[kLayers];
+  bf16* Bd[kLayers];
+  int cin_true[kLayers], cout_true[kLayers], cin[kLayers], cout[kLayers];
+};
+
+__global__ void pack_all_kernel(PackJob job) {
+  const int i = blockIdx.y;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int CIN = job.cin[i], COUT = job.cout[i], cit = job.cin_true[i], cot = job.cout_true[i];
+  if (idx >= 9 * COUT * CIN) return;
+  const float* w = job.w[i];
+  if (blockIdx.z == 0) {
+    const int t = idx / (COUT * CIN), co = (idx / CIN) % COUT, ci = idx % CIN;
+    const float v = (ci < cit && co < cot) ? w[((size_t)co * 9 + t) * cit + ci] : 0.f;
+    job.Bf[i][packed_off(t, co, ci, CIN, COUT)] = __float2bfloat16_rn(v);
+  } else if (i > 0) {
+    const int t = idx / (COUT * CIN), ci = (idx / COUT) % CIN, co = idx % COUT;
+    const float v = (ci < cit && co < cot) ? w[((size_t)co * 9 + (8 - t)) * cit + ci] : 0.f;
+    job.Bd[i][packed_off(t, ci, co, COUT, CIN)] = __float2bfloat16_rn(v);
+  }
+}
+
 cudaError_t pack_all(const Net& n, const float* params, const Ws& w, bool dgrad, cudaStream_t st) {
+  PackJob job{};
+  int most = 0;
   for (int i = 0; i < kLayers; ++i) {
     const Layer& l = n.layer[i];
-    pack_fwd_kernel<<<grid1d(packed_fwd_elems(l)), 256, 0, st>>>(params + l.w_off, l.cin_true, l.cout_true, l.cin,
-                                                                  l.cout, w.Bf[i]);
-    count_launches(1);
-    if (dgrad && i > 0) {
-      pack_dgrad_kernel<<<grid1d(packed_dgrad_elems(l)), 256, 0, st>>>(params + l.w_off, l.cin_true, l.cout_true,
-                                                                        l.cin, l.cout, w.Bd[i]);
-      count_launches(1);
-    }
+    job.w[i] = params + l.w_off;
+    job.Bf[i] = w.Bf[i];
+    job.Bd[i] = w.Bd[i];
+    job.cin_true[i] = l.cin_true;
+    job.cout_true[i] = l.cout_true;
+    job.cin[i] = l.cin;
+    job.cout[i] = l.cout;
+    most = std::max(most, 9 * l.cin * l.cout);
   }
+  pack_all_kernel<<<dim3((unsigned)((most + 255) / 256), (unsigned)kLayers, dgrad ? 2u : 1u), 256, 0, st>>>(job);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -866,7 +984,7 @@ msp_status msp_net_forward(const msp_net_shape* s, const float* params, const fl
   const size_t P = (size_t)H * Wd;
   LEARN_CK(cudaMemsetAsync(w.err, 0, sizeof(int), cs));
   LEARN_CK(pack_all(n, params, w, false, cs));
-  input_kernel<<<grid1d(P * 16), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x);
+  input_kernel<<<grid1d(P), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x);
   count_launches(1);
   LEARN_CK(forward(n, params, w, H, Wd, false, cs));
   output_kernel<<<grid1d(P * L), 256, 0, cs>>>(w.pre[kLayers - 1], L, P, (float)s->scale_d, dV_prop);
@@ -885,7 +1003,7 @@ static msp_status net_loss_grad(const msp_net_shape* s, const Net& n, const Ws& 
   const size_t P = (size_t)H * Wd;
   LEARN_CK(cudaMemsetAsync(w.err, 0, sizeof(int), cs));
   LEARN_CK(pack_all(n, params, w, true, cs));
-  input_kernel<<<grid1d(P * 16), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x);
+  input_kernel<<<grid1d(P), 256, 0, cs>>>(V, G, L, P, (float)s->scale_v, (float)s->scale_g, w.x);
   count_launches(1);
   LEARN_CK(forward(n, params, w, H, Wd, true, cs));
   const int lb = 512;
