@@ -1052,15 +1052,33 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="the timed loss/gradient steps and e2e only")
     ap.add_argument("--config", default="c2",
-                    choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3", "peaks"],
+                    choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3", "peaks", "learned_c5"],
                     help="workload (default c2: W = 128, L = 4, S = 1024, the benchmark configuration; "
                          "smd_gaas: Algorithm 2 on the Table 1 setting; peaks: FFMA and tcgen05 tf32 "
-                         "MMA micro-benchmarks)")
+                         "MMA micro-benchmarks; learned_c5: the learned-proposal form alone, with "
+                         "--steps Adam steps)")
     args = ap.parse_args()
     global CFG
     smd = args.config in synth.SMD_CONFIGS
     if args.config == "peaks":
         run_peaks(args)
+        return
+    if args.config == "learned_c5":
+        if args.impl == "reference" or int(os.environ.get("RANK", 0)) != 0:
+            if args.impl == "reference":
+                print(json.dumps({"impl": "reference", "unavailable": "the learned proposal has no reference arm"}))
+            return
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2205_03902_gb300 import msp
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        r = learned_proposal_run(msp, torch, dev, torch.cuda.current_stream(), read_peaks(), train_steps=args.steps)
+        t = r["time_to_plain_final_loss"]
+        print(json.dumps({"metric": "wall time to the plain method's final loss", "value": t["learned_ms"],
+                          "unit": "ms", "higher_is_better": False, "n_gpus": 1, "dtype": "bf16",
+                          "data": "synthetic", "config": {"workload": r["workload"]}, **r}), flush=True)
         return
     if args.config == "dft_c3":
         if args.impl == "reference":
