@@ -683,7 +683,8 @@ def net_macs_per_pixel(L):
     return sum(9 * ch[i] * ch[i + 1] for i in range(6))
 
 
-def learned_proposal_run(msp, torch, dev, stream, peaks, n_train=4, sweeps=16, train_steps=300, every=2):
+def learned_proposal_run(msp, torch, dev, stream, peaks, n_train=4, sweeps=16, train_steps=300, every=2,
+                         horizon=None):
     """The learned-proposal form on the eight-slice workload: a corpus from plain-method
     trajectories of `n_train` seeded specimens, Adam training, the network's kernel rates, and the
     wall time to the plain method's final loss on a held-out specimen, learned (acceptance loop)
@@ -699,7 +700,7 @@ def learned_proposal_run(msp, torch, dev, stream, peaks, n_train=4, sweeps=16, t
         g, gd, pos, d_pos, ws, _, p, I = make_inputs(msp, torch, dev, c)
         probe, I = torch.from_numpy(p).to(dev), torch.from_numpy(I).to(dev)
         states, _ = learned.plain_trajectory(g, probe, zeros(), d_pos, I, sweeps, ws=ws)
-        learned.add_trajectory(corpus, g, probe, d_pos, I, states, every=every, ws=ws)
+        learned.add_trajectory(corpus, g, probe, d_pos, I, states, every=every, horizon=horizon, ws=ws)
         del ws
     torch.cuda.synchronize()
     corpus_s = time.perf_counter() - t0
@@ -756,7 +757,9 @@ def learned_proposal_run(msp, torch, dev, stream, peaks, n_train=4, sweeps=16, t
     return {
         "workload": cfg5.name, "specimens": {"train": [100 + k for k in range(n_train)], "held_out": 200},
         "corpus": {"samples": len(corpus), "trajectory_sweeps": sweeps, "state_every": every,
-                   "build_s": corpus_s, "note": "target = V_K - V_k along each plain trajectory"},
+                   "build_s": corpus_s,
+                   "target": "V_K - V_k" if horizon is None else f"V_min(k+{horizon},K) - V_k",
+                   "note": "k along each plain trajectory of K sweeps"},
         "scales": {"s_V": sv, "s_G": sg, "s_D": sd},
         "training": {"steps": train_steps, "ms": train_ms, "loss_first10": float(np.mean(tl[:10])),
                      "loss_last10": float(np.mean(tl[-10:]))},

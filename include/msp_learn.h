@@ -1,6 +1,6 @@
 /*
- * msp_learn.h -- C ABI of the learned-proposal form of libmsp (the NEXT-3 direction of this
- * hot path; the paper itself has no learned component).
+ * msp_learn.h -- C ABI of the learned-proposal form of libmsp: an extension of the method of
+ * arXiv 2205.03902, which itself has no learned component.
  *
  * A small convolutional network proposes an update of every slice potential from the current
  * potentials and their gradients; the proposal is kept only if the true multislice loss of

@@ -3,7 +3,7 @@
 A six-layer convolutional network proposes an update of all slice potentials from the current
 potentials V and their gradient dL/dV.  It is trained on trajectories of the plain method
 (Algorithm 1, msp_reconstruct): from a state V_k of a trajectory the target is the change that
-trajectory still makes, V_K - V_k.  In use every proposal is judged by the true multislice loss
+trajectory still makes, V_K - V_k (or, with a horizon h, the change of the next h sweeps).  In use every proposal is judged by the true multislice loss
 (Sec. 3.2): msp_learned_propose keeps it only if the loss drops, and otherwise this driver takes
 one sweep of the plain method instead.
 
@@ -45,14 +45,17 @@ def plain_trajectory(g, probe, V0, pos, I_meas, sweeps: int, ws=None, stream=Non
     return states, torch.stack(losses).cpu().numpy()
 
 
-def add_trajectory(corpus: Corpus, g, probe, pos, I_meas, states, every: int = 1, ws=None, stream=None):
-    """Samples (V_k, dL/dV at V_k, V_K - V_k) for k = 0, every, 2 every, ... < K."""
+def add_trajectory(corpus: Corpus, g, probe, pos, I_meas, states, every: int = 1, horizon=None, ws=None,
+                   stream=None):
+    """Samples (V_k, dL/dV at V_k, V_j - V_k) for k = 0, every, 2 every, ... < K, with j = K (the
+    trajectory's end) or, given a horizon h, j = min(k + h, K)."""
     K = len(states) - 1
     for k in range(0, K, every):
+        j = K if horizon is None else min(k + horizon, K)
         _, G, _ = msp.loss_grad(g, probe, states[k], pos, I_meas, want_dprobe=False, ws=ws, stream=stream)
         corpus.V.append(states[k])
         corpus.G.append(G)
-        corpus.T.append(states[K] - states[k])
+        corpus.T.append(states[j] - states[k])
 
 
 def input_scales(corpus: Corpus) -> tuple[float, float, float]:
