@@ -55,16 +55,18 @@ def fft_flops(S, L, W):
 
 
 def measured_traffic(kernel: str, root: str = ROOT):
-    """DRAM bytes per launch of `kernel` from its committed ncu capture (profiles/traffic.json:
-    per kernel the counters, the workload, the command and a hash of the kernel's sources),
-    or None if those sources changed since the counters were taken."""
+    """DRAM bytes of `kernel` from its committed ncu capture (profiles/traffic.json: per kernel
+    the counters, per call (all its launches in one call) or per launch as the record's `per`
+    says, the workload, the command and a hash of the kernel's sources), or None if those
+    sources changed since the counters were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(root, "profiles", "traffic.json")))[kernel]
         h = hashlib.sha1()
         for f in rec["sources"]:
             h.update(open(os.path.join(root, f), "rb").read())
-        return rec["dram_bytes_per_launch"] if rec.get("source_sha1") == h.hexdigest() else None
+        val = rec.get("dram_bytes_per_call", rec.get("dram_bytes_per_launch"))
+        return val if rec.get("source_sha1") == h.hexdigest() else None
     except Exception:
         return None
 
@@ -909,7 +911,8 @@ def run_msp(args, rank, world, local_rank):
         msp.profile_enable(False)
         extra["layer_step"] = {"call": "msp_layer_step(layer=0, auto step)", "ms": lms,
                                "value": S * L / (lms * 1e-3), "unit": UNIT,
-                               "fused_kernel_ms": pl["fused_ms"] / max(1, pl["fused_launches"])}
+                               "fused_kernel_ms": pl["fused_ms"] / 10,
+                               "fused_launches_per_call": pl["fused_launches"] / 10}
         # the precise-forward mode's cost per pass on the same state
         gp = msp.geometry(**gd, precision=msp.MSP_PRECISION_FP64_FORWARD)
         wsp = msp.make_workspace(gp, dev)
@@ -968,7 +971,7 @@ def run_msp(args, rank, world, local_rank):
         c3ms = time_events(lambda: msp.loss_grad(g3, p3, V3, d_pos3, I3d, ws=ws3), 5, stream, flush)
         p3p = msp.profile_read(reset=True)
         msp.profile_enable(False)
-        k3 = p3p["fused_ms"] / max(1, p3p["fused_launches"])
+        k3 = p3p["fused_ms"] / 5
         extra["c3_full"] = {"workload": c3.name, "call": "msp_loss_grad", "ms": c3ms,
                             "value": c3.n_pos * c3.n_slices / (c3ms * 1e-3), "unit": UNIT, "fused_kernel_ms": k3,
                             "fused_kernel_tflops": fft_flops(c3.n_pos, c3.n_slices, c3.win) / (k3 * 1e-3) / 1e12}
@@ -988,7 +991,9 @@ def run_msp(args, rank, world, local_rank):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s: SMs x FP32 lanes x FMA x clock
-    fused_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
+    # the fused kernel's time per call (a call may run it in several position batches)
+    fused_ms = prof["fused_ms"] / args.steps
+    fused_launches_per_call = prof["fused_launches"] / args.steps
     achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
     kname = "position_kernel<128, LOSS_GRAD>" if W == 128 else ("position_cluster_kernel<LOSS_GRAD>" if W == 256
                                                                  else f"position_kernel<{W}, LOSS_GRAD>")
@@ -1005,6 +1010,7 @@ def run_msp(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
                      "kernel": kname + " (fused fwd+adjoint)", "kernel_ms": fused_ms,
+                     "kernel_launches_per_call": fused_launches_per_call,
                      "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["all_launches"]),

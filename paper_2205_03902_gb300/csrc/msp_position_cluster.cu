@@ -14,7 +14,9 @@
 //
 // Local layout: wave element (rl, c) of CTA-local row rl lives at rl * 256 + (c ^ (rl & 15)),
 // which keeps the row accesses and the (local or remote) column accesses of a
-// half-warp on sixteen distinct banks.
+// half-warp on sixteen distinct banks.  Column accesses use explicit shared::cluster
+// addresses (mapa, ld/st.shared::cluster), which keep them on the shared-memory path;
+// generic pointers into another CTA's shared memory take the global load/store path.
 #include <cooperative_groups.h>
 
 #include "msp_fft.cuh"
@@ -23,6 +25,21 @@
 namespace cg = cooperative_groups;
 
 namespace msp {
+
+// 8-byte access to the shared memory of a CTA of this cluster, by shared::cluster address
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, int rank) {
+  uint32_t a;
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(rank));
+  return a;
+}
+__device__ __forceinline__ float2 ld_cluster(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float2 v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
 
 namespace c256 {
 constexpr int W = 256;
@@ -67,15 +84,17 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
   __syncthreads();
   const RegisterTwiddles<W, T> tw(s_tw, j);
 
-  // Rows of the wave on every CTA of the cluster (generic pointers into distributed shared memory).
-  float2* rows[CL];
+  // Rows of the wave on every CTA of the cluster (shared::cluster addresses of element 0).
+  uint32_t rows[CL];
 #pragma unroll
-  for (int k = 0; k < CL; ++k) rows[k] = cluster.map_shared_rank(sm, k);
+  for (int k = 0; k < CL; ++k) rows[k] = cluster_addr(sm, k);
 
   // local row rl, element j + 16m
   auto rix = [&](int rl, int m) { return rl * W + ((j ^ (rl & 15)) + T * m); };
   // column c, global row j + 16m: CTA m >> 2, local row j + 16 (m & 3)
   auto cix = [&](int c, int m) { return (j + T * (m & 3)) * W + (c ^ j); };
+  auto col_ld = [&](int c, int m) { return ld_cluster(rows[m >> 2] + 8u * (uint32_t)cix(c, m)); };
+  auto col_st = [&](int c, int m, float2 v) { st_cluster(rows[m >> 2] + 8u * (uint32_t)cix(c, m), v); };
 
   const int L = p.L;
   const float zthr2 = (MODE == MODE_FORWARD) ? 0.f : (float)p.zthr2[0];
@@ -144,14 +163,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
           const int c = rank * RW + grp + GROUPS * it;
           float2 v[N1];
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = rows[m >> 2][cix(c, m)];
+          for (int m = 0; m < N1; ++m) v[m] = col_ld(c, m);
           line_fft<W, false, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
           const float2 hx = s_h1[c];
 #pragma unroll
           for (int m = 0; m < N1; ++m) v[m] = cmul(v[m], cmul(s_h1[j + T * m], hx));
           line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
 #pragma unroll
-          for (int m = 0; m < N1; ++m) rows[m >> 2][cix(c, m)] = v[m];
+          for (int m = 0; m < N1; ++m) col_st(c, m, v[m]);
         }
         cluster.sync();
         // local rows: F^-1, transmit slice l+1, keep the exit wave, F
@@ -196,7 +215,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
             for (int m = 0; m < N1; ++m) im[m] = __ldcs(ip + (size_t)(j + T * m) * W);   // read once: evict first
           }
 #pragma unroll
-          for (int m = 0; m < N1; ++m) v[m] = rows[m >> 2][cix(c, m)];
+          for (int m = 0; m < N1; ++m) v[m] = col_ld(c, m);
           line_fft<W, false, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
           if (MODE == MODE_FORWARD) {
             float* out = p.I_out + s * WW + c;
@@ -216,7 +235,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
             }
             line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) rows[m >> 2][cix(c, m)] = v[m];
+            for (int m = 0; m < N1; ++m) col_st(c, m, v[m]);
           }
         }
         if (MODE != MODE_FORWARD) {
@@ -300,14 +319,14 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         const int c = rank * RW + grp + GROUPS * it;
         float2 v[N1];
 #pragma unroll
-        for (int m = 0; m < N1; ++m) v[m] = rows[m >> 2][cix(c, m)];
+        for (int m = 0; m < N1; ++m) v[m] = col_ld(c, m);
         line_fft<W, false, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
         const float2 hx = s_h1[c];
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = cmulc(v[m], cmul(s_h1[j + T * m], hx));
         line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
 #pragma unroll
-        for (int m = 0; m < N1; ++m) rows[m >> 2][cix(c, m)] = v[m];
+        for (int m = 0; m < N1; ++m) col_st(c, m, v[m]);
       }
       cluster.sync();
     }
