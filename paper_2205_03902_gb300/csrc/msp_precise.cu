@@ -16,7 +16,8 @@
 // (B W^2 x 16 bytes) stay resident in L2 across the passes over them.  Every operator is
 // its own batched kernel over [B][W][W]:
 //   lines_fft_kernel   W-point DFTs of every row or every column of every wave of the batch
-//                      (radix-2, in shared memory; unnormalised, either direction)
+//                      (four-step W = N1 x 8 in registers, as in the fast path; unnormalised,
+//                      either direction)
 //   start / transmit   E_1 = P o X_1, E_m = psi_m o X_m, keeping E_m (or psi_m) for the adjoint
 //   propagator         x h(ky, kx) / W^2 (the separable factor h1 of Eq. fresnel_element)
 //   residual           loss, R, intensities
@@ -131,61 +132,169 @@ __device__ __forceinline__ bool window_ok(int2 ps, int Ny, int Nx, int W) {
 }
 
 // ---------------------------------------------------------------------------
-// batched line DFTs
+// batched line DFTs: the four-step split W = N1 x 8 of the fast path in registers, for the
+// three arithmetics (FP32, FP64, double-float)
 // ---------------------------------------------------------------------------
-constexpr int kLines = 8;        // lines per CTA
-constexpr int kFftThreads = 256;
+template <typename C> __device__ __forceinline__ C conj_(C a) { return mk<C>(a.x, -a.y); }
+template <> __device__ __forceinline__ dfc conj_<dfc>(dfc a) { return {a.re, df_neg(a.im)}; }
+template <typename C> __device__ __forceinline__ C rot_mi(C a) { return mk<C>(a.y, -a.x); }   // a (-i)
+template <> __device__ __forceinline__ dfc rot_mi<dfc>(dfc a) { return {a.im, df_neg(a.re)}; }
+template <typename C> __device__ __forceinline__ C neg_(C a) { return mk<C>(-a.x, -a.y); }
+template <> __device__ __forceinline__ dfc neg_<dfc>(dfc a) { return {df_neg(a.re), df_neg(a.im)}; }
 
-template <int W> struct Log2;
-template <> struct Log2<64> { static constexpr int v = 6; };
-template <> struct Log2<128> { static constexpr int v = 7; };
-template <> struct Log2<256> { static constexpr int v = 8; };
+// cos and sin of 2 pi k / 16, k = 0..3, as exact decimal expansions of the regular 16-gon
+constexpr double kCos16[4] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173};
 
-// y_k = sum_n x_n exp(-+2 pi i k n / W) (unnormalised; INV: the + sign) of kLines lines of one
-// wave: rows (ROWS) or columns.  The lines are read in bit-reversed order into shared memory,
-// transformed by log2(W) radix-2 decimation-in-time stages and written back in natural order.
-// Twiddles exp(-+2 pi i k / W), k < W/2, are evaluated in double and, for float2, rounded once.
-// Grid: (W / kLines, batch).
-template <typename C, int W, bool ROWS>
-__global__ void __launch_bounds__(kFftThreads) lines_fft_kernel(C* __restrict__ data, int inverse) {
-  __shared__ C buf[kLines][W];
-  __shared__ C tw[W / 2];
-  const int tid = threadIdx.x;
-  const int line0 = blockIdx.x * kLines;
-  C* img = data + (size_t)blockIdx.y * W * W;
-  for (int k = tid; k < W / 2; k += kFftThreads) {
-    double sn, cs;
-    sincospi(2.0 * (double)k / (double)W, &sn, &cs);
-    tw[k] = from_d<C>(cs, inverse ? sn : -sn);
+// w_16^K = exp(-2 pi i K / 16) in the type's arithmetic (constants folded at compile time)
+template <typename C, int K> __device__ __forceinline__ C w16c();
+template <int K>
+__device__ __forceinline__ constexpr double cos16() {
+  return (K % 16) <= 4 ? kCos16[K % 16] : (K % 16) <= 8 ? -kCos16[8 - K % 16] : (K % 16) <= 12 ? -kCos16[K % 16 - 8]
+                                                                                        : kCos16[16 - K % 16];
+}
+template <int K>
+__device__ __forceinline__ constexpr double sin16() { return cos16<K + 12>(); }   // sin x = cos(x - pi/2)
+template <> __device__ __forceinline__ float2 w16c<float2, 0>() { return make_float2(1.f, 0.f); }
+#define MSP_W16(K)                                                                                        \
+  template <> __device__ __forceinline__ float2 w16c<float2, K>() {                                      \
+    return make_float2((float)cos16<K>(), (float)-sin16<K>());                                           \
+  }                                                                                                       \
+  template <> __device__ __forceinline__ double2 w16c<double2, K>() { return make_double2(cos16<K>(), -sin16<K>()); } \
+  template <> __device__ __forceinline__ dfc w16c<dfc, K>() {                                            \
+    constexpr double c = cos16<K>(), sn = -sin16<K>();                                                    \
+    constexpr float ch = (float)c, sh = (float)sn;                                                        \
+    return {{ch, (float)(c - (double)ch)}, {sh, (float)(sn - (double)sh)}};                               \
   }
-  for (int i = tid; i < kLines * W; i += kFftThreads) {
-    // rows: consecutive i run along a row; columns: consecutive i run across the kLines columns
-    const int line = ROWS ? i / W : i % kLines;
-    const int k = ROWS ? i % W : i / kLines;
-    const size_t e = ROWS ? (size_t)(line0 + line) * W + k : (size_t)k * W + line0 + line;
-    buf[line][__brev((unsigned)k) >> (32 - Log2<W>::v)] = img[e];
+MSP_W16(1) MSP_W16(2) MSP_W16(3) MSP_W16(5) MSP_W16(6) MSP_W16(7) MSP_W16(9) MSP_W16(10) MSP_W16(11)
+MSP_W16(13) MSP_W16(14) MSP_W16(15)
+#undef MSP_W16
+
+template <typename C, int K>
+__device__ __forceinline__ C tw16g(C v) {   // v w_16^K; the quarter turns are exact
+  constexpr int k = K & 15;
+  if constexpr (k == 0) return v;
+  else if constexpr (k == 4) return rot_mi(v);
+  else if constexpr (k == 8) return neg_(v);
+  else if constexpr (k == 12) return neg_(rot_mi(v));
+  else return mul(v, w16c<C, k>());
+}
+template <typename C, int N, int K>
+__device__ __forceinline__ void dit_bfly_g(const C* E, const C* O, C* X) {
+  if constexpr (K < N / 2) {
+    const C t = tw16g<C, (K * 16) / N>(O[K]);
+    X[K] = add(E[K], t);
+    X[K + N / 2] = sub(E[K], t);
+    dit_bfly_g<C, N, K + 1>(E, O, X);
   }
-  __syncthreads();
-#pragma unroll 1
-  for (int half = 1; half < W; half <<= 1) {
-    const int stride = W / (2 * half);   // twiddle index step of this stage
-    for (int b = tid; b < kLines * (W / 2); b += kFftThreads) {
-      const int line = b / (W / 2), j = b % (W / 2);
-      const int q = j % half;
-      const int p0 = (j / half) * 2 * half + q;
-      const C u = buf[line][p0];
-      const C v = mul(buf[line][p0 + half], tw[q * stride]);
-      buf[line][p0] = add(u, v);
-      buf[line][p0 + half] = sub(u, v);
+}
+// X[k] = sum_n x[n S] w_N^(n k), N <= 16, in registers
+template <typename C, int N, int S>
+__device__ __forceinline__ void dft_g(const C* x, C* X) {
+  if constexpr (N == 1) {
+    X[0] = x[0];
+  } else if constexpr (N == 2) {
+    X[0] = add(x[0], x[S]);
+    X[1] = sub(x[0], x[S]);
+  } else {
+    C E[N / 2], O[N / 2];
+    dft_g<C, N / 2, 2 * S>(x, E);
+    dft_g<C, N / 2, 2 * S>(x + S, O);
+    dit_bfly_g<C, N, 0>(E, O, X);
+  }
+}
+// N1-point DFTs for N1 = 32 (W = 256): two 16-point DFTs and one radix-2 combination with the
+// twiddles w_32^k = from the line's table (tw32[k] = w_W^(k W / 32)).
+template <typename C, int N1>
+__device__ __forceinline__ void dft_n1(const C* x, C* X, const C* __restrict__ tw32) {
+  if constexpr (N1 <= 16) {
+    dft_g<C, N1, 1>(x, X);
+  } else {
+    C E[16], O[16];
+    dft_g<C, 16, 2>(x, E);
+    dft_g<C, 16, 2>(x + 1, O);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const C t = k == 0 ? O[0] : mul(O[k], tw32[k]);
+      X[k] = add(E[k], t);
+      X[k + 16] = sub(E[k], t);
     }
-    __syncthreads();
   }
-  for (int i = tid; i < kLines * W; i += kFftThreads) {
-    const int line = ROWS ? i / W : i % kLines;
-    const int k = ROWS ? i % W : i / kLines;
-    const size_t e = ROWS ? (size_t)(line0 + line) * W + k : (size_t)k * W + line0 + line;
-    img[e] = buf[line][k];
+}
+
+constexpr int kT = 8;   // threads per line
+
+// Lines per CTA of type C and size W: as many as keep the exchange buffers within 40 KB of
+// static shared memory (at most 32).
+template <typename C, int W>
+struct LinesCfg {
+  static constexpr int N1 = W / kT;
+  static constexpr int XS = N1 + 1;
+  static constexpr int fit = 40960 / (kT * XS * (int)sizeof(C));
+  static constexpr int LPC = fit >= 32 ? 32 : fit >= 16 ? 16 : fit >= 8 ? 8 : 4;
+  static constexpr int THREADS = LPC * kT;
+};
+
+// y_k = sum_n x_n exp(-+2 pi i k n / W) (unnormalised; INV: the + sign) of every row (ROWS)
+// or column of the waves [nb][W][W].  Thread j of a line's eight holds elements j + 8m; step A
+// is an N1-point DFT in registers, step B the twiddles w_W^(j k1) from the table
+// wtab[k] = w_256^k (rounded or split once from double), an exchange through the group's
+// shared buffer, step C N1/8 eight-point DFTs; the output indices are again j + 8m.
+// Grid: (W / LPC, nb).
+template <typename C, int W, bool ROWS, bool INV>
+__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) lines_fft_kernel(C* __restrict__ data,
+                                                                           const C* __restrict__ wtab) {
+  using Cfg = LinesCfg<C, W>;
+  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC, NC = N1 / kT;
+  constexpr int STEP = 256 / W;   // wtab holds the 256th roots
+  __shared__ C s_tw[N1 * kT];     // w_W^(j k1) at [k1 kT + j]
+  __shared__ C s_t32[16];         // w_32^k (N1 = 32 only)
+  __shared__ C xbuf[LPC][kT * XS];
+  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
+  for (int i = tid; i < N1 * kT; i += Cfg::THREADS) s_tw[i] = wtab[((i / kT) * (i % kT) * STEP) % 256];
+  if (N1 > 16 && tid < 16) s_t32[tid] = wtab[tid * 8];
+  __syncthreads();
+  const int line = blockIdx.x * LPC + grp;
+  C* img = data + (size_t)blockIdx.y * W * W;
+  C v[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const C x = ROWS ? img[(size_t)line * W + j + kT * m] : img[(size_t)(j + kT * m) * W + line];
+    v[m] = INV ? conj_(x) : x;
   }
+  C y[N1];
+  dft_n1<C, N1>(v, y, s_t32);
+  C* xw = xbuf[grp] + j * XS;
+  xw[0] = y[0];
+#pragma unroll
+  for (int k1 = 1; k1 < N1; ++k1) xw[k1] = mul(y[k1], s_tw[k1 * kT + j]);
+  __syncwarp();
+  C b[NC][kT];
+  const C* xr = xbuf[grp] + j;
+#pragma unroll
+  for (int mc = 0; mc < NC; ++mc)
+#pragma unroll
+    for (int n2 = 0; n2 < kT; ++n2) b[mc][n2] = xr[n2 * XS + kT * mc];
+#pragma unroll
+  for (int mc = 0; mc < NC; ++mc) {
+    C X[kT];
+    dft_g<C, kT, 1>(b[mc], X);
+#pragma unroll
+    for (int k2 = 0; k2 < kT; ++k2) {
+      const int m = mc + NC * k2;   // spectrum element k1 + N1 k2 with k1 = j + kT mc
+      const C r = INV ? conj_(X[k2]) : X[k2];
+      if (ROWS) img[(size_t)line * W + j + kT * m] = r;
+      else img[(size_t)(j + kT * m) * W + line] = r;
+    }
+  }
+}
+
+// wtab[k] = exp(-2 pi i k / 256), evaluated in double, rounded (FP32) or split (double-float) once
+template <typename C>
+__global__ void wtab_kernel(C* __restrict__ wtab) {
+  const int k = threadIdx.x;
+  double sn, cs;
+  sincospi(2.0 * (double)k / 256.0, &sn, &cs);
+  wtab[k] = from_d<C>(cs, -sn);
 }
 
 // ---------------------------------------------------------------------------
@@ -373,17 +482,23 @@ __global__ void flag_windows_kernel(const int2* __restrict__ pos, int S, int Ny,
 // ---------------------------------------------------------------------------
 
 template <typename C, int W>
-static void fft2(C* data, int nb, bool inverse, cudaStream_t st) {
-  const dim3 grid(W / kLines, nb);
-  lines_fft_kernel<C, W, true><<<grid, kFftThreads, 0, st>>>(data, inverse ? 1 : 0);
-  lines_fft_kernel<C, W, false><<<grid, kFftThreads, 0, st>>>(data, inverse ? 1 : 0);
+static void fft2(C* data, const C* wtab, int nb, bool inverse, cudaStream_t st) {
+  const dim3 grid(W / LinesCfg<C, W>::LPC, nb);
+  constexpr int NT = LinesCfg<C, W>::THREADS;
+  if (inverse) {
+    lines_fft_kernel<C, W, true, true><<<grid, NT, 0, st>>>(data, wtab);
+    lines_fft_kernel<C, W, false, true><<<grid, NT, 0, st>>>(data, wtab);
+  } else {
+    lines_fft_kernel<C, W, true, false><<<grid, NT, 0, st>>>(data, wtab);
+    lines_fft_kernel<C, W, false, false><<<grid, NT, 0, st>>>(data, wtab);
+  }
 }
 
 template <typename C>
-static void fft2_w(int W, C* data, int nb, bool inverse, cudaStream_t st) {
-  if (W == 64) fft2<C, 64>(data, nb, inverse, st);
-  else if (W == 128) fft2<C, 128>(data, nb, inverse, st);
-  else fft2<C, 256>(data, nb, inverse, st);
+static void fft2_w(int W, C* data, const C* wtab, int nb, bool inverse, cudaStream_t st) {
+  if (W == 64) fft2<C, 64>(data, wtab, nb, inverse, st);
+  else if (W == 128) fft2<C, 128>(data, wtab, nb, inverse, st);
+  else fft2<C, 256>(data, wtab, nb, inverse, st);
 }
 
 static int elem_blocks(size_t n, int sms) {
@@ -417,6 +532,8 @@ struct Segs {
   double2* dp64 = nullptr;    // [W][W] probe-gradient sum
   void* mat_f = nullptr;      // split-BF16 DFT matrices, forward and inverse (split BF16)
   void* mat_i = nullptr;
+  void* wtab16 = nullptr;     // [256] exp(-2 pi i k / 256), FP64 or double-float (the forward's type)
+  float2* wtab8 = nullptr;    // [256] the same rounded to FP32 (the adjoint)
   size_t bytes = 0;
 };
 
@@ -441,6 +558,9 @@ Segs carve(int precision, int W, int L, int Ny, int Nx, int S, char* base) {
   if (tc) {
     g.mat_f = take(tcdft_matrix_bytes(W));
     g.mat_i = take(tcdft_matrix_bytes(W));
+  } else {
+    g.wtab16 = take(256 * sizeof(double2));
+    g.wtab8 = (float2*)take(256 * sizeof(float2));
   }
   g.bytes = off;
   return g;
@@ -455,7 +575,7 @@ size_t precise_extra_bytes(int precision, int W, int L, int Ny, int Nx, int S) {
 // The forward model and the adjoint of `mode` over all positions in batches, writing what the
 // fused kernel writes: I_out (forward), loss_part, the window gradients and illumination, and
 // the probe gradient into dprobe_part[0] (one partial).  FP64-forward mode: FP64 forward with the
-// radix-2 FFT, FP32 adjoint.  Double-float mode: the same with the forward in double-float.  Split-BF16 mode: every 2-D transform as two tensor-core passes,
+// four-step line FFT, FP32 adjoint.  Double-float mode: the same with the forward in double-float.  Split-BF16 mode: every 2-D transform as two tensor-core passes,
 // FP32 waves.  Reports the number of kernels launched.
 cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in, cudaStream_t st, long long* launches) {
   using namespace precise;
@@ -477,12 +597,16 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
                                                                                  (dfc*)g.T64, (size_t)L * plane,
                                                                                  in.sigma);
     h1_64_kernel<dfc><<<(W + 255) / 256, 256, 0, st>>>((dfc*)g.h1d, W, in.dzlam, in.dq);
-    n_launch += 2;
+    wtab_kernel<dfc><<<1, 256, 0, st>>>((dfc*)g.wtab16);
+    wtab_kernel<float2><<<1, 256, 0, st>>>(g.wtab8);
+    n_launch += 4;
   } else {
     table64_kernel<double2><<<elem_blocks((size_t)L * plane, in.sms), 256, 0, st>>>(in.X ? nullptr : in.V, in.X,
                                                                                      g.T64, (size_t)L * plane, in.sigma);
     h1_64_kernel<double2><<<(W + 255) / 256, 256, 0, st>>>(g.h1d, W, in.dzlam, in.dq);
-    n_launch += 2;
+    wtab_kernel<double2><<<1, 256, 0, st>>>((double2*)g.wtab16);
+    wtab_kernel<float2><<<1, 256, 0, st>>>(g.wtab8);
+    n_launch += 4;
   }
   flag_windows_kernel<<<(S + 255) / 256, 256, 0, st>>>(p.pos, S, p.Ny, p.Nx, W, p.err);
   ++n_launch;
@@ -496,9 +620,9 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
       keep_first(tcdft_pass(W, (float2*)g.wave, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
       keep_first(tcdft_pass(W, g.tmp, (float2*)g.wave, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
     } else if (df) {
-      fft2_w<dfc>(W, (dfc*)g.wave, nb, inverse, st);
+      fft2_w<dfc>(W, (dfc*)g.wave, (const dfc*)g.wtab16, nb, inverse, st);
     } else {
-      fft2_w<double2>(W, (double2*)g.wave, nb, inverse, st);
+      fft2_w<double2>(W, (double2*)g.wave, (const double2*)g.wtab16, nb, inverse, st);
     }
     n_launch += 2;
   };
@@ -507,7 +631,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
       keep_first(tcdft_pass(W, g.chi, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
       keep_first(tcdft_pass(W, g.tmp, g.chi, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
     } else {
-      fft2_w<float2>(W, g.chi, nb, inverse, st);
+      fft2_w<float2>(W, g.chi, g.wtab8, nb, inverse, st);
     }
     n_launch += 2;
   };
