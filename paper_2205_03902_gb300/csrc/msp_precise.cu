@@ -33,6 +33,7 @@
 
 #include <cstdint>
 #include <string>
+#include <type_traits>
 
 #include "msp.h"
 #include "msp_kernels.cuh"
@@ -113,6 +114,21 @@ __device__ __forceinline__ dff df_from(double x) {
   return {h, (float)(x - (double)h)};
 }
 __device__ __forceinline__ double df_to(dff x) { return (double)x.h + (double)x.l; }
+// Square root and quotient: an FP32 seed corrected by one Newton step whose residual is formed
+// exactly (Karp and Markstein, ACM TOMS 1997); about 46 significand bits.
+__device__ __forceinline__ dff df_sqrt(dff x) {
+  if (!(x.h > 0.f)) return {0.f, 0.f};
+  const float s = sqrtf(x.h);
+  const float p = s * s, e = fmaf(s, s, -p);   // s^2 = p + e exactly
+  const float r = ((x.h - p) - e) + x.l;       // x - s^2 (x.h - p exact: p is within a factor 2 of x.h)
+  return fast_two_sum(s, r * (0.5f / s));
+}
+__device__ __forceinline__ dff df_div(dff a, dff b) {   // a / b, b != 0
+  const float q0 = a.h / b.h;
+  const float p = q0 * b.h, e = fmaf(q0, b.h, -p);   // q0 b.h = p + e exactly
+  const float r = (((a.h - p) - e) + a.l) - q0 * b.l; // a - q0 b
+  return fast_two_sum(q0, r / b.h);
+}
 
 __device__ __forceinline__ dfc add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
 __device__ __forceinline__ dfc sub(dfc a, dfc b) { return {df_add(a.re, df_neg(b.re)), df_add(a.im, df_neg(b.im))}; }
@@ -370,8 +386,9 @@ __global__ void propagator_kernel(Batch bt, const H* __restrict__ h1, C* __restr
   }
 }
 
-// Far field Psi (FP64) -> the loss of each position, R = Psi - sqrt(I) Psi / |Psi| (the fraction 0
-// where |Psi|^2 <= thr2) rounded to FP32, or the intensities |Psi|^2.  One CTA per position.
+// Far field Psi (FP64 or double-float) -> the loss of each position, R = Psi - sqrt(I) Psi / |Psi|
+// (the fraction 0 where |Psi|^2 <= thr2) rounded to FP32, or the intensities |Psi|^2.  One CTA
+// per position.  The double-float form keeps the arithmetic on the FP32 pipe.
 template <typename C>
 __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __restrict__ psi,
                                                        const float* __restrict__ I_meas, const double* __restrict__ zthr2,
@@ -384,6 +401,26 @@ __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __rest
   const bool ok = window_ok(bt.pos[b], bt.Ny, bt.Nx, W);
   const double thr2 = I_out ? 0.0 : zthr2[0];
   double acc = 0.0;
+  if constexpr (std::is_same<C, dfc>::value) {
+    // double-float: the same quantities on the FP32 pipe; FP64 only for the loss sum and the
+    // zero-rule comparison
+    for (size_t k = tid; k < WW; k += 256) {
+      const dfc v = psi[(size_t)b * WW + k];
+      const dff a2 = df_add(df_mul(v.re, v.re), df_mul(v.im, v.im));
+      if (I_out) {
+        I_out[(size_t)b * WW + k] = a2.h + a2.l;
+        continue;
+      }
+      const dff a = df_sqrt(a2), rt = df_sqrt(dff{I_meas[(size_t)b * WW + k], 0.f});
+      const dff d = df_add(rt, df_neg(a));
+      const double dd = df_to(d);
+      acc += dd * dd;
+      const bool live = df_to(a2) > thr2;
+      const dff f = live ? df_add(dff{1.f, 0.f}, df_neg(df_div(rt, a))) : dff{1.f, 0.f};
+      const dff rx = df_mul(v.re, f), ry = df_mul(v.im, f);
+      R[(size_t)b * WW + k] = make_float2(rx.h + rx.l, ry.h + ry.l);
+    }
+  } else {
   for (size_t k = tid; k < WW; k += 256) {
     const double2 v = widen(psi[(size_t)b * WW + k]);
     const double a2 = v.x * v.x + v.y * v.y;
@@ -396,6 +433,7 @@ __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __rest
     acc += d * d;
     const double f = (a2 > thr2) ? 1.0 - rt / a : 1.0;
     R[(size_t)b * WW + k] = make_float2((float)(v.x * f), (float)(v.y * f));
+  }
   }
   if (I_out) return;
 #pragma unroll
