@@ -151,6 +151,7 @@ __device__ __forceinline__ bool window_ok(int2 ps, int Ny, int Nx, int W) {
 // batched line DFTs: the four-step split W = N1 x 8 of the fast path in registers, for the
 // three arithmetics (FP32, FP64, double-float)
 // ---------------------------------------------------------------------------
+template <typename C> __device__ __forceinline__ C from_h(C h) { return h; }
 template <typename C> __device__ __forceinline__ C conj_(C a) { return mk<C>(a.x, -a.y); }
 template <> __device__ __forceinline__ dfc conj_<dfc>(dfc a) { return {a.re, df_neg(a.im)}; }
 template <typename C> __device__ __forceinline__ C rot_mi(C a) { return mk<C>(a.y, -a.x); }   // a (-i)
@@ -250,42 +251,24 @@ struct LinesCfg {
   static constexpr int THREADS = LPC * kT;
 };
 
-// y_k = sum_n x_n exp(-+2 pi i k n / W) (unnormalised; INV: the + sign) of every row (ROWS)
-// or column of the waves [nb][W][W].  Thread j of a line's eight holds elements j + 8m; step A
-// is an N1-point DFT in registers, step B the twiddles w_W^(j k1) from the table
-// wtab[k] = w_256^k (rounded or split once from double), an exchange through the group's
-// shared buffer, step C N1/8 eight-point DFTs; the output indices are again j + 8m.
-// Grid: (W / LPC, nb).
-template <typename C, int W, bool ROWS, bool INV>
-__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) lines_fft_kernel(C* __restrict__ data,
-                                                                           const C* __restrict__ wtab) {
-  using Cfg = LinesCfg<C, W>;
-  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC, NC = N1 / kT;
-  constexpr int STEP = 256 / W;   // wtab holds the 256th roots
-  __shared__ C s_tw[N1 * kT];     // w_W^(j k1) at [k1 kT + j]
-  __shared__ C s_t32[16];         // w_32^k (N1 = 32 only)
-  __shared__ C xbuf[LPC][kT * XS];
-  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
-  for (int i = tid; i < N1 * kT; i += Cfg::THREADS) s_tw[i] = wtab[((i / kT) * (i % kT) * STEP) % 256];
-  if (N1 > 16 && tid < 16) s_t32[tid] = wtab[tid * 8];
-  __syncthreads();
-  const int line = blockIdx.x * LPC + grp;
-  C* img = data + (size_t)blockIdx.y * W * W;
-  C v[N1];
-#pragma unroll
-  for (int m = 0; m < N1; ++m) {
-    const C x = ROWS ? img[(size_t)line * W + j + kT * m] : img[(size_t)(j + kT * m) * W + line];
-    v[m] = INV ? conj_(x) : x;
-  }
+// Forward unnormalised W-point DFT of one line held by eight threads: thread j holds elements
+// j + 8m on entry and spectrum elements j + 8m on exit.  Step A is an N1-point DFT in registers,
+// step B the twiddles w_W^(j k1) (s_tw[k1 kT + j]), an exchange through the group's shared
+// buffer xb, step C N1/8 eight-point DFTs.
+template <typename C, int W>
+__device__ __forceinline__ void line_dft(C (&v)[W / kT], const C* __restrict__ s_tw, const C* __restrict__ s_t32,
+                                         C* xb, int j) {
+  constexpr int N1 = W / kT, XS = N1 + 1, NC = N1 / kT;
   C y[N1];
   dft_n1<C, N1>(v, y, s_t32);
-  C* xw = xbuf[grp] + j * XS;
+  __syncwarp();   // the group's previous transform has read the buffer
+  C* xw = xb + j * XS;
   xw[0] = y[0];
 #pragma unroll
   for (int k1 = 1; k1 < N1; ++k1) xw[k1] = mul(y[k1], s_tw[k1 * kT + j]);
   __syncwarp();
   C b[NC][kT];
-  const C* xr = xbuf[grp] + j;
+  const C* xr = xb + j;
 #pragma unroll
   for (int mc = 0; mc < NC; ++mc)
 #pragma unroll
@@ -295,13 +278,80 @@ __global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) lines_fft_kernel(C* _
     C X[kT];
     dft_g<C, kT, 1>(b[mc], X);
 #pragma unroll
-    for (int k2 = 0; k2 < kT; ++k2) {
-      const int m = mc + NC * k2;   // spectrum element k1 + N1 k2 with k1 = j + kT mc
-      const C r = INV ? conj_(X[k2]) : X[k2];
-      if (ROWS) img[(size_t)line * W + j + kT * m] = r;
-      else img[(size_t)(j + kT * m) * W + line] = r;
-    }
+    for (int k2 = 0; k2 < kT; ++k2) v[mc + NC * k2] = X[k2];   // spectrum element k1 + N1 k2, k1 = j + kT mc
   }
+}
+
+// The twiddle tables of a CTA's line transforms: s_tw[k1 kT + j] = w_W^(j k1) and, for N1 = 32,
+// s_t32[k] = w_32^k, from wtab[k] = w_256^k.
+template <typename C, int W, int NT>
+__device__ __forceinline__ void load_twiddles(C* s_tw, C* s_t32, const C* __restrict__ wtab) {
+  constexpr int N1 = W / kT, STEP = 256 / W;
+  for (int i = threadIdx.x; i < N1 * kT; i += NT) s_tw[i] = wtab[((i / kT) * (i % kT) * STEP) % 256];
+  if (N1 > 16 && threadIdx.x < 16) s_t32[threadIdx.x] = wtab[threadIdx.x * 8];
+}
+
+// y_k = sum_n x_n exp(-+2 pi i k n / W) (unnormalised; INV: the + sign, as conj(F(conj x))) of
+// every row (ROWS) or column of the waves [nb][W][W].  Grid: (W / LPC, nb).
+template <typename C, int W, bool ROWS, bool INV>
+__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) lines_fft_kernel(C* __restrict__ data,
+                                                                           const C* __restrict__ wtab) {
+  using Cfg = LinesCfg<C, W>;
+  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC;
+  __shared__ C s_tw[N1 * kT];
+  __shared__ C s_t32[16];
+  __shared__ C xbuf[LPC][kT * XS];
+  load_twiddles<C, W, Cfg::THREADS>(s_tw, s_t32, wtab);
+  __syncthreads();
+  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
+  const int line = blockIdx.x * LPC + grp;
+  C* img = data + (size_t)blockIdx.y * W * W;
+  C v[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const C x = ROWS ? img[(size_t)line * W + j + kT * m] : img[(size_t)(j + kT * m) * W + line];
+    v[m] = INV ? conj_(x) : x;
+  }
+  line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const C r = INV ? conj_(v[m]) : v[m];
+    if (ROWS) img[(size_t)line * W + j + kT * m] = r;
+    else img[(size_t)(j + kT * m) * W + line] = r;
+  }
+}
+
+// The column half of a Fresnel propagation of row-transformed waves: every column is
+// transformed, multiplied by the separable propagator h1(ky) h1(kx) (CONJ: its conjugate, for
+// G^H) and transformed back (unnormalised inverse); with row transforms before and after this
+// is F^-1 (H o F x) up to the normalisation that h1 carries.  Grid: (W / LPC, nb).
+template <typename C, typename H, int W, bool CONJ>
+__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) cols_propagate_kernel(C* __restrict__ data,
+                                                                                const C* __restrict__ wtab,
+                                                                                const H* __restrict__ h1) {
+  using Cfg = LinesCfg<C, W>;
+  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC;
+  __shared__ C s_tw[N1 * kT];
+  __shared__ C s_t32[16];
+  __shared__ C xbuf[LPC][kT * XS];
+  load_twiddles<C, W, Cfg::THREADS>(s_tw, s_t32, wtab);
+  __syncthreads();
+  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
+  const int line = blockIdx.x * LPC + grp;   // column kx
+  C* img = data + (size_t)blockIdx.y * W * W;
+  C v[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) v[m] = img[(size_t)(j + kT * m) * W + line];
+  line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);
+  const C hx = from_h<C>(h1[line]);
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const C h = mul(from_h<C>(h1[j + kT * m]), hx);   // ky = j + kT m
+    v[m] = conj_(CONJ ? mulc(v[m], h) : mul(v[m], h));   // conj: the inverse transform follows
+  }
+  line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);
+#pragma unroll
+  for (int m = 0; m < N1; ++m) img[(size_t)(j + kT * m) * W + line] = conj_(v[m]);
 }
 
 // wtab[k] = exp(-2 pi i k / 256), evaluated in double, rounded (FP32) or split (double-float) once
@@ -372,6 +422,54 @@ __global__ void transmit_kernel(Batch bt, int l, const float2* __restrict__ prob
     wave[i] = e;
     if (keep) stash[((size_t)b * bt.L + (l - stash_l0)) * WW + (i % WW)] = narrow(cplx ? psi : e);
   }
+}
+
+// Row pass of the forward model at slice l, fused: the inverse row transform that ends the
+// propagation of slice l - 1 (START: none, the probe is the incident wave of slice 0), the
+// transmit E = psi o X_l with its stash for the adjoint (the incident psi in transmission mode),
+// and the forward row transform that starts the next propagation or the far field.  A window
+// outside the object gives zeros.  Grid: (W / LPC, nb).
+template <typename C, int W, bool START>
+__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) rows_transmit_kernel(
+    C* __restrict__ wave, const C* __restrict__ wtab, Batch bt, int l, const float2* __restrict__ probe,
+    const C* __restrict__ T, float2* __restrict__ stash, int keep, int cplx) {
+  using Cfg = LinesCfg<C, W>;
+  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC;
+  constexpr size_t WW = (size_t)W * W;
+  __shared__ C s_tw[N1 * kT];
+  __shared__ C s_t32[16];
+  __shared__ C xbuf[LPC][kT * XS];
+  load_twiddles<C, W, Cfg::THREADS>(s_tw, s_t32, wtab);
+  __syncthreads();
+  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
+  const int r = blockIdx.x * LPC + grp, b = blockIdx.y;
+  C* row = wave + (size_t)b * WW + (size_t)r * W;
+  const int2 ps = bt.pos[b];
+  const bool ok = window_ok(ps, bt.Ny, bt.Nx, W);
+  C v[N1];
+  if (START) {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = from_f2<C>(probe[(size_t)r * W + j + kT * m]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = conj_(row[j + kT * m]);
+    line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = conj_(v[m]);   // unnormalised inverse row transform
+  }
+  const C* Tr = T + (size_t)l * bt.plane + (size_t)(ps.x + r) * bt.Nx + ps.y;
+  float2* st = stash + ((size_t)b * bt.L + l) * WW + (size_t)r * W;
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const int c = j + kT * m;
+    const C psi = ok ? v[m] : from_d<C>(0.0, 0.0);
+    const C e = ok ? mul(psi, Tr[c]) : psi;
+    if (keep) st[c] = narrow(cplx ? psi : e);
+    v[m] = e;
+  }
+  line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);
+#pragma unroll
+  for (int m = 0; m < N1; ++m) row[j + kT * m] = v[m];
 }
 
 // x h1(ky) h1(kx) (CONJ: the conjugate, for G^H) on the spectrum of every wave.
@@ -532,6 +630,68 @@ static void fft2(C* data, const C* wtab, int nb, bool inverse, cudaStream_t st) 
   }
 }
 
+// A Fresnel propagation of the waves: rows F, columns (F, x h1 h1 or its conjugate, F^-1),
+// rows F^-1: three passes over the batch.
+template <typename C, int W>
+static void propagate2(C* data, const C* wtab, const C* h1, int nb, bool conj, cudaStream_t st) {
+  const dim3 grid(W / LinesCfg<C, W>::LPC, nb);
+  constexpr int NT = LinesCfg<C, W>::THREADS;
+  lines_fft_kernel<C, W, true, false><<<grid, NT, 0, st>>>(data, wtab);
+  if (conj) cols_propagate_kernel<C, C, W, true><<<grid, NT, 0, st>>>(data, wtab, h1);
+  else cols_propagate_kernel<C, C, W, false><<<grid, NT, 0, st>>>(data, wtab, h1);
+  lines_fft_kernel<C, W, true, true><<<grid, NT, 0, st>>>(data, wtab);
+}
+template <typename C, int W>
+static void rows_transmit(bool start, C* wave, const C* wtab, const Batch& bt, int l, const float2* probe, const C* T,
+                          float2* stash, int keep, int cplx, cudaStream_t st) {
+  const dim3 grid(W / LinesCfg<C, W>::LPC, bt.nb);
+  constexpr int NT = LinesCfg<C, W>::THREADS;
+  if (start) rows_transmit_kernel<C, W, true><<<grid, NT, 0, st>>>(wave, wtab, bt, l, probe, T, stash, keep, cplx);
+  else rows_transmit_kernel<C, W, false><<<grid, NT, 0, st>>>(wave, wtab, bt, l, probe, T, stash, keep, cplx);
+}
+template <typename C>
+static void rows_transmit_w(bool start, C* wave, const C* wtab, const Batch& bt, int l, const float2* probe,
+                            const C* T, float2* stash, int keep, int cplx, cudaStream_t st) {
+  if (bt.W == 64) rows_transmit<C, 64>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
+  else if (bt.W == 128) rows_transmit<C, 128>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
+  else rows_transmit<C, 256>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
+}
+// The column half of a propagation (the rows are fused with the transmit).
+template <typename C>
+static void cols_propagate_w(int W, C* data, const C* wtab, const C* h1, int nb, cudaStream_t st) {
+#define MSP_COLS(WW_)                                                                                   \
+  if (W == WW_) {                                                                                       \
+    cols_propagate_kernel<C, C, WW_, false>                                                             \
+        <<<dim3(WW_ / LinesCfg<C, WW_>::LPC, nb), LinesCfg<C, WW_>::THREADS, 0, st>>>(data, wtab, h1);  \
+    return;                                                                                             \
+  }
+  MSP_COLS(64)
+  MSP_COLS(128)
+  MSP_COLS(256)
+#undef MSP_COLS
+}
+// The column pass of the far-field transform (the rows were transformed by the last transmit).
+template <typename C>
+static void cols_fft_w(int W, C* data, const C* wtab, int nb, cudaStream_t st) {
+#define MSP_COLF(WW_)                                                                                   \
+  if (W == WW_) {                                                                                       \
+    lines_fft_kernel<C, WW_, false, false>                                                              \
+        <<<dim3(WW_ / LinesCfg<C, WW_>::LPC, nb), LinesCfg<C, WW_>::THREADS, 0, st>>>(data, wtab);      \
+    return;                                                                                             \
+  }
+  MSP_COLF(64)
+  MSP_COLF(128)
+  MSP_COLF(256)
+#undef MSP_COLF
+}
+
+template <typename C>
+static void propagate2_w(int W, C* data, const C* wtab, const C* h1, int nb, bool conj, cudaStream_t st) {
+  if (W == 64) propagate2<C, 64>(data, wtab, h1, nb, conj, st);
+  else if (W == 128) propagate2<C, 128>(data, wtab, h1, nb, conj, st);
+  else propagate2<C, 256>(data, wtab, h1, nb, conj, st);
+}
+
 template <typename C>
 static void fft2_w(int W, C* data, const C* wtab, int nb, bool inverse, cudaStream_t st) {
   if (W == 64) fft2<C, 64>(data, wtab, nb, inverse, st);
@@ -683,23 +843,38 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     Batch bt{p.pos + b0, nb, W, p.Ny, p.Nx, L, plane};
     const int eb = elem_blocks((size_t)nb * WW, in.sms);
     // forward: slice 0, then (propagate, transmit) for every later slice
-    for (int l = 0; l < L; ++l) {
-      const int keep = !fwd && l >= lowest;
-      if (l > 0) {
-        fwd2(nb, false);
-        if (tc) propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, (float2*)g.wave, 0);
-        else if (df) propagator_kernel<dfc, dfc><<<eb, 256, 0, st>>>(bt, (const dfc*)g.h1d, (dfc*)g.wave, 0);
-        else propagator_kernel<double2, double2><<<eb, 256, 0, st>>>(bt, g.h1d, (double2*)g.wave, 0);
-        fwd2(nb, true);
+    if (tc) {
+      for (int l = 0; l < L; ++l) {
+        const int keep = !fwd && l >= lowest;
+        if (l > 0) {
+          fwd2(nb, false);
+          propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, (float2*)g.wave, 0);
+          fwd2(nb, true);
+          ++n_launch;
+        }
+        transmit_kernel<float2><<<eb, 256, 0, st>>>(bt, l, p.probe, p.T, (float2*)g.wave, g.stash, 0, keep, p.cplx);
         ++n_launch;
       }
-      if (tc) transmit_kernel<float2><<<eb, 256, 0, st>>>(bt, l, p.probe, p.T, (float2*)g.wave, g.stash, 0, keep, p.cplx);
-      else if (df)
-        transmit_kernel<dfc><<<eb, 256, 0, st>>>(bt, l, p.probe, (const dfc*)g.T64, (dfc*)g.wave, g.stash, 0, keep, p.cplx);
-      else transmit_kernel<double2><<<eb, 256, 0, st>>>(bt, l, p.probe, g.T64, (double2*)g.wave, g.stash, 0, keep, p.cplx);
-      ++n_launch;
+      fwd2(nb, false);   // far field Psi = F(E_L)
+    } else {
+      // row passes fused with the transmits: [start: probe o X_1, rows F], then per slice
+      // [columns F, x H, F^-1] [rows F^-1, o X_l, rows F], then [columns F] = the far field
+      auto fused = [&](auto* wave, const auto* wtab, const auto* T, const auto* h1d) {
+        for (int l = 0; l < L; ++l) {
+          const int keep = !fwd && l >= lowest;
+          if (l > 0) {
+            cols_propagate_w(W, wave, wtab, h1d, nb, st);
+            ++n_launch;
+          }
+          rows_transmit_w(l == 0, wave, wtab, bt, l, p.probe, T, g.stash, keep, p.cplx, st);
+          ++n_launch;
+        }
+        cols_fft_w(W, wave, wtab, nb, st);
+        ++n_launch;
+      };
+      if (df) fused((dfc*)g.wave, (const dfc*)g.wtab16, (const dfc*)g.T64, (const dfc*)g.h1d);
+      else fused((double2*)g.wave, (const double2*)g.wtab16, (const double2*)g.T64, (const double2*)g.h1d);
     }
-    fwd2(nb, false);   // far field Psi = F(E_L)
     const float* Im = fwd ? nullptr : p.I_meas + (size_t)b0 * WW;
     double* lp = fwd ? nullptr : p.loss_part + b0;
     float* Io = fwd ? p.I_out + (size_t)b0 * WW : nullptr;
@@ -725,10 +900,15 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
                                          p.two_sigma);
       ++n_launch;
       if (!go_on || l == 0) break;
-      adj2(nb, false);
-      propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, g.chi, 1);
-      adj2(nb, true);
-      ++n_launch;
+      if (tc) {
+        adj2(nb, false);
+        propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, g.chi, 1);
+        adj2(nb, true);
+        ++n_launch;
+      } else {
+        propagate2_w<float2>(W, g.chi, g.wtab8, p.h1, nb, true, st);
+        n_launch += 3;
+      }
     }
     if (want_dprobe) {
       dprobe_accumulate_kernel<<<(int)((WW + 255) / 256), 256, 0, st>>>(g.contrib, nb, (int)WW, g.dp64, b0 == 0);
