@@ -589,6 +589,58 @@ __global__ void adjoint_kernel(Batch bt, int l, float2* __restrict__ chi, const 
   }
 }
 
+// Row pass of the adjoint at slice l, fused: the inverse row transform that ends chi_l's
+// transform (a propagation, or F^-1 of the residual), the adjoint step of adjoint_kernel, and
+// (NEXT) the forward row transform that starts the propagation by G^H.  Grid: (W / LPC, nb).
+template <int W, bool NEXT>
+__global__ void __launch_bounds__(LinesCfg<float2, W>::THREADS) rows_adjoint_kernel(
+    float2* __restrict__ chi, const float2* __restrict__ wtab, Batch bt, int l, const float2* __restrict__ stash_l,
+    const float2* __restrict__ X, AdjOut o, int go_on, int cplx, float two_sigma) {
+  using Cfg = LinesCfg<float2, W>;
+  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC;
+  constexpr size_t WW = (size_t)W * W;
+  __shared__ float2 s_tw[N1 * kT];
+  __shared__ float2 s_t32[16];
+  __shared__ float2 xbuf[LPC][kT * XS];
+  load_twiddles<float2, W, Cfg::THREADS>(s_tw, s_t32, wtab);
+  __syncthreads();
+  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
+  const int r = blockIdx.x * LPC + grp, b = blockIdx.y;
+  float2* row = chi + (size_t)b * WW + (size_t)r * W;
+  const int2 ps = bt.pos[b];
+  const bool ok = window_ok(ps, bt.Ny, bt.Nx, W);
+  const size_t s = (size_t)(o.s0 + b);
+  float2 v[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) v[m] = conj_(row[j + kT * m]);
+  line_dft<float2, W>(v, s_tw, s_t32, xbuf[grp], j);
+#pragma unroll
+  for (int m = 0; m < N1; ++m) {
+    const int c = j + kT * m;
+    const size_t k = (size_t)r * W + c;
+    float2 u = ok ? conj_(v[m]) : make_float2(0.f, 0.f);   // chi_l at (r, c)
+    if (o.wgrad || o.willum) {
+      const float2 e = stash_l[(size_t)b * bt.L * WW + k];
+      if (o.wgrad) {
+        if (cplx) reinterpret_cast<float2*>(o.wgrad)[(o.wstride / 2) * s + k] = mulc(u, e);
+        else o.wgrad[o.wstride * s + k] = two_sigma * (e.x * u.y - e.y * u.x);
+      }
+      if (o.willum) o.willum[s * WW + k] = e.x * e.x + e.y * e.y;
+    }
+    if (go_on) {
+      const float2 t = ok ? X[(size_t)l * bt.plane + (size_t)(ps.x + r) * bt.Nx + ps.y + c] : make_float2(0.f, 0.f);
+      u = mulc(u, t);
+      if (l == 0 && o.contrib) o.contrib[(size_t)b * WW + k] = u;
+    }
+    v[m] = u;
+  }
+  if (NEXT) {
+    line_dft<float2, W>(v, s_tw, s_t32, xbuf[grp], j);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) row[j + kT * m] = v[m];
+  }
+}
+
 // dp64[k] += sum_{b < nb} contrib[b][k], b ascending (FP64, fixed order).
 __global__ void dprobe_accumulate_kernel(const float2* __restrict__ contrib, int nb, int WW, double2* __restrict__ dp64,
                                          int first) {
@@ -656,12 +708,13 @@ static void rows_transmit_w(bool start, C* wave, const C* wtab, const Batch& bt,
   else if (bt.W == 128) rows_transmit<C, 128>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
   else rows_transmit<C, 256>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
 }
-// The column half of a propagation (the rows are fused with the transmit).
-template <typename C>
+// The column half of a propagation (the rows are fused with the transmit or the adjoint step);
+// CONJ: by G^H.
+template <typename C, bool CONJ = false>
 static void cols_propagate_w(int W, C* data, const C* wtab, const C* h1, int nb, cudaStream_t st) {
 #define MSP_COLS(WW_)                                                                                   \
   if (W == WW_) {                                                                                       \
-    cols_propagate_kernel<C, C, WW_, false>                                                             \
+    cols_propagate_kernel<C, C, WW_, CONJ>                                                              \
         <<<dim3(WW_ / LinesCfg<C, WW_>::LPC, nb), LinesCfg<C, WW_>::THREADS, 0, st>>>(data, wtab, h1);  \
     return;                                                                                             \
   }
@@ -670,12 +723,13 @@ static void cols_propagate_w(int W, C* data, const C* wtab, const C* h1, int nb,
   MSP_COLS(256)
 #undef MSP_COLS
 }
-// The column pass of the far-field transform (the rows were transformed by the last transmit).
-template <typename C>
+// A column pass alone: the far-field transform (its rows were transformed by the last transmit),
+// or (INV) the column half of F^-1 of the residual.
+template <typename C, bool INV = false>
 static void cols_fft_w(int W, C* data, const C* wtab, int nb, cudaStream_t st) {
 #define MSP_COLF(WW_)                                                                                   \
   if (W == WW_) {                                                                                       \
-    lines_fft_kernel<C, WW_, false, false>                                                              \
+    lines_fft_kernel<C, WW_, false, INV>                                                                \
         <<<dim3(WW_ / LinesCfg<C, WW_>::LPC, nb), LinesCfg<C, WW_>::THREADS, 0, st>>>(data, wtab);      \
     return;                                                                                             \
   }
@@ -683,6 +737,22 @@ static void cols_fft_w(int W, C* data, const C* wtab, int nb, cudaStream_t st) {
   MSP_COLF(128)
   MSP_COLF(256)
 #undef MSP_COLF
+}
+
+static void rows_adjoint_w(bool next, float2* chi, const float2* wtab, const Batch& bt, int l, const float2* stash_l,
+                           const float2* X, const AdjOut& o, int go_on, int cplx, float two_sigma, cudaStream_t st) {
+#define MSP_ROWA(WW_)                                                                                             \
+  if (bt.W == WW_) {                                                                                              \
+    const dim3 grid(WW_ / LinesCfg<float2, WW_>::LPC, bt.nb);                                                     \
+    constexpr int NT = LinesCfg<float2, WW_>::THREADS;                                                            \
+    if (next) rows_adjoint_kernel<WW_, true><<<grid, NT, 0, st>>>(chi, wtab, bt, l, stash_l, X, o, go_on, cplx, two_sigma); \
+    else rows_adjoint_kernel<WW_, false><<<grid, NT, 0, st>>>(chi, wtab, bt, l, stash_l, X, o, go_on, cplx, two_sigma);    \
+    return;                                                                                                       \
+  }
+  MSP_ROWA(64)
+  MSP_ROWA(128)
+  MSP_ROWA(256)
+#undef MSP_ROWA
 }
 
 template <typename C>
@@ -884,30 +954,52 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     ++n_launch;
     if (fwd) continue;
     // adjoint: chi_L = F^H R, then down the slices
-    adj2(nb, true);
-    for (int l = L - 1; l >= lowest; --l) {
-      const bool grad_here = mode == MODE_LOSS_GRAD || (mode == MODE_LAYER && l == p.layer);
-      const bool go_on = (l > lowest) || (l == 0 && want_dprobe);
-      AdjOut o{};
-      o.s0 = b0;
-      if (grad_here) {
-        o.wgrad = mode == MODE_LOSS_GRAD ? p.wgrad + (size_t)CW * l * WW : p.wgrad;
-        o.wstride = (size_t)CW * WW * (mode == MODE_LOSS_GRAD ? L : 1);
-        if (mode == MODE_LAYER) o.willum = p.willum;
-      }
-      if (l == 0 && want_dprobe) o.contrib = g.contrib;
-      adjoint_kernel<<<eb, 256, 0, st>>>(bt, l, g.chi, g.stash + (size_t)l * WW, p.T, o, go_on ? 1 : 0, p.cplx,
-                                         p.two_sigma);
-      ++n_launch;
-      if (!go_on || l == 0) break;
-      if (tc) {
+    if (tc) {
+      adj2(nb, true);
+      for (int l = L - 1; l >= lowest; --l) {
+        const bool grad_here = mode == MODE_LOSS_GRAD || (mode == MODE_LAYER && l == p.layer);
+        const bool go_on = (l > lowest) || (l == 0 && want_dprobe);
+        AdjOut o{};
+        o.s0 = b0;
+        if (grad_here) {
+          o.wgrad = mode == MODE_LOSS_GRAD ? p.wgrad + (size_t)CW * l * WW : p.wgrad;
+          o.wstride = (size_t)CW * WW * (mode == MODE_LOSS_GRAD ? L : 1);
+          if (mode == MODE_LAYER) o.willum = p.willum;
+        }
+        if (l == 0 && want_dprobe) o.contrib = g.contrib;
+        adjoint_kernel<<<eb, 256, 0, st>>>(bt, l, g.chi, g.stash + (size_t)l * WW, p.T, o, go_on ? 1 : 0, p.cplx,
+                                           p.two_sigma);
+        ++n_launch;
+        if (!go_on || l == 0) break;
         adj2(nb, false);
         propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, g.chi, 1);
         adj2(nb, true);
         ++n_launch;
-      } else {
-        propagate2_w<float2>(W, g.chi, g.wtab8, p.h1, nb, true, st);
-        n_launch += 3;
+      }
+    } else {
+      // the row passes fused with the adjoint steps: [columns F^-1 of R], then per slice
+      // [rows F^-1, adjoint step, rows F] [columns F, x conj H, F^-1], the last slice's row pass
+      // without the forward transform
+      cols_fft_w<float2, true>(W, g.chi, g.wtab8, nb, st);
+      ++n_launch;
+      for (int l = L - 1; l >= lowest; --l) {
+        const bool grad_here = mode == MODE_LOSS_GRAD || (mode == MODE_LAYER && l == p.layer);
+        const bool go_on = (l > lowest) || (l == 0 && want_dprobe);
+        const bool next = go_on && l > 0;
+        AdjOut o{};
+        o.s0 = b0;
+        if (grad_here) {
+          o.wgrad = mode == MODE_LOSS_GRAD ? p.wgrad + (size_t)CW * l * WW : p.wgrad;
+          o.wstride = (size_t)CW * WW * (mode == MODE_LOSS_GRAD ? L : 1);
+          if (mode == MODE_LAYER) o.willum = p.willum;
+        }
+        if (l == 0 && want_dprobe) o.contrib = g.contrib;
+        rows_adjoint_w(next, g.chi, g.wtab8, bt, l, g.stash + (size_t)l * WW, p.T, o, go_on ? 1 : 0, p.cplx,
+                       p.two_sigma, st);
+        ++n_launch;
+        if (!next) break;
+        cols_propagate_w<float2, true>(W, g.chi, g.wtab8, p.h1, nb, st);
+        ++n_launch;
       }
     }
     if (want_dprobe) {
