@@ -641,13 +641,25 @@ __global__ void __launch_bounds__(LinesCfg<float2, W>::THREADS) rows_adjoint_ker
   }
 }
 
-// dp64[k] += sum_{b < nb} contrib[b][k], b ascending (FP64, fixed order).
+// dp64[k] += sum_{b < nb} contrib[b][k], b ascending (FP64, fixed order); eight loads in flight
+// per thread, added in the same order.
 __global__ void dprobe_accumulate_kernel(const float2* __restrict__ contrib, int nb, int WW, double2* __restrict__ dp64,
                                          int first) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= WW) return;
   double2 a = first ? make_double2(0.0, 0.0) : dp64[k];
-  for (int b = 0; b < nb; ++b) {
+  int b = 0;
+  for (; b + 8 <= nb; b += 8) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = contrib[(size_t)(b + u) * WW + k];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a.x += v[u].x;
+      a.y += v[u].y;
+    }
+  }
+  for (; b < nb; ++b) {
     const float2 v = contrib[(size_t)b * WW + k];
     a.x += v.x;
     a.y += v.y;
