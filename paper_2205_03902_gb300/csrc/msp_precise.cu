@@ -1,4 +1,4 @@
-// msp_precise.cu -- the precise-forward mode (MSP_PRECISION_FP64_FORWARD).
+// msp_precise.cu -- the precise-forward modes (MSP_PRECISION_FP64_FORWARD, MSP_PRECISION_DF_FORWARD).
 //
 // The gradients of Sec. 3.2 are linear in the far-field residual R = Psi - sqrt(I) Psi/|Psi|.
 // Near a fit (the states a reconstruction visits), ||R|| is a small fraction of ||Psi||, so
@@ -13,22 +13,24 @@
 // error is already in the exit wave of the last slice.
 //
 // Layout: positions are taken in batches of B, sized so that one batch's FP64 waves
-// (B W^2 x 16 bytes) stay resident in L2 across the passes over them.  Every operator is
-// its own batched kernel over [B][W][W]:
-//   lines_fft_kernel   W-point DFTs of every row or every column of every wave of the batch
-//                      (four-step W = N1 x 8 in registers, as in the fast path; unnormalised,
-//                      either direction)
-//   start / transmit   E_1 = P o X_1, E_m = psi_m o X_m, keeping E_m (or psi_m) for the adjoint
-//   propagator         x h(ky, kx) / W^2 (the separable factor h1 of Eq. fresnel_element)
-//   residual           loss, R, intensities
-//   adjoint step       window gradients, conj(X_m) o chi_m, the probe-gradient terms
+// (B W^2 x 16 bytes) stay resident in L2 across the passes over them.  The line transforms
+// (W-point DFTs of rows or columns, the fast path's four-step W = N1 x 8 split in registers)
+// carry the operators next to them, so that a pass over the batch is one of
+//   [probe o X_1, rows F]                         start of the forward model
+//   [columns F, x h(ky) h(kx), columns F^-1]       a Fresnel propagation's middle (G or G^H)
+//   [rows F^-1, o X_l and the stash, rows F]       a transmit between two propagations
+//   [columns F, loss, R, columns F^-1 (FP32)]      the far field, the residual, chi_L's columns
+//   [rows F^-1, adjoint step, rows F]              window gradients, conj(X_m) o chi_m, the probe term
+// (double-float or FP64 up to R, FP32 after it).  The FP64 mode is this structure in FP64;
+// the double-float mode (MSP_PRECISION_DF_FORWARD) in unevaluated pairs of FP32 numbers.
 // The window gradients land in the same per-position buffers as the fused kernel's, so the
 // overlap-add, the reductions and the updates downstream are shared with the fast path.
 //
-// The same batched structure runs the split-BF16 precision form (MSP_PRECISION_BF16X3_DFT):
-// every 2-D transform of the forward and of the adjoint is two tensor-core passes of the W-point
-// DFT as a matrix product with 3-term split-BF16 operands (msp_tcdft.cu), the waves are FP32,
-// and the loss and the probe-gradient sum accumulate in FP64.
+// The split-BF16 precision form (MSP_PRECISION_BF16X3_DFT) runs the same steps one operator per
+// pass: every 2-D transform of the forward and of the adjoint is two tensor-core passes of the
+// W-point DFT as a matrix product with 3-term split-BF16 operands (msp_tcdft.cu), with separate
+// transmit, propagator, residual and adjoint kernels; the waves are FP32, and the loss and the
+// probe-gradient sum accumulate in FP64.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -291,36 +293,6 @@ __device__ __forceinline__ void load_twiddles(C* s_tw, C* s_t32, const C* __rest
   if (N1 > 16 && threadIdx.x < 16) s_t32[threadIdx.x] = wtab[threadIdx.x * 8];
 }
 
-// y_k = sum_n x_n exp(-+2 pi i k n / W) (unnormalised; INV: the + sign, as conj(F(conj x))) of
-// every row (ROWS) or column of the waves [nb][W][W].  Grid: (W / LPC, nb).
-template <typename C, int W, bool ROWS, bool INV>
-__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) lines_fft_kernel(C* __restrict__ data,
-                                                                           const C* __restrict__ wtab) {
-  using Cfg = LinesCfg<C, W>;
-  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC;
-  __shared__ C s_tw[N1 * kT];
-  __shared__ C s_t32[16];
-  __shared__ C xbuf[LPC][kT * XS];
-  load_twiddles<C, W, Cfg::THREADS>(s_tw, s_t32, wtab);
-  __syncthreads();
-  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
-  const int line = blockIdx.x * LPC + grp;
-  C* img = data + (size_t)blockIdx.y * W * W;
-  C v[N1];
-#pragma unroll
-  for (int m = 0; m < N1; ++m) {
-    const C x = ROWS ? img[(size_t)line * W + j + kT * m] : img[(size_t)(j + kT * m) * W + line];
-    v[m] = INV ? conj_(x) : x;
-  }
-  line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);
-#pragma unroll
-  for (int m = 0; m < N1; ++m) {
-    const C r = INV ? conj_(v[m]) : v[m];
-    if (ROWS) img[(size_t)line * W + j + kT * m] = r;
-    else img[(size_t)(j + kT * m) * W + line] = r;
-  }
-}
-
 // The column half of a Fresnel propagation of row-transformed waves: every column is
 // transformed, multiplied by the separable propagator h1(ky) h1(kx) (CONJ: its conjugate, for
 // G^H) and transformed back (unnormalised inverse); with row transforms before and after this
@@ -484,9 +456,10 @@ __global__ void propagator_kernel(Batch bt, const H* __restrict__ h1, C* __restr
   }
 }
 
-// Far field Psi (FP64 or double-float) -> the loss of each position, R = Psi - sqrt(I) Psi / |Psi|
-// (the fraction 0 where |Psi|^2 <= thr2) rounded to FP32, or the intensities |Psi|^2.  One CTA
-// per position.  The double-float form keeps the arithmetic on the FP32 pipe.
+// Far field Psi (FP32 waves of the split-BF16 form) -> the loss of each position,
+// R = Psi - sqrt(I) Psi / |Psi| (the fraction 0 where |Psi|^2 <= thr2) in FP64 and rounded to
+// FP32, or the intensities |Psi|^2.  One CTA per position.  (The FP64 and double-float forms
+// compute these in cols_farfield_kernel.)
 template <typename C>
 __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __restrict__ psi,
                                                        const float* __restrict__ I_meas, const double* __restrict__ zthr2,
@@ -499,26 +472,6 @@ __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __rest
   const bool ok = window_ok(bt.pos[b], bt.Ny, bt.Nx, W);
   const double thr2 = I_out ? 0.0 : zthr2[0];
   double acc = 0.0;
-  if constexpr (std::is_same<C, dfc>::value) {
-    // double-float: the same quantities on the FP32 pipe; FP64 only for the loss sum and the
-    // zero-rule comparison
-    for (size_t k = tid; k < WW; k += 256) {
-      const dfc v = psi[(size_t)b * WW + k];
-      const dff a2 = df_add(df_mul(v.re, v.re), df_mul(v.im, v.im));
-      if (I_out) {
-        I_out[(size_t)b * WW + k] = a2.h + a2.l;
-        continue;
-      }
-      const dff a = df_sqrt(a2), rt = df_sqrt(dff{I_meas[(size_t)b * WW + k], 0.f});
-      const dff d = df_add(rt, df_neg(a));
-      const double dd = df_to(d);
-      acc += dd * dd;
-      const bool live = df_to(a2) > thr2;
-      const dff f = live ? df_add(dff{1.f, 0.f}, df_neg(df_div(rt, a))) : dff{1.f, 0.f};
-      const dff rx = df_mul(v.re, f), ry = df_mul(v.im, f);
-      R[(size_t)b * WW + k] = make_float2(rx.h + rx.l, ry.h + ry.l);
-    }
-  } else {
   for (size_t k = tid; k < WW; k += 256) {
     const double2 v = widen(psi[(size_t)b * WW + k]);
     const double a2 = v.x * v.x + v.y * v.y;
@@ -532,7 +485,6 @@ __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __rest
     const double f = (a2 > thr2) ? 1.0 - rt / a : 1.0;
     R[(size_t)b * WW + k] = make_float2((float)(v.x * f), (float)(v.y * f));
   }
-  }
   if (I_out) return;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -543,6 +495,96 @@ __global__ void __launch_bounds__(256) residual_kernel(Batch bt, const C* __rest
     for (int w = 0; w < 8; ++w) s += red[w];
     loss_part[b] = ok ? s : 0.0;   // a skipped position contributes nothing (as in the fused kernel)
   }
+}
+
+// One far-field value: R = Psi (1 - sqrt(I) / |Psi|) (the fraction 0 where |Psi|^2 <= thr2) in
+// FP32, and (sqrt(I) - |Psi|)^2 added to acc; FP64 or double-float arithmetic, as the residual
+// kernel.
+__device__ __forceinline__ float2 residual_value(double2 v, float I, double thr2, double& acc) {
+  const double a2 = v.x * v.x + v.y * v.y;
+  const double a = sqrt(a2), rt = sqrt((double)I);
+  const double d = rt - a;
+  acc += d * d;
+  const double f = (a2 > thr2) ? 1.0 - rt / a : 1.0;
+  return make_float2((float)(v.x * f), (float)(v.y * f));
+}
+__device__ __forceinline__ float2 residual_value(dfc v, float I, double thr2, double& acc) {
+  const dff a2 = df_add(df_mul(v.re, v.re), df_mul(v.im, v.im));
+  const dff a = df_sqrt(a2), rt = df_sqrt(dff{I, 0.f});
+  const double dd = df_to(df_add(rt, df_neg(a)));
+  acc += dd * dd;
+  const dff f = df_to(a2) > thr2 ? df_add(dff{1.f, 0.f}, df_neg(df_div(rt, a))) : dff{1.f, 0.f};
+  const dff rx = df_mul(v.re, f), ry = df_mul(v.im, f);
+  return make_float2(rx.h + rx.l, ry.h + ry.l);
+}
+__device__ __forceinline__ float intensity_value(double2 v) { return (float)(v.x * v.x + v.y * v.y); }
+__device__ __forceinline__ float intensity_value(dfc v) {
+  const dff a2 = df_add(df_mul(v.re, v.re), df_mul(v.im, v.im));
+  return a2.h + a2.l;
+}
+
+// Column pass of the far field, fused (FP64 or double-float forward): every column of the
+// row-transformed exit wave is transformed (Psi = F E_L), then either the intensities |Psi|^2
+// are written (I_out), or the residual R is formed (as residual_kernel does) and transformed back
+// by the FP32 inverse column DFT, which leaves the columns of chi_L = F^-1 R for the adjoint's
+// first row pass; part[b][blockIdx.x] receives the CTA's share of the loss of position b (0 for
+// a window outside the object).  Grid: (W / LPC, nb).
+template <typename C, int W>
+__global__ void __launch_bounds__(LinesCfg<C, W>::THREADS) cols_farfield_kernel(
+    const C* __restrict__ wave, const C* __restrict__ wtab, const float2* __restrict__ wtab8, Batch bt,
+    const float* __restrict__ I_meas, const double* __restrict__ zthr2, float2* __restrict__ chi,
+    double* __restrict__ part, float* __restrict__ I_out) {
+  using Cfg = LinesCfg<C, W>;
+  constexpr int N1 = Cfg::N1, XS = Cfg::XS, LPC = Cfg::LPC, NT = Cfg::THREADS;
+  constexpr size_t WW = (size_t)W * W;
+  __shared__ C s_tw[N1 * kT];
+  __shared__ C s_t32[16];
+  __shared__ float2 s_tw8[N1 * kT];
+  __shared__ float2 s_t328[16];
+  __shared__ C xbuf[LPC][kT * XS];
+  __shared__ double red[NT / 32];
+  load_twiddles<C, W, NT>(s_tw, s_t32, wtab);
+  load_twiddles<float2, W, NT>(s_tw8, s_t328, wtab8);
+  __syncthreads();
+  const int tid = threadIdx.x, j = tid % kT, grp = tid / kT;
+  const int c = blockIdx.x * LPC + grp, b = blockIdx.y;
+  C v[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m) v[m] = wave[(size_t)b * WW + (size_t)(j + kT * m) * W + c];
+  line_dft<C, W>(v, s_tw, s_t32, xbuf[grp], j);   // Psi at (ky = j + kT m, kx = c)
+  if (I_out) {
+#pragma unroll
+    for (int m = 0; m < N1; ++m) I_out[(size_t)b * WW + (size_t)(j + kT * m) * W + c] = intensity_value(v[m]);
+    return;
+  }
+  const double thr2 = zthr2[0];
+  double acc = 0.0;
+  float2 r[N1];
+#pragma unroll
+  for (int m = 0; m < N1; ++m)
+    r[m] = conj_(residual_value(v[m], I_meas[(size_t)b * WW + (size_t)(j + kT * m) * W + c], thr2, acc));
+  line_dft<float2, W>(r, s_tw8, s_t328, reinterpret_cast<float2*>(xbuf[grp]), j);   // conj(F conj R) = F^-1 R
+#pragma unroll
+  for (int m = 0; m < N1; ++m) chi[(size_t)b * WW + (size_t)(j + kT * m) * W + c] = conj_(r[m]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tid & 31) == 0) red[tid >> 5] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) sum += red[w];
+    part[(size_t)b * gridDim.x + blockIdx.x] = window_ok(bt.pos[b], bt.Ny, bt.Nx, W) ? sum : 0.0;
+  }
+}
+
+// loss_part[b] = sum of the far-field kernel's nparts partials of position b, in order.
+__global__ void loss_parts_kernel(const double* __restrict__ part, int nb, int nparts, double* __restrict__ loss_part) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  double sum = 0.0;
+  for (int i = 0; i < nparts; ++i) sum += part[(size_t)b * nparts + i];
+  loss_part[b] = sum;
 }
 
 // Adjoint at slice l on chi = dL/dconj(E_l) (FP32): the window gradient of slice l
@@ -682,30 +724,6 @@ __global__ void flag_windows_kernel(const int2* __restrict__ pos, int S, int Ny,
 // ---------------------------------------------------------------------------
 
 template <typename C, int W>
-static void fft2(C* data, const C* wtab, int nb, bool inverse, cudaStream_t st) {
-  const dim3 grid(W / LinesCfg<C, W>::LPC, nb);
-  constexpr int NT = LinesCfg<C, W>::THREADS;
-  if (inverse) {
-    lines_fft_kernel<C, W, true, true><<<grid, NT, 0, st>>>(data, wtab);
-    lines_fft_kernel<C, W, false, true><<<grid, NT, 0, st>>>(data, wtab);
-  } else {
-    lines_fft_kernel<C, W, true, false><<<grid, NT, 0, st>>>(data, wtab);
-    lines_fft_kernel<C, W, false, false><<<grid, NT, 0, st>>>(data, wtab);
-  }
-}
-
-// A Fresnel propagation of the waves: rows F, columns (F, x h1 h1 or its conjugate, F^-1),
-// rows F^-1: three passes over the batch.
-template <typename C, int W>
-static void propagate2(C* data, const C* wtab, const C* h1, int nb, bool conj, cudaStream_t st) {
-  const dim3 grid(W / LinesCfg<C, W>::LPC, nb);
-  constexpr int NT = LinesCfg<C, W>::THREADS;
-  lines_fft_kernel<C, W, true, false><<<grid, NT, 0, st>>>(data, wtab);
-  if (conj) cols_propagate_kernel<C, C, W, true><<<grid, NT, 0, st>>>(data, wtab, h1);
-  else cols_propagate_kernel<C, C, W, false><<<grid, NT, 0, st>>>(data, wtab, h1);
-  lines_fft_kernel<C, W, true, true><<<grid, NT, 0, st>>>(data, wtab);
-}
-template <typename C, int W>
 static void rows_transmit(bool start, C* wave, const C* wtab, const Batch& bt, int l, const float2* probe, const C* T,
                           float2* stash, int keep, int cplx, cudaStream_t st) {
   const dim3 grid(W / LinesCfg<C, W>::LPC, bt.nb);
@@ -720,6 +738,25 @@ static void rows_transmit_w(bool start, C* wave, const C* wtab, const Batch& bt,
   else if (bt.W == 128) rows_transmit<C, 128>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
   else rows_transmit<C, 256>(start, wave, wtab, bt, l, probe, T, stash, keep, cplx, st);
 }
+// The fused far-field column pass; returns the loss partials per position (0 in the forward mode).
+template <typename C>
+static int cols_farfield_w(int W, const C* wave, const C* wtab, const float2* wtab8, const Batch& bt,
+                           const float* I_meas, const double* zthr2, float2* chi, double* part, float* I_out,
+                           cudaStream_t st) {
+#define MSP_FAR(WW_)                                                                                             \
+  if (W == WW_) {                                                                                                \
+    const dim3 grid(WW_ / LinesCfg<C, WW_>::LPC, bt.nb);                                                         \
+    cols_farfield_kernel<C, WW_><<<grid, LinesCfg<C, WW_>::THREADS, 0, st>>>(wave, wtab, wtab8, bt, I_meas, zthr2, \
+                                                                             chi, part, I_out);                  \
+    return WW_ / LinesCfg<C, WW_>::LPC;                                                                          \
+  }
+  MSP_FAR(64)
+  MSP_FAR(128)
+  MSP_FAR(256)
+#undef MSP_FAR
+  return 0;
+}
+
 // The column half of a propagation (the rows are fused with the transmit or the adjoint step);
 // CONJ: by G^H.
 template <typename C, bool CONJ = false>
@@ -734,21 +771,6 @@ static void cols_propagate_w(int W, C* data, const C* wtab, const C* h1, int nb,
   MSP_COLS(128)
   MSP_COLS(256)
 #undef MSP_COLS
-}
-// A column pass alone: the far-field transform (its rows were transformed by the last transmit),
-// or (INV) the column half of F^-1 of the residual.
-template <typename C, bool INV = false>
-static void cols_fft_w(int W, C* data, const C* wtab, int nb, cudaStream_t st) {
-#define MSP_COLF(WW_)                                                                                   \
-  if (W == WW_) {                                                                                       \
-    lines_fft_kernel<C, WW_, false, INV>                                                                \
-        <<<dim3(WW_ / LinesCfg<C, WW_>::LPC, nb), LinesCfg<C, WW_>::THREADS, 0, st>>>(data, wtab);      \
-    return;                                                                                             \
-  }
-  MSP_COLF(64)
-  MSP_COLF(128)
-  MSP_COLF(256)
-#undef MSP_COLF
 }
 
 static void rows_adjoint_w(bool next, float2* chi, const float2* wtab, const Batch& bt, int l, const float2* stash_l,
@@ -765,20 +787,6 @@ static void rows_adjoint_w(bool next, float2* chi, const float2* wtab, const Bat
   MSP_ROWA(128)
   MSP_ROWA(256)
 #undef MSP_ROWA
-}
-
-template <typename C>
-static void propagate2_w(int W, C* data, const C* wtab, const C* h1, int nb, bool conj, cudaStream_t st) {
-  if (W == 64) propagate2<C, 64>(data, wtab, h1, nb, conj, st);
-  else if (W == 128) propagate2<C, 128>(data, wtab, h1, nb, conj, st);
-  else propagate2<C, 256>(data, wtab, h1, nb, conj, st);
-}
-
-template <typename C>
-static void fft2_w(int W, C* data, const C* wtab, int nb, bool inverse, cudaStream_t st) {
-  if (W == 64) fft2<C, 64>(data, wtab, nb, inverse, st);
-  else if (W == 128) fft2<C, 128>(data, wtab, nb, inverse, st);
-  else fft2<C, 256>(data, wtab, nb, inverse, st);
 }
 
 static int elem_blocks(size_t n, int sms) {
@@ -813,6 +821,7 @@ struct Segs {
   void* mat_f = nullptr;      // split-BF16 DFT matrices, forward and inverse (split BF16)
   void* mat_i = nullptr;
   void* wtab16 = nullptr;     // [256] exp(-2 pi i k / 256), FP64 or double-float (the forward's type)
+  double* lpart = nullptr;    // [B][W / 4] loss partials of the fused far-field pass
   float2* wtab8 = nullptr;    // [256] the same rounded to FP32 (the adjoint)
   size_t bytes = 0;
 };
@@ -841,6 +850,7 @@ Segs carve(int precision, int W, int L, int Ny, int Nx, int S, char* base) {
   } else {
     g.wtab16 = take(256 * sizeof(double2));
     g.wtab8 = (float2*)take(256 * sizeof(float2));
+    g.lpart = (double*)take(B * (W / 4) * sizeof(double));
   }
   g.bytes = off;
   return g;
@@ -895,24 +905,15 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
   auto keep_first = [&](cudaError_t e) {
     if (err == cudaSuccess) err = e;
   };
+  // split-BF16 form: a 2-D transform is two tensor-core DFT passes (each transposes the waves)
   auto fwd2 = [&](int nb, bool inverse) {   // the forward model's waves
-    if (tc) {
-      keep_first(tcdft_pass(W, (float2*)g.wave, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
-      keep_first(tcdft_pass(W, g.tmp, (float2*)g.wave, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
-    } else if (df) {
-      fft2_w<dfc>(W, (dfc*)g.wave, (const dfc*)g.wtab16, nb, inverse, st);
-    } else {
-      fft2_w<double2>(W, (double2*)g.wave, (const double2*)g.wtab16, nb, inverse, st);
-    }
+    keep_first(tcdft_pass(W, (float2*)g.wave, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+    keep_first(tcdft_pass(W, g.tmp, (float2*)g.wave, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
     n_launch += 2;
   };
   auto adj2 = [&](int nb, bool inverse) {   // the adjoint's waves
-    if (tc) {
-      keep_first(tcdft_pass(W, g.chi, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
-      keep_first(tcdft_pass(W, g.tmp, g.chi, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
-    } else {
-      fft2_w<float2>(W, g.chi, g.wtab8, nb, inverse, st);
-    }
+    keep_first(tcdft_pass(W, g.chi, g.tmp, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
+    keep_first(tcdft_pass(W, g.tmp, g.chi, nb, inverse ? g.mat_i : g.mat_f, p.err, in.wait_limit, st));
     n_launch += 2;
   };
 
@@ -940,7 +941,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
       fwd2(nb, false);   // far field Psi = F(E_L)
     } else {
       // row passes fused with the transmits: [start: probe o X_1, rows F], then per slice
-      // [columns F, x H, F^-1] [rows F^-1, o X_l, rows F], then [columns F] = the far field
+      // [columns F, x H, F^-1] [rows F^-1, o X_l, rows F]; the far field's columns follow
       auto fused = [&](auto* wave, const auto* wtab, const auto* T, const auto* h1d) {
         for (int l = 0; l < L; ++l) {
           const int keep = !fwd && l >= lowest;
@@ -951,8 +952,6 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
           rows_transmit_w(l == 0, wave, wtab, bt, l, p.probe, T, g.stash, keep, p.cplx, st);
           ++n_launch;
         }
-        cols_fft_w(W, wave, wtab, nb, st);
-        ++n_launch;
       };
       if (df) fused((dfc*)g.wave, (const dfc*)g.wtab16, (const dfc*)g.T64, (const dfc*)g.h1d);
       else fused((double2*)g.wave, (const double2*)g.wtab16, (const double2*)g.T64, (const double2*)g.h1d);
@@ -960,10 +959,21 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     const float* Im = fwd ? nullptr : p.I_meas + (size_t)b0 * WW;
     double* lp = fwd ? nullptr : p.loss_part + b0;
     float* Io = fwd ? p.I_out + (size_t)b0 * WW : nullptr;
-    if (tc) residual_kernel<float2><<<nb, 256, 0, st>>>(bt, (const float2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
-    else if (df) residual_kernel<dfc><<<nb, 256, 0, st>>>(bt, (const dfc*)g.wave, Im, p.zthr2, g.chi, lp, Io);
-    else residual_kernel<double2><<<nb, 256, 0, st>>>(bt, (const double2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
-    ++n_launch;
+    if (tc) {
+      residual_kernel<float2><<<nb, 256, 0, st>>>(bt, (const float2*)g.wave, Im, p.zthr2, g.chi, lp, Io);
+      ++n_launch;
+    } else {
+      // [columns F of the far field, the residual, columns F^-1 of R]: chi_L's columns
+      const int np = df ? cols_farfield_w(W, (const dfc*)g.wave, (const dfc*)g.wtab16, g.wtab8, bt, Im, p.zthr2, g.chi,
+                                          g.lpart, Io, st)
+                        : cols_farfield_w(W, (const double2*)g.wave, (const double2*)g.wtab16, g.wtab8, bt, Im,
+                                          p.zthr2, g.chi, g.lpart, Io, st);
+      ++n_launch;
+      if (!fwd) {
+        loss_parts_kernel<<<(nb + 127) / 128, 128, 0, st>>>(g.lpart, nb, np, lp);
+        ++n_launch;
+      }
+    }
     if (fwd) continue;
     // adjoint: chi_L = F^H R, then down the slices
     if (tc) {
@@ -989,11 +999,9 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
         ++n_launch;
       }
     } else {
-      // the row passes fused with the adjoint steps: [columns F^-1 of R], then per slice
-      // [rows F^-1, adjoint step, rows F] [columns F, x conj H, F^-1], the last slice's row pass
-      // without the forward transform
-      cols_fft_w<float2, true>(W, g.chi, g.wtab8, nb, st);
-      ++n_launch;
+      // the row passes fused with the adjoint steps (the columns of F^-1 R came with the far
+      // field): per slice [rows F^-1, adjoint step, rows F] [columns F, x conj H, F^-1], the last
+      // slice's row pass without the forward transform
       for (int l = L - 1; l >= lowest; --l) {
         const bool grad_here = mode == MODE_LOSS_GRAD || (mode == MODE_LAYER && l == p.layer);
         const bool go_on = (l > lowest) || (l == 0 && want_dprobe);
