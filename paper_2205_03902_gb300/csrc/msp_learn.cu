@@ -17,6 +17,7 @@
 // Operands are staged through shared memory in the canonical no-swizzle layouts (core matrices
 // of 8 rows x 16 bytes, loaded with cp.async); one thread issues the MMAs and commits them to
 // mbarriers whose bounded waits record a timeout in the error word.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -67,7 +68,8 @@ __device__ __forceinline__ float gelu_grad(float x) {
 constexpr int kRows = 137;   // staged pixels per channel group (130 used); 137 x 16 B staggers the banks
 constexpr int kCSlots = 5;   // staged input rows of the weight-gradient kernel: three in use, two in flight
 constexpr int kFSlots = 5;   // staged input rows of the convolution: three in use, two in flight
-constexpr int kFLag = kFSlots - 3;
+constexpr int kTRows = 136;  // staged pixels per channel group of the convolution (130 used; 136 x 16 B
+                             // keeps every group 128-byte aligned for the tensor loads)
 constexpr int kGSlots = 3;   // staged gradient rows of the weight-gradient kernel: one in use, two in flight
 
 // packed weights of conv2_kernel: [9 taps][CIN / 8 channel groups][COUT rows][8 channels]
@@ -78,6 +80,21 @@ __host__ __device__ constexpr size_t packed_off(int t, int n, int k, int CIN, in
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
+// Tensor memory access (TMA): a tiled load of a box of the tensor described by `tmap` into
+// shared memory, completing on an mbarrier by transaction count.  Coordinates are elements,
+// innermost first; boxes reaching outside the tensor are filled with zeros.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tmap, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(tc::smem_u32(bar))
+      : "memory");
+}
+
 // Programmatic dependent launch: wait for the preceding kernel of the stream to complete (its
 // writes visible), and allow the next one to be scheduled.
 __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -85,16 +102,15 @@ __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddep
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // all but the most recent group of this thread's copies have landed
 __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-// all but the N most recent groups have landed
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int CIN, int COUT>
 struct Conv {
   static constexpr int G = CIN / 8;                                  // channel groups
-  static constexpr uint32_t SLOT = (uint32_t)G * kRows * 16;         // bytes of one staged row
+  static constexpr uint32_t GRP = kTRows * 16;                       // bytes of one group of a staged row
+  static constexpr uint32_t SLOT = (uint32_t)G * GRP;                // bytes of one staged row
   static constexpr uint32_t WB = 9u * COUT * CIN * 2;                // bytes of the weights
   static constexpr uint32_t TC = COUT < 32 ? 32 : COUT;              // TMEM columns per accumulator
   static constexpr size_t SMEM = 1024 + (size_t)WB + (size_t)kFSlots * SLOT + 2 * 8 * kFSlots + 4 * 8 + 16;
@@ -124,7 +140,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
                                                                const float* __restrict__ bias,
                                                                const float* __restrict__ aux, float* __restrict__ pre,
                                                                bf16* __restrict__ out, int nbias, int H, int Wd,
-                                                               int rows_per_cta, int* err, int wait_limit) {
+                                                               int rows_per_cta, int* err, int wait_limit,
+                                                               const __grid_constant__ CUtensorMap tmap) {
   using C = Conv<CIN, COUT>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -167,39 +184,31 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
   const uint32_t tmem = *tslot;
 
   if (warp == 8) {
-    // ---- producer: staged rows 0 .. n + 1 (input rows y0 - 1 .. y0 + n) ----
+    // ---- producer, one thread: staged rows 0 .. n + 1 (input rows y0 - 1 .. y0 + n) by tensor
+    // loads, one box of 8 channels x 130 pixels per channel group, completing on full[slot] ----
     // The prologue above (barriers, tensor memory, weights packed by an earlier kernel) may
     // overlap the preceding kernel; the input it wrote is read only after it has completed.
-    grid_dependency_wait();
-    if (lane == 0) grid_dependents_launch();
-    int i = 0;
-    for (; i < n + 2; ++i) {
-      const int slot = i % kFSlots;
-      if (i >= kFSlots && !tc::wait_phase(&empty[slot], (uint32_t)((i / kFSlots - 1) & 1), wait_limit)) *flag = 2;
-      __syncwarp();
-      if (*flag) break;
-      const int yy = y0 - 1 + i;
-      const uint32_t base = tc::smem_u32(srow + slot * C::SLOT);
-      for (int q = lane; q < 130 * C::G; q += 32) {
-        const int r = q / C::G, j = q % C::G;
-        const int xx = x0 - 1 + r;
-        const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-        const bf16* src = ok ? in + ((size_t)yy * Wd + xx) * CIN + 8 * j : in;
-        cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
+    if (lane == 0) {
+      grid_dependency_wait();
+      grid_dependents_launch();
+      int i = 0;
+      for (; i < n + 2 && !*flag; ++i) {
+        const int slot = i % kFSlots;
+        if (i >= kFSlots && !tc::wait_phase(&empty[slot], (uint32_t)((i / kFSlots - 1) & 1), wait_limit)) {
+          *flag = 2;
+          break;
+        }
+        mbar_expect_tx(&full[slot], (uint32_t)(C::G * 130 * 16));   // G boxes of 130 pixels x 16 B
+        const uint32_t dst = tc::smem_u32(srow + slot * C::SLOT);
+#pragma unroll 1
+        for (int j = 0; j < C::G; ++j) tma_load_3d(dst + (uint32_t)j * C::GRP, &tmap, 8 * j, x0 - 1, y0 - 1 + i, &full[slot]);
       }
-      cp_async_commit();
-      if (i >= kFLag) {   // row i - kFLag has landed: hand it to the MMA thread
-        cp_async_wait_group<kFLag>();
-        tc::fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&full[(i - kFLag) % kFSlots]);
-      }
+      // after an abort, the loads in flight land before the shared memory is released: the latest
+      // load of each slot is the last completion of its barrier
+      if (*flag)
+        for (int r = max(0, i - kFSlots); r < i; ++r)
+          if (!tc::wait_phase(&full[r % kFSlots], (uint32_t)((r / kFSlots) & 1), kDrainLimit)) *flag = 3;
     }
-    cp_async_wait_all();
-    tc::fence_proxy_async();
-    __syncwarp();
-    if (lane == 0 && !*flag)
-      for (int r = max(0, i - kFLag); r < i; ++r) tc::mbar_arrive(&full[r % kFSlots]);
   } else if (warp == 9) {
     // ---- MMA issuer ----
     if (lane == 0) {
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
           const uint32_t b = b0 + (uint32_t)t * (COUT * CIN * 2);
 #pragma unroll
           for (int s = 0; s < CIN / 16; ++s)
-            tc::mma_bf16(dcol, tc::smem_desc(a + (uint32_t)(2 * s) * (kRows * 16), kRows * 16, 128),
+            tc::mma_bf16(dcol, tc::smem_desc(a + (uint32_t)(2 * s) * C::GRP, C::GRP, 128),
                          tc::smem_desc(b + (uint32_t)(2 * s) * (COUT * 16), COUT * 16, 128), idesc,
                          (t > 0 || s > 0) ? 1u : 0u);
         }
@@ -724,6 +733,32 @@ Ws carve(const Net& n, int H, int Wd, char* base) {
 
 msp_status fail(msp_status s, const std::string& m) { return set_last_error(s, m); }
 
+// Tensor map of an NHWC bf16 image [H][Wd][C] for the convolution's row loads: boxes of
+// 8 channels x 130 pixels x 1 row, zero fill outside.  The encoder comes from the driver
+// through the runtime's entry-point query.
+cudaError_t encode_rows_map(CUtensorMap* map, const bf16* img, int C, int Wd, int H) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)Wd, (cuuint64_t)H};
+  const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)Wd * C * 2};
+  const cuuint32_t box[3] = {8, 130, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(img), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CIN, int COUT, int EPI>
 cudaError_t launch_conv(const bf16* in, const bf16* Bp, const float* bias, const float* aux, float* pre, bf16* out,
                         int nbias, int H, int Wd, int* err, cudaStream_t st) {
@@ -747,6 +782,9 @@ cudaError_t launch_conv(const bf16* in, const bf16* Bp, const float* bias, const
   const int want = std::max(1, sms * resident[dev] / strips);   // CTAs along the rows
   const int rows = (H + std::min(want, H) - 1) / std::min(want, H);
   const int ny = (H + rows - 1) / rows;
+  alignas(64) CUtensorMap tmap;
+  const cudaError_t me = encode_rows_map(&tmap, in, CIN, Wd, H);
+  if (me != cudaSuccess) return me;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -758,7 +796,7 @@ cudaError_t launch_conv(const bf16* in, const bf16* Bp, const float* bias, const
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, conv_kernel<CIN, COUT, EPI>, in, Bp, bias, aux, pre, out, nbias, H, Wd,
-                                           rows, err, tc_wait_limit());
+                                           rows, err, tc_wait_limit(), tmap);
   count_launches(1);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
