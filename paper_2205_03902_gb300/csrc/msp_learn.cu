@@ -15,8 +15,9 @@
 //     is one more row of it (a constant group of ones); the per-CTA partial sums are added in a
 //     fixed order.
 // Operands are staged through shared memory in the canonical no-swizzle layouts (core matrices
-// of 8 rows x 16 bytes, loaded with cp.async); one thread issues the MMAs and commits them to
-// mbarriers whose bounded waits record a timeout in the error word.
+// of 8 rows x 16 bytes), fetched by tensor loads (TMA) that complete on mbarriers; one thread
+// issues the MMAs and commits them to mbarriers; every wait is bounded and records a timeout in
+// the error word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -62,15 +63,17 @@ __device__ __forceinline__ float gelu_grad(float x) {
 // image) and keeps all nine taps of the weights resident; the nine taps of an output row then
 // read the staged rows through matrix descriptors whose start is offset by the tap (dx pixels
 // = dx x 16 bytes: pixels are consecutive 16-byte rows of the K-major core matrices, the 8-channel
-// groups are kRows x 16 bytes apart).  The accumulator is double-buffered in tensor memory: the
-// MMAs of row k run while all eight warps drain the other buffer (the epilogue of row k - 1)
-// and rows k + 3 and k + 4 are fetched with cp.async.
-constexpr int kRows = 137;   // staged pixels per channel group (130 used); 137 x 16 B staggers the banks
-constexpr int kCSlots = 5;   // staged input rows of the weight-gradient kernel: three in use, two in flight
+// groups are kTRows x 16 bytes apart).  Warp roles: one thread of warp 8 fetches rows with tensor
+// loads, one thread of warp 9 issues the MMAs, warps 0-7 run the epilogue.  The accumulator is
+// double-buffered in tensor memory: the MMAs of row k run while the epilogue warps drain the
+// other buffer (row k - 1) and the next rows are in flight.
+constexpr int kTRows = 136;  // staged pixels per channel group (130 used); 136 x 16 B keeps every
+                             // group 128-byte aligned for the tensor loads
+constexpr uint32_t kBox = 130 * 16;   // bytes of one tensor-load box: 8 channels x 130 pixels
 constexpr int kFSlots = 5;   // staged input rows of the convolution: three in use, two in flight
-constexpr int kTRows = 136;  // staged pixels per channel group of the convolution (130 used; 136 x 16 B
-                             // keeps every group 128-byte aligned for the tensor loads)
-constexpr int kGSlots = 3;   // staged gradient rows of the weight-gradient kernel: one in use, two in flight
+constexpr int kCSlots = 5;   // staged input rows of the weight-gradient kernel
+constexpr int kGSlots = 3;   // staged gradient rows of the weight-gradient kernel
+constexpr int kWSteps = 3;   // row steps of the weight-gradient kernel in flight (one barrier pair each)
 
 // packed weights of conv2_kernel: [9 taps][CIN / 8 channel groups][COUT rows][8 channels]
 __host__ __device__ constexpr size_t packed_off(int t, int n, int k, int CIN, int COUT) {
@@ -102,9 +105,6 @@ __device__ __forceinline__ void grid_dependents_launch() { asm volatile("griddep
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// all but the most recent group of this thread's copies have landed
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <int CIN, int COUT>
 struct Conv {
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
           *flag = 2;
           break;
         }
-        mbar_expect_tx(&full[slot], (uint32_t)(C::G * 130 * 16));   // G boxes of 130 pixels x 16 B
+        mbar_expect_tx(&full[slot], (uint32_t)C::G * kBox);   // G boxes of 130 pixels x 16 B
         const uint32_t dst = tc::smem_u32(srow + slot * C::SLOT);
 #pragma unroll 1
         for (int j = 0; j < C::G; ++j) tma_load_3d(dst + (uint32_t)j * C::GRP, &tmap, 8 * j, x0 - 1, y0 - 1 + i, &full[slot]);
@@ -323,12 +323,19 @@ constexpr size_t conv_smem() {
 // D_t[ci][co] = sum_p in[p + off(t)][ci] g[p][co] over the pixels of a CTA's strip and rows, on
 // the tensor core with M = 128 rows of c_in (the first CIN real) and N = COUT, K = 16 pixels per
 // MMA.  Both operands come from staged NHWC rows exactly as in the convolution: for one pixel the
-// channels are 16 contiguous bytes, so they are MN-major operands (channel groups kRows x 16 bytes
-// apart, 8-pixel groups 128 bytes apart) and a tap's pixel shift is again a start offset.  Row
-// CIN of the input operand reads a constant group of ones, which turns the centre tap's row CIN
-// into the bias gradient sum_p g[p][co].  Each CTA accumulates all its rows in tensor memory
+// channels are 16 contiguous bytes, so they are MN-major operands (channel groups kTRows x 16
+// bytes apart, 8-pixel groups 128 bytes apart) and a tap's pixel shift is again a start offset.
+// Row CIN of the input operand reads a constant group of ones, which turns the centre tap's row
+// CIN into the bias gradient sum_p g[p][co].  Each CTA accumulates all its rows in tensor memory
 // (five or four taps x COUT columns: the taps are split over two CTA groups) and writes one
 // partial sum; the partials are then added in a fixed order.
+//
+// Roles: one thread of warp 4 fetches rows by tensor loads, one thread of warp 5 issues the MMAs,
+// warps 0-3 read the accumulator at the end.  Row step k (output row y0 + k) needs input rows
+// k .. k + 2 and gradient row k; its loads (rows 0 .. 2 at k = 0, row k + 2 after) complete on
+// full[k % kWSteps], its MMAs commit to done[k % kWSteps].  The slots step k fills held input and
+// gradient rows k - 3, which step k - 3 was the last to read, so the fetch of step k waits for
+// done of step k - 3 and three steps are in flight.
 constexpr int kMaxSpatial = 512;   // spatial CTAs of one weight-gradient launch at most
 // MN-major operands without swizzle: the descriptor's LBO is the stride between 8-row K groups and
 // its SBO the stride between 8-element MN groups (the reverse of the K-major roles).
@@ -337,30 +344,33 @@ constexpr uint32_t kMnStrideLbo = 0;
 template <int CIN, int COUT>
 struct WGrad {
   static constexpr int G = CIN / 8, GO = COUT / 8;
-  static constexpr uint32_t GRP = kRows * 16;              // bytes of one channel group of a staged row
+  static constexpr uint32_t GRP = kTRows * 16;             // bytes of one channel group of a staged row
   static constexpr uint32_t ISLOT = (G + 1) * GRP;         // an input row and a group of ones
   static constexpr uint32_t GSLOT = GO * GRP;              // a gradient row
   static constexpr uint32_t PAD = (16 - G - 1) * GRP;      // the M = 128 operand spans 16 groups
   static constexpr int TAPS = 5;                           // taps [0, 5) or [5, 9) per CTA
   static constexpr uint32_t TC = TAPS * COUT <= 128 ? 128 : (TAPS * COUT <= 256 ? 256 : 512);
   static constexpr size_t SMEM = 1024 + (size_t)kCSlots * ISLOT + PAD + kGSlots * (size_t)GSLOT + 64;
+  static_assert(kCSlots == kWSteps + 2 && kGSlots == kWSteps, "slot reuse follows the step pipeline");
 };
 
-// g [H][Wd][COUT], in [H][Wd][CIN] (bf16 NHWC).  CTA (strip blockIdx.x, rows blockIdx.y,
-// taps blockIdx.z) writes part[sp][t][co][ci] for its taps (sp = blockIdx.y * gridDim.x +
-// blockIdx.x) and, for the centre tap's group, bpart[sp][co].
+// imap: tensor map of in [H][Wd][CIN], gmap: of g [H][Wd][COUT] (bf16 NHWC, boxes of 8 channels
+// x 130 pixels x 1 row).  CTA (strip blockIdx.x, rows blockIdx.y, taps blockIdx.z) writes
+// part[sp][t][co][ci] for its taps (sp = blockIdx.y * gridDim.x + blockIdx.x) and, for the
+// centre tap's group, bpart[sp][co].
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restrict__ g, const bf16* __restrict__ in,
-                                                            float* __restrict__ part, float* __restrict__ bpart,
-                                                            int H, int Wd, int rows_per_cta, int* err,
-                                                            int wait_limit) {
+__global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(float* __restrict__ part, float* __restrict__ bpart,
+                                                            int H, int rows_per_cta, int* err, int wait_limit,
+                                                            const __grid_constant__ CUtensorMap gmap,
+                                                            const __grid_constant__ CUtensorMap imap) {
   using C = WGrad<CIN, COUT>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sin = smem;
   uint8_t* sg = sin + kCSlots * C::ISLOT + C::PAD;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sg + kGSlots * C::GSLOT);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sg + kGSlots * C::GSLOT);
+  uint64_t* done = full + kWSteps;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + kWSteps);
   volatile int* flag = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int x0 = blockIdx.x * kPix, y0 = blockIdx.y * rows_per_cta;
@@ -369,94 +379,94 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
   const int n = min(rows_per_cta, H - y0);
   if (n <= 0) return;
 
-  auto stage = [&](const bf16* src_img, int C_, uint8_t* dst_base, int yy) {   // 130 pixels, halo, zeros outside
-    const int GG = C_ / 8;
-    const uint32_t base = tc::smem_u32(dst_base);
-    for (int q = tid; q < 130 * GG; q += kThreads) {
-      const int r = q / GG, j = q % GG;
-      const int xx = x0 - 1 + r;
-      const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-      const bf16* src = ok ? src_img + ((size_t)yy * Wd + xx) * C_ + 8 * j : src_img;
-      cp_async16(base + (uint32_t)(j * kRows + r) * 16u, src, ok);
-    }
-  };
-  auto stage_in = [&](int i) { stage(in, CIN, sin + (i % kCSlots) * C::ISLOT, y0 - 1 + i); };
-  auto stage_g = [&](int k) { stage(g, COUT, sg + (k % kGSlots) * C::GSLOT, y0 + k); };
-
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int i = 0; i < kWSteps; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&done[i], 1);
+    }
     tc::fence_mbar_init();
     *flag = 0;
   }
   {   // the group of ones after every input slot; the padding after the last slot is zero
     const uint4 ones = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);   // bf16 1.0 x 8
-    for (int i = tid; i < kCSlots * kRows; i += kThreads)
-      *reinterpret_cast<uint4*>(sin + (i / kRows) * C::ISLOT + C::G * C::GRP + (i % kRows) * 16) = ones;
+    for (int i = tid; i < kCSlots * kTRows; i += kThreads)
+      *reinterpret_cast<uint4*>(sin + (i / kTRows) * C::ISLOT + C::G * C::GRP + (i % kTRows) * 16) = ones;
     for (int i = tid; i < (int)(C::PAD / 16); i += kThreads)
       reinterpret_cast<uint4*>(sin + kCSlots * C::ISLOT)[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (warp == 0) tc::tmem_alloc(tslot, C::TC);
-  grid_dependency_wait();   // the gradient rows come from the preceding kernel
-  if (tid == 0) grid_dependents_launch();
-  for (int i = 0; i < 3; ++i) stage_in(i);
-  stage_g(0);
-  cp_async_commit();
-  cp_async_wait_all();
-  if (3 < n + 2) stage_in(3);   // the next rows in flight: one group per row step
-  if (1 < n) stage_g(1);
-  cp_async_commit();
   tc::fence_proxy_async();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *tslot;
-  constexpr uint32_t idesc = tc::idesc_bf16(kPix, COUT) | (1u << 15) | (1u << 16);   // A and B MN-major
-  constexpr uint32_t LBO = kMnStrideLbo ? C::GRP : 128u, SBO = kMnStrideLbo ? 128u : C::GRP;
-  const uint32_t a0 = tc::smem_u32(sin), b0 = tc::smem_u32(sg);
-  int issued = -1, confirmed = -1;
 
+  if (warp == 4) {
+    if (lane == 0) {   // ---- producer ----
+      grid_dependency_wait();   // the gradient rows come from the preceding kernel
+      grid_dependents_launch();
+      int k = 0;
+      for (; k < n && !*flag; ++k) {
+        const int b = k % kWSteps;
+        if (k >= kWSteps && !tc::wait_phase(&done[b], (uint32_t)((k / kWSteps - 1) & 1), wait_limit)) {
+          *flag = 2;
+          break;
+        }
+        const int i0 = k == 0 ? 0 : k + 2;
+        mbar_expect_tx(&full[b], (uint32_t)((k + 3 - i0) * C::G + C::GO) * kBox);
 #pragma unroll 1
-  for (int k = 0; k < n; ++k) {
-    if (tid == 0) {   // input rows k .. k + 2 and gradient row k are staged (the next ones in flight)
-      tc::fence_after();
-      const uint32_t b = b0 + (uint32_t)(k % kGSlots) * C::GSLOT + 16u;   // gradient pixel r at staged index r + 1
+        for (int i = i0; i <= k + 2; ++i) {   // staged input row i = image row y0 - 1 + i
+          const uint32_t dst = tc::smem_u32(sin + (i % kCSlots) * C::ISLOT);
 #pragma unroll 1
-      for (int tl = 0; tl < nt; ++tl) {
-        const int t = t0 + tl, dy = t / 3, dx = t % 3;
-        const uint32_t a = a0 + (uint32_t)((k + dy) % kCSlots) * C::ISLOT + (uint32_t)dx * 16u;
+          for (int j = 0; j < C::G; ++j) tma_load_3d(dst + (uint32_t)j * C::GRP, &imap, 8 * j, x0 - 1, y0 - 1 + i, &full[b]);
+        }
+        const uint32_t dst = tc::smem_u32(sg + (k % kGSlots) * C::GSLOT);
+#pragma unroll 1
+        for (int j = 0; j < C::GO; ++j) tma_load_3d(dst + (uint32_t)j * C::GRP, &gmap, 8 * j, x0 - 1, y0 + k, &full[b]);
+      }
+      // after an abort, the loads in flight land before the shared memory is released
+      if (*flag)
+        for (int r = max(0, k - kWSteps); r < k; ++r)
+          if (!tc::wait_phase(&full[r % kWSteps], (uint32_t)((r / kWSteps) & 1), kDrainLimit)) *flag = 3;
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {   // ---- MMA issuer ----
+      constexpr uint32_t idesc = tc::idesc_bf16(kPix, COUT) | (1u << 15) | (1u << 16);   // A and B MN-major
+      constexpr uint32_t LBO = kMnStrideLbo ? C::GRP : 128u, SBO = kMnStrideLbo ? 128u : C::GRP;
+      const uint32_t a0 = tc::smem_u32(sin), b0 = tc::smem_u32(sg);
+      int issued = -1;
+#pragma unroll 1
+      for (int k = 0; k < n && !*flag; ++k) {
+        if (!tc::wait_phase(&full[k % kWSteps], (uint32_t)((k / kWSteps) & 1), wait_limit)) {
+          *flag = 2;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t b = b0 + (uint32_t)(k % kGSlots) * C::GSLOT + 16u;   // gradient pixel r at staged index r + 1
+#pragma unroll 1
+        for (int tl = 0; tl < nt; ++tl) {
+          const int t = t0 + tl, dy = t / 3, dx = t % 3;
+          const uint32_t a = a0 + (uint32_t)((k + dy) % kCSlots) * C::ISLOT + (uint32_t)dx * 16u;
 #pragma unroll
-        for (int s = 0; s < kPix / 16; ++s)
-          tc::mma_bf16(tmem + (uint32_t)(tl * COUT), tc::smem_desc(a + (uint32_t)s * 256u, LBO, SBO),
-                       tc::smem_desc(b + (uint32_t)s * 256u, LBO, SBO), idesc, (k > 0 || s > 0) ? 1u : 0u);
+          for (int s = 0; s < kPix / 16; ++s)
+            tc::mma_bf16(tmem + (uint32_t)(tl * COUT), tc::smem_desc(a + (uint32_t)s * 256u, LBO, SBO),
+                         tc::smem_desc(b + (uint32_t)s * 256u, LBO, SBO), idesc, (k > 0 || s > 0) ? 1u : 0u);
+        }
+        tc::commit(&done[k % kWSteps]);
+        issued = k;
       }
-      tc::commit(&bar[k & 1]);
-      issued = k;
-    }
-    if (k >= 1) {   // the MMAs of row k - 1 are done: its input slot and gradient slot are free
-      if (tid == 0) {
-        if (tc::wait_phase(&bar[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), wait_limit)) confirmed = k - 1;
-        else *flag = 2;
+      // the last commit covers every MMA issued; it is the latest completion of its barrier
+      if (issued >= 0) {
+        const bool aborted = *flag != 0;
+        if (!tc::wait_phase(&done[issued % kWSteps], (uint32_t)((issued / kWSteps) & 1),
+                            aborted ? kDrainLimit : wait_limit))
+          *flag = aborted ? 3 : 2;
       }
-      __syncthreads();
-      if (*flag) break;
     }
-    if (k + 4 < n + 2) stage_in(k + 4);   // into the slots of row k - 1
-    if (k + 2 < n) stage_g(k + 2);
-    cp_async_commit();
-    cp_async_wait_prior();                 // input row k + 3 and gradient row k + 1 have landed
-    tc::fence_proxy_async();
-    tc::fence_before();
-    __syncthreads();
   }
-  if (!*flag) {
-    if (tid == 0) {
-      if (tc::wait_phase(&bar[(n - 1) & 1], (uint32_t)(((n - 1) >> 1) & 1), wait_limit)) confirmed = n - 1;
-      else *flag = 2;
-    }
-    __syncthreads();
-    tc::fence_after();
-  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
   if (!*flag && warp < 4) {   // lane = row of D: c_in (< CIN) or the bias row (CIN)
     const int row = 32 * warp + lane;
     const bool active = __any_sync(0xffffffffu, row <= CIN);
@@ -480,11 +490,6 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(const bf16* __restri
         }
       }
     }
-  }
-  cp_async_wait_all();
-  if (tid == 0 && *flag) {
-    for (int k = confirmed + 1; k <= issued; ++k)
-      if (!tc::wait_phase(&bar[k & 1], (uint32_t)((k >> 1) & 1), kDrainLimit)) *flag = 3;
   }
   tc::fence_before();
   __syncthreads();
@@ -844,6 +849,10 @@ cudaError_t launch_wgrad(const bf16* g, const bf16* in, float* part, float* bpar
   want = std::min(want, H);
   const int rows = (H + want - 1) / want;
   const int ny = (H + rows - 1) / rows;
+  alignas(64) CUtensorMap gmap, imap;
+  cudaError_t me = encode_rows_map(&gmap, g, COUT, Wd, H);
+  if (me == cudaSuccess) me = encode_rows_map(&imap, in, CIN, Wd, H);
+  if (me != cudaSuccess) return me;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -854,8 +863,8 @@ cudaError_t launch_wgrad(const bf16* g, const bf16* in, float* part, float* bpar
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, wgrad_kernel<CIN, COUT>, g, in, part, bpart, H, Wd, rows, err,
-                                     tc_wait_limit());
+  cudaError_t e = cudaLaunchKernelEx(&cfg, wgrad_kernel<CIN, COUT>, part, bpart, H, rows, err, tc_wait_limit(),
+                                     gmap, imap);
   if (e != cudaSuccess) return e;
   const int nred = 9 * COUT * CIN + cout_true;
   wgrad_reduce_kernel<<<(nred + 255) / 256, 256, 0, st>>>(part, bpart, strips * ny, COUT, CIN, cout_true, cin_true,
@@ -878,7 +887,6 @@ cudaError_t wgrad(int cin, int cout, const bf16* g, const bf16* in, float* part,
 
 int grid1d(size_t n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096); }
 
-// Packs every layer's forward (and, for training, data-gradient) operand from the FP32 weights.
 // Packs every layer's forward (and, for training, data-gradient) operand from the FP32 weights,
 // in one launch: blockIdx.y is the layer, blockIdx.z the operand.
 struct PackJob {
