@@ -814,6 +814,8 @@ def run_msp(args, rank, world, local_rank):
     def step():
         msp.loss_grad(g, probe, V, d_pos, I_meas, ws=ws, loss=loss, dV=dV, dprobe=dprobe)
 
+    msp.set_overlap_add(msp.OVERLAP_L2_REDUCE if args.overlap_add == "l2" else msp.OVERLAP_FIXED_ORDER)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -906,6 +908,20 @@ def run_msp(args, rank, world, local_rank):
     # ---- further measurements of this run (rank 0), clocks still sampled ----
     extra = {}
     if not args.quick:
+        # the other overlap-add of the same step: reductions in L2 from the fused kernel (or the gather)
+        other = msp.OVERLAP_FIXED_ORDER if args.overlap_add == "l2" else msp.OVERLAP_L2_REDUCE
+        msp.set_overlap_add(other)
+        step()
+        msp.profile_read(reset=True)
+        msp.profile_enable(True)
+        oms = time_events(step, 20, stream, flush)
+        po = msp.profile_read(reset=True)
+        msp.profile_enable(False)
+        msp.set_overlap_add(msp.OVERLAP_L2_REDUCE if args.overlap_add == "l2" else msp.OVERLAP_FIXED_ORDER)
+        extra["other_overlap_add"] = {
+            "overlap_add": "l2_reduce" if other == msp.OVERLAP_L2_REDUCE else "fixed_order",
+            "call": "msp_loss_grad, the same step", "ms": oms, "value": S * L / (oms * 1e-3), "unit": UNIT,
+            "fused_kernel_ms": po["fused_ms"] / 20, "launches_per_call": po["all_launches"] / 20}
         # the layer step of Algorithm 1 on the same state
         Vl = torch.zeros_like(V)
         lb, mu = torch.empty(1, dtype=torch.float64, device=dev), torch.empty(1, dtype=torch.float64, device=dev)
@@ -1003,7 +1019,9 @@ def run_msp(args, rank, world, local_rank):
     achieved = fft_flops(S, L, W) / (fused_ms * 1e-3) / 1e12
     kname = "position_kernel<128, LOSS_GRAD>" if W == 128 else ("position_cluster_kernel<LOSS_GRAD>" if W == 256
                                                                  else f"position_kernel<{W}, LOSS_GRAD>")
-    traffic = measured_traffic("position_kernel_loss_grad") if cfg is synth.C2 else None
+    traffic = None
+    if cfg is synth.C2:
+        traffic = measured_traffic("position_kernel_loss_grad" + ("_l2_reduce" if args.overlap_add == "l2" else ""))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -1012,6 +1030,7 @@ def run_msp(args, rank, world, local_rank):
                    "positions": S, "slices": L, "window": W, "object": [cfg.obj, cfg.obj],
                    "state": "V = 0, probe guess (20 A defocus error), Poisson-noisy patterns",
                    "l2": "flushed between timed steps (256 MiB write outside the step events)",
+                   "overlap_add": "l2_reduce" if args.overlap_add == "l2" else "fixed_order",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
@@ -1066,6 +1085,10 @@ def main():
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="the timed loss/gradient steps and e2e only")
+    ap.add_argument("--overlap-add", default="fixed", choices=["fixed", "l2"],
+                    help="how msp_loss_grad sums the window gradients of the timed steps: fixed (a gather "
+                         "in scan order, bit-reproducible; the default) or l2 (reductions in L2 from the "
+                         "fused kernel)")
     ap.add_argument("--train-steps", type=int, default=1500, help="Adam steps of the learned proposal (learned_c5)")
     ap.add_argument("--config", default="c2",
                     choices=sorted(synth.CONFIGS) + sorted(synth.SMD_CONFIGS) + ["dft_c3", "peaks", "learned_c5"],

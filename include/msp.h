@@ -253,6 +253,20 @@ msp_status msp_check_workspace(void* ws, void* stream);
  * freeing their tensor memory, leaving the device usable. */
 msp_status msp_set_wait_limit(int32_t polls);
 
+/* How msp_loss_grad forms dV, the sum over scan positions of the window gradients (the sum
+ * over s in the gradient of Eq. Opt_Prob_Layerwise), for every later call of this process:
+ *   MSP_OVERLAP_FIXED_ORDER (default): the fused kernel writes each position's window
+ *     gradients to the workspace and a gather adds them per object pixel in ascending scan
+ *     order: dV is bit-reproducible.
+ *   MSP_OVERLAP_L2_REDUCE: the fused kernel adds each window gradient into dV as it is
+ *     produced, with FP32 reductions performed in L2 (dV is zeroed first); no per-position
+ *     buffer is written and no gather runs.  The order of the additions depends on the
+ *     schedule, so dV agrees between runs only to rounding.  Applies to the FP32 mode
+ *     (MSP_PRECISION_FP32); the other modes keep the fixed order.
+ * Returns MSP_EINVAL for any other value. */
+enum { MSP_OVERLAP_FIXED_ORDER = 0, MSP_OVERLAP_L2_REDUCE = 1 };
+msp_status msp_set_overlap_add(int32_t mode);
+
 /* Profiling hooks, off by default.  While enabled, every launch of the dominant
  * kernel of a call is bracketed by CUDA events recorded on its stream: the fused
  * per-position kernel (the forward / adjoint of all positions) of the calls above,

@@ -455,6 +455,8 @@ void count_launches(int n) { counted(n); }
 
 // Poll bound of the tensor-core kernels' mbarrier waits (msp_set_wait_limit).
 static std::atomic<int> g_wait_limit{1 << 20};
+// Overlap-add of msp_loss_grad's window gradients (msp_set_overlap_add).
+static std::atomic<int> g_overlap{MSP_OVERLAP_FIXED_ORDER};
 int tc_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
 
 // Devices on which a tensor-core kernel reported that its drain wait ran out (workspace
@@ -771,13 +773,21 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   PosParams p = base_params(g, probe, V, pos, c);
   p.I_meas = I_meas;
   p.want_dprobe = dprobe != nullptr;
+  const size_t dV_bytes = (size_t)g->n_slices * plane * sizeof(float) * (p.cplx ? 2 : 1);
   if (g->n_pos == 0) {
-    if (dV) MSP_CK(cudaMemsetAsync(dV, 0, (size_t)g->n_slices * plane * sizeof(float) * (p.cplx ? 2 : 1), c.st));
+    if (dV) MSP_CK(cudaMemsetAsync(dV, 0, dV_bytes, c.st));
     if (dprobe) MSP_CK(cudaMemsetAsync(dprobe, 0, WW * sizeof(float2), c.st));
     return reduce_loss(g, c, loss);
   }
+  // in the FP32 mode the fused kernels can add the window gradients into dV themselves
+  const bool l2_reduce = dV && !precise(g) && g_overlap.load(std::memory_order_relaxed) == MSP_OVERLAP_L2_REDUCE;
+  if (l2_reduce) {
+    if (misaligned(dV, p.cplx ? 8 : 4)) return fail(MSP_EINVAL, "dV must be aligned to its element");
+    MSP_CK(cudaMemsetAsync(dV, 0, dV_bytes, c.st));
+    p.dVred = dV;
+  }
   MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
-  if (dV) {
+  if (dV && !l2_reduce) {
     dim3 grid((g->obj_nx + kGatherTX - 1) / kGatherTX, (g->obj_ny + kGatherTY - 1) / kGatherTY, g->n_slices);
     if (p.cplx)
       gather_kernel<true, false><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos,
@@ -957,6 +967,14 @@ msp_status msp_reconstruct(const msp_geometry* g, const msp_plan* plan, float* p
 msp_status msp_set_wait_limit(int32_t polls) {
   g_err.clear();
   g_wait_limit.store(polls >= 1 ? polls : polls == 0 ? (1 << 20) : 0, std::memory_order_relaxed);
+  return MSP_OK;
+}
+
+msp_status msp_set_overlap_add(int32_t mode) {
+  g_err.clear();
+  if (mode != MSP_OVERLAP_FIXED_ORDER && mode != MSP_OVERLAP_L2_REDUCE)
+    return fail(MSP_EINVAL, "overlap-add mode must be MSP_OVERLAP_FIXED_ORDER or MSP_OVERLAP_L2_REDUCE");
+  g_overlap.store(mode, std::memory_order_relaxed);
   return MSP_OK;
 }
 

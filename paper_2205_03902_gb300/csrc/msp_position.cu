@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
       } else {
         if (tid == 0) p.loss_part[s] = 0.0;
         constexpr int CW = CPLX ? 2 : 1;
-        if (MODE == MODE_LOSS_GRAD)
+        if (MODE == MODE_LOSS_GRAD && !p.dVred)
           for (size_t i = tid; i < CW * WW * L; i += G::NT) p.wgrad[CW * s * WW * L + i] = 0.f;
         if (MODE == MODE_LAYER) {
           for (size_t i = tid; i < CW * WW; i += G::NT) p.wgrad[CW * s * WW + i] = 0.f;
@@ -392,7 +392,17 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
         LINE_FFT<W, true>(v, tw, xb, j);   // v = chi_l (row r)
         if (grad_here) {
-          if (CPLX) {
+          if (MODE == MODE_LOSS_GRAD && p.dVred) {
+            // added into the object-frame gradient at once (reductions in L2)
+            const size_t o = (size_t)l * plane + win0 + (size_t)r * p.Nx + j;
+            if (CPLX) {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) atomicAdd(reinterpret_cast<float2*>(p.dVred) + o + 8 * m, cmulc(v[m], e[m]));
+            } else {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) atomicAdd(p.dVred + o + 8 * m, p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x));
+            }
+          } else if (CPLX) {
             // dL/dconj(o_l) on the window: conj(psi_in,l) o chi_l
             float2* wg2 = reinterpret_cast<float2*>(wg) + r * W + j;
 #pragma unroll

@@ -115,7 +115,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
       } else {
         if (tid == 0) p.loss_part[(size_t)s * CL + rank] = 0.0;
         constexpr int CW = CPLX ? 2 : 1;
-        if (MODE == MODE_LOSS_GRAD)
+        if (MODE == MODE_LOSS_GRAD && !p.dVred)
           for (int l = 0; l < L; ++l)
             for (size_t i = CW * r0 + tid; i < CW * r1; i += NT) p.wgrad[CW * ((size_t)s * L + l) * WW + i] = 0.f;
         if (MODE == MODE_LAYER) {
@@ -275,7 +275,17 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         for (int m = 0; m < N1; ++m) v[m] = sm[rix(rl, m)];
         line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);   // v = chi_l (row gr)
         if (grad_here) {
-          if (CPLX) {
+          if (MODE == MODE_LOSS_GRAD && p.dVred) {
+            // added into the object-frame gradient at once (reductions in L2)
+            const size_t o = (size_t)l * plane + win0 + (size_t)gr * p.Nx + j;
+            if (CPLX) {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) atomicAdd(reinterpret_cast<float2*>(p.dVred) + o + T * m, cmulc(v[m], e[m]));
+            } else {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) atomicAdd(p.dVred + o + T * m, p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x));
+            }
+          } else if (CPLX) {
             float2* wg2 = reinterpret_cast<float2*>(wg) + (size_t)gr * W + j;
 #pragma unroll
             for (int m = 0; m < N1; ++m) __stcs(wg2 + T * m, cmulc(v[m], e[m]));

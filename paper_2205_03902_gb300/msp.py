@@ -122,6 +122,7 @@ _SIGS = {
     "msp_forward_noalloc": ([_G, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "msp_profile_enable": ([ctypes.c_int32], ctypes.c_int),
     "msp_set_wait_limit": ([ctypes.c_int32], ctypes.c_int),
+    "msp_set_overlap_add": ([ctypes.c_int32], ctypes.c_int),
     "msp_profile_read": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int32], ctypes.c_int),
     "msp_smd_validate_geometry": ([_GS], ctypes.c_int),
@@ -342,6 +343,16 @@ def set_wait_limit(polls: int = 0) -> None:
     """Poll bound of the tensor-core kernels' waits (0: the default, < 0: no poll at all); a test hook
     for failure detection."""
     _check(lib().msp_set_wait_limit(int(polls)), "msp_set_wait_limit")
+
+
+OVERLAP_FIXED_ORDER, OVERLAP_L2_REDUCE = 0, 1
+
+
+def set_overlap_add(mode: int = OVERLAP_FIXED_ORDER) -> None:
+    """How loss_grad sums the window gradients into dV: OVERLAP_FIXED_ORDER (a gather in scan
+    order, bit-reproducible; the default) or OVERLAP_L2_REDUCE (reductions in L2 from the fused
+    kernel, no gather; reproducible to rounding).  Process-wide."""
+    _check(lib().msp_set_overlap_add(int(mode)), "msp_set_overlap_add")
 
 
 def profile_enable(on: bool = True) -> None:

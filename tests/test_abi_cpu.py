@@ -160,6 +160,14 @@ def test_wait_limit_hook_needs_no_device(lib):
     assert lib.msp_set_wait_limit(0) == msp.MSP_OK
 
 
+def test_overlap_add_switch(lib):
+    assert lib.msp_set_overlap_add(msp.OVERLAP_L2_REDUCE) == msp.MSP_OK
+    assert lib.msp_set_overlap_add(msp.OVERLAP_FIXED_ORDER) == msp.MSP_OK
+    for bad in (-1, 2, 1 << 30):
+        assert lib.msp_set_overlap_add(bad) == msp.MSP_EINVAL
+    assert b"overlap" in lib.msp_last_error_message()
+
+
 # ---- learned proposal (include/msp_learn.h) ----------------------------------------------------
 @pytest.mark.parametrize("kw,status", [
     ({}, msp.MSP_OK),

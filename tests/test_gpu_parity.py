@@ -674,3 +674,80 @@ def test_full_size_sampled_intensities_and_gradient_property(msp, cfg_name, samp
     an = float(np.sum(dV.cpu().numpy().astype(np.float64) * D))
     print(cfg_name, "fd", fd, "analytic", an)
     assert abs(fd - an) <= 2e-2 * abs(an)
+
+
+# --------------------------------------------------------------------------- overlap-add by L2 reductions
+# MSP_OVERLAP_L2_REDUCE: the fused kernel adds every window gradient into dV as it is produced.
+# The loss and dprobe do not depend on the switch (bit for bit); dV is the same sum of the same
+# FP32 terms in another order, so it meets the oracle at the fixed-order path's bar and agrees
+# with the fixed-order dV to the rounding of a reordered sum.
+REORDER_TOL = 1e-5
+
+
+class l2_reduce:
+    def __init__(self, msp):
+        self.msp = msp
+
+    def __enter__(self):
+        self.msp.set_overlap_add(self.msp.OVERLAP_L2_REDUCE)
+
+    def __exit__(self, *exc):
+        self.msp.set_overlap_add(self.msp.OVERLAP_FIXED_ORDER)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2_ragged", "c1_strong", "c2_strong", "c3_sub", "c4_sub", "c4_strong"])
+def test_l2_reduce_overlap_add(msp, which, request):
+    c = request.getfixturevalue(which)
+    g, p, V, pos, I = c.dev(msp)
+    ws = msp.make_workspace(g)
+    loss_a, dV_a, dp_a = msp.loss_grad(g, p, V, pos, I, ws=ws)
+    with l2_reduce(msp):
+        loss_b, dV_b, dp_b = msp.loss_grad(g, p, V, pos, I, ws=ws)
+    msp.check_workspace(ws)
+    assert loss_a.item() == loss_b.item()
+    assert torch.equal(dp_a, dp_b)
+    dV_b = dV_b.cpu().numpy()
+    assert rel(dV_b, dV_a.cpu().numpy()) <= REORDER_TOL
+    ref = O.loss_grad(c.gd, c.probe, c.pos, c.I, V=c.V)
+    assert rel(dV_b, ref["dV"]) <= c.tol()
+    for l in range(c.gd["n_slices"]):
+        assert rel(dV_b[l], ref["dV"][l]) <= c.tol()
+
+
+@pytest.mark.parametrize("which", ["c2_strong", "c4_strong"])
+def test_l2_reduce_transmission_mode(msp, which, request):
+    c = request.getfixturevalue(which)
+    T = transmission_case(c)
+    g, p, X, pos, I = tdev(msp, c, T)
+    _, dX_a, _ = msp.loss_grad(g, p, X, pos, I)
+    with l2_reduce(msp):
+        _, dX_b, _ = msp.loss_grad(g, p, X, pos, I)
+    dX_b = dX_b.cpu().numpy()
+    assert rel(dX_b, dX_a.cpu().numpy()) <= REORDER_TOL
+    assert rel(dX_b, O.loss_grad(c.gd, c.probe, c.pos, c.I, T=T)["dX"]) <= TOL
+
+
+def test_l2_reduce_skips_windows_outside_the_object(msp, c1):
+    """A position outside the object adds nothing (and is flagged), as in the fixed-order path."""
+    g, p, V, pos, I = c1.dev(msp)
+    bad = pos.clone()
+    bad[3] = torch.tensor([c1.cfg.obj - c1.cfg.win + 1, 0], dtype=torch.int32)
+    ws = msp.make_workspace(g)
+    _, dV_a, _ = msp.loss_grad(g, p, V, bad, I, ws=ws)
+    with pytest.raises(msp.MspError):
+        msp.check_workspace(ws)
+    with l2_reduce(msp):
+        _, dV_b, _ = msp.loss_grad(g, p, V, bad, I, ws=ws)
+    with pytest.raises(msp.MspError) as e:
+        msp.check_workspace(ws)
+    assert e.value.status == msp.MSP_EINVAL
+    assert rel(dV_b.cpu().numpy(), dV_a.cpu().numpy()) <= REORDER_TOL
+
+
+def test_l2_reduce_leaves_the_precise_modes_in_fixed_order(msp, c2_ragged):
+    g, p, V, pos, I = c2_ragged.dev(msp, precise="df")
+    ws = msp.make_workspace(g)
+    a = msp.loss_grad(g, p, V, pos, I, ws=ws)[1].clone()
+    with l2_reduce(msp):
+        b = msp.loss_grad(g, p, V, pos, I, ws=ws)[1]
+    assert torch.equal(a, b)
