@@ -50,8 +50,10 @@
  *     raise a flag in the workspace, which msp_check_workspace reports as MSP_EINVAL.
  *   - msp_last_error_message() describes the most recent failure of this thread.
  *
- * Results are deterministic: no atomics are used on data, every sum runs in a
- * fixed order, so repeated calls on the same device give bit-identical results.
+ * Results are deterministic by default: no atomics are used on data, every sum runs in a
+ * fixed order, so repeated calls on the same device give bit-identical results.  The one
+ * exception is opt-in: msp_set_overlap_add(MSP_OVERLAP_L2_REDUCE) trades the fixed order of
+ * the sums over positions for reductions in L2 (results then agree to rounding).
  */
 #ifndef MSP_H
 #define MSP_H
@@ -254,15 +256,17 @@ msp_status msp_check_workspace(void* ws, void* stream);
 msp_status msp_set_wait_limit(int32_t polls);
 
 /* How msp_loss_grad forms dV, the sum over scan positions of the window gradients (the sum
- * over s in the gradient of Eq. Opt_Prob_Layerwise), for every later call of this process:
- *   MSP_OVERLAP_FIXED_ORDER (default): the fused kernel writes each position's window
- *     gradients to the workspace and a gather adds them per object pixel in ascending scan
- *     order: dV is bit-reproducible.
- *   MSP_OVERLAP_L2_REDUCE: the fused kernel adds each window gradient into dV as it is
- *     produced, with FP32 reductions performed in L2 (dV is zeroed first); no per-position
- *     buffer is written and no gather runs.  The order of the additions depends on the
- *     schedule, so dV agrees between runs only to rounding.  Applies to the FP32 mode
- *     (MSP_PRECISION_FP32); the other modes keep the fixed order.
+ * over s in the gradient of Eq. Opt_Prob_Layerwise), and msp_layer_step (so also
+ * msp_reconstruct) its slice's gradient and illumination maps, for every later call of this
+ * process:
+ *   MSP_OVERLAP_FIXED_ORDER (default): the fused kernel writes each position's windows to the
+ *     workspace and a gather adds them per object pixel in ascending scan order: the results
+ *     are bit-reproducible.
+ *   MSP_OVERLAP_L2_REDUCE: the fused kernel adds each window into the object-frame map as it
+ *     is produced, with FP32 reductions performed in L2 (the map is zeroed first); no
+ *     per-position buffer is written and no gather runs.  The order of the additions depends
+ *     on the schedule, so results agree between runs only to rounding.  Applies to the FP32
+ *     mode (MSP_PRECISION_FP32); the other modes keep the fixed order.
  * Returns MSP_EINVAL for any other value. */
 enum { MSP_OVERLAP_FIXED_ORDER = 0, MSP_OVERLAP_L2_REDUCE = 1 };
 msp_status msp_set_overlap_add(int32_t mode);

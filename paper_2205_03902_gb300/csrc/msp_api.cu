@@ -171,6 +171,25 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   }
 }
 
+// Per 32 x 8 object tile, the maximum of `map` (the gather's tiles and block-maximum layout):
+// the illumination maximum when the fused kernel summed the illumination map itself.
+__global__ void __launch_bounds__(256) tile_max_kernel(const float* __restrict__ map, int Ny, int Nx,
+                                                       double* __restrict__ blockmax) {
+  __shared__ float wmax[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int px = blockIdx.x * kGatherTX + (tid % kGatherTX), py = blockIdx.y * kGatherTY + (tid / kGatherTX);
+  float m = (py < Ny && px < Nx) ? map[(size_t)py * Nx + px] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) wmax[w] = m;
+  __syncthreads();
+  if (tid == 0) {
+    float b = 0.f;
+    for (int i = 0; i < 8; ++i) b = fmaxf(b, wmax[i]);
+    blockmax[blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
+  }
+}
+
 // prod_{m > layer} max_pixel |o_m|^2 (FP64; 1 when layer is the last slice): the factor by
 // which non-unimodular later slices can enlarge ||Q_l||^2 (transmission-mode step size).
 __global__ void __launch_bounds__(1024) later_slices_gain_kernel(const float2* __restrict__ X, int L, size_t plane,
@@ -836,11 +855,21 @@ msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, c
   PosParams p = base_params(g, probe, V, pos, c);
   p.I_meas = I_meas;
   p.layer = layer;
-  MSP_TRY(run_position(g, MODE_LAYER, p, c));
   dim3 grid((g->obj_nx + kGatherTX - 1) / kGatherTX, (g->obj_ny + kGatherTY - 1) / kGatherTY, 1);
   const int nblk = (int)(grid.x * grid.y);
   if (nblk > kRedSlots) return fail(MSP_EUNSUPPORTED, "object too large for the illumination reduction");
-  if (p.cplx)
+  // in the FP32 mode the fused kernels can add the gradient and illumination windows into the maps
+  const bool l2_reduce = !precise(g) && g_overlap.load(std::memory_order_relaxed) == MSP_OVERLAP_L2_REDUCE;
+  if (l2_reduce) {
+    MSP_CK(cudaMemsetAsync(c.ws.map0, 0, plane * sizeof(float) * (p.cplx ? 2 : 1), c.st));
+    MSP_CK(cudaMemsetAsync(c.ws.map1, 0, plane * sizeof(float), c.st));
+    p.dVred = c.ws.map0;
+    p.illumred = c.ws.map1;
+  }
+  MSP_TRY(run_position(g, MODE_LAYER, p, c));
+  if (l2_reduce)
+    tile_max_kernel<<<grid, 256, 0, c.st>>>(c.ws.map1, g->obj_ny, g->obj_nx, c.ws.red);
+  else if (p.cplx)
     gather_kernel<true, true><<<grid, 256, 0, c.st>>>(c.ws.wgrad, c.ws.willum, 1, (const int2*)pos, g->n_pos, W,
                                                       g->obj_ny, g->obj_nx, c.ws.map0, c.ws.map1, c.ws.red);
   else

@@ -20,9 +20,11 @@ struct PosParams {
   float2* stash;           // [G][Ls][W][W] exit waves kept for the adjoint
   float* wgrad;            // [S][Lg][W][W] per-position window gradients (float2 in transmission mode)
   float* willum;           // [S][W][W] per-position |psi_in,l|^2 (layer step)
-  float* dVred;            // [L][Ny][Nx] (float2 in transmission mode), zeroed: when set, the loss-and-
-                           // gradient pass adds every window gradient into it with reductions in L2
-                           // instead of writing wgrad (the order of the additions is not fixed)
+  float* dVred;            // [L][Ny][Nx] (loss and gradients) or [Ny][Nx] (layer step), float2 in
+                           // transmission mode, zeroed: when set, the kernel adds every window
+                           // gradient into it with reductions in L2 instead of writing wgrad (the
+                           // order of the additions is not fixed)
+  float* illumred;         // [Ny][Nx], zeroed: the layer step's |psi_in,l|^2 likewise, instead of willum
   float2* dprobe_part;     // [G][W][W] per-CTA probe-gradient partial sums
   double* loss_part;       // [S] per-position loss
   const double* zthr2;     // [1] squared far-field amplitude that counts as zero

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         constexpr int CW = CPLX ? 2 : 1;
         if (MODE == MODE_LOSS_GRAD && !p.dVred)
           for (size_t i = tid; i < CW * WW * L; i += G::NT) p.wgrad[CW * s * WW * L + i] = 0.f;
-        if (MODE == MODE_LAYER) {
+        if (MODE == MODE_LAYER && !p.dVred) {
           for (size_t i = tid; i < CW * WW; i += G::NT) p.wgrad[CW * s * WW + i] = 0.f;
           for (size_t i = tid; i < WW; i += G::NT) p.willum[s * WW + i] = 0.f;
         }
@@ -392,9 +392,10 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         for (int m = 0; m < N1; ++m) v[m] = sm[ra(m)];
         LINE_FFT<W, true>(v, tw, xb, j);   // v = chi_l (row r)
         if (grad_here) {
-          if (MODE == MODE_LOSS_GRAD && p.dVred) {
+          // object-frame offset of this row's first element (the layer step's map is one slice)
+          const size_t o = (MODE == MODE_LOSS_GRAD ? (size_t)l * plane : 0) + win0 + (size_t)r * p.Nx + j;
+          if (p.dVred) {
             // added into the object-frame gradient at once (reductions in L2)
-            const size_t o = (size_t)l * plane + win0 + (size_t)r * p.Nx + j;
             if (CPLX) {
 #pragma unroll
               for (int m = 0; m < N1; ++m) atomicAdd(reinterpret_cast<float2*>(p.dVred) + o + 8 * m, cmulc(v[m], e[m]));
@@ -413,8 +414,13 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
             for (int m = 0; m < N1; ++m) __stcs(wg + r * W + j + 8 * m, p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x));
           }
           if (MODE == MODE_LAYER) {   // |psi_in,l|^2 (= |E_l|^2 for unimodular slices)
+            if (p.illumred) {
 #pragma unroll
-            for (int m = 0; m < N1; ++m) __stcs(p.willum + s * WW + r * W + j + 8 * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));
+              for (int m = 0; m < N1; ++m) atomicAdd(p.illumred + o + 8 * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));
+            } else {
+#pragma unroll
+              for (int m = 0; m < N1; ++m) __stcs(p.willum + s * WW + r * W + j + 8 * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));
+            }
           }
         }
         if (go_on) {

@@ -118,7 +118,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         if (MODE == MODE_LOSS_GRAD && !p.dVred)
           for (int l = 0; l < L; ++l)
             for (size_t i = CW * r0 + tid; i < CW * r1; i += NT) p.wgrad[CW * ((size_t)s * L + l) * WW + i] = 0.f;
-        if (MODE == MODE_LAYER) {
+        if (MODE == MODE_LAYER && !p.dVred) {
           for (size_t i = CW * r0 + tid; i < CW * r1; i += NT) p.wgrad[CW * s * WW + i] = 0.f;
           for (size_t i = r0 + tid; i < r1; i += NT) p.willum[s * WW + i] = 0.f;
         }
@@ -275,9 +275,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         for (int m = 0; m < N1; ++m) v[m] = sm[rix(rl, m)];
         line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);   // v = chi_l (row gr)
         if (grad_here) {
-          if (MODE == MODE_LOSS_GRAD && p.dVred) {
+          // object-frame offset of this row's first element (the layer step's map is one slice)
+          const size_t o = (MODE == MODE_LOSS_GRAD ? (size_t)l * plane : 0) + win0 + (size_t)gr * p.Nx + j;
+          if (p.dVred) {
             // added into the object-frame gradient at once (reductions in L2)
-            const size_t o = (size_t)l * plane + win0 + (size_t)gr * p.Nx + j;
             if (CPLX) {
 #pragma unroll
               for (int m = 0; m < N1; ++m) atomicAdd(reinterpret_cast<float2*>(p.dVred) + o + T * m, cmulc(v[m], e[m]));
@@ -294,7 +295,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
             for (int m = 0; m < N1; ++m)
               __stcs(wg + (size_t)gr * W + j + T * m, p.two_sigma * fmaf(e[m].x, v[m].y, -e[m].y * v[m].x));
           }
-          if (MODE == MODE_LAYER) {
+          if (MODE == MODE_LAYER && p.illumred) {
+#pragma unroll
+            for (int m = 0; m < N1; ++m) atomicAdd(p.illumred + o + T * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));
+          } else if (MODE == MODE_LAYER) {
 #pragma unroll
             for (int m = 0; m < N1; ++m)
               __stcs(p.willum + s * WW + (size_t)gr * W + j + T * m, fmaf(e[m].x, e[m].x, e[m].y * e[m].y));

@@ -349,9 +349,10 @@ OVERLAP_FIXED_ORDER, OVERLAP_L2_REDUCE = 0, 1
 
 
 def set_overlap_add(mode: int = OVERLAP_FIXED_ORDER) -> None:
-    """How loss_grad sums the window gradients into dV: OVERLAP_FIXED_ORDER (a gather in scan
-    order, bit-reproducible; the default) or OVERLAP_L2_REDUCE (reductions in L2 from the fused
-    kernel, no gather; reproducible to rounding).  Process-wide."""
+    """How loss_grad and layer_step (so also reconstruct) sum the per-position windows into the
+    object-frame maps: OVERLAP_FIXED_ORDER (a gather in scan order, bit-reproducible; the
+    default) or OVERLAP_L2_REDUCE (reductions in L2 from the fused kernel, no gather;
+    reproducible to rounding).  FP32 mode only; process-wide."""
     _check(lib().msp_set_overlap_add(int(mode)), "msp_set_overlap_add")
 
 

@@ -751,3 +751,34 @@ def test_l2_reduce_leaves_the_precise_modes_in_fixed_order(msp, c2_ragged):
     with l2_reduce(msp):
         b = msp.loss_grad(g, p, V, pos, I, ws=ws)[1]
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("which,layer", [("c1", 1), ("c2_ragged", 0), ("c2_strong", 3), ("c4_sub", 11)])
+def test_l2_reduce_layer_step(msp, which, layer, request):
+    """The layer step with its gradient and illumination maps summed in L2: the same step size
+    (the illumination maximum is a maximum of the same sums) to rounding, the same update."""
+    c = request.getfixturevalue(which)
+    g, p, V, pos, I = c.dev(msp)
+    Va, Vb = V.clone(), V.clone()
+    mu_a, mu_b = (torch.empty(1, dtype=torch.float64, device=DEV) for _ in range(2))
+    msp.layer_step(g, p, Va, pos, I, layer, mu=mu_a)
+    with l2_reduce(msp):
+        msp.layer_step(g, p, Vb, pos, I, layer, mu=mu_b)
+    assert abs(mu_b.item() - mu_a.item()) <= REORDER_TOL * mu_a.item()
+    keep = [m for m in range(c.gd["n_slices"]) if m != layer]
+    assert torch.equal(Va[keep], Vb[keep])
+    d_a = (Va[layer] - V[layer]).double().cpu().numpy()
+    d_b = (Vb[layer] - V[layer]).double().cpu().numpy()
+    assert rel(d_b, d_a) <= 10 * REORDER_TOL
+
+
+def test_l2_reduce_transmission_layer_step(msp, c2_strong):
+    T = transmission_case(c2_strong)
+    g, p, X, pos, I = tdev(msp, c2_strong, T)
+    Xa, Xb = X.clone(), X.clone()
+    msp.layer_step(g, p, Xa, pos, I, 1)
+    with l2_reduce(msp):
+        msp.layer_step(g, p, Xb, pos, I, 1)
+    d_a = (Xa[1] - X[1]).cpu().numpy()
+    d_b = (Xb[1] - X[1]).cpu().numpy()
+    assert rel(d_b, d_a) <= 10 * REORDER_TOL
