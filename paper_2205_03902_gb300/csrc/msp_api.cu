@@ -62,13 +62,15 @@ __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, 
 
 // Overlap-add of per-position window arrays into object-frame maps.  One CTA of 256
 // threads owns a 32 x 8 object tile of one slice (one pixel per thread, one warp per tile
-// row, so a warp reads 128 contiguous bytes of a window per position).  Positions
-// are taken in chunks of 256: the chunk's positions whose window overlaps the tile are
-// compacted (ballot, order kept) into a shared list, and the CTA adds their window
-// values in ascending scan order, sixteen positions in flight per thread.  Every pixel
-// therefore sums its covering positions in a fixed order (bit-reproducible, no atomics)
-// and no thread spends time on positions that miss its tile.
+// row, so a warp reads 128 contiguous bytes of a window per position).  Positions are
+// scanned in chunks of 256: the chunk's positions whose window overlaps the tile are
+// appended (ballot, order kept) to a shared list of up to kGatherList entries.  The CTA
+// then adds the listed windows' values in list order, i.e. ascending scan order, with the
+// loads of the next sixteen positions issued before the sums of the current sixteen.  Every
+// pixel therefore sums its covering positions in a fixed order (bit-reproducible, no
+// atomics) and no thread spends time on positions that miss its tile.
 constexpr int kGatherTX = 32, kGatherTY = 8;   // object tile of one CTA: one warp per tile row
+constexpr int kGatherList = 1024;              // listed positions per pass over the list
 
 // CPLX: the gathered channel is complex (float2, transmission mode); ILLUM: a second, real
 // channel (the illumination windows of a layer step) is gathered too and its per-tile
@@ -80,10 +82,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
                                                      float* __restrict__ out1, double* __restrict__ blockmax) {
   constexpr int TX = kGatherTX, TY = kGatherTY;
   constexpr int U = 16;
-  __shared__ int2 spos[256];
+  __shared__ int2 spos[kGatherList];
   // per listed position, the element offsets of window pixel (0, 0) moved to the object
   // origin: window value (dy, dx) of object pixel (py, px) sits at base + py W + px
-  __shared__ long long sbase0[256], sbase1[256];
+  __shared__ long long sbase0[kGatherList], sbase1[ILLUM ? kGatherList : 1];
   __shared__ int wcount[8];
   __shared__ float wmax[8];
   const int tid = threadIdx.x;
@@ -95,6 +97,49 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   const long long pix = (long long)py * W + px;   // this thread's pixel, window-row stride
   float2 acc0 = make_float2(0.f, 0.f);
   float acc1 = 0.f;
+
+  // the values of list entries q0 .. q0 + U - 1 at this thread's pixel (zero past the list's
+  // end and where the window misses the pixel)
+  auto fetch = [&](int q0, int total, float2 (&v0)[U], float (&v1)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + u;
+      const bool live = q < total;   // the list has `total` entries; nothing past it is read
+      int2 pq = make_int2(-(1 << 29), -(1 << 29));
+      long long o0 = 0, o1 = 0;
+      if (live) {
+        pq = spos[q];
+        o0 = sbase0[q] + pix;
+        if (ILLUM) o1 = sbase1[q] + pix;
+      }
+      const bool in = ((unsigned)(px - pq.y) < (unsigned)W) && ((unsigned)(py - pq.x) < (unsigned)W);
+      if (CPLX) v0[u] = in ? __ldcs(reinterpret_cast<const float2*>(src0) + o0) : make_float2(0.f, 0.f);
+      else v0[u] = make_float2(in ? __ldcs(src0 + o0) : 0.f, 0.f);
+      v1[u] = (ILLUM && in) ? __ldcs(src1 + o1) : 0.f;
+    }
+  };
+  auto add = [&](const float2 (&v0)[U], const float (&v1)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      acc0.x += v0[u].x;
+      if (CPLX) acc0.y += v0[u].y;
+      if (ILLUM) acc1 += v1[u];
+    }
+  };
+  // sums the list's `total` entries in order, two batches of U in flight
+  auto drain = [&](int total) {
+    float2 a0[U], b0[U];
+    float a1[U], b1[U];
+    fetch(0, total, a0, a1);
+    for (int q0 = 0; q0 < total; q0 += 2 * U) {
+      fetch(q0 + U, total, b0, b1);
+      add(a0, a1);
+      fetch(q0 + 2 * U, total, a0, a1);
+      add(b0, b1);
+    }
+  };
+
+  int listed = 0;   // entries in the list (the same in every thread)
   for (int base = 0; base < S; base += 256) {
     const int n = min(256, S - base);
     int2 ps = make_int2(0, 0);
@@ -104,7 +149,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
       ov = ps.x < ty0 + TY && ps.x + W > ty0 && ps.y < tx0 + TX && ps.y + W > tx0;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, ov);
-    __syncthreads();                      // the previous chunk's list is no longer read
+    __syncthreads();                      // the previous chunk's counts are no longer read
     if (lane == 0) wcount[w] = __popc(mask);
     __syncthreads();
     int off = 0, total = 0;
@@ -113,41 +158,22 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
       off += (i < w) ? wcount[i] : 0;
       total += wcount[i];
     }
+    if (listed + total > kGatherList) {   // full: sum the list so far, then start it again
+      drain(listed);
+      listed = 0;
+      __syncthreads();                    // the list is no longer read
+    }
     if (ov) {
-      const int q = off + __popc(mask & ((1u << lane) - 1u));
+      const int q = listed + off + __popc(mask & ((1u << lane) - 1u));
       const long long sq = base + tid, shift = (long long)ps.x * W + ps.y;
       spos[q] = ps;
       sbase0[q] = (sq * nl_src + l) * (long long)WW - shift;
-      sbase1[q] = sq * (long long)WW - shift;
+      if (ILLUM) sbase1[q] = sq * (long long)WW - shift;
     }
-    __syncthreads();
-    for (int q0 = 0; q0 < total; q0 += U) {
-      float2 v0[U];
-      float v1[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int q = q0 + u;
-        const bool live = q < total;   // the list has `total` entries; nothing past it is read
-        int2 pq = make_int2(-(1 << 29), -(1 << 29));
-        long long o0 = 0, o1 = 0;
-        if (live) {
-          pq = spos[q];
-          o0 = sbase0[q] + pix;
-          if (ILLUM) o1 = sbase1[q] + pix;
-        }
-        const bool in = ((unsigned)(px - pq.y) < (unsigned)W) && ((unsigned)(py - pq.x) < (unsigned)W);
-        if (CPLX) v0[u] = in ? __ldcs(reinterpret_cast<const float2*>(src0) + o0) : make_float2(0.f, 0.f);
-        else v0[u] = make_float2(in ? __ldcs(src0 + o0) : 0.f, 0.f);
-        if (ILLUM) v1[u] = in ? __ldcs(src1 + o1) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        acc0.x += v0[u].x;
-        if (CPLX) acc0.y += v0[u].y;
-        if (ILLUM) acc1 += v1[u];
-      }
-    }
+    listed += total;
   }
+  __syncthreads();
+  drain(listed);
   float m = 0.f;
   if (py < Ny && px < Nx) {
     const size_t oi = ((size_t)l * Ny + py) * Nx + px;
