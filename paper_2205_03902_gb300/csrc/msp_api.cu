@@ -818,6 +818,7 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   PosParams p = base_params(g, probe, V, pos, c);
   p.I_meas = I_meas;
   p.want_dprobe = dprobe != nullptr;
+  p.loss_only = !dV && !dprobe;   // the adjoint is skipped
   const size_t dV_bytes = (size_t)g->n_slices * plane * sizeof(float) * (p.cplx ? 2 : 1);
   if (g->n_pos == 0) {
     if (dV) MSP_CK(cudaMemsetAsync(dV, 0, dV_bytes, c.st));

@@ -32,6 +32,7 @@ struct PosParams {
   int L, Ny, Nx, S;
   int layer;               // slice of a layer step
   int want_dprobe;
+  int loss_only;           // loss-and-gradient pass with neither gradient wanted: forward and loss only
   int cplx;                // transmission mode: T is the caller's complex slices, gradients complex
   float two_sigma;
 };

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
 
   const int L = p.L;
   const float zthr2 = (MODE == MODE_FORWARD) ? 0.f : (float)p.zthr2[0];
-  const bool need_stash = (MODE == MODE_LOSS_GRAD) || (MODE == MODE_LAYER);
+  const bool need_stash = (MODE == MODE_LOSS_GRAD && !p.loss_only) || (MODE == MODE_LAYER);
   const int lowest = (MODE == MODE_LAYER) ? p.layer : 0;
   bool first_dprobe = true;
   // TMEM stash (W = 128 only): slot of slice l, or -1 for the global stash
@@ -341,9 +341,11 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
               v[m] = make_float2(v[m].x * f, v[m].y * f);
             }
             // chi = F^H R: inverse column transforms now, rows below
-            LINE_FFT<W, true>(v, tw, xb, j);
+            if (!p.loss_only) {
+              LINE_FFT<W, true>(v, tw, xb, j);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
+              for (int m = 0; m < N1; ++m) sm[ca(m)] = v[m];
+            }
           }
         }
         if (MODE != MODE_FORWARD) {
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(4 * W, 1) position_kernel(const PosParams p) {
         }
       }
     }
-    if (MODE == MODE_FORWARD) {
+    if (MODE == MODE_FORWARD || p.loss_only) {
       __syncthreads();
       continue;
     }

@@ -98,7 +98,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
 
   const int L = p.L;
   const float zthr2 = (MODE == MODE_FORWARD) ? 0.f : (float)p.zthr2[0];
-  const bool need_stash = (MODE == MODE_LOSS_GRAD) || (MODE == MODE_LAYER);
+  const bool need_stash = (MODE == MODE_LOSS_GRAD && !p.loss_only) || (MODE == MODE_LAYER);
   const int lowest = (MODE == MODE_LAYER) ? p.layer : 0;
   const size_t slot = (MODE == MODE_LOSS_GRAD ? (size_t)L : 1) * WW;   // stash per cluster
   bool first_dprobe = true;
@@ -233,9 +233,11 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
               const float f = (a2 > zthr2) ? (1.f - rt / a) : 1.f;
               v[m] = make_float2(v[m].x * f, v[m].y * f);
             }
-            line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
+            if (!p.loss_only) {
+              line_fft<W, true, RegisterTwiddles<W, T>, T>(v, tw, xb, j);
 #pragma unroll
-            for (int m = 0; m < N1; ++m) col_st(c, m, v[m]);
+              for (int m = 0; m < N1; ++m) col_st(c, m, v[m]);
+            }
           }
         }
         if (MODE != MODE_FORWARD) {
@@ -253,7 +255,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(512, 1) position_clu
         cluster.sync();
       }
     }
-    if (MODE == MODE_FORWARD) continue;   // the far-field phase ended with a cluster barrier
+    if (MODE == MODE_FORWARD || p.loss_only) continue;   // the far-field phase ended with a cluster barrier
 
     // ---------------- adjoint: slices L-1 .. lowest ----------------
 #pragma unroll 1
