@@ -255,8 +255,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
     // ---- epilogue: warps w and w + 4 read TMEM lanes 32 (w % 4) .., the lower and the upper
     // half of the channels (warps 0..3 all of them if COUT = 16) ----
     constexpr int HALF = COUT >= 32 ? COUT / 2 : COUT;
+    constexpr int NCH = HALF / 16;   // 16-column chunks of a thread's accumulator row
     const bool active = !(COUT < 32 && warp >= 4);
     const int q = warp & 3, c0 = (warp >> 2) * HALF;
+    // this thread's biases, in registers (written by an earlier kernel: read after the wait)
+    grid_dependency_wait();
+    float bsum[HALF];
+#pragma unroll
+    for (int u = 0; u < HALF; ++u) bsum[u] = (c0 + u < nbias) ? bias[c0 + u] : 0.f;
     for (int k = 0; k < n; ++k) {
       if (lane == 0 && !tc::wait_phase(&acc_full[k & 1], (uint32_t)((k >> 1) & 1), wait_limit)) *flag = 2;
       __syncwarp();
@@ -266,14 +272,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
         const int y = y0 + k, r = 32 * q + lane, x = x0 + r;
         const size_t p = (size_t)y * Wd + x;
         const uint32_t acc = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(k & 1) * C::TC;
-#pragma unroll 1
-        for (int j0 = c0; j0 < c0 + HALF; j0 += 16) {
-          uint32_t d[16];
-          tc::tmem_ld16(acc + (uint32_t)j0, d);
+        // the next chunk's tensor-memory load is in flight while this chunk is processed
+        uint32_t d[2][16];
+        tc::tmem_ld16(acc + (uint32_t)c0, d[0]);
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int j0 = c0 + 16 * ch;
           tc::tmem_wait_ld();
+          tc::tmem_ready(d[ch & 1]);
+          if (ch + 1 < NCH) tc::tmem_ld16(acc + (uint32_t)(j0 + 16), d[(ch + 1) & 1]);
           float v[16];
 #pragma unroll
-          for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[u]) + (j0 + u < nbias ? bias[j0 + u] : 0.f);
+          for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[ch & 1][u]) + bsum[16 * ch + u];
           if (pre) {
             float4* dst = reinterpret_cast<float4*>(pre + p * COUT + j0);
 #pragma unroll

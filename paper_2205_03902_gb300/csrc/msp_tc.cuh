@@ -117,6 +117,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Placed after tmem_wait_ld: ties the registers of an earlier tmem_ld16 to this point, so that no
+// use of them can be scheduled before the wait (a load's registers are written asynchronously).
+__device__ __forceinline__ void tmem_ready(uint32_t (&r)[16]) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]));
+}
 
 // The warp's 32 TMEM lanes x 8 consecutive 32-bit columns starting at taddr: lo to the first
 // four, hi to the next four.
