@@ -510,6 +510,21 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_kernel(float* __restrict__ 
   if (tid == 0 && *flag) atomicMax(err, *flag);
 }
 
+// x[0] + x[stride] + ... + x[(n - 1) stride], added in that order, eight loads in flight.
+__device__ __forceinline__ float sum_in_order(const float* __restrict__ x, int stride, int n) {
+  float s = 0.f;
+  int i = 0;
+  for (; i + 8 <= n; i += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = x[(size_t)(i + u) * stride];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s += v[u];
+  }
+  for (; i < n; ++i) s += x[(size_t)i * stride];
+  return s;
+}
+
 // dW[co][t][ci] (co < cout_true, ci < cin_true, the parameter layout) = sum over the nsp spatial
 // partials in order; db[co] likewise.
 __global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ bpart, int nsp, int COUT,
@@ -520,14 +535,10 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float*
   if (idx < nw) {
     const int t = idx / (COUT * CIN), co = (idx / CIN) % COUT, ci = idx % CIN;
     if (co >= cout_true || ci >= cin_true) return;
-    float s = 0.f;
-    for (int i = 0; i < nsp; ++i) s += part[(size_t)i * nw + idx];
-    dW[((size_t)co * 9 + t) * cin_true + ci] = s;
+    dW[((size_t)co * 9 + t) * cin_true + ci] = sum_in_order(part + idx, nw, nsp);
   } else if (idx < nw + cout_true) {
     const int co = idx - nw;
-    float s = 0.f;
-    for (int i = 0; i < nsp; ++i) s += bpart[(size_t)i * COUT + co];
-    db[co] = s;
+    db[co] = sum_in_order(bpart + co, COUT, nsp);
   }
 }
 

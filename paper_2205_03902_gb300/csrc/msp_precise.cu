@@ -918,6 +918,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
   };
 
   const bool fwd = mode == MODE_FORWARD;
+  const bool loss_only = mode == MODE_LOSS_GRAD && p.loss_only;   // the forward and the loss only
   const int lowest = mode == MODE_LAYER ? p.layer : 0;
   const bool want_dprobe = mode != MODE_LAYER && !fwd && p.want_dprobe;
   const int CW = p.cplx ? 2 : 1;
@@ -928,7 +929,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
     // forward: slice 0, then (propagate, transmit) for every later slice
     if (tc) {
       for (int l = 0; l < L; ++l) {
-        const int keep = !fwd && l >= lowest;
+        const int keep = !fwd && !loss_only && l >= lowest;
         if (l > 0) {
           fwd2(nb, false);
           propagator_kernel<float2, float2><<<eb, 256, 0, st>>>(bt, p.h1, (float2*)g.wave, 0);
@@ -944,7 +945,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
       // [columns F, x H, F^-1] [rows F^-1, o X_l, rows F]; the far field's columns follow
       auto fused = [&](auto* wave, const auto* wtab, const auto* T, const auto* h1d) {
         for (int l = 0; l < L; ++l) {
-          const int keep = !fwd && l >= lowest;
+          const int keep = !fwd && !loss_only && l >= lowest;
           if (l > 0) {
             cols_propagate_w(W, wave, wtab, h1d, nb, st);
             ++n_launch;
@@ -974,7 +975,7 @@ cudaError_t run_precise(int mode, const PosParams& p, int W, const PreciseIn& in
         ++n_launch;
       }
     }
-    if (fwd) continue;
+    if (fwd || loss_only) continue;
     // adjoint: chi_L = F^H R, then down the slices
     if (tc) {
       adj2(nb, true);

@@ -782,3 +782,19 @@ def test_l2_reduce_transmission_layer_step(msp, c2_strong):
     d_a = (Xa[1] - X[1]).cpu().numpy()
     d_b = (Xb[1] - X[1]).cpu().numpy()
     assert rel(d_b, d_a) <= 10 * REORDER_TOL
+
+
+# --------------------------------------------------------------------------- loss-only passes
+@pytest.mark.parametrize("which", ["c1", "c2_ragged", "c4_sub"])
+@pytest.mark.parametrize("prec", ["FP32", "FP64_FORWARD", "DF_FORWARD", "BF16X3_DFT"])
+def test_loss_only_pass_gives_the_same_loss(msp, which, prec, request):
+    """With neither gradient wanted the pass stops after the far-field loss: the same loss, bit
+    for bit, as the full loss-and-gradient pass in every arithmetic form and window size."""
+    c = request.getfixturevalue(which)
+    _, p, V, pos, I = c.dev(msp)
+    g = msp.geometry(**c.gd, precision=getattr(msp, "MSP_PRECISION_" + prec))
+    ws = msp.make_workspace(g)
+    full = msp.loss_grad(g, p, V, pos, I, ws=ws)[0].item()
+    only = msp.loss_grad(g, p, V, pos, I, want_dV=False, want_dprobe=False, ws=ws)[0].item()
+    msp.check_workspace(ws)
+    assert only == full
