@@ -75,11 +75,12 @@ constexpr int kGatherList = 1024;              // listed positions per pass over
 // CPLX: the gathered channel is complex (float2, transmission mode); ILLUM: a second, real
 // channel (the illumination windows of a layer step) is gathered too and its per-tile
 // maximum written to `blockmax`.
+// The tile (bx, by) of slice l; gx tiles per row (the block-maximum index is by gx + bx).
 template <bool CPLX, bool ILLUM>
-__global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ src0, const float* __restrict__ src1,
-                                                     int nl_src, const int2* __restrict__ pos, int S, int W,
-                                                     int Ny, int Nx, float* __restrict__ out0,
-                                                     float* __restrict__ out1, double* __restrict__ blockmax) {
+__device__ __forceinline__ void gather_tile(const float* __restrict__ src0, const float* __restrict__ src1,
+                                            int nl_src, const int2* __restrict__ pos, int S, int W, int Ny, int Nx,
+                                            float* __restrict__ out0, float* __restrict__ out1,
+                                            double* __restrict__ blockmax, int bx, int by, int l, int gx) {
   constexpr int TX = kGatherTX, TY = kGatherTY;
   constexpr int U = 16;
   __shared__ int2 spos[kGatherList];
@@ -90,8 +91,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
   __shared__ float wmax[8];
   const int tid = threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
-  const int l = blockIdx.z;
-  const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+  const int tx0 = bx * TX, ty0 = by * TY;
   const int px = tx0 + (tid % TX), py = ty0 + (tid / TX);
   const size_t WW = (size_t)W * W;
   const long long pix = (long long)py * W + px;   // this thread's pixel, window-row stride
@@ -192,9 +192,18 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
     if (tid == 0) {
       float b = 0.f;
       for (int i = 0; i < 8; ++i) b = fmaxf(b, wmax[i]);
-      blockmax[blockIdx.y * gridDim.x + blockIdx.x] = (double)b;
+      blockmax[by * gx + bx] = (double)b;
     }
   }
+}
+
+template <bool CPLX, bool ILLUM>
+__global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ src0, const float* __restrict__ src1,
+                                                     int nl_src, const int2* __restrict__ pos, int S, int W,
+                                                     int Ny, int Nx, float* __restrict__ out0,
+                                                     float* __restrict__ out1, double* __restrict__ blockmax) {
+  gather_tile<CPLX, ILLUM>(src0, src1, nl_src, pos, S, W, Ny, Nx, out0, out1, blockmax, blockIdx.x, blockIdx.y,
+                           blockIdx.z, gridDim.x);
 }
 
 // Per 32 x 8 object tile, the maximum of `map` (the gather's tiles and block-maximum layout):
@@ -280,31 +289,29 @@ __global__ void __launch_bounds__(256) sum_blocks_kernel(const float* __restrict
 
 // dprobe[i] = sum_b part[b][i] (FP64 accumulation, fixed order).  A block of 256 threads owns 32
 // consecutive probe values: warp g sums the partials b = g, g + 8, g + 16, ... (lane = value, so
-// every load is 256 contiguous bytes), four loads in flight per thread, and the eight warp sums
+// every load is 256 contiguous bytes), all of them in flight at once, and the eight warp sums
 // are added in warp order.  512 blocks for W = 128 keep every SM loading.
 constexpr int kDprobeVals = 32;
-__global__ void __launch_bounds__(256) dprobe_reduce_kernel(const float2* __restrict__ part, int G, int WW,
-                                                            float2* __restrict__ out) {
+__device__ __forceinline__ void dprobe_block(const float2* __restrict__ part, int G, int WW, float2* __restrict__ out,
+                                             int blk) {
   __shared__ double2 acc_w[8][kDprobeVals];
   const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int i = blockIdx.x * kDprobeVals + lane;
+  const int i = blk * kDprobeVals + lane;
   double re = 0.0, im = 0.0;
   if (i < WW) {
-    int b = g;
-    for (; b + 24 < G; b += 32) {
-      float2 v[4];
+    // all of a warp's partials (up to 24 at once) in flight, then added in ascending order
+    constexpr int kBatch = 24;
+    for (int b0 = g; b0 < G; b0 += 8 * kBatch) {
+      float2 v[kBatch];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __ldcs(part + (size_t)(b + 8 * u) * WW + i);
+      for (int u = 0; u < kBatch; ++u)   // past the last partial: a repeat of it, added as zero below
+        v[u] = __ldcs(part + (size_t)min(b0 + 8 * u, G - 1) * WW + i);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        re += v[u].x;
-        im += v[u].y;
+      for (int u = 0; u < kBatch; ++u) {
+        const bool live = b0 + 8 * u < G;
+        re += live ? (double)v[u].x : 0.0;
+        im += live ? (double)v[u].y : 0.0;
       }
-    }
-    for (; b < G; b += 8) {
-      const float2 v = __ldcs(part + (size_t)b * WW + i);
-      re += v.x;
-      im += v.y;
     }
   }
   acc_w[g][lane] = make_double2(re, im);
@@ -316,6 +323,57 @@ __global__ void __launch_bounds__(256) dprobe_reduce_kernel(const float2* __rest
       t.y += acc_w[w][lane].y;
     }
     out[i] = make_float2((float)t.x, (float)t.y);
+  }
+}
+
+__global__ void __launch_bounds__(256) dprobe_reduce_kernel(const float2* __restrict__ part, int G, int WW,
+                                                            float2* __restrict__ out) {
+  dprobe_block(part, G, WW, out, blockIdx.x);
+}
+
+// The loss: the sum of n FP64 values in reduce_kernel's order (1024 strided partial sums, then
+// a halving tree), by one block of 256 threads.
+__device__ __forceinline__ void loss_block(const double* __restrict__ in, int n, double* __restrict__ out,
+                                           double* __restrict__ out2) {
+  __shared__ double sh[1024];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int t = tid + 256 * k;
+    double a = 0.0;
+    for (int i = t; i < n; i += 1024) a = a + in[i];
+    sh[t] = a;
+  }
+  __syncthreads();
+  for (int h = 512; h > 0; h >>= 1) {
+    for (int t = tid; t < h; t += 256) sh[t] = sh[t] + sh[t + h];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    out[0] = sh[0];
+    if (out2) out2[0] = sh[0];
+  }
+}
+
+// What follows the fused kernel in a loss-and-gradient pass, in one launch: blocks [0, n_gather)
+// gather dV (tile bx, by of slice l), the next n_dprobe blocks sum the probe-gradient partials,
+// and the last block sums the loss.  The three parts are independent of one another.
+template <bool CPLX>
+__global__ void __launch_bounds__(256) loss_grad_finish_kernel(const float* __restrict__ wgrad, const int2* __restrict__ pos,
+                                                               int S, int W, int L, int Ny, int Nx, int gx, int gy,
+                                                               float* __restrict__ dV, int n_gather,
+                                                               const float2* __restrict__ dprobe_part, int G,
+                                                               float2* __restrict__ dprobe, int n_dprobe,
+                                                               const double* __restrict__ loss_part, int n_loss,
+                                                               double* __restrict__ loss, double* __restrict__ loss2) {
+  const int b = blockIdx.x;
+  if (b < n_gather) {
+    const int bx = b % gx, by = (b / gx) % gy, l = b / (gx * gy);
+    gather_tile<CPLX, false>(wgrad, nullptr, L, pos, S, W, Ny, Nx, dV, nullptr, nullptr, bx, by, l, gx);
+  } else if (b < n_gather + n_dprobe) {
+    dprobe_block(dprobe_part, G, W * W, dprobe, b - n_gather);
+  } else {
+    loss_block(loss_part, n_loss, loss, loss2);
   }
 }
 
@@ -833,24 +891,24 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
     p.dVred = dV;
   }
   MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
-  if (dV && !l2_reduce) {
-    dim3 grid((g->obj_nx + kGatherTX - 1) / kGatherTX, (g->obj_ny + kGatherTY - 1) / kGatherTY, g->n_slices);
-    if (p.cplx)
-      gather_kernel<true, false><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos,
-                                                         W, g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
-    else
-      gather_kernel<false, false><<<grid, 256, 0, c.st>>>(c.ws.wgrad, nullptr, g->n_slices, (const int2*)pos, g->n_pos,
-                                                          W, g->obj_ny, g->obj_nx, dV, nullptr, nullptr);
-    MSP_CK(cudaGetLastError());
+  // the gather of dV, the probe-gradient sum and the loss sum, in one launch
+  const int gx = (g->obj_nx + kGatherTX - 1) / kGatherTX, gy = (g->obj_ny + kGatherTY - 1) / kGatherTY;
+  const int n_gather = (dV && !l2_reduce) ? gx * gy * g->n_slices : 0;
+  const int n_dprobe = dprobe ? (int)((WW + kDprobeVals - 1) / kDprobeVals) : 0;
+  const int nblk = n_gather + n_dprobe + 1;
+  if (p.cplx)
+    loss_grad_finish_kernel<true><<<nblk, 256, 0, c.st>>>(
+        c.ws.wgrad, (const int2*)pos, g->n_pos, W, g->n_slices, g->obj_ny, g->obj_nx, gx, gy, dV, n_gather,
+        c.ws.dprobe_part, c.parts, (float2*)dprobe, n_dprobe, c.ws.loss_part, g->n_pos * loss_slots(g), c.ws.scal,
+        loss);
+  else
+    loss_grad_finish_kernel<false><<<nblk, 256, 0, c.st>>>(
+        c.ws.wgrad, (const int2*)pos, g->n_pos, W, g->n_slices, g->obj_ny, g->obj_nx, gx, gy, dV, n_gather,
+        c.ws.dprobe_part, c.parts, (float2*)dprobe, n_dprobe, c.ws.loss_part, g->n_pos * loss_slots(g), c.ws.scal,
+        loss);
+  MSP_CK(cudaGetLastError());
   counted();
-  }
-  if (dprobe) {
-    dprobe_reduce_kernel<<<(int)((WW + kDprobeVals - 1) / kDprobeVals), 256, 0, c.st>>>(c.ws.dprobe_part, c.parts, (int)WW,
-                                                                   (float2*)dprobe);
-    MSP_CK(cudaGetLastError());
-  counted();
-  }
-  return reduce_loss(g, c, loss);
+  return MSP_OK;
 }
 
 msp_status msp_layer_step(const msp_geometry* g, const float* probe, float* V, const int32_t* pos,
