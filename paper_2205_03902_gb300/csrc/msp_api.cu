@@ -10,6 +10,7 @@
 //   reductions        FP64, fixed order: loss, illumination maximum, pattern sums
 //   updates           the gradient steps of Algorithm 1 and of Sec. 3.5
 #include <cuda_runtime.h>
+#include <type_traits>
 
 #include <algorithm>
 #include <atomic>
@@ -61,31 +62,42 @@ __global__ void propagator_kernel(float2* __restrict__ h1, int W, double dzlam, 
 }
 
 // Overlap-add of per-position window arrays into object-frame maps.  One CTA of 256
-// threads owns a 32 x 8 object tile of one slice (one pixel per thread, one warp per tile
-// row, so a warp reads 128 contiguous bytes of a window per position).  Positions are
+// threads owns a 32 x 8 object tile (one pixel per thread, one warp per tile row, so a warp
+// reads 128 contiguous bytes of a window per position) and a run of slices.  Positions are
 // scanned in chunks of 256: the chunk's positions whose window overlaps the tile are
-// appended (ballot, order kept) to a shared list of up to kGatherList entries.  The CTA
-// then adds the listed windows' values in list order, i.e. ascending scan order, with the
-// loads of the next sixteen positions issued before the sums of the current sixteen.  Every
-// pixel therefore sums its covering positions in a fixed order (bit-reproducible, no
-// atomics) and no thread spends time on positions that miss its tile.
+// appended (ballot, order kept) to a shared list of up to kGatherList entries, which serves
+// every slice of the run (the covering positions do not depend on the slice).  The CTA then
+// adds the listed windows' values in list order, i.e. ascending scan order, LG slices at a
+// time, with the loads of the next batch of positions issued before the sums of the current
+// one.  Every pixel of every slice therefore sums its covering positions in a fixed order
+// (bit-reproducible, no atomics) and no thread spends time on positions that miss its tile.
 constexpr int kGatherTX = 32, kGatherTY = 8;   // object tile of one CTA: one warp per tile row
 constexpr int kGatherList = 1024;              // listed positions per pass over the list
+constexpr int kGatherSlices = 4;               // slices summed together by the loss-and-gradient gather
+
+__device__ __forceinline__ void accum(float& a, float v) { a += v; }
+__device__ __forceinline__ void accum(float2& a, float2 v) {
+  a.x += v.x;
+  a.y += v.y;
+}
 
 // CPLX: the gathered channel is complex (float2, transmission mode); ILLUM: a second, real
 // channel (the illumination windows of a layer step) is gathered too and its per-tile
-// maximum written to `blockmax`.
-// The tile (bx, by) of slice l; gx tiles per row (the block-maximum index is by gx + bx).
-template <bool CPLX, bool ILLUM>
+// maximum written to `blockmax` (one slice, LG = 1).  The tile (bx, by) of slices l_first ..
+// l_first + n_l - 1; gx tiles per row (the block-maximum index is by gx + bx).
+template <bool CPLX, bool ILLUM, int LG>
 __device__ __forceinline__ void gather_tile(const float* __restrict__ src0, const float* __restrict__ src1,
                                             int nl_src, const int2* __restrict__ pos, int S, int W, int Ny, int Nx,
                                             float* __restrict__ out0, float* __restrict__ out1,
-                                            double* __restrict__ blockmax, int bx, int by, int l, int gx) {
+                                            double* __restrict__ blockmax, int bx, int by, int l_first, int n_l,
+                                            int gx) {
+  static_assert(!ILLUM || LG == 1, "the illumination channel is gathered for one slice");
+  using Val = typename std::conditional<CPLX, float2, float>::type;
   constexpr int TX = kGatherTX, TY = kGatherTY;
-  constexpr int U = 16;
+  constexpr int U = LG == 1 ? 16 : 8;   // positions per batch of loads
   __shared__ int2 spos[kGatherList];
-  // per listed position, the element offsets of window pixel (0, 0) moved to the object
-  // origin: window value (dy, dx) of object pixel (py, px) sits at base + py W + px
+  // per listed position, the element offsets of window pixel (0, 0) of slice l_first moved to
+  // the object origin: window value (dy, dx) of object pixel (py, px) sits at base + py W + px
   __shared__ long long sbase0[kGatherList], sbase1[ILLUM ? kGatherList : 1];
   __shared__ int wcount[8];
   __shared__ float wmax[8];
@@ -95,12 +107,12 @@ __device__ __forceinline__ void gather_tile(const float* __restrict__ src0, cons
   const int px = tx0 + (tid % TX), py = ty0 + (tid / TX);
   const size_t WW = (size_t)W * W;
   const long long pix = (long long)py * W + px;   // this thread's pixel, window-row stride
-  float2 acc0 = make_float2(0.f, 0.f);
+  const Val zero = Val();
   float acc1 = 0.f;
 
-  // the values of list entries q0 .. q0 + U - 1 at this thread's pixel (zero past the list's
-  // end and where the window misses the pixel)
-  auto fetch = [&](int q0, int total, float2 (&v0)[U], float (&v1)[U]) {
+  // the values of list entries q0 .. q0 + U - 1 at this thread's pixel, slices lg .. lg + LG - 1
+  // of the run (zero past the list's end, past the run and where the window misses the pixel)
+  auto fetch = [&](int q0, int total, int lg, Val (&v0)[U][LG], float (&v1)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int q = q0 + u;
@@ -113,78 +125,92 @@ __device__ __forceinline__ void gather_tile(const float* __restrict__ src0, cons
         if (ILLUM) o1 = sbase1[q] + pix;
       }
       const bool in = ((unsigned)(px - pq.y) < (unsigned)W) && ((unsigned)(py - pq.x) < (unsigned)W);
-      if (CPLX) v0[u] = in ? __ldcs(reinterpret_cast<const float2*>(src0) + o0) : make_float2(0.f, 0.f);
-      else v0[u] = make_float2(in ? __ldcs(src0 + o0) : 0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < LG; ++k) {
+        const bool ok = in && lg + k < n_l;
+        const long long o = o0 + (long long)(lg + k) * (long long)WW;
+        if constexpr (CPLX) v0[u][k] = ok ? __ldcs(reinterpret_cast<const float2*>(src0) + o) : zero;
+        else v0[u][k] = ok ? __ldcs(src0 + o) : zero;
+      }
       v1[u] = (ILLUM && in) ? __ldcs(src1 + o1) : 0.f;
     }
   };
-  auto add = [&](const float2 (&v0)[U], const float (&v1)[U]) {
+  auto add = [&](Val (&acc)[LG], const Val (&v0)[U][LG], const float (&v1)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      acc0.x += v0[u].x;
-      if (CPLX) acc0.y += v0[u].y;
+#pragma unroll
+      for (int k = 0; k < LG; ++k) accum(acc[k], v0[u][k]);
       if (ILLUM) acc1 += v1[u];
     }
   };
   // sums the list's `total` entries in order, two batches of U in flight
-  auto drain = [&](int total) {
-    float2 a0[U], b0[U];
+  auto drain = [&](int total, int lg, Val (&acc)[LG]) {
+    Val a0[U][LG], b0[U][LG];
     float a1[U], b1[U];
-    fetch(0, total, a0, a1);
+    fetch(0, total, lg, a0, a1);
     for (int q0 = 0; q0 < total; q0 += 2 * U) {
-      fetch(q0 + U, total, b0, b1);
-      add(a0, a1);
-      fetch(q0 + 2 * U, total, a0, a1);
-      add(b0, b1);
+      fetch(q0 + U, total, lg, b0, b1);
+      add(acc, a0, a1);
+      fetch(q0 + 2 * U, total, lg, a0, a1);
+      add(acc, b0, b1);
     }
   };
 
-  int listed = 0;   // entries in the list (the same in every thread)
-  for (int base = 0; base < S; base += 256) {
-    const int n = min(256, S - base);
-    int2 ps = make_int2(0, 0);
-    bool ov = false;
-    if (tid < n) {
-      ps = pos[base + tid];
-      ov = ps.x < ty0 + TY && ps.x + W > ty0 && ps.y < tx0 + TX && ps.y + W > tx0;
-    }
-    const unsigned mask = __ballot_sync(0xffffffffu, ov);
-    __syncthreads();                      // the previous chunk's counts are no longer read
-    if (lane == 0) wcount[w] = __popc(mask);
-    __syncthreads();
-    int off = 0, total = 0;
+  for (int lg = 0; lg < n_l; lg += LG) {
+    Val acc[LG];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      off += (i < w) ? wcount[i] : 0;
-      total += wcount[i];
+    for (int k = 0; k < LG; ++k) acc[k] = zero;
+    int listed = 0;   // entries in the list (the same in every thread)
+    for (int base = 0; base < S; base += 256) {
+      const int n = min(256, S - base);
+      int2 ps = make_int2(0, 0);
+      bool ov = false;
+      if (tid < n) {
+        ps = pos[base + tid];
+        ov = ps.x < ty0 + TY && ps.x + W > ty0 && ps.y < tx0 + TX && ps.y + W > tx0;
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, ov);
+      __syncthreads();                      // the previous chunk's counts and the list are no longer read
+      if (lane == 0) wcount[w] = __popc(mask);
+      __syncthreads();
+      int off = 0, total = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        off += (i < w) ? wcount[i] : 0;
+        total += wcount[i];
+      }
+      if (listed + total > kGatherList) {   // full: sum the list so far, then start it again
+        drain(listed, lg, acc);
+        listed = 0;
+        __syncthreads();                    // the list is no longer read
+      }
+      if (ov) {
+        const int q = listed + off + __popc(mask & ((1u << lane) - 1u));
+        const long long sq = base + tid, shift = (long long)ps.x * W + ps.y;
+        spos[q] = ps;
+        sbase0[q] = (sq * nl_src + l_first) * (long long)WW - shift;
+        if (ILLUM) sbase1[q] = sq * (long long)WW - shift;
+      }
+      listed += total;
     }
-    if (listed + total > kGatherList) {   // full: sum the list so far, then start it again
-      drain(listed);
-      listed = 0;
-      __syncthreads();                    // the list is no longer read
-    }
-    if (ov) {
-      const int q = listed + off + __popc(mask & ((1u << lane) - 1u));
-      const long long sq = base + tid, shift = (long long)ps.x * W + ps.y;
-      spos[q] = ps;
-      sbase0[q] = (sq * nl_src + l) * (long long)WW - shift;
-      if (ILLUM) sbase1[q] = sq * (long long)WW - shift;
-    }
-    listed += total;
-  }
-  __syncthreads();
-  drain(listed);
-  float m = 0.f;
-  if (py < Ny && px < Nx) {
-    const size_t oi = ((size_t)l * Ny + py) * Nx + px;
-    if (CPLX) reinterpret_cast<float2*>(out0)[oi] = acc0;
-    else out0[oi] = acc0.x;
-    if (ILLUM) {
-      out1[(size_t)py * Nx + px] = acc1;
-      m = acc1;
+    __syncthreads();
+    drain(listed, lg, acc);
+    if (py < Ny && px < Nx) {
+#pragma unroll
+      for (int k = 0; k < LG; ++k)
+        if (lg + k < n_l) {
+          const size_t oi = ((size_t)(l_first + lg + k) * Ny + py) * Nx + px;
+          if constexpr (CPLX) reinterpret_cast<float2*>(out0)[oi] = acc[k];
+          else out0[oi] = acc[k];
+        }
     }
   }
   if (ILLUM) {
+    float m = 0.f;
+    if (py < Ny && px < Nx) {
+      out1[(size_t)py * Nx + px] = acc1;
+      m = acc1;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) wmax[w] = m;
@@ -202,8 +228,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const float* __restrict__ s
                                                      int nl_src, const int2* __restrict__ pos, int S, int W,
                                                      int Ny, int Nx, float* __restrict__ out0,
                                                      float* __restrict__ out1, double* __restrict__ blockmax) {
-  gather_tile<CPLX, ILLUM>(src0, src1, nl_src, pos, S, W, Ny, Nx, out0, out1, blockmax, blockIdx.x, blockIdx.y,
-                           blockIdx.z, gridDim.x);
+  gather_tile<CPLX, ILLUM, 1>(src0, src1, nl_src, pos, S, W, Ny, Nx, out0, out1, blockmax, blockIdx.x, blockIdx.y,
+                              blockIdx.z, 1, gridDim.x);
 }
 
 // Per 32 x 8 object tile, the maximum of `map` (the gather's tiles and block-maximum layout):
@@ -356,8 +382,9 @@ __device__ __forceinline__ void loss_block(const double* __restrict__ in, int n,
 }
 
 // What follows the fused kernel in a loss-and-gradient pass, in one launch: blocks [0, n_gather)
-// gather dV (tile bx, by of slice l), the next n_dprobe blocks sum the probe-gradient partials,
-// and the last block sums the loss.  The three parts are independent of one another.
+// gather dV (one tile and up to kGatherSlices slices each), the next n_dprobe blocks sum the
+// probe-gradient partials, and the last block sums the loss.  The three parts are independent
+// of one another.
 template <bool CPLX>
 __global__ void __launch_bounds__(256) loss_grad_finish_kernel(const float* __restrict__ wgrad, const int2* __restrict__ pos,
                                                                int S, int W, int L, int Ny, int Nx, int gx, int gy,
@@ -368,8 +395,11 @@ __global__ void __launch_bounds__(256) loss_grad_finish_kernel(const float* __re
                                                                double* __restrict__ loss, double* __restrict__ loss2) {
   const int b = blockIdx.x;
   if (b < n_gather) {
-    const int bx = b % gx, by = (b / gx) % gy, l = b / (gx * gy);
-    gather_tile<CPLX, false>(wgrad, nullptr, L, pos, S, W, Ny, Nx, dV, nullptr, nullptr, bx, by, l, gx);
+    // the tile (bx, by) of slices l0 .. l0 + LG - 1 (LG = kGatherSlices, two if complex)
+    constexpr int LG = CPLX ? 2 : kGatherSlices;
+    const int t = b % (gx * gy), l0 = (b / (gx * gy)) * LG;
+    gather_tile<CPLX, false, LG>(wgrad, nullptr, L, pos, S, W, Ny, Nx, dV, nullptr, nullptr, t % gx, t / gx, l0,
+                                 min(LG, L - l0), gx);
   } else if (b < n_gather + n_dprobe) {
     dprobe_block(dprobe_part, G, W * W, dprobe, b - n_gather);
   } else {
@@ -893,7 +923,8 @@ msp_status msp_loss_grad(const msp_geometry* g, const float* probe, const float*
   MSP_TRY(run_position(g, MODE_LOSS_GRAD, p, c));
   // the gather of dV, the probe-gradient sum and the loss sum, in one launch
   const int gx = (g->obj_nx + kGatherTX - 1) / kGatherTX, gy = (g->obj_ny + kGatherTY - 1) / kGatherTY;
-  const int n_gather = (dV && !l2_reduce) ? gx * gy * g->n_slices : 0;
+  const int lg = p.cplx ? 2 : kGatherSlices;   // slices per gather block
+  const int n_gather = (dV && !l2_reduce) ? gx * gy * ((g->n_slices + lg - 1) / lg) : 0;
   const int n_dprobe = dprobe ? (int)((WW + kDprobeVals - 1) / kDprobeVals) : 0;
   const int nblk = n_gather + n_dprobe + 1;
   if (p.cplx)
