@@ -239,3 +239,37 @@ def test_conv_wait_that_runs_out_is_reported(msp):
     msp.check_workspace(ws)
     ref = P.proposal(p.cpu().numpy(), L, V, G, SCALES["scale_v"], SCALES["scale_g"], SCALES["scale_d"])
     assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-2
+
+
+def test_weight_gradient_wait_that_runs_out_is_reported(msp):
+    """The backward pass under msp_set_wait_limit(-1): every tensor-core kernel of it, the
+    weight-gradient kernel's tensor-load producer and MMA thread included, gives up at its first
+    wait, drains what it issued with its own fixed bound and frees its tensor memory; the
+    workspace reads MSP_ETIMEOUT and the next call's loss and gradient are right."""
+    L, H, W = 2, 64, 256
+    V, G, T = _problem(L, H, W, seed=6)
+    s = _shape(msp, L, H, W)
+    d = lambda a: torch.from_numpy(a).cuda()
+    p = msp.net_init(s, 2)
+    ws = msp.net_make_workspace(s)
+    timed_out = False
+    try:
+        msp.set_wait_limit(-1)
+        for _ in range(3):
+            msp.net_loss_grad(s, p, d(V), d(G), d(T), ws=ws)
+            try:
+                msp.check_workspace(ws)
+            except msp.MspError as e:
+                assert e.status == msp.MSP_ETIMEOUT
+                timed_out = True
+                break
+    finally:
+        msp.set_wait_limit(0)
+    assert timed_out
+    loss, grad = msp.net_loss_grad(s, p, d(V), d(G), d(T), ws=ws)
+    msp.check_workspace(ws)
+    sc = (SCALES["scale_v"], SCALES["scale_g"], SCALES["scale_d"])
+    loss_o, grad_o = P.loss_and_grad(p.cpu().numpy(), L, V, G, T, *sc)
+    assert abs(loss.item() - loss_o) / loss_o < 1e-2
+    g = grad.cpu().numpy()
+    assert np.linalg.norm(g - grad_o) / np.linalg.norm(grad_o) < 5e-2
