@@ -49,9 +49,11 @@ constexpr int kDrainLimit = 1 << 20;
 
 enum Epi { EPI_NONE = 0, EPI_GELU = 1, EPI_GELU_GRAD = 2 };
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float x) {
-  return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+// GELU(x) = x Phi(x), GELU'(x) = Phi(x) + x phi(x), from e = 1 + erf(x / sqrt 2) = 2 Phi(x)
+__device__ __forceinline__ float gelu_e(float x) { return 1.f + erff(x * 0.70710678118654752f); }
+__device__ __forceinline__ float gelu_from(float x, float e) { return 0.5f * x * e; }
+__device__ __forceinline__ float gelu_grad_from(float x, float e) {
+  return 0.5f * e + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
 
@@ -118,21 +120,25 @@ struct Conv {
 
 // in  [H][Wd][CIN] bf16 (NHWC); Bp packed as packed_off.  Output rows [y0, y0 + rows_per_cta)
 // of column strip blockIdx.x, with y0 = blockIdx.y * rows_per_cta.
-// pre (FP32 [H][Wd][COUT], may be NULL) receives D + bias (bias[c] for c < nbias, else 0).
+// pre (FP32 [H][Wd][COUT], may be NULL) receives, with EPI_NONE, the pre-activation D + bias
+// (bias[c] for c < nbias, else 0) and, with EPI_GELU, the derivative gelu'(D + bias) that the
+// backward pass multiplies by (computed once here instead of from the pre-activation there).
 // EPI_GELU: out = gelu(D + bias) in bf16 (NHWC).
-// EPI_GELU_GRAD: out = D * gelu'(aux) (aux FP32 [H][Wd][COUT]) in bf16 (NHWC).
+// EPI_GELU_GRAD: out = D * aux (aux FP32 [H][Wd][COUT], gelu' of the forward's pre-activation)
+// in bf16 (NHWC).
 //
-// Warp roles, synchronised by mbarriers only:
-//   warp 8 (producer): stages input row i into slot i % kFSlots once the MMAs of output row
-//     i - kFSlots released it (empty[slot]), then waits for its own copies, fences them to the
-//     async proxy and arrives on full[slot];
+// Roles, synchronised by mbarriers only:
+//   warp 8, one thread (producer): fetches input row i into slot i % kFSlots by tensor loads
+//     once the MMAs of output row i - kFSlots released it (empty[slot]); the loads complete on
+//     full[slot] by transaction count;
 //   warp 9, one thread (MMA): for output row k waits for staged row k + 2 (full) and for the
 //     epilogue to have drained accumulator k & 1 (acc_empty), issues the 9 x CIN / 16 MMAs,
 //     commits to acc_full[k & 1] and to empty[k % kFSlots] (row k has no later reader);
 //   warps 0..7 (epilogue): wait for acc_full, read the accumulator, write the outputs, arrive on
 //     acc_empty.
 // Every wait is bounded: the first that runs out raises the flag, the other roles see it and
-// stop, and the MMA thread waits for its last commit before the tensor memory is released.
+// stop, the producer waits for the loads it issued, and the MMA thread waits for its last
+// commit before the tensor memory is released.
 constexpr int kConvThreads = 320;
 
 template <int CIN, int COUT, int EPI>
@@ -284,10 +290,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
           float v[16];
 #pragma unroll
           for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[ch & 1][u]) + bsum[16 * ch + u];
-          if (pre) {
-            float4* dst = reinterpret_cast<float4*>(pre + p * COUT + j0);
+          float e[16];
+          if (EPI == EPI_GELU) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            for (int u = 0; u < 16; ++u) e[u] = gelu_e(v[u]);
+          }
+          if (pre) {   // the pre-activation, or with GELU its derivative there
+            float4* dst = reinterpret_cast<float4*>(pre + p * COUT + j0);
+            float q[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) q[u] = EPI == EPI_GELU ? gelu_grad_from(v[u], e[u]) : v[u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dst[u] = make_float4(q[4 * u], q[4 * u + 1], q[4 * u + 2], q[4 * u + 3]);
           }
           if (EPI != EPI_NONE) {
             float g[16];
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
             }
             __align__(16) bf16 o[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16_rn(EPI == EPI_GELU ? gelu(v[u]) : v[u] * gelu_grad(g[u]));
+            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16_rn(EPI == EPI_GELU ? gelu_from(v[u], e[u]) : v[u] * g[u]);
             uint4* dst = reinterpret_cast<uint4*>(out + p * COUT + j0);
             dst[0] = reinterpret_cast<const uint4*>(o)[0];
             dst[1] = reinterpret_cast<const uint4*>(o)[1];
@@ -725,7 +739,8 @@ struct Ws {
   double* loss_part;            // [512]
   bf16* x;                      // [P][16] input, NHWC
   bf16* act[kLayers - 1];       // [P][64] outputs of the hidden layers (gelu), NHWC
-  float* pre[kLayers];          // [P][cout] pre-activations (FP32)
+  float* pre[kLayers];          // [P][cout] FP32: gelu' of the hidden layers' pre-activations (training),
+                                // the last layer's pre-activation
   bf16* g[2];                   // [P][64] gradients of a pre-activation, NHWC (ping-pong)
   bf16* Bf[kLayers];            // packed forward weights
   bf16* Bd[kLayers];            // packed data-gradient weights
