@@ -49,11 +49,33 @@ constexpr int kDrainLimit = 1 << 20;
 
 enum Epi { EPI_NONE = 0, EPI_GELU = 1, EPI_GELU_GRAD = 2 };
 
-// GELU(x) = x Phi(x), GELU'(x) = Phi(x) + x phi(x), from e = 1 + erf(x / sqrt 2) = 2 Phi(x)
-__device__ __forceinline__ float gelu_e(float x) { return 1.f + erff(x * 0.70710678118654752f); }
-__device__ __forceinline__ float gelu_from(float x, float e) { return 0.5f * x * e; }
-__device__ __forceinline__ float gelu_grad_from(float x, float e) {
-  return 0.5f * e + x * 0.39894228040143268f * expf(-0.5f * x * x);
+// The normal CDF Phi(x) = erfc(-x / sqrt 2) / 2, branch-free: with z = min(|x| / sqrt 2, 6) and
+// g(z) = -log erfc(z) = z h(z), Phi = exp(-g) / 2 for x < 0 and 1 - exp(-g) / 2 otherwise, so
+// both tails keep their accuracy.  h is a degree-11 least-squares fit in the Chebyshev basis of
+// u = z / 3 - 1, written as monomials in u (csrc/gen_phi_fit.py prints them and the error:
+// |Phi error| < 1e-7 in FP32).  One exponential and twelve fused multiply-adds.
+__device__ __forceinline__ float phi_cdf(float x) {
+  const float z = fminf(fabsf(x) * 0.70710678118654752f, 6.f);
+  const float u = fmaf(z, 1.f / 3.f, -1.f);
+  float h = 7.291426300e-04f;
+  h = fmaf(h, u, -1.261031372e-03f);
+  h = fmaf(h, u, -2.603480243e-04f);
+  h = fmaf(h, u, 1.729566371e-03f);
+  h = fmaf(h, u, -2.867543837e-03f);
+  h = fmaf(h, u, 7.777833380e-03f);
+  h = fmaf(h, u, -1.878948696e-02f);
+  h = fmaf(h, u, 3.874455020e-02f);
+  h = fmaf(h, u, -7.517043501e-02f);
+  h = fmaf(h, u, 1.418747455e-01f);
+  h = fmaf(h, u, 2.730299234e+00f);
+  h = fmaf(h, u, 3.573454380e+00f);
+  const float t = 0.5f * exp2f(-1.44269504088896341f * (h * z));   // exp(-g) / 2
+  return x < 0.f ? t : 1.f - t;
+}
+// GELU(x) = x Phi(x), GELU'(x) = Phi(x) + x phi(x), from p = Phi(x)
+__device__ __forceinline__ float gelu_from(float x, float p) { return x * p; }
+__device__ __forceinline__ float gelu_grad_from(float x, float p) {
+  return p + x * 0.39894228040143268f * expf(-0.5f * x * x);
 }
 
 
@@ -290,16 +312,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
           float v[16];
 #pragma unroll
           for (int u = 0; u < 16; ++u) v[u] = __uint_as_float(d[ch & 1][u]) + bsum[16 * ch + u];
-          float e[16];
+          float ph[16];   // Phi of the pre-activations (GELU)
           if (EPI == EPI_GELU) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) e[u] = gelu_e(v[u]);
+            for (int u = 0; u < 16; ++u) ph[u] = phi_cdf(v[u]);
           }
           if (pre) {   // the pre-activation, or with GELU its derivative there
             float4* dst = reinterpret_cast<float4*>(pre + p * COUT + j0);
             float q[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) q[u] = EPI == EPI_GELU ? gelu_grad_from(v[u], e[u]) : v[u];
+            for (int u = 0; u < 16; ++u) q[u] = EPI == EPI_GELU ? gelu_grad_from(v[u], ph[u]) : v[u];
 #pragma unroll
             for (int u = 0; u < 4; ++u) dst[u] = make_float4(q[4 * u], q[4 * u + 1], q[4 * u + 2], q[4 * u + 3]);
           }
@@ -315,7 +337,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv_kernel(const bf16* __res
             }
             __align__(16) bf16 o[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16_rn(EPI == EPI_GELU ? gelu_from(v[u], e[u]) : v[u] * g[u]);
+            for (int u = 0; u < 16; ++u) o[u] = __float2bfloat16_rn(EPI == EPI_GELU ? gelu_from(v[u], ph[u]) : v[u] * g[u]);
             uint4* dst = reinterpret_cast<uint4*>(out + p * COUT + j0);
             dst[0] = reinterpret_cast<const uint4*>(o)[0];
             dst[1] = reinterpret_cast<const uint4*>(o)[1];
