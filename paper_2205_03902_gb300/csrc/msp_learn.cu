@@ -15,9 +15,9 @@
 //     is one more row of it (a constant group of ones); the per-CTA partial sums are added in a
 //     fixed order.
 // Operands are staged through shared memory in the canonical no-swizzle layouts (core matrices
-// of 8 rows x 16 bytes), fetched by tensor loads (TMA) that complete on mbarriers; one thread
-// issues the MMAs and commits them to mbarriers; every wait is bounded and records a timeout in
-// the error word.
+// of 8 rows x 16 bytes): the image rows by tensor loads (TMA) that complete on mbarriers, the
+// convolution's resident weights once per CTA with cp.async.  One thread issues the MMAs and
+// commits them to mbarriers; every wait is bounded and records a timeout in the error word.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
