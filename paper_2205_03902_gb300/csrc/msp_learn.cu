@@ -803,15 +803,13 @@ cudaError_t encode_rows_map(CUtensorMap* map, const bf16* img, int C, int Wd, in
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Encode encode = nullptr;
-  if (!encode) {
+  static const Encode encode = [] {   // looked up once (thread-safe static initialisation)
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-    encode = reinterpret_cast<Encode>(fn);
-  }
+    return (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ? reinterpret_cast<Encode>(fn) : nullptr;
+  }();
+  if (!encode) return cudaErrorNotSupported;
   const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)Wd, (cuuint64_t)H};
   const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)Wd * C * 2};
   const cuuint32_t box[3] = {8, 130, 1};
